@@ -1,0 +1,236 @@
+"""ctypes wrapper around the C oracle (rv_oracle.c). Test infrastructure only.
+
+Every function here forwards to the C code, which follows the method step by
+step in FP64 (App. A pair matrices, the cell grid and covering radius, the
+threshold sin^2(delta + r), the vote, the (score desc, idx asc) ranking, the
+octant children and the Eq. (stack) eigenvector fit with its refit rule).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "lib", "pair_M", "pair_S", "quad", "quat_to_R", "cell_exists", "cell_geom", "tau",
+    "level_cells", "vote_cells", "rank", "jacobi4", "canonical", "solve", "OracleResult",
+    "AMBIG", "cell_of_point",
+]
+
+AMBIG = 1e-6
+
+_lib = None
+
+_f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+
+class _Result(C.Structure):
+    _fields_ = [("q", C.c_double * 4), ("R", C.c_double * 9), ("best_count", C.c_int32),
+                ("inliers", C.c_int32), ("best_cell", C.c_int64), ("tests", C.c_int64),
+                ("ambiguous", C.c_int64), ("status", C.c_int32), ("refits", C.c_int32)]
+
+
+class _Trace(C.Structure):
+    _fields_ = [("cap", C.c_int64), ("ncells", C.c_void_p), ("idx", C.c_void_p), ("count", C.c_void_p),
+                ("amb", C.c_void_p), ("tau", C.c_void_p), ("topk_idx", C.c_void_p),
+                ("topk_score", C.c_void_p), ("nkept", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.rvo_pair_M.argtypes = [_f32p, _f32p, _f64p]
+        L.rvo_pair_S.argtypes = [_f32p, _f32p, _f64p]
+        L.rvo_quad.argtypes = [_f64p, _f64p]
+        L.rvo_quad.restype = C.c_double
+        L.rvo_quat_to_R.argtypes = [_f64p, _f64p]
+        L.rvo_cell_exists.argtypes = [C.c_int, C.c_int64, C.c_int64, C.c_int64]
+        L.rvo_cell_exists.restype = C.c_int
+        L.rvo_cell_geom.argtypes = [C.c_int, C.c_int64, C.c_int64, C.c_int64, _f64p, C.POINTER(C.c_double)]
+        L.rvo_tau.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.rvo_tau.restype = C.c_double
+        L.rvo_level_cells.argtypes = [C.c_int, C.c_void_p]
+        L.rvo_level_cells.restype = C.c_int64
+        L.rvo_vote_cells.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, _i64p, C.c_int64,
+                                     _i32p, _i32p, _f64p, C.c_int]
+        L.rvo_vote_cells.restype = C.c_int
+        L.rvo_rank.argtypes = [_i32p, _f64p, _i64p, C.c_int64, C.c_int64, C.c_int, C.c_int64, _i64p, _f64p]
+        L.rvo_rank.restype = C.c_int64
+        L.rvo_jacobi4.argtypes = [_f64p, _f64p, _f64p]
+        L.rvo_canonical.argtypes = [_f64p]
+        L.rvo_solve.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
+                                C.c_int, C.c_int, C.POINTER(_Result), C.POINTER(_Trace)]
+        L.rvo_solve.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _v3(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(3))
+
+
+def pair_M(a, b) -> np.ndarray:
+    """M = L(a)^T L'(b) of App. A (4x4)."""
+    M = np.zeros(16)
+    lib().rvo_pair_M(_v3(a), _v3(b), M)
+    return M.reshape(4, 4)
+
+
+def pair_S(a, b) -> np.ndarray:
+    """S = (I - M)/2 = I - P (4x4)."""
+    S = np.zeros(16)
+    lib().rvo_pair_S(_v3(a), _v3(b), S)
+    return S.reshape(4, 4)
+
+
+def quad(S, q) -> float:
+    return float(lib().rvo_quad(np.ascontiguousarray(S, dtype=np.float64).reshape(16),
+                                np.ascontiguousarray(q, dtype=np.float64)))
+
+
+def quat_to_R(q) -> np.ndarray:
+    R = np.zeros(9)
+    lib().rvo_quat_to_R(np.ascontiguousarray(q, dtype=np.float64), R)
+    return R.reshape(3, 3)
+
+
+def cell_exists(n, ix, iy, iz) -> bool:
+    return bool(lib().rvo_cell_exists(int(n), int(ix), int(iy), int(iz)))
+
+
+def cell_geom(n, ix, iy, iz):
+    """(q_cell[4], chord) of cell (ix, iy, iz) of the n^3 grid."""
+    q = np.zeros(4)
+    ch = C.c_double()
+    lib().rvo_cell_geom(int(n), int(ix), int(iy), int(iz), q, C.byref(ch))
+    return q, ch.value
+
+
+def tau(delta: float, chord: float) -> float:
+    return float(lib().rvo_tau(np.sin(delta), np.cos(delta), chord))
+
+
+def level_cells(n: int) -> np.ndarray:
+    cnt = lib().rvo_level_cells(int(n), None)
+    out = np.zeros(cnt, dtype=np.int64)
+    lib().rvo_level_cells(int(n), out.ctypes.data)
+    return out
+
+
+def cell_of_point(n: int, v) -> int:
+    """Linear index of the n^3 cell whose box contains the vector part v."""
+    h = 2.0 / n
+    i = [min(n - 1, max(0, int(np.floor((float(v[k]) + 1.0) / h)))) for k in range(3)]
+    return (i[2] * n + i[1]) * n + i[0]
+
+
+def _f32_pairs(a, b):
+    a = np.ascontiguousarray(a, dtype=np.float32).reshape(-1, 3)
+    b = np.ascontiguousarray(b, dtype=np.float32).reshape(-1, 3)
+    assert a.shape == b.shape
+    return a, b
+
+
+def vote_cells(a, b, delta: float, n_side: int, cells, nthreads: int = 1):
+    """(count, ambiguous, tau) for each linear cell index in `cells`."""
+    a, b = _f32_pairs(a, b)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    cnt = np.zeros(len(cells), dtype=np.int32)
+    amb = np.zeros(len(cells), dtype=np.int32)
+    tau_ = np.zeros(len(cells), dtype=np.float64)
+    rc = lib().rvo_vote_cells(a.reshape(-1), b.reshape(-1), a.shape[0], float(delta), int(n_side), cells,
+                              len(cells), cnt, amb, tau_, int(nthreads))
+    assert rc == 0
+    return cnt, amb, tau_
+
+
+def rank(count, tau_, idx, n_pairs: int, rank_mode: int = 0, k: int = 16):
+    """Positions of the top-k cells in (score desc, idx asc) order, and their scores."""
+    count = np.ascontiguousarray(count, dtype=np.int32)
+    tau_ = np.ascontiguousarray(tau_, dtype=np.float64)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    pos = np.zeros(k, dtype=np.int64)
+    sc = np.zeros(k, dtype=np.float64)
+    kk = lib().rvo_rank(count, tau_, idx, len(idx), int(n_pairs), int(rank_mode), int(k), pos, sc)
+    return pos[:kk], sc[:kk]
+
+
+def jacobi4(A):
+    """(eigenvalues ascending, eigenvector columns) of a symmetric 4x4."""
+    ev = np.zeros(4)
+    V = np.zeros(16)
+    lib().rvo_jacobi4(np.ascontiguousarray(A, dtype=np.float64).reshape(16), ev, V)
+    return ev, V.reshape(4, 4)
+
+
+def canonical(q) -> np.ndarray:
+    q = np.array(q, dtype=np.float64)
+    lib().rvo_canonical(q)
+    return q
+
+
+@dataclasses.dataclass
+class OracleResult:
+    q: np.ndarray
+    R: np.ndarray
+    best_count: int
+    inliers: int
+    best_cell: int
+    tests: int
+    ambiguous: int
+    status: int
+    refits: int
+    levels: list  # per level: dict(idx, count, amb, tau, topk_idx, topk_score)
+
+
+def solve(a, b, delta: float, grid_n: int, levels: int = 0, top_k: int = 16, rank_mode: int = 0,
+          refit_iters: int = 8, nthreads: int = 1, trace: bool = True) -> OracleResult:
+    """The full path: vote on each level, rank, subdivide, fit."""
+    a, b = _f32_pairs(a, b)
+    L = lib()
+    res = _Result()
+    tr_p = None
+    keep = []
+    if trace:
+        cap = int(L.rvo_level_cells(int(grid_n), None))
+        cap = max(cap, 8 * top_k)
+        nl = levels + 1
+        arrs = dict(ncells=np.zeros(nl, np.int64), idx=np.zeros(nl * cap, np.int64),
+                    count=np.zeros(nl * cap, np.int32), amb=np.zeros(nl * cap, np.int32),
+                    tau=np.zeros(nl * cap, np.float64), topk_idx=np.zeros(nl * top_k, np.int64),
+                    topk_score=np.zeros(nl * top_k, np.float64), nkept=np.zeros(nl, np.int64))
+        tr = _Trace(cap, *(arrs[k].ctypes.data for k in
+                           ("ncells", "idx", "count", "amb", "tau", "topk_idx", "topk_score", "nkept")))
+        tr_p = C.byref(tr)
+        keep = [tr, arrs]
+    L.rvo_solve(a.reshape(-1), b.reshape(-1), a.shape[0], float(delta), int(grid_n), int(levels), int(top_k),
+                int(rank_mode), int(refit_iters), int(nthreads), C.byref(res), tr_p)
+    per_level = []
+    if trace:
+        arrs = keep[1]
+        cap = keep[0].cap
+        for lev in range(levels + 1):
+            nc = int(arrs["ncells"][lev])
+            nk = int(arrs["nkept"][lev])
+            sl = slice(lev * cap, lev * cap + nc)
+            per_level.append(dict(
+                idx=arrs["idx"][sl].copy(), count=arrs["count"][sl].copy(), amb=arrs["amb"][sl].copy(),
+                tau=arrs["tau"][sl].copy(),
+                topk_idx=arrs["topk_idx"][lev * top_k: lev * top_k + nk].copy(),
+                topk_score=arrs["topk_score"][lev * top_k: lev * top_k + nk].copy()))
+    return OracleResult(q=np.array(res.q[:]), R=np.array(res.R[:]).reshape(3, 3), best_count=res.best_count,
+                        inliers=res.inliers, best_cell=res.best_cell, tests=res.tests,
+                        ambiguous=res.ambiguous, status=res.status, refits=res.refits, levels=per_level)
+
+
+def default_threads() -> int:
+    return max(1, (os.cpu_count() or 1))

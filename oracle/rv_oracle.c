@@ -1,0 +1,579 @@
+/*
+ * rv_oracle.c -- plain FP64 CPU oracle for the rotation-voting hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may load, link or
+ * call this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline leg do.  It shares no code, header or constant table with the
+ * CUDA library.
+ *
+ * Everything is computed in double from double casts of the float32 inputs,
+ * one (cell, pair) test at a time, in the order the method states it:
+ *
+ *   1. pair step   -- M_i = L(a)^T L'(b) from the two 4x4 matrices printed in
+ *                     App. A; S_i = (I - M_i)/2 = I - P_i, the projector onto
+ *                     the orthogonal complement of the quaternion-circle plane
+ *                     (Lemma 1, Sec. 4.2; App. A shows the circle is the +1
+ *                     eigenspace of M_i).
+ *   2. grid        -- cells of an n^3 grid over the cube [-1,1]^3 that meet
+ *                     the closed unit ball of quaternion vector parts, w >= 0
+ *                     (the hemisphere of Sec. 4.3.1, charted by (x, y, z)).
+ *   3. cell radius -- a covering radius r_cell on S^3.
+ *   4. threshold   -- tau = sin^2(delta + r_cell), 1 once delta + r >= pi/2.
+ *   5. vote        -- cell votes for pair i iff q_cell^T S_i q_cell <= tau
+ *                     (the dense "cell tests every circle" dual of Alg. 1).
+ *   6. rank        -- score = count - N tau (EXCESS) or count (RAW),
+ *                     order (score desc, idx asc), keep the top K.
+ *   7. children    -- the 8 octants of each kept cell at the next level.
+ *   8. fit         -- smallest eigenvector of sum_{inliers} S_i, i.e. of
+ *                     Q^T Q of Eq. (stack), Sec. 4.2; refit with the
+ *                     delta-only inlier rule.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
+ * arithmetic is the written sequence of IEEE double operations).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define RVO_AMBIG 1e-6 /* |v - tau| <= this: the (cell, pair) decision is reported ambiguous */
+
+enum { RVO_OK = 0, RVO_EINVAL = -1, RVO_EDEGENERATE = -6 };
+
+/* ------------------------------------------------------------------ */
+/* 1. pair step (App. A)                                              */
+/* ------------------------------------------------------------------ */
+
+/* The two 4x4 matrices of App. A with q^T L(a)^T L'(b) q = b^T R(q) a. */
+static void appA_L(const double a[3], double L[16]) {
+    const double a1 = a[0], a2 = a[1], a3 = a[2];
+    const double m[16] = {0.0, -a1, -a2, -a3,
+                          a1, 0.0, a3, -a2,
+                          a2, -a3, 0.0, a1,
+                          a3, a2, -a1, 0.0};
+    memcpy(L, m, sizeof m);
+}
+
+static void appA_Lp(const double b[3], double L[16]) {
+    const double b1 = b[0], b2 = b[1], b3 = b[2];
+    const double m[16] = {0.0, -b1, -b2, -b3,
+                          b1, 0.0, -b3, b2,
+                          b2, b3, 0.0, -b1,
+                          b3, -b2, b1, 0.0};
+    memcpy(L, m, sizeof m);
+}
+
+/* M = L(a)^T L'(b) (App. A); row-major 4x4. */
+void rvo_pair_M(const float a32[3], const float b32[3], double M[16]) {
+    double a[3] = {a32[0], a32[1], a32[2]}, b[3] = {b32[0], b32[1], b32[2]};
+    double La[16], Lb[16];
+    appA_L(a, La);
+    appA_Lp(b, Lb);
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double acc = 0.0;
+            for (int k = 0; k < 4; ++k) acc += La[k * 4 + r] * Lb[k * 4 + c];
+            M[r * 4 + c] = acc;
+        }
+}
+
+/* S = (I - M)/2: for unit a, b, M has eigenvalues (1,1,-1,-1) and the +1
+ * eigenspace is the circle plane, so (I - M)/2 = I - P. */
+void rvo_pair_S(const float a32[3], const float b32[3], double S[16]) {
+    double M[16];
+    rvo_pair_M(a32, b32, M);
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) S[r * 4 + c] = ((r == c ? 1.0 : 0.0) - M[r * 4 + c]) / 2.0;
+}
+
+/* q^T S q */
+double rvo_quad(const double S[16], const double q[4]) {
+    double v = 0.0;
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) v += q[r] * S[r * 4 + c] * q[c];
+    return v;
+}
+
+/* Rotation matrix of q (App. A), row-major. */
+void rvo_quat_to_R(const double q[4], double R[9]) {
+    const double q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+    R[0] = q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3;
+    R[1] = 2.0 * (q1 * q2 - q0 * q3);
+    R[2] = 2.0 * (q1 * q3 + q0 * q2);
+    R[3] = 2.0 * (q1 * q2 + q0 * q3);
+    R[4] = q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3;
+    R[5] = 2.0 * (q2 * q3 - q0 * q1);
+    R[6] = 2.0 * (q1 * q3 - q0 * q2);
+    R[7] = 2.0 * (q2 * q3 + q0 * q1);
+    R[8] = q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3;
+}
+
+/* ------------------------------------------------------------------ */
+/* 2-4. grid, cell radius, threshold                                  */
+/* ------------------------------------------------------------------ */
+
+static double dist0(double lo, double hi) { /* distance from 0 to [lo, hi] */
+    if (lo > 0.0) return lo;
+    if (hi < 0.0) return -hi;
+    return 0.0;
+}
+
+/* Cell (ix, iy, iz) of an n^3 grid over [-1,1]^3 exists iff its box meets
+ * the closed unit ball. */
+int rvo_cell_exists(int n, int64_t ix, int64_t iy, int64_t iz) {
+    const double h = 2.0 / (double)n;
+    const int64_t id[3] = {ix, iy, iz};
+    double d2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        if (id[k] < 0 || id[k] >= n) return 0;
+        const double lo = -1.0 + (double)id[k] * h, hi = lo + h;
+        const double d = dist0(lo, hi);
+        d2 += d * d;
+    }
+    return d2 <= 1.0;
+}
+
+int64_t rvo_cell_index(int n, int64_t ix, int64_t iy, int64_t iz) {
+    return (iz * (int64_t)n + iy) * (int64_t)n + ix;
+}
+
+/* Cell centre quaternion and covering chord.
+ *   c = box centre; c' = c, or c/|c| when |c| > 1; q = (sqrt(1 - |c'|^2), c').
+ *   Every point p of (box cap ball) maps to (sqrt(1-|p|^2), p); its chord to q
+ *   is at most sqrt(dv^2 + dw^2) with
+ *     dv = |p - c'| <= (sqrt 3 / 2) h + max(0, |c| - 1)
+ *     dw = |sqrt(1-|p|^2) - sqrt(1-|c'|^2)| <= min(sqrt(D), D / w_c),
+ *     D  = max over the box of | |p|^2 - |c'|^2 |, |p|^2 clamped to [.., 1].
+ *   The geodesic covering radius is r = 2 asin(chord / 2). */
+void rvo_cell_geom(int n, int64_t ix, int64_t iy, int64_t iz, double q[4], double *chord) {
+    const double h = 2.0 / (double)n;
+    const int64_t id[3] = {ix, iy, iz};
+    double c[3], c2 = 0.0, maxv2 = 0.0, minv2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double lo = -1.0 + (double)id[k] * h, hi = lo + h;
+        c[k] = -1.0 + ((double)id[k] + 0.5) * h;
+        c2 += c[k] * c[k];
+        const double m = (lo * lo > hi * hi) ? lo * lo : hi * hi;
+        maxv2 += m;
+        const double d = dist0(lo, hi);
+        minv2 += d * d;
+    }
+    const double cn = sqrt(c2);
+    double cp[3], cp2;
+    if (cn > 1.0) {
+        cp2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            cp[k] = c[k] / cn;
+            cp2 += cp[k] * cp[k];
+        }
+    } else {
+        for (int k = 0; k < 3; ++k) cp[k] = c[k];
+        cp2 = c2;
+    }
+    const double w2 = 1.0 - cp2;
+    q[0] = w2 > 0.0 ? sqrt(w2) : 0.0;
+    q[1] = cp[0];
+    q[2] = cp[1];
+    q[3] = cp[2];
+
+    const double dv = (sqrt(3.0) / 2.0) * h + (cn > 1.0 ? cn - 1.0 : 0.0);
+    const double hi2 = maxv2 < 1.0 ? maxv2 : 1.0;
+    const double d1 = fabs(hi2 - cp2), d2 = fabs(cp2 - minv2);
+    const double D = d1 > d2 ? d1 : d2;
+    double dw = sqrt(D);
+    if (q[0] > 0.0) {
+        const double alt = D / q[0];
+        if (alt < dw) dw = alt;
+    }
+    *chord = sqrt(dv * dv + dw * dw);
+}
+
+/* tau = sin^2(delta + r), r = 2 asin(x), x = min(1, chord / 2); tau = 1 once
+ * delta + r >= pi/2.  Written with cos r = 1 - 2x^2, sin r = 2x sqrt(1-x^2)
+ * (an identity), so that it needs only sqrt. */
+double rvo_tau(double sin_d, double cos_d, double chord) {
+    double x = chord / 2.0;
+    if (x > 1.0) x = 1.0;
+    const double cr = 1.0 - 2.0 * x * x;
+    const double sr = 2.0 * x * sqrt(1.0 - x * x);
+    const double cos_sum = cos_d * cr - sin_d * sr; /* cos(delta + r) */
+    if (cos_sum <= 0.0) return 1.0;
+    const double s = sin_d * cr + cos_d * sr; /* sin(delta + r) */
+    return s * s;
+}
+
+/* Level-0 cells in increasing linear index; returns the count. */
+int64_t rvo_level_cells(int n, int64_t *idx_out) {
+    int64_t cnt = 0;
+    for (int64_t iz = 0; iz < n; ++iz)
+        for (int64_t iy = 0; iy < n; ++iy)
+            for (int64_t ix = 0; ix < n; ++ix)
+                if (rvo_cell_exists(n, ix, iy, iz)) {
+                    if (idx_out) idx_out[cnt] = rvo_cell_index(n, ix, iy, iz);
+                    ++cnt;
+                }
+    return cnt;
+}
+
+static void unpack_idx(int n, int64_t idx, int64_t *ix, int64_t *iy, int64_t *iz) {
+    *ix = idx % n;
+    *iy = (idx / n) % n;
+    *iz = idx / ((int64_t)n * n);
+}
+
+/* ------------------------------------------------------------------ */
+/* 5. vote                                                            */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const double *S;  /* [n_pairs][16] */
+    int64_t n_pairs;
+    int n_side;
+    const int64_t *cells;
+    int64_t c0, c1;
+    double sin_d, cos_d;
+    int32_t *count, *amb;
+    double *tau_out;
+} vote_job;
+
+static void *vote_worker(void *arg) {
+    vote_job *j = (vote_job *)arg;
+    for (int64_t c = j->c0; c < j->c1; ++c) {
+        int64_t ix, iy, iz;
+        unpack_idx(j->n_side, j->cells[c], &ix, &iy, &iz);
+        double q[4], chord;
+        rvo_cell_geom(j->n_side, ix, iy, iz, q, &chord);
+        const double tau = rvo_tau(j->sin_d, j->cos_d, chord);
+        int32_t cnt = 0, amb = 0;
+        for (int64_t i = 0; i < j->n_pairs; ++i) {
+            const double v = rvo_quad(j->S + 16 * i, q);
+            if (v <= tau) ++cnt;
+            if (fabs(v - tau) <= RVO_AMBIG) ++amb;
+        }
+        j->count[c] = cnt;
+        if (j->amb) j->amb[c] = amb;
+        if (j->tau_out) j->tau_out[c] = tau;
+    }
+    return NULL;
+}
+
+static void vote_cells_S(const double *S, int64_t n, int n_side, const int64_t *cells, int64_t ncells,
+                         double sin_d, double cos_d, int32_t *count, int32_t *amb, double *tau_out,
+                         int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if ((int64_t)nthreads > ncells) nthreads = ncells > 0 ? (int)ncells : 1;
+    vote_job jobs[256];
+    pthread_t th[256];
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = (vote_job){S, n, n_side, cells, ncells * t / nthreads, ncells * (t + 1) / nthreads,
+                             sin_d, cos_d, count, amb, tau_out};
+    }
+    if (nthreads == 1) {
+        vote_worker(&jobs[0]);
+        return;
+    }
+    for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, vote_worker, &jobs[t]);
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+}
+
+static double *all_pair_S(const float *a, const float *b, int64_t n) {
+    double *S = (double *)malloc(sizeof(double) * 16 * (size_t)(n > 0 ? n : 1));
+    if (!S) return NULL;
+    for (int64_t i = 0; i < n; ++i) rvo_pair_S(a + 3 * i, b + 3 * i, S + 16 * i);
+    return S;
+}
+
+/* Counts (and ambiguous counts, and tau) for an arbitrary list of cells of
+ * the n_side grid. */
+int rvo_vote_cells(const float *a, const float *b, int64_t n, double delta, int n_side,
+                   const int64_t *cells, int64_t ncells, int32_t *count, int32_t *amb, double *tau_out,
+                   int nthreads) {
+    double *S = all_pair_S(a, b, n);
+    if (!S) return RVO_EINVAL;
+    vote_cells_S(S, n, n_side, cells, ncells, sin(delta), cos(delta), count, amb, tau_out, nthreads);
+    free(S);
+    return RVO_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* 6. rank                                                            */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    double score;
+    int64_t idx;
+    int64_t pos;
+} rank_item;
+
+static int rank_cmp(const void *x, const void *y) {
+    const rank_item *a = (const rank_item *)x, *b = (const rank_item *)y;
+    if (a->score > b->score) return -1;
+    if (a->score < b->score) return 1;
+    if (a->idx < b->idx) return -1;
+    if (a->idx > b->idx) return 1;
+    return 0;
+}
+
+/* Order cells by (score desc, idx asc); score = count - n*tau (EXCESS,
+ * rank_mode 0) or count (RAW, rank_mode 1).  Writes the positions (into the
+ * input arrays) of the first k in rank order; returns how many. */
+int64_t rvo_rank(const int32_t *count, const double *tau, const int64_t *idx, int64_t ncells, int64_t n_pairs,
+                 int rank_mode, int64_t k, int64_t *pos_out, double *score_out) {
+    rank_item *it = (rank_item *)malloc(sizeof(rank_item) * (size_t)(ncells > 0 ? ncells : 1));
+    if (!it) return -1;
+    for (int64_t c = 0; c < ncells; ++c) {
+        const double score = rank_mode == 1 ? (double)count[c] : (double)count[c] - (double)n_pairs * tau[c];
+        it[c] = (rank_item){score, idx[c], c};
+    }
+    qsort(it, (size_t)ncells, sizeof(rank_item), rank_cmp);
+    const int64_t kk = k < ncells ? k : ncells;
+    for (int64_t r = 0; r < kk; ++r) {
+        pos_out[r] = it[r].pos;
+        if (score_out) score_out[r] = it[r].score;
+    }
+    free(it);
+    return kk;
+}
+
+/* ------------------------------------------------------------------ */
+/* 8. fit                                                             */
+/* ------------------------------------------------------------------ */
+
+/* Cyclic Jacobi eigen-decomposition of a symmetric 4x4 (row-major).
+ * Eigenvalues ascending in evals; eigenvector k is column k of V. */
+void rvo_jacobi4(const double A_in[16], double evals[4], double V_out[16]) {
+    double A[4][4], V[4][4];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            A[r][c] = A_in[r * 4 + c];
+            V[r][c] = r == c ? 1.0 : 0.0;
+        }
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < 4; ++p)
+            for (int q = p + 1; q < 4; ++q) off += A[p][q] * A[p][q];
+        if (off < 1e-300) break;
+        for (int p = 0; p < 3; ++p)
+            for (int q = p + 1; q < 4; ++q) {
+                if (A[p][q] == 0.0) continue;
+                /* rotation that zeroes A[p][q]: t = tan(phi), theta = cot(2 phi) */
+                const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 4; ++k) { /* A <- A J */
+                    const double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 4; ++k) { /* A <- J^T A */
+                    const double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 4; ++k) { /* V <- V J */
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    int order[4] = {0, 1, 2, 3};
+    for (int i = 1; i < 4; ++i) /* insertion sort by eigenvalue, ascending */
+        for (int j = i; j > 0 && A[order[j]][order[j]] < A[order[j - 1]][order[j - 1]]; --j) {
+            const int t = order[j];
+            order[j] = order[j - 1];
+            order[j - 1] = t;
+        }
+    for (int k = 0; k < 4; ++k) {
+        evals[k] = A[order[k]][order[k]];
+        for (int r = 0; r < 4; ++r) V_out[r * 4 + k] = V[r][order[k]];
+    }
+}
+
+/* Sign convention: w > 0; if w == 0, the first nonzero component > 0. */
+void rvo_canonical(double q[4]) {
+    for (int k = 0; k < 4; ++k) {
+        if (q[k] > 0.0) return;
+        if (q[k] < 0.0) {
+            for (int j = 0; j < 4; ++j) q[j] = -q[j];
+            return;
+        }
+    }
+}
+
+/* Smallest eigenvector of sum_{i in set} S_i (Eq. stack: the least-squares
+ * solution of Q q = 0 is the eigenvector of Q^T Q with the smallest
+ * eigenvalue; Q^T Q = sum_i (q_b3 q_b3^T + q_b4 q_b4^T) = sum_i S_i).
+ * Returns 1 if the two smallest eigenvalues are within 1e-12 * trace. */
+static int fit_set(const double *S, const unsigned char *in, int64_t n, double q[4]) {
+    double A[16] = {0};
+    for (int64_t i = 0; i < n; ++i)
+        if (in[i])
+            for (int k = 0; k < 16; ++k) A[k] += S[16 * i + k];
+    double ev[4], V[16];
+    rvo_jacobi4(A, ev, V);
+    for (int r = 0; r < 4; ++r) q[r] = V[r * 4 + 0];
+    const double tr = A[0] + A[5] + A[10] + A[15];
+    return (ev[1] - ev[0]) <= 1e-12 * tr;
+}
+
+/* ------------------------------------------------------------------ */
+/* full solve                                                         */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    double q[4];
+    double R[9];
+    int32_t best_count;
+    int32_t inliers;
+    int64_t best_cell; /* linear index at the last level */
+    int64_t tests;     /* cells x pairs over all levels */
+    int64_t ambiguous; /* (cell, pair) tests with |v - tau| <= 1e-6 */
+    int32_t status;
+    int32_t refits;    /* refit iterations performed */
+} rvo_result;
+
+/* Optional per-level trace: for level l, up to cap cells (idx, count, amb,
+ * tau) in table order and the top-k positions in rank order. */
+typedef struct {
+    int64_t cap;
+    int64_t *ncells;   /* [levels+1] */
+    int64_t *idx;      /* [levels+1][cap] */
+    int32_t *count;    /* [levels+1][cap] */
+    int32_t *amb;      /* [levels+1][cap] */
+    double *tau;       /* [levels+1][cap] */
+    int64_t *topk_idx; /* [levels+1][top_k] */
+    double *topk_score;
+    int64_t *nkept;    /* [levels+1] */
+} rvo_trace;
+
+int rvo_solve(const float *a, const float *b, int64_t n, double delta, int grid_n, int levels, int top_k,
+              int rank_mode, int refit_iters, int nthreads, rvo_result *res, rvo_trace *tr) {
+    memset(res, 0, sizeof *res);
+    if (n < 2 || grid_n < 1 || levels < 0 || top_k < 1 || !(delta > 0.0)) {
+        res->status = RVO_EINVAL;
+        return RVO_EINVAL;
+    }
+    double *S = all_pair_S(a, b, n);
+    if (!S) return RVO_EINVAL;
+    const double sd = sin(delta), cd = cos(delta);
+
+    int64_t nc = rvo_level_cells(grid_n, NULL);
+    int64_t *cells = (int64_t *)malloc(sizeof(int64_t) * (size_t)nc);
+    rvo_level_cells(grid_n, cells);
+    int64_t win_idx = -1, win_n = grid_n;
+    int32_t win_count = 0;
+    double win_tau = 0.0;
+
+    for (int lev = 0; lev <= levels; ++lev) {
+        const int n_side = grid_n << lev;
+        int32_t *count = (int32_t *)malloc(sizeof(int32_t) * (size_t)nc);
+        int32_t *amb = (int32_t *)malloc(sizeof(int32_t) * (size_t)nc);
+        double *tau = (double *)malloc(sizeof(double) * (size_t)nc);
+        vote_cells_S(S, n, n_side, cells, nc, sd, cd, count, amb, tau, nthreads);
+        res->tests += nc * n;
+        for (int64_t c = 0; c < nc; ++c) res->ambiguous += amb[c];
+
+        int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)top_k);
+        double *score = (double *)malloc(sizeof(double) * (size_t)top_k);
+        const int64_t kept = rvo_rank(count, tau, cells, nc, n, rank_mode, top_k, pos, score);
+
+        if (tr) {
+            tr->ncells[lev] = nc;
+            tr->nkept[lev] = kept;
+            const int64_t m = nc < tr->cap ? nc : tr->cap;
+            for (int64_t c = 0; c < m; ++c) {
+                tr->idx[lev * tr->cap + c] = cells[c];
+                tr->count[lev * tr->cap + c] = count[c];
+                tr->amb[lev * tr->cap + c] = amb[c];
+                tr->tau[lev * tr->cap + c] = tau[c];
+            }
+            for (int64_t r = 0; r < kept; ++r) {
+                tr->topk_idx[lev * top_k + r] = cells[pos[r]];
+                tr->topk_score[lev * top_k + r] = score[r];
+            }
+        }
+        win_idx = cells[pos[0]];
+        win_count = count[pos[0]];
+        win_tau = tau[pos[0]];
+        win_n = n_side;
+
+        if (lev < levels) { /* 7. children of the kept cells */
+            int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)(8 * kept));
+            int64_t nn = 0;
+            for (int64_t r = 0; r < kept; ++r) {
+                int64_t ix, iy, iz;
+                unpack_idx(n_side, cells[pos[r]], &ix, &iy, &iz);
+                for (int dz = 0; dz < 2; ++dz)
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dx = 0; dx < 2; ++dx) {
+                            const int64_t cx = 2 * ix + dx, cy = 2 * iy + dy, cz = 2 * iz + dz;
+                            if (rvo_cell_exists(2 * n_side, cx, cy, cz))
+                                next[nn++] = rvo_cell_index(2 * n_side, cx, cy, cz);
+                        }
+            }
+            free(cells);
+            cells = next;
+            nc = nn;
+        }
+        free(count);
+        free(amb);
+        free(tau);
+        free(pos);
+        free(score);
+    }
+    free(cells);
+
+    /* 8. fit */
+    int64_t ix, iy, iz;
+    unpack_idx((int)win_n, win_idx, &ix, &iy, &iz);
+    double qc[4], chord;
+    rvo_cell_geom((int)win_n, ix, iy, iz, qc, &chord);
+    res->best_cell = win_idx;
+    res->best_count = win_count;
+
+    unsigned char *in0 = (unsigned char *)calloc((size_t)n, 1);
+    unsigned char *in1 = (unsigned char *)calloc((size_t)n, 1);
+    int64_t n_in = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (rvo_quad(S + 16 * i, qc) <= win_tau) {
+            in0[i] = 1;
+            ++n_in;
+        }
+    double q[4] = {qc[0], qc[1], qc[2], qc[3]};
+    int status = RVO_OK;
+    if (n_in < 2 || fit_set(S, in0, n, q)) {
+        memcpy(q, qc, sizeof q);
+        status = RVO_EDEGENERATE;
+    } else {
+        const double thr = sd * sd; /* sin^2(delta) */
+        for (int t = 1; t <= refit_iters; ++t) {
+            int64_t m = 0, changed = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                in1[i] = rvo_quad(S + 16 * i, q) <= thr;
+                m += in1[i];
+                changed += in1[i] != in0[i];
+            }
+            if (m < 2 || changed == 0) break;
+            double qn[4];
+            if (fit_set(S, in1, n, qn)) break;
+            memcpy(q, qn, sizeof q);
+            unsigned char *tmp = in0;
+            in0 = in1;
+            in1 = tmp;
+            n_in = m;
+            res->refits = t;
+        }
+    }
+    rvo_canonical(q);
+    memcpy(res->q, q, sizeof q);
+    rvo_quat_to_R(q, res->R);
+    res->inliers = (int32_t)n_in;
+    res->status = status;
+    free(in0);
+    free(in1);
+    free(S);
+    return status;
+}

@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Benchmark of the rotation-voting hot path on GB300.
+
+One step = one full solve (pair step, vote on every level, top-K, children,
+fit) of the 1e5-pair workload: 99% outliers, sigma 0.01, delta 0.03,
+64^3 coarse grid + 3 levels of 2x2x2 refinement of the top 16 cells.
+
+Prints ONE JSON line: metric / value (cell-correspondence tests per second,
+whole job), rotations/s, p50/p99 solve latency, e2e through the C ABI with
+pinned host buffers, the dominant kernel's roofline, clocks, and the oracle's
+CPU baseline.  `--impl reference` times the FP64 oracle on the host cores
+instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-correspondence tests/sec and rotations/sec at 1 GB300; p50/p99 solve latency"
+UNIT = "cell-correspondence tests/s"
+WORKLOAD = "fp32_n1e5_64L3"
+WORKLOAD_DESC = ("N=1e5 float32 unit pairs, 99% uniform outliers, inlier noise sigma=0.01, delta=0.03 rad; "
+                 "64^3 coarse grid over the vector-part ball (146,864 cells) + 3 levels of 2x2x2 "
+                 "subdivision of the top-16 cells; exact counts, EXCESS ranking, FP64 fit with 8 refits")
+FLOPS_PER_TEST = 20.0  # 10 multiply-adds of the (cell monomials . pair S entries) contraction
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-extra", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read-only queries)."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _angle(q1, q2) -> float:
+    """Angle between the rotations of two unit quaternions (for the report line)."""
+    w = abs(sum(float(x) * float(y) for x, y in zip(q1, q2)))
+    return 2.0 * math.atan2(math.sqrt(max(0.0, 1.0 - w * w)), w)
+
+
+def percentile(xs, p):
+    s = sorted(xs)
+    if not s:
+        return None
+    k = min(len(s) - 1, max(0, int(math.ceil(p / 100.0 * len(s))) - 1))
+    return s[k]
+
+
+def cpu_oracle_rate(p, grid_n, seconds: float, threads: int):
+    """Oracle (FP64 C, as it stands) vote over a bounded sample of coarse cells:
+    tests/s on `threads` host threads."""
+    import numpy as np
+    import oracle
+    cells = oracle.level_cells(grid_n)
+    rng = np.random.default_rng(0)
+    order = rng.permutation(len(cells))
+    # calibrate on a few cells, then size the sample to ~seconds
+    m0 = max(threads, 8)
+    t0 = time.perf_counter()
+    oracle.vote_cells(p.a, p.b, float(np.float32(p.delta)), grid_n, cells[order[:m0]], nthreads=threads)
+    dt0 = max(1e-3, time.perf_counter() - t0)
+    m = int(min(len(cells), max(m0, m0 * seconds / dt0)))
+    t0 = time.perf_counter()
+    oracle.vote_cells(p.a, p.b, float(np.float32(p.delta)), grid_n, cells[order[:m]], nthreads=threads)
+    dt = time.perf_counter() - t0
+    return m * p.n / dt, m, dt
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, bounded samples."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2506_11547_gb300 import synth
+    p, grid_n, levels = synth.config_problem(args.workload)
+    threads = os.cpu_count() or 1
+    per_step = max(0.5, min(5.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(p, grid_n, per_step / 4, threads)
+    rates, samples = [], []
+    for _ in range(args.steps):
+        r, m, dt = cpu_oracle_rate(p, grid_n, per_step, threads)
+        rates.append(r)
+        samples.append(m)
+    total_tests = sum(m * p.n for m in samples)
+    value = float(sum(rates) / len(rates))
+    line = {
+        "metric": METRIC, "impl": "reference", "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESC},
+        "ms_per_step": 1e3 * total_tests / value / args.steps,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"per step ~{per_step:.1f}s: the FP64 oracle's vote of {samples[0]} random "
+                                   f"coarse cells x {p.n} pairs ({threads} threads over cells)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2506_11547_gb300 import rot_vote as rv
+    from paper_2506_11547_gb300 import synth
+
+    # weak scaling: each rank solves its own problem instance of the same shape
+    p, grid_n, levels = synth.config_problem(args.workload, rep=rank)
+    a_d = torch.from_numpy(p.a).to(dev)
+    b_d = torch.from_numpy(p.b).to(dev)
+    stream = torch.cuda.current_stream()
+    ctx = rv.Context(grid_n=grid_n, levels=levels, precision=args.precision, cuda_stream=stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    arr = (rv.rot_vote_problem * 1)()
+    arr[0], keep = rv.problem(a_d, b_d, p.delta)
+    out = (rv.rot_vote_result * 1)()
+    for _ in range(max(3, args.warmup)):
+        ctx.solve_raw(arr, 1, out)
+    res0 = rv.Result.of(out[0])
+    tests_per_step = res0.tests
+
+    # ---- device-timed steps (inputs resident in HBM; L2 flushed before each) ----
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            ctx.solve_raw(arr, 1, out)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    per = [s.elapsed_time(e) for s, e in evs]
+    elapsed = sum(per)
+    if dist:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    total_tests = tests_per_step * args.steps * ws
+    value = total_tests / (elapsed / 1e3)
+    ms_per_step = elapsed / args.steps
+    clocks = clk.summary()
+
+    # ---- e2e: public API with pinned host inputs, copies inside the timed region ----
+    a_h = torch.from_numpy(p.a).pin_memory()
+    b_h = torch.from_numpy(p.b).pin_memory()
+    arr_h = (rv.rot_vote_problem * 1)()
+    arr_h[0], keep_h = rv.problem(a_h, b_h, p.delta)
+    ctx.solve_raw(arr_h, 1, out)
+    e2e_t = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve_raw(arr_h, 1, out)  # blocking: H2D, pipeline, D2H of the result
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_t)
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = tests_per_step * args.steps * ws / e2e_s
+    h2d = 2 * p.n * 3 * 4
+    d2h = ctypes.sizeof(rv.rot_vote_result) + 4  # result struct + device error word
+
+    # ---- roofline of the dominant kernel (profiled solves on the same stream) ----
+    prof = rv.Context(grid_n=grid_n, levels=levels, precision=args.precision, cuda_stream=stream.cuda_stream,
+                      keep_trace=2)
+    stage_ms = {}
+    n_prof = 5
+    launches = 0
+    for _ in range(n_prof + 1):
+        flush.zero_()
+        prof.solve([(a_d, b_d, p.delta)])
+        st = prof.stage_times()
+        launches = len(st)
+        for kind, lev, ms in st:
+            stage_ms.setdefault((kind, lev), []).append(ms)
+    n_cells0 = len(prof.level_trace(0, 0)[0])
+    prof.close()
+    stage_avg = {k: sum(v[1:]) / len(v[1:]) for k, v in stage_ms.items()}
+    dom = max(stage_avg, key=stage_avg.get)
+    peaks, peak_src = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    tests_dom = (n_cells0 * p.n) if dom == ("vote", 0) else None
+    roofline = None
+    if tests_dom:
+        achieved = FLOPS_PER_TEST * tests_dom / (stage_avg[dom] / 1e3) / 1e12
+        if args.precision == "fp32":
+            peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            bound, note = "alu", f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flops x {peaks.get('sm_max_mhz')} MHz"
+        else:
+            peak = peaks["bf16_tflops"]
+            bound, note = "tensor", f"dense bf16 tensor peak ({peak_src})"
+        roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": f"{dom[0]} level {dom[1]}", "kernel_ms": stage_avg[dom],
+                    "flops_per_test": FLOPS_PER_TEST, "tests_per_launch": tests_dom, "peak_source": note,
+                    "share_of_step": stage_avg[dom] / sum(stage_avg.values())}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
+    cpu = None
+    if rank == 0 and ws == 1:
+        threads = os.cpu_count() or 1
+        rate, m, dt = cpu_oracle_rate(p, grid_n, args.cpu_seconds, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{m} random coarse cells x {p.n} pairs of this workload's level 0 ({dt:.1f} s, "
+                         f"FP64 C oracle, threads over cells)"}
+
+    lat = per
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else args.precision, "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESC, "precision": args.precision,
+                   "tests_per_step": tests_per_step, "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"independent problem per GPU x{ws}"},
+        "rotations_per_s": ws * args.steps / (elapsed / 1e3),
+        "latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "mean": ms_per_step},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": 1e3 * e2e_s / args.steps},
+        "gpu_launches": launches * args.steps,
+        "roofline": roofline,
+        "stage_ms": {f"{k[0]}:{k[1]}": v for k, v in sorted(stage_avg.items(), key=lambda x: -x[1])},
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "result": {"status": res0.status, "angle_to_truth_rad": None, "rechecked": res0.rechecked,
+                   "ambiguous": res0.ambiguous},
+    }
+    line["result"]["angle_to_truth_rad"] = _angle(res0.q, p.q_true)
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

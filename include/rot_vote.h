@@ -1,0 +1,191 @@
+/*
+ * rot_vote.h -- C ABI of the GB300 (sm_103a) rotation-voting library.
+ *
+ * Method: "Linearly Solving Robust Rotation Estimation" (arXiv 2506.11547).
+ * Each correspondence (a_i, b_i), b_i ~ R a_i, confines the unit quaternion
+ * of R to a great circle of S^3 (Sec. 4.1).  Lemma 1 (Sec. 4.2) writes that
+ * circle as two linear equations; App. A shows the circle is the +1
+ * eigenspace of the symmetric M_i = L(a_i)^T L'(b_i), so with
+ * S_i = (I - M_i)/2 = I - P_i the quadratic form q^T S_i q is
+ * sin^2(distance on S^3 from q to circle i).  App. D gives the same S_i as
+ * A_i^T A_i / 4 for the rank-2 skew matrix A_i with A_i q = 0.
+ *
+ * The library votes over a grid on the w >= 0 hemisphere charted by the
+ * quaternion's vector part (x, y, z) in the unit ball (Sec. 4.3.1 reduces
+ * the search to a hemisphere and to a 3-D accumulator): cell c votes for
+ * pair i iff q_c^T S_i q_c <= tau_c = sin^2(delta + r_c), r_c a covering
+ * radius of the cell.  That is the dense "each cell tests each circle" dual
+ * of Alg. 1 (Sec. 4.3.2).  It then ranks cells, refines the top K by 2x2x2
+ * subdivision for `levels` levels, and fits the rotation as the smallest
+ * eigenvector of sum_{inliers} S_i -- the least-squares solution of the
+ * stacked system Q q = 0 of Eq. (stack), Sec. 4.2.
+ *
+ * Vote counts are exact: every (cell, pair) decision equals the decision of
+ * an FP64 evaluation of q^T S_i q <= tau, except for pairs within 1e-6 of the
+ * threshold, which are counted as the FP32 re-check decides and reported in
+ * rot_vote_result.ambiguous.
+ *
+ * Conventions
+ *   - Quaternions are (w, x, y, z), scalar first; rotation matrices are
+ *     row-major 3x3 (App. A).
+ *   - Every call returns a rot_vote_status.  Per-problem outcomes go in
+ *     rot_vote_result.status.
+ *   - Pointers a, b may be host or device memory (the library asks the CUDA
+ *     driver which).  Host inputs are copied to the device inside the call.
+ *     The caller owns a and b; they must stay valid until rot_vote_solve
+ *     returns, or until rot_vote_poll returns a terminal status for the
+ *     ticket.  The library never frees caller memory.
+ *   - A context is not thread-safe: use one context per thread, or lock.
+ *     (rot_vote_submit / rot_vote_poll may be called from one thread while
+ *     the context's own scheduler thread runs.)
+ *   - The library never prints; rot_vote_last_error describes the last
+ *     failure on a context.
+ *   - Device memory is allocated with cudaMalloc by the context (workspace
+ *     grown on demand up to config.device_mem_budget) and freed by
+ *     rot_vote_destroy.
+ */
+#ifndef ROT_VOTE_H
+#define ROT_VOTE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rot_vote_ctx rot_vote_ctx;
+
+typedef enum {
+    ROT_VOTE_OK = 0,
+    ROT_VOTE_PENDING = 1,       /* rot_vote_poll: not finished within the timeout */
+    ROT_VOTE_EINVAL = -1,       /* bad argument or invalid input data */
+    ROT_VOTE_ENOMEM = -2,       /* device (or pinned host) allocation failed or over budget */
+    ROT_VOTE_ECUDA = -3,        /* a CUDA runtime call failed; see rot_vote_last_error */
+    ROT_VOTE_EAGAIN = -4,       /* rot_vote_submit: admission queue full */
+    ROT_VOTE_ETIMEDOUT = -5,    /* a bounded device-side wait gave up */
+    ROT_VOTE_EDEGENERATE = -6,  /* fit degenerate: < 2 inliers or a repeated smallest eigenvalue */
+    ROT_VOTE_ENOTFOUND = -7     /* rot_vote_poll: unknown or already collected ticket */
+} rot_vote_status;
+
+/* Arithmetic of the dominant (cell, pair) contraction.  All modes give the
+ * same exact counts; they differ in speed and in how many tests need the
+ * FP32 re-check.
+ *   FP32    -- CUDA-core FP32 FMA form, 10 multiply-adds per test.
+ *   FP16    -- tcgen05 tensor-core form, monomials and S entries in FP16
+ *              (K = 10 + 2 threshold columns, padded to 16), FP32
+ *              accumulation in tensor memory.
+ *   BF16    -- as FP16 with BF16 operands.
+ *   FP16X2, BF16X2 -- hi/lo split operands (K = 32): far fewer re-checks. */
+typedef enum {
+    ROT_PREC_FP32 = 0,
+    ROT_PREC_FP16 = 1,
+    ROT_PREC_BF16 = 2,
+    ROT_PREC_FP16X2 = 3,
+    ROT_PREC_BF16X2 = 4
+} rot_vote_precision;
+
+typedef enum { ROT_RANK_EXCESS = 0, ROT_RANK_RAW = 1 } rot_vote_rank_mode;
+
+/* Context configuration.  Every field has a default; 0 selects it. */
+typedef struct {
+    int grid_n;               /* coarse cells per axis over [-1,1]^3; power of two in [2, 1024]; default 32 */
+    int levels;               /* refinement levels (2x2x2 split of the kept cells); default 0 */
+    int top_k;                /* cells kept per level; default 16, at most 64 */
+    int precision;            /* rot_vote_precision; default ROT_PREC_FP32 */
+    float recheck_band;       /* requested low-precision re-check band; the band used is
+                                 max(requested, the rigorous error bound of the mode) */
+    int rank_mode;            /* rot_vote_rank_mode: EXCESS (score = count - N tau, default) or RAW */
+    int refit_iters;          /* refit iterations T; default 8; negative = no refit */
+    size_t device_mem_budget; /* bytes of device workspace the context may hold; default 16 GiB */
+    int max_inflight;         /* serving: problems in flight at once; default 256 */
+    void *cuda_stream;        /* cudaStream_t to run on (e.g. torch's current stream); NULL = own stream */
+    int use_graphs;           /* 1 = capture the solve pipeline in a CUDA graph and replay it for
+                                 repeated solves of the same shape; default 1; negative = off */
+    int keep_trace;           /* 1 = keep per-level cell counts for rot_vote_level_trace; 2 = that and
+                                 per-kernel timing for rot_vote_stage_times; default 0 */
+} rot_vote_config;
+
+/* One problem.  a, b: [n, 3] row-major float32 unit vectors (host or device).
+ * Inputs are valid iff n >= 2, every value is finite, and | |a_i|^2 - 1 |,
+ * | |b_i|^2 - 1 | <= 1e-5; otherwise the problem's status is ROT_VOTE_EINVAL. */
+typedef struct {
+    const float *a;
+    const float *b;
+    int64_t n;
+    float delta;  /* vote tolerance: an angle on S^3 in radians, 0 < delta < pi/2.
+                     The residual angle angle(R a_i, b_i) is 2x the S^3 distance. */
+    int grid_n;   /* 0 = context default */
+    int levels;   /* 0 = context default; negative = force 0 levels */
+} rot_vote_problem;
+
+typedef struct {
+    double q[4];          /* fitted rotation, unit quaternion with w > 0 (or first nonzero > 0) */
+    double R[9];          /* its rotation matrix, row-major */
+    int32_t best_count;   /* vote count of the winning cell (rank 1 at the last level) */
+    int32_t inliers;      /* pairs in the final fit */
+    int64_t best_cell;    /* linear index (iz*n + iy)*n + ix of the winner at its level */
+    int32_t best_level;   /* level of the winner */
+    int32_t refits;       /* refit iterations performed */
+    int64_t tests;        /* (cell, pair) tests over all levels */
+    int64_t rechecked;    /* tests re-evaluated by the FP32 re-check */
+    int64_t ambiguous;    /* re-checked tests within 1e-6 of the threshold */
+    int32_t status;       /* rot_vote_status of this problem */
+    float ms_gpu;         /* device time of the solve call that produced it (batched: the batch) */
+    float latency_ms;     /* serving: submit -> completion observed; else 0 */
+} rot_vote_result;
+
+/* Create a context on the current CUDA device.  cfg may be NULL (all defaults).
+ * Errors: EINVAL (bad config), ECUDA, ENOMEM. */
+int rot_vote_create(const rot_vote_config *cfg, rot_vote_ctx **out);
+
+/* Solve n_problems independent problems and block until their results are
+ * in out[0..n_problems).  n_problems > 1 runs them batched: each kernel of
+ * the path covers every problem in one launch.  A problem's result does not
+ * depend on which other problems share the call.
+ * Returns OK when the call ran (per-problem status in out[k].status), or
+ * EINVAL / ENOMEM / ECUDA when it could not run at all. */
+int rot_vote_solve(rot_vote_ctx *ctx, const rot_vote_problem *p, int n_problems, rot_vote_result *out);
+
+/* Serving: queue one problem without blocking.  The context's scheduler
+ * admits queued problems as in-flight slots and device memory free up and
+ * launches them in waves that overlap on the device (continuous batching).
+ * Returns OK and a ticket, or EAGAIN when the admission queue is full. */
+int rot_vote_submit(rot_vote_ctx *ctx, const rot_vote_problem *p, uint64_t *ticket);
+
+/* Serving: wait up to timeout_us (0 = just check) for a ticket.  Returns OK
+ * (result written, ticket released), PENDING, or ENOTFOUND. */
+int rot_vote_poll(rot_vote_ctx *ctx, uint64_t ticket, rot_vote_result *out, int timeout_us);
+
+/* Test/diagnostic: the cells of one level of one problem of the last
+ * rot_vote_solve on a context created with keep_trace = 1.  Writes up to cap
+ * (linear index, count) pairs in table order and up to top_k kept cells in
+ * rank order.  Returns OK, EINVAL (no trace / out of range) or ECUDA. */
+int rot_vote_level_trace(rot_vote_ctx *ctx, int problem, int level, int64_t *idx, int32_t *count,
+                         int64_t cap, int64_t *ncells, int64_t *kept_idx, int32_t *nkept);
+
+/* Diagnostic: device time of each kernel launch of the last rot_vote_solve on
+ * a context created with keep_trace = 2.  Such a context launches the
+ * pipeline stage by stage (no CUDA graph) with a pair of CUDA events on its
+ * stream around every kernel.  kind: 0 pair step, 1 vote, 2 top-K, 3
+ * children, 4 fit; level: the level (-1 for pair step and fit).
+ * Writes up to cap entries and their total count.  Returns OK or EINVAL. */
+typedef struct {
+    int32_t kind;
+    int32_t level;
+    float ms;
+} rot_vote_stage;
+
+int rot_vote_stage_times(rot_vote_ctx *ctx, rot_vote_stage *out, int cap, int *count);
+
+/* Destroy a context: waits for in-flight work, frees its memory. */
+void rot_vote_destroy(rot_vote_ctx *ctx);
+
+/* Text of the last error on ctx ("" if none); valid until the next call on ctx. */
+const char *rot_vote_last_error(const rot_vote_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROT_VOTE_H */

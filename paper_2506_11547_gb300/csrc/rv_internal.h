@@ -1,0 +1,124 @@
+// rv_internal.h -- data layouts and kernel launch interfaces shared by the
+// translation units of librot_vote.so (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rot_vote.h"
+
+namespace rv {
+
+constexpr int kMaxLevels = 12;      // refinement levels per problem
+constexpr int kMaxTopK = 64;
+constexpr int kPairTile = 128;      // pairs per pool tile (tensor-core B tile rows)
+constexpr int kCellTile = 128;      // cells per tensor-core A tile (TMEM lanes)
+constexpr float kAmbig = 1e-6f;     // |v - tau| below this: the decision is reported ambiguous
+constexpr float kBandFP32 = 4e-6f;  // rigorous bound on |v_fast - v_exact| of the FP32 FMA form
+constexpr int kSelChunk = 4096;     // cells per top-K phase-1 block
+
+// Per-cell record of a level table (structure of arrays).
+//   q     FP64 centre quaternion (w, x, y, z)
+//   chord FP64 covering chord (r = 2 asin(chord / 2))
+//   idx   linear cell index (iz*n + iy)*n + ix at the table's level
+//   m32   monomials [w2 x2 y2 z2 2wx 2wy 2wz 2xy 2xz 2yz] rounded to f32, + 2 pad (48 B)
+//   R32   rotation matrix of q rounded to f32, row-major, + 3 pad (48 B)
+struct CellSoA {
+    double4_32a *q;
+    double *chord;
+    int64_t *idx;
+    float4 *m32;  // 3 float4 per cell
+    float4 *R32;  // 3 float4 per cell
+};
+
+// One (problem, level) of a solve.
+struct LevelRef {
+    CellSoA cells;
+    const int32_t *ncells;  // device count of cells at this level
+    int32_t *counts;        // [cap] vote counts (zeroed before the vote)
+    int32_t cap;            // capacity of the table
+    int32_t n_side;         // grid side at this level
+};
+
+// One problem of a solve.
+struct ProbRef {
+    const float *a;      // caller / staged input, [n][3]
+    const float *b;
+    int64_t n;
+    int64_t pool_off;    // first pair in the pair pool (multiple of kPairTile)
+    double sin_d, cos_d; // of delta
+    float delta;
+    int32_t levels;      // last level index (0 = coarse only)
+    int32_t grid_n;
+};
+
+// Per-problem device outputs / statistics.
+struct ProbStats {
+    unsigned long long tests;
+    unsigned long long rechecked;
+    unsigned long long ambiguous;
+    int32_t invalid;     // input validation failed
+    int32_t pad;
+};
+
+// A vote work item: cells [cell_begin, cell_begin + cells) of (prob, level)
+// against pairs [pair_begin, pair_end) of the problem.
+struct VoteItem {
+    int32_t prob;
+    int32_t cell_begin;
+    int32_t pair_begin;
+    int32_t pair_end;
+};
+
+// Top-K candidate.
+struct Cand {
+    double score;
+    int64_t idx;
+    int32_t pos;  // position in the level table; -1 = none
+    int32_t pad;
+};
+
+// Pair pool: one record per pair, padded to kPairTile per problem.
+//   s32  [P][3] float4: S entries [S00 S11 S22 S33 S01 S02 S03 S12 S13 S23] + 2 pad
+//   pr   [P][2] float4: a0 a1 a2 b0 | b1 b2 c 0, c = (|a|^2 + |b|^2 - 2)/4
+//   tcb  tensor-core operand tiles (16-bit), layout described in k_vote_tc.cu
+struct PairPool {
+    float4 *s32;
+    float4 *pr;
+    void *tcb;
+    int tc_k;  // 16 or 32 (0 if absent)
+};
+
+// ---- launchers (each returns cudaGetLastError() of its launch) ----
+
+// Coarse table of an n^3 grid from its non-empty rows {first table position, ix_lo, ix_hi, iz*n + iy}.
+cudaError_t launch_build_level0(const int4 *rows, int nrows, int n, int64_t ncells, CellSoA out, cudaStream_t s);
+
+// Pair step over a list of {problem, pair tile}: validates inputs and fills the pair pool.
+cudaError_t launch_pair_prep(const ProbRef *probs, const int2 *tiles, int ntiles, PairPool pool, int tc_prec,
+                             ProbStats *stats, cudaStream_t s);
+
+// Vote, CUDA-core FP32 form.
+cudaError_t launch_vote_simt(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
+                             int level_stride, int level, PairPool pool, ProbStats *stats, int cells_per_thread,
+                             int grid_blocks, cudaStream_t s);
+
+// Vote, tcgen05 tensor-core form. prec: ROT_PREC_FP16 .. BF16X2.
+cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
+                           int level_stride, int level, PairPool pool, ProbStats *stats, int prec, float band_req,
+                           int grid_blocks, int *err_flag, cudaStream_t s);
+
+// Top-K phase 1 (per chunk of cells) and phase 2 (per problem merge) + children.
+cudaError_t launch_topk(const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride, int level,
+                        int top_k, int rank_mode, int max_cells, Cand *cand, int chunks_per_prob,
+                        int32_t *kept_pos, int32_t *nkept, ProbStats *stats, cudaStream_t s);
+
+cudaError_t launch_children(const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride, int level,
+                            int top_k, const int32_t *kept_pos, const int32_t *nkept, cudaStream_t s);
+
+// Fit: winner voters, FP64 sum of S_i, Jacobi, refit loop; writes results.
+cudaError_t launch_fit(const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride,
+                       const int32_t *kept_pos, int top_k, int refit_iters, PairPool pool, uint8_t *member,
+                       const ProbStats *stats, rot_vote_result *results, cudaStream_t s);
+
+}  // namespace rv

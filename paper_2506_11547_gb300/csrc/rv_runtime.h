@@ -1,0 +1,152 @@
+// rv_runtime.h -- host-side context, waves and plans (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <list>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "rot_vote.h"
+#include "rv_internal.h"
+
+namespace rv {
+
+size_t align_up(size_t x, size_t a);
+int check_problem(const rot_vote_problem &p, int grid_n, int levels, std::string *why);
+int simt_cells_per_item(int cells_per_thread);
+
+struct GridTable {
+    int n = 0;
+    int64_t ncells = 0;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    CellSoA cells{};
+    int32_t *ncells_dev = nullptr;
+};
+
+// Host description and device layout of one planned batch.
+struct Plan {
+    std::string signature;
+    int nprob = 0, prec = 0, top_k = 16, stride = 1, max_level = 0;
+    int chunks_per_prob = 1, grid_blocks = 1;
+    int64_t pool_pairs = 0, in_floats = 0;
+    bool inputs_on_device = true;
+    std::vector<ProbRef> probs_h;
+    std::vector<LevelRef> lref_h;
+    std::vector<std::vector<VoteItem>> items_h;
+    std::vector<int2> tiles_h;
+    std::vector<int64_t> in_off;
+    // device pointers (inside the wave's workspace)
+    ProbRef *d_probs = nullptr;
+    LevelRef *d_lref = nullptr;
+    std::vector<VoteItem *> d_items;
+    float *d_in = nullptr;
+    PairPool pool{};
+    uint8_t *d_member = nullptr;
+    int2 *d_tiles = nullptr;
+    size_t zero_off = 0, zero_bytes = 0;
+    int32_t *d_counts0 = nullptr, *d_countsL = nullptr, *d_nc = nullptr, *d_nkept = nullptr, *d_kept = nullptr;
+    ProbStats *d_stats = nullptr;
+    Cand *d_cand = nullptr;
+    rot_vote_result *d_res = nullptr;
+    int *d_err = nullptr;
+};
+
+class Context;
+
+// A workspace + stream + pinned staging: one batch in flight at a time.
+struct Wave {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *base = nullptr;
+    size_t cap = 0;
+    void *pinned = nullptr;
+    size_t pinned_cap = 0;
+    void *stage = nullptr;
+    size_t stage_cap = 0;
+    rot_vote_result *results_h = nullptr;
+    int results_cap = 0;
+    int *err_h = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    void *graph_base = nullptr;
+    Plan plan;
+    // serving bookkeeping
+    bool busy = false;
+    std::vector<uint64_t> tickets;
+    std::vector<double> t_submit;
+
+    int init(cudaStream_t s, bool own);
+    int ensure(size_t bytes, Context &ctx);
+    int ensure_pinned(size_t bytes);
+    int ensure_stage(size_t bytes);
+    int ensure_results(int n);
+    void release(Context &ctx);
+};
+
+struct Pending {
+    uint64_t ticket;
+    rot_vote_problem prob;
+    double t_submit;
+};
+
+class Context {
+  public:
+    rot_vote_config cfg{};
+    int device = 0, sm_count = 148;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0, bytes_held = 0;
+    int simt_cpt = 4;
+    int test_fail_alloc = 0;
+    // per-kernel profiling (keep_trace == 2)
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<rot_vote_stage> prof;
+    std::string last_error;
+    std::list<GridTable> grids;  // list: stable addresses
+    Wave main_wave;
+    bool trace_valid = false;
+    std::vector<int> trace_sel;
+
+    // serving
+    std::mutex mu;          // guards everything below and every launch
+    std::condition_variable cv;
+    std::deque<Pending> queue;
+    std::vector<Wave> waves;
+    std::unordered_map<uint64_t, rot_vote_result> done;
+    uint64_t next_ticket = 1;
+    int64_t inflight = 0;
+    bool stop = false;
+    std::thread sched;
+    bool sched_started = false;
+
+    int init(const rot_vote_config &c);
+    void shutdown();
+    int fail(int code, const std::string &msg);
+    int cuda_fail(cudaError_t e, const char *what);
+    int grid_table(int n, const GridTable **out);
+    int tc_k_of(int prec) const;
+    int plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<int> &sel);
+    int upload(Wave &w, const rot_vote_problem *p, const std::vector<int> &sel);
+    int enqueue_pipeline(Wave &w);
+    int launch_batch(Wave &w, const rot_vote_problem *p, const std::vector<int> &sel);
+    int collect(Wave &w, const std::vector<int> &sel, rot_vote_result *out);
+    int solve(const rot_vote_problem *p, int n, rot_vote_result *out);
+    int level_trace(int problem, int level, int64_t *idx, int32_t *count, int64_t cap, int64_t *ncells,
+                    int64_t *kept_idx, int32_t *nkept);
+    int stage_times(rot_vote_stage *out, int cap, int *count);
+    int submit(const rot_vote_problem &p, uint64_t *ticket);
+    int poll(uint64_t ticket, rot_vote_result *out, int timeout_us);
+    void sched_loop();
+};
+
+double now_s();
+
+}  // namespace rv

@@ -1,0 +1,240 @@
+"""ctypes binding of librot_vote.so (include/rot_vote.h): argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels. There is no CPU
+fallback: if the library is not built, `load()` raises.
+
+Inputs may be numpy float32 arrays (host memory: the library copies them to
+the device inside the call), torch CUDA float32 tensors, or any object with a
+`data_ptr()` of device memory.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librot_vote.so")
+
+OK, PENDING, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEDOUT, EDEGENERATE, ENOTFOUND = 0, 1, -1, -2, -3, -4, -5, -6, -7
+PREC = {"fp32": 0, "fp16": 1, "bf16": 2, "fp16x2": 3, "bf16x2": 4}
+RANK = {"excess": 0, "raw": 1}
+
+
+class rot_vote_config(C.Structure):
+    _fields_ = [("grid_n", C.c_int), ("levels", C.c_int), ("top_k", C.c_int), ("precision", C.c_int),
+                ("recheck_band", C.c_float), ("rank_mode", C.c_int), ("refit_iters", C.c_int),
+                ("device_mem_budget", C.c_size_t), ("max_inflight", C.c_int), ("cuda_stream", C.c_void_p),
+                ("use_graphs", C.c_int), ("keep_trace", C.c_int)]
+
+
+class rot_vote_problem(C.Structure):
+    _fields_ = [("a", C.c_void_p), ("b", C.c_void_p), ("n", C.c_int64), ("delta", C.c_float),
+                ("grid_n", C.c_int), ("levels", C.c_int)]
+
+
+class rot_vote_result(C.Structure):
+    _fields_ = [("q", C.c_double * 4), ("R", C.c_double * 9), ("best_count", C.c_int32), ("inliers", C.c_int32),
+                ("best_cell", C.c_int64), ("best_level", C.c_int32), ("refits", C.c_int32), ("tests", C.c_int64),
+                ("rechecked", C.c_int64), ("ambiguous", C.c_int64), ("status", C.c_int32), ("ms_gpu", C.c_float),
+                ("latency_ms", C.c_float)]
+
+
+class rot_vote_stage(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("level", C.c_int32), ("ms", C.c_float)]
+
+
+STAGE_KIND = {0: "pair_prep", 1: "vote", 2: "topk", 3: "children", 4: "fit"}
+
+_lib = None
+
+EXPORTS = ("rot_vote_create", "rot_vote_solve", "rot_vote_submit", "rot_vote_poll", "rot_vote_level_trace",
+           "rot_vote_stage_times", "rot_vote_destroy", "rot_vote_last_error")
+
+
+def load(path: str = LIB_PATH):
+    """Loads the library (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(path)
+    L.rot_vote_create.argtypes = [C.POINTER(rot_vote_config), C.POINTER(C.c_void_p)]
+    L.rot_vote_create.restype = C.c_int
+    L.rot_vote_solve.argtypes = [C.c_void_p, C.POINTER(rot_vote_problem), C.c_int, C.POINTER(rot_vote_result)]
+    L.rot_vote_solve.restype = C.c_int
+    L.rot_vote_submit.argtypes = [C.c_void_p, C.POINTER(rot_vote_problem), C.POINTER(C.c_uint64)]
+    L.rot_vote_submit.restype = C.c_int
+    L.rot_vote_poll.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(rot_vote_result), C.c_int]
+    L.rot_vote_poll.restype = C.c_int
+    L.rot_vote_level_trace.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int64,
+                                       C.POINTER(C.c_int64), C.c_void_p, C.POINTER(C.c_int32)]
+    L.rot_vote_level_trace.restype = C.c_int
+    L.rot_vote_stage_times.argtypes = [C.c_void_p, C.POINTER(rot_vote_stage), C.c_int, C.POINTER(C.c_int)]
+    L.rot_vote_stage_times.restype = C.c_int
+    L.rot_vote_destroy.argtypes = [C.c_void_p]
+    L.rot_vote_destroy.restype = None
+    L.rot_vote_last_error.argtypes = [C.c_void_p]
+    L.rot_vote_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+@dataclasses.dataclass
+class Result:
+    q: np.ndarray
+    R: np.ndarray
+    best_count: int
+    inliers: int
+    best_cell: int
+    best_level: int
+    refits: int
+    tests: int
+    rechecked: int
+    ambiguous: int
+    status: int
+    ms_gpu: float
+    latency_ms: float
+
+    @staticmethod
+    def of(r: rot_vote_result) -> "Result":
+        return Result(q=np.array(r.q[:]), R=np.array(r.R[:]).reshape(3, 3), best_count=r.best_count,
+                      inliers=r.inliers, best_cell=r.best_cell, best_level=r.best_level, refits=r.refits,
+                      tests=r.tests, rechecked=r.rechecked, ambiguous=r.ambiguous, status=r.status,
+                      ms_gpu=r.ms_gpu, latency_ms=r.latency_ms)
+
+
+class RotVoteError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rot_vote error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(x):
+    """(address, keepalive) of a float32 [n, 3] array or device tensor."""
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "dtype") and str(x.dtype) != "torch.float32":
+            raise TypeError("inputs must be float32")
+        if hasattr(x, "is_contiguous") and not x.is_contiguous():
+            raise TypeError("inputs must be contiguous")
+        return x.data_ptr(), x
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    return a.ctypes.data, a
+
+
+def _nrows(x) -> int:
+    return int(x.shape[0])
+
+
+def problem(a, b, delta: float, grid_n: int = 0, levels: int = 0):
+    """A rot_vote_problem and the objects that keep its buffers alive."""
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    n = _nrows(a)
+    if _nrows(b) != n:
+        raise ValueError("a and b differ in length")
+    return rot_vote_problem(pa, pb, n, float(delta), int(grid_n), int(levels)), (ka, kb)
+
+
+class Context:
+    """A rot_vote context (rot_vote_create ... rot_vote_destroy)."""
+
+    def __init__(self, grid_n=0, levels=0, top_k=0, precision="fp32", recheck_band=0.0, rank_mode="excess",
+                 refit_iters=0, device_mem_budget=0, max_inflight=0, cuda_stream=None, use_graphs=0,
+                 keep_trace=0):
+        L = load()
+        self._L = L
+        cfg = rot_vote_config(int(grid_n), int(levels), int(top_k),
+                              PREC[precision] if isinstance(precision, str) else int(precision),
+                              float(recheck_band), RANK[rank_mode] if isinstance(rank_mode, str) else int(rank_mode),
+                              int(refit_iters), int(device_mem_budget), int(max_inflight),
+                              C.c_void_p(cuda_stream) if cuda_stream else None, int(use_graphs), int(keep_trace))
+        h = C.c_void_p()
+        rc = L.rot_vote_create(C.byref(cfg), C.byref(h))
+        if rc != OK:
+            raise RotVoteError(rc, "rot_vote_create failed")
+        self._h = h
+        self._keep = {}
+
+    def last_error(self) -> str:
+        return self._L.rot_vote_last_error(self._h).decode()
+
+    def _check(self, rc: int):
+        if rc not in (OK, PENDING):
+            raise RotVoteError(rc, self.last_error())
+        return rc
+
+    def solve(self, problems):
+        """problems: list of (a, b, delta[, grid_n[, levels]]). Returns list of Result."""
+        n = len(problems)
+        arr = (rot_vote_problem * n)()
+        keep = []
+        for k, pr in enumerate(problems):
+            arr[k], kk = problem(*pr)
+            keep.append(kk)
+        out = (rot_vote_result * n)()
+        self._check(self._L.rot_vote_solve(self._h, arr, n, out))
+        return [Result.of(out[k]) for k in range(n)]
+
+    def solve_raw(self, arr, n, out):
+        """Calls rot_vote_solve on prepared ctypes arrays (for timing loops)."""
+        return self._check(self._L.rot_vote_solve(self._h, arr, n, out))
+
+    def submit(self, a, b, delta, grid_n=0, levels=0) -> int:
+        pr, kk = problem(a, b, delta, grid_n, levels)
+        t = C.c_uint64()
+        rc = self._L.rot_vote_submit(self._h, C.byref(pr), C.byref(t))
+        if rc == EAGAIN:
+            return -1
+        self._check(rc)
+        self._keep[t.value] = kk
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """Result, or None while pending."""
+        out = rot_vote_result()
+        rc = self._L.rot_vote_poll(self._h, int(ticket), C.byref(out), int(timeout_us))
+        if rc == PENDING:
+            return None
+        self._check(rc)
+        self._keep.pop(ticket, None)
+        return Result.of(out)
+
+    def level_trace(self, problem: int, level: int, cap: int = 1 << 22):
+        """(idx[n], count[n], kept_idx[k]) of one level of the last solve (keep_trace=1)."""
+        idx = np.zeros(cap, np.int64)
+        cnt = np.zeros(cap, np.int32)
+        kept = np.zeros(64, np.int64)
+        nc = C.c_int64()
+        nk = C.c_int32()
+        self._check(self._L.rot_vote_level_trace(self._h, int(problem), int(level), idx.ctypes.data,
+                                                 cnt.ctypes.data, cap, C.byref(nc), kept.ctypes.data, C.byref(nk)))
+        m = min(nc.value, cap)
+        return idx[:m], cnt[:m], kept[:nk.value]
+
+    def stage_times(self):
+        """[(kind, level, ms)] of the last solve (context created with keep_trace=2)."""
+        buf = (rot_vote_stage * 256)()
+        n = C.c_int()
+        self._check(self._L.rot_vote_stage_times(self._h, buf, 256, C.byref(n)))
+        return [(STAGE_KIND[buf[k].kind], buf[k].level, buf[k].ms) for k in range(min(n.value, 256))]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.rot_vote_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

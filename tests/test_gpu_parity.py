@@ -1,0 +1,176 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Counts: every cell's count equals the oracle's except by at most the number
+of that cell's tests within 1e-6 of the threshold (the oracle reports them).
+Ranking: kept cells equal the oracle's (near-ties within 1e-9 may swap).
+Rotation: within 1e-4 rad of the oracle's.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2506_11547_gb300 import synth
+from tests._util import f32, quat_angle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+from paper_2506_11547_gb300 import rot_vote as rv  # noqa: E402
+
+ROT_TOL = 1e-4
+NTHREADS = max(1, os.cpu_count() or 1)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def check_counts(gpu_idx, gpu_cnt, lev):
+    assert np.array_equal(gpu_idx, lev["idx"]), "level tables differ"
+    d = np.abs(gpu_cnt.astype(np.int64) - lev["count"].astype(np.int64))
+    bad = np.nonzero(d > lev["amb"])[0]
+    assert len(bad) == 0, f"{len(bad)} cells differ beyond ambiguity, e.g. pos {bad[:5]}"
+
+
+def check_kept(gpu_kept, lev, n_pairs):
+    want = lev["topk_idx"]
+    if np.array_equal(gpu_kept, want):
+        return
+    # allow swaps only among near-ties of the oracle's scores
+    assert len(gpu_kept) == len(want)
+    sc = dict(zip(lev["idx"].tolist(), (lev["count"] - n_pairs * lev["tau"]).tolist()))
+    ws = np.array([sc[i] for i in want])
+    gs = np.array([sc[i] for i in gpu_kept])
+    assert np.allclose(np.sort(ws), np.sort(gs), atol=1e-9) and np.max(np.abs(ws - gs)) < 1e-9 + 2 * lev["amb"].max()
+
+
+def run_both(p, grid_n, levels, precision="fp32", top_k=16, rank_mode="excess", refit=8, device=True):
+    import oracle
+    a, b = (dev(p.a), dev(p.b)) if device else (p.a, p.b)
+    with rv.Context(grid_n=grid_n, levels=levels, top_k=top_k, precision=precision, rank_mode=rank_mode,
+                    refit_iters=refit if refit else -1, keep_trace=1) as ctx:
+        r = ctx.solve([(a, b, p.delta)])[0]
+        tr = [ctx.level_trace(0, lev) for lev in range(levels + 1)]
+    o = oracle.solve(p.a, p.b, f32(p.delta), grid_n=grid_n, levels=levels, top_k=top_k,
+                     rank_mode=rv.RANK[rank_mode], refit_iters=refit, nthreads=NTHREADS)
+    return r, tr, o
+
+
+def assert_parity(p, r, tr, o, levels):
+    for lev in range(levels + 1):
+        idx, cnt, kept = tr[lev]
+        check_counts(idx, cnt, o.levels[lev])
+        check_kept(kept, o.levels[lev], p.n)
+    assert r.status == o.status
+    assert r.best_cell == o.best_cell
+    assert abs(r.best_count - o.best_count) <= o.levels[-1]["amb"].max()
+    assert quat_angle(r.q, o.q) < ROT_TOL
+    assert r.tests == o.tests
+    assert r.q[0] >= 0
+
+
+def test_small_workload_every_cell():
+    p, g, L = synth.config_problem("small_n1e3_32")
+    r, tr, o = run_both(p, g, L)
+    assert_parity(p, r, tr, o, L)
+    assert abs(r.inliers - o.inliers) <= 2
+
+
+def test_multilevel_every_level():
+    p = synth.make_problem(3000, rho=0.9, sigma=0.01, delta=0.03, seed=77)
+    r, tr, o = run_both(p, 16, 3)
+    assert_parity(p, r, tr, o, 3)
+
+
+@pytest.mark.parametrize("n", [2, 3, 127, 128, 129, 257, 1000])
+def test_ragged_sizes(n):
+    p = synth.make_problem(n, rho=0.5, sigma=0.01, delta=0.05, seed=100 + n)
+    r, tr, o = run_both(p, 8, 2)
+    assert_parity(p, r, tr, o, 2)
+
+
+@pytest.mark.parametrize("grid_n,levels,top_k,rank", [(2, 0, 1, "excess"), (4, 3, 1, "raw"), (8, 1, 64, "excess"),
+                                                      (32, 2, 5, "raw")])
+def test_grid_and_rank_options(grid_n, levels, top_k, rank):
+    p = synth.make_problem(700, rho=0.8, sigma=0.02, delta=0.06, seed=grid_n * 10 + levels)
+    r, tr, o = run_both(p, grid_n, levels, top_k=top_k, rank_mode=rank)
+    assert_parity(p, r, tr, o, levels)
+
+
+def test_no_refit_and_degenerate():
+    p = synth.make_problem(500, rho=0.9, sigma=0.01, delta=0.03, seed=5)
+    r, tr, o = run_both(p, 16, 1, refit=0)
+    assert_parity(p, r, tr, o, 1)
+    assert r.refits == 0
+    # pure outliers and a tiny tolerance: the winner has < 2 voters -> degenerate
+    q = synth.make_problem(50, rho=1.0, sigma=0.0, delta=1e-4, seed=6)
+    r2, tr2, o2 = run_both(q, 4, 0)
+    assert r2.status == o2.status
+    if o2.status == rv.EDEGENERATE:
+        assert quat_angle(r2.q, o2.q) < 1e-12
+
+
+def test_host_inputs_equal_device_inputs():
+    p = synth.make_problem(5000, rho=0.9, sigma=0.01, delta=0.03, seed=9)
+    with rv.Context(grid_n=32, levels=2) as ctx:
+        rh = ctx.solve([(p.a, p.b, p.delta)])[0]
+        rd = ctx.solve([(dev(p.a), dev(p.b), p.delta)])[0]
+    assert np.array_equal(rh.q, rd.q) and rh.best_count == rd.best_count and rh.inliers == rd.inliers
+
+
+def test_batched_equals_alone_and_deterministic():
+    probs = [synth.make_problem(n, rho=0.8, sigma=0.01, delta=d, seed=s)
+             for n, d, s in ((50, 0.03, 1), (700, 0.02, 2), (4096, 0.05, 3), (129, 0.04, 4), (20000, 0.03, 5))]
+    args = [(dev(p.a), dev(p.b), p.delta) for p in probs]
+    with rv.Context(grid_n=32, levels=2) as ctx:
+        batch = ctx.solve(args)
+        batch2 = ctx.solve(args)
+        alone = [ctx.solve([x])[0] for x in args]
+    for rb, rb2, ra in zip(batch, batch2, alone):
+        for x in (rb2, ra):
+            assert np.array_equal(rb.q, x.q)
+            assert (rb.best_count, rb.inliers, rb.best_cell, rb.tests, rb.rechecked) == \
+                   (x.best_count, x.inliers, x.best_cell, x.tests, x.rechecked)
+
+
+def test_graph_replay_with_new_inputs():
+    """The captured pipeline is replayed for a second solve of the same shape
+    with different data; results must be those of the new data."""
+    import oracle
+    p1 = synth.make_problem(3000, rho=0.9, sigma=0.01, delta=0.03, seed=11)
+    p2 = synth.make_problem(3000, rho=0.9, sigma=0.01, delta=0.04, seed=12)
+    with rv.Context(grid_n=16, levels=2, use_graphs=1) as cg, rv.Context(grid_n=16, levels=2, use_graphs=-1) as cn:
+        g1 = cg.solve([(dev(p1.a), dev(p1.b), p1.delta)])[0]
+        g2 = cg.solve([(dev(p2.a), dev(p2.b), p2.delta)])[0]
+        n2 = cn.solve([(dev(p2.a), dev(p2.b), p2.delta)])[0]
+    o2 = oracle.solve(p2.a, p2.b, f32(p2.delta), grid_n=16, levels=2)
+    assert np.array_equal(g2.q, n2.q) and g2.best_cell == n2.best_cell
+    assert quat_angle(g2.q, o2.q) < ROT_TOL
+    assert g1.best_cell != g2.best_cell or not np.array_equal(g1.q, g2.q)
+
+
+def test_invalid_inputs_are_rejected():
+    p = synth.make_problem(300, rho=0.5, sigma=0.01, delta=0.03, seed=13)
+    bad_nan = p.a.copy()
+    bad_nan[7, 1] = np.nan
+    bad_norm = p.a.copy()
+    bad_norm[3] *= 1.001
+    with rv.Context(grid_n=8) as ctx:
+        res = ctx.solve([(p.a[:1], p.b[:1], 0.03), (bad_nan, p.b, 0.03), (bad_norm, p.b, 0.03),
+                         (p.a, p.b, 0.0), (p.a, p.b, 2.0), (p.a, p.b, 0.03)])
+    assert [r.status for r in res[:5]] == [rv.EINVAL] * 5
+    assert res[5].status == 0
+
+
+def test_full_size_fp32_workload():
+    """The 1e5-pair, 64^3 + 3-level workload at full size, in the launch
+    configuration the benchmark times: the oracle's complete solve (threads
+    over cells) against the GPU's every level."""
+    p, g, L = synth.config_problem("fp32_n1e5_64L3")
+    r, tr, o = run_both(p, g, L)
+    assert_parity(p, r, tr, o, L)
+    assert quat_angle(r.q, p.q_true) < 0.01

@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = [
     "lib", "pair_M", "pair_S", "quad", "quat_to_R", "cell_exists", "cell_geom", "tau",
     "level_cells", "vote_cells", "rank", "jacobi4", "canonical", "solve", "OracleResult",
-    "AMBIG", "cell_of_point",
+    "AMBIG", "cell_of_point", "fit_cell",
 ]
 
 AMBIG = 1e-6
@@ -70,6 +70,9 @@ def lib():
         L.rvo_solve.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
                                 C.c_int, C.c_int, C.POINTER(_Result), C.POINTER(_Trace)]
         L.rvo_solve.restype = C.c_int
+        L.rvo_fit_cell.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int64, C.c_int,
+                                   C.POINTER(_Result)]
+        L.rvo_fit_cell.restype = C.c_int
         _lib = L
     return _lib
 
@@ -230,6 +233,17 @@ def solve(a, b, delta: float, grid_n: int, levels: int = 0, top_k: int = 16, ran
     return OracleResult(q=np.array(res.q[:]), R=np.array(res.R[:]).reshape(3, 3), best_count=res.best_count,
                         inliers=res.inliers, best_cell=res.best_cell, tests=res.tests,
                         ambiguous=res.ambiguous, status=res.status, refits=res.refits, levels=per_level)
+
+
+def fit_cell(a, b, delta: float, n_side: int, idx: int, refit_iters: int = 8) -> OracleResult:
+    """The fit alone (step 8), from winning cell `idx` of the n_side grid."""
+    a, b = _f32_pairs(a, b)
+    res = _Result()
+    lib().rvo_fit_cell(a.reshape(-1), b.reshape(-1), a.shape[0], float(delta), int(n_side), int(idx),
+                       int(refit_iters), C.byref(res))
+    return OracleResult(q=np.array(res.q[:]), R=np.array(res.R[:]).reshape(3, 3), best_count=res.best_count,
+                        inliers=res.inliers, best_cell=res.best_cell, tests=res.tests, ambiguous=res.ambiguous,
+                        status=res.status, refits=res.refits, levels=[])
 
 
 def default_threads() -> int:

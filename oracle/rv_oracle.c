@@ -449,6 +449,9 @@ typedef struct {
     int64_t *nkept;    /* [levels+1] */
 } rvo_trace;
 
+static int fit_from_cell(const double *S, int64_t n, double sd, double cd, int n_side, int64_t idx,
+                         int refit_iters, rvo_result *res);
+
 int rvo_solve(const float *a, const float *b, int64_t n, double delta, int grid_n, int levels, int top_k,
               int rank_mode, int refit_iters, int nthreads, rvo_result *res, rvo_trace *tr) {
     memset(res, 0, sizeof *res);
@@ -525,14 +528,25 @@ int rvo_solve(const float *a, const float *b, int64_t n, double delta, int grid_
         free(score);
     }
     free(cells);
-
-    /* 8. fit */
-    int64_t ix, iy, iz;
-    unpack_idx((int)win_n, win_idx, &ix, &iy, &iz);
-    double qc[4], chord;
-    rvo_cell_geom((int)win_n, ix, iy, iz, qc, &chord);
+    (void)win_tau;
     res->best_cell = win_idx;
     res->best_count = win_count;
+    const int status = fit_from_cell(S, n, sd, cd, (int)win_n, win_idx, refit_iters, res);
+    free(S);
+    return status;
+}
+
+/* 8. fit, from the winning cell (index idx of the n_side grid):
+ * I_0 = voters of the cell, q_0 = smallest eigenvector of sum_{I_0} S_i; then
+ * I_t = {i : q_{t-1}^T S_i q_{t-1} <= sin^2(delta)}, stopping when |I_t| < 2 or
+ * I_t = I_{t-1}; the cell centre is returned if the first fit is degenerate. */
+static int fit_from_cell(const double *S, int64_t n, double sd, double cd, int n_side, int64_t idx,
+                         int refit_iters, rvo_result *res) {
+    int64_t ix, iy, iz;
+    unpack_idx(n_side, idx, &ix, &iy, &iz);
+    double qc[4], chord;
+    rvo_cell_geom(n_side, ix, iy, iz, qc, &chord);
+    const double win_tau = rvo_tau(sd, cd, chord);
 
     unsigned char *in0 = (unsigned char *)calloc((size_t)n, 1);
     unsigned char *in1 = (unsigned char *)calloc((size_t)n, 1);
@@ -574,6 +588,17 @@ int rvo_solve(const float *a, const float *b, int64_t n, double delta, int grid_
     res->status = status;
     free(in0);
     free(in1);
+    return status;
+}
+
+/* The fit alone, from a given winning cell. */
+int rvo_fit_cell(const float *a, const float *b, int64_t n, double delta, int n_side, int64_t idx, int refit_iters,
+                 rvo_result *res) {
+    memset(res, 0, sizeof *res);
+    double *S = all_pair_S(a, b, n);
+    if (!S) return RVO_EINVAL;
+    res->best_cell = idx;
+    const int status = fit_from_cell(S, n, sin(delta), cos(delta), n_side, idx, refit_iters, res);
     free(S);
     return status;
 }

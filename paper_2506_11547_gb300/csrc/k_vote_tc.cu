@@ -1,11 +1,548 @@
-// k_vote_tc.cu -- tensor-core (tcgen05) vote.  Not built yet in this revision.
+// k_vote_tc.cu -- the vote on the tcgen05 tensor cores (sm_103a).
+//
+// D[c][i] = sum_k A[c][k] B[i][k] with
+//   A row (cell c):  K = 16: [m(q_c) (10), -tau_hi, -tau_lo, 0 x4]
+//                    K = 32: [m_hi (10), m_hi (10), m_lo (10), -tau_hi, -tau_lo]
+//   B row (pair i):  K = 16: [s_i (10), 1, 1, 0 x4]
+//                    K = 32: [s_hi (10), s_lo (10), s_hi (10), 1, 1]
+// so D = m.s - tau ~ q_c^T S_i q_c - tau_c, in FP32 in tensor memory.  The
+// cell votes for the pair iff D <= 0; the epilogue counts sign bits and flags
+// |D| <= band_c, a rigorous per-cell bound on |D - (v - tau)_exact| (operand
+// rounding to 16 bits, the FP32 pair step, FP32 accumulation).  Flagged tests
+// are re-evaluated with the FP32 re-check |b - R_c a|^2/4 - c_i, whose error
+// is below 7e-7, so every decision with |v - tau| > 1e-6 is the FP64 one.
+//
+// One persistent CTA per SM:
+//   warp 0      lane 0 streams 128-pair B tiles global -> shared with the bulk
+//               copy engine (cp.async.bulk + mbarrier complete_tx), kNB stages
+//   warp 1      allocates 512 TMEM columns; lane 0 issues tcgen05.mma
+//               (M = 128 cells, N = 128 pairs, K = 16 per instruction) into
+//               one of kNAcc accumulator stages and commits to mbarriers
+//   warps 2-3   build the 128-row A tile of each work item in shared memory
+//               (double buffered)
+//   warps 4..   G epilogue warpgroups; tile j belongs to warpgroup j % G and
+//               accumulator stage j % kNAcc; each thread owns one TMEM lane =
+//               one cell, reads 32 columns per tcgen05.ld
+// Every mbarrier wait is bounded (2 s or 2^24 polls): on expiry the CTA sets
+// *err_flag, stops all roles, waits (bounded) for its own copies and MMAs,
+// frees its TMEM and returns.
+//
+// Operand tiles use the canonical no-swizzle K-major layout: 8 rows x 16 B
+// core matrices stored contiguously (128 B); SBO = 128 B between 8-row
+// groups, LBO = 2048 B between the 8-column halves of a K = 16 slice.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "rv_geom.cuh"
 #include "rv_internal.h"
 
 namespace rv {
 
-cudaError_t launch_vote_tc(const VoteItem *, int, const ProbRef *, const LevelRef *, int, int, PairPool, ProbStats *,
-                           int, float, int, int *, cudaStream_t) {
-    return cudaErrorNotSupported;
+namespace {
+
+constexpr int kNB = 6;           // B stages
+constexpr int kNAcc = 4;         // accumulator stages x 128 TMEM columns = 512
+constexpr int kTileBytesMax = 8192;
+constexpr int kGuard = 64 * 1024;  // slack after the operand tiles; also keeps one CTA per SM (> 116 KB)
+constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr uint32_t kWaitPolls = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase of parity `parity` to complete.  Returns false
+// when the CTA was aborted or the wait expired.
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t it = 1; it < kWaitPolls; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31) == 0) {
+            if (*abort_flag) return false;
+            if (gtimer() - t0 > kWaitNs) return false;
+        }
+    }
+    return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc512(uint32_t *slot) {  // whole warp
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(smem_u32(slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc512(uint32_t taddr) {  // whole warp
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(taddr) : "memory");
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+// 32 consecutive 32-bit TMEM columns of this thread's lane; the wait binds the
+// registers so no use is scheduled before the data has arrived.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor, canonical K-major layout without swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(2048u >> 4) << 16) | ((uint64_t)(128u >> 4) << 32) |
+           (1ull << 46);
+}
+// Instruction descriptor of kind::f16: D = F32, A = B = F16 (0) or BF16 (1),
+// both K-major, N = 128 (>> 3 at bit 17), M = 128 (>> 4 at bit 24).
+template <bool BF16>
+__host__ __device__ constexpr uint32_t idesc_f16() {
+    return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ int tc_off(int r, int k) { return (k >> 3) * 2048 + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+template <bool BF16>
+__device__ __forceinline__ uint16_t h16(float x) {
+    if (BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    return __half_as_ushort(__float2half_rn(x));
+}
+template <bool BF16>
+__device__ __forceinline__ float f16(uint16_t x) {
+    if (BF16) return __bfloat162float(__ushort_as_bfloat16(x));
+    return __half2float(__ushort_as_half(x));
+}
+
+// Rigorous per-cell bound on |D - (v - tau)| (see the file comment).
+template <int KSTEPS, bool BF16>
+__device__ __forceinline__ float cell_band(const float m[10]) {
+    const float u32 = 5.9604645e-8f;
+    const float u16 = BF16 ? 3.90625e-3f : 4.8828125e-4f;
+    const float sub = BF16 ? 0.f : 2.9802322e-8f;  // half the FP16 subnormal spacing
+    const float smax[10] = {1.f, 1.f, 1.f, 1.f, 0.5f, 0.5f, 0.5f, 1.f, 1.f, 1.f};
+    float msum = 0.f, mabs = 0.f;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        msum = fmaf(fabsf(m[k]), smax[k], msum);
+        mabs += fabsf(m[k]);
+    }
+    const int K = 16 * KSTEPS;
+    const float accum = (14.f + 12.f * K) * u32 + 1e-6f;
+    float b;
+    if (KSTEPS == 1)
+        b = (2.f * u16 + u16 * u16 + 2.f * u32) * msum + sub * (mabs + 8.5f) + accum;
+    else
+        b = (3.f * u16 * u16 + u16 * u16 * u16 + 2.f * u32) * msum + 2.f * sub * (mabs + 8.5f) + accum;
+    return b * 1.25f;
+}
+
+struct ItemView {
+    VoteItem W;
+    ProbRef P;
+    LevelRef L;
+    int ncell;
+    int ntiles;
+};
+
+__device__ __forceinline__ bool load_item(const VoteItem *items, int it, const ProbRef *probs, const LevelRef *lref,
+                                          int level_stride, int level, ItemView &v) {
+    v.W = items[it];
+    v.P = probs[v.W.prob];
+    if (level > v.P.levels) return false;
+    v.L = lref[v.W.prob * level_stride + level];
+    v.ncell = *v.L.ncells;
+    if (v.W.cell_begin >= v.ncell) return false;
+    v.ntiles = (v.W.pair_end - v.W.pair_begin) / kPairTile;
+    return v.ntiles > 0;
+}
+
+template <int G, int KSTEPS, bool BF16>
+__global__ void __launch_bounds__(128 + 128 * G, 1)
+    vote_tc_kernel(const VoteItem *__restrict__ items, int n_items, const ProbRef *__restrict__ probs,
+                   const LevelRef *__restrict__ lref, int level_stride, int level, PairPool pool, ProbStats *stats,
+                   float band_req, int *err_flag) {
+    constexpr int kTileBytes = kPairTile * 16 * KSTEPS * 2;  // 128 rows x K x 2 B
+    constexpr int K = 16 * KSTEPS;
+    constexpr uint32_t IDESC = idesc_f16<BF16>();
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;                                   // 2 x kTileBytesMax
+    uint8_t *sB = smem + 2 * kTileBytesMax;               // kNB x kTileBytesMax
+    uint64_t *bars = (uint64_t *)(sB + kNB * kTileBytesMax + kGuard);
+    uint64_t *b_full = bars, *b_empty = bars + kNB, *acc_full = bars + 2 * kNB, *acc_empty = acc_full + kNAcc;
+    uint64_t *a_full = acc_empty + kNAcc, *a_empty = a_full + 2, *mma_done = a_empty + 2;
+    uint32_t *tmem_slot = (uint32_t *)(mma_done + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kNB; ++s) {
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_empty[s], 1);
+        }
+        for (int s = 0; s < kNAcc; ++s) {
+            mbar_init(&acc_full[s], 1);
+            mbar_init(&acc_empty[s], 4);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&a_full[s], 2);
+            mbar_init(&a_empty[s], 1);
+        }
+        mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc512(tmem_slot);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicExch(err_flag, 1);
+    };
+
+    if (warp == 0) {
+        // ------------------------------ producer ------------------------------
+        if (lane == 0) {
+            int64_t j = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+                ItemView v;
+                if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
+                const uint8_t *src = (const uint8_t *)pool.tcb +
+                                     ((v.P.pool_off + v.W.pair_begin) / kPairTile) * (int64_t)kTileBytes;
+                for (int t = 0; t < v.ntiles; ++t, ++j) {
+                    const int bs = (int)(j % kNB);
+                    const uint32_t u = (uint32_t)(j / kNB);
+                    if (!mbar_wait(&b_empty[bs], (u & 1u) ^ 1u, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&b_full[bs], kTileBytes);
+                    bulk_g2s(sB + bs * kTileBytesMax, src + (int64_t)t * kTileBytes, kTileBytes, &b_full[bs]);
+                }
+            }
+            // drain: the last issued copy of each stage has completed before exit
+            for (int64_t jj = j - 1; jj >= 0 && jj >= j - kNB; --jj) {
+                const int bs = (int)(jj % kNB);
+                const uint32_t u = (uint32_t)(jj / kNB);
+                volatile int never = 0;
+                if (!mbar_wait(&b_full[bs], u & 1u, &never)) atomicExch(err_flag, 1);
+            }
+        }
+    } else if (warp == 1) {
+        // --------------------------------- MMA --------------------------------
+        if (lane == 0) {
+            int64_t j = 0;
+            int i = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+                ItemView v;
+                if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
+                const int ab = i & 1;
+                const uint32_t ua = (uint32_t)(i >> 1);
+                if (!mbar_wait(&a_full[ab], ua & 1u, abort_flag)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a_addr = smem_u32(sA + ab * kTileBytesMax);
+                for (int t = 0; t < v.ntiles; ++t, ++j) {
+                    const int bs = (int)(j % kNB), as = (int)(j % kNAcc);
+                    const uint32_t ub = (uint32_t)(j / kNB), uc = (uint32_t)(j / kNAcc);
+                    if (!mbar_wait(&b_full[bs], ub & 1u, abort_flag) ||
+                        !mbar_wait(&acc_empty[as], (uc & 1u) ^ 1u, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t b_addr = smem_u32(sB + bs * kTileBytesMax);
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(as * 128);
+#pragma unroll
+                    for (int k = 0; k < KSTEPS; ++k)
+                        mma_f16(d_tmem, sdesc(a_addr + k * 4096), sdesc(b_addr + k * 4096), IDESC, k > 0 ? 1u : 0u);
+                    mma_commit(&b_empty[bs]);
+                    mma_commit(&acc_full[as]);
+                }
+                if (!ok) break;
+                mma_commit(&a_empty[ab]);
+                ++i;
+            }
+            mma_commit(mma_done);  // arrives once every MMA issued above has completed
+        }
+    } else if (warp < 4) {
+        // ---------------------------- A-tile builder ---------------------------
+        const int r0 = (warp - 2) * 64 + lane;
+        int i = 0;
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+            ItemView v;
+            if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
+            const int ab = i & 1;
+            const uint32_t ua = (uint32_t)(i >> 1);
+            // warp-uniform outcome of the bounded wait
+            if (!__all_sync(0xffffffffu, mbar_wait(&a_empty[ab], (ua & 1u) ^ 1u, abort_flag))) {
+                fail();
+                break;
+            }
+            uint8_t *tile = sA + ab * kTileBytesMax;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + 32 * h;
+                const int pos = v.W.cell_begin + r;
+                uint16_t row[32];
+#pragma unroll
+                for (int k = 0; k < 32; ++k) row[k] = 0;
+                if (pos < v.ncell) {
+                    const float4 m0 = v.L.cells.m32[3 * pos], m1 = v.L.cells.m32[3 * pos + 1],
+                                 m2 = v.L.cells.m32[3 * pos + 2];
+                    const float m[10] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y};
+                    const float tau = (float)tau_of(v.P.sin_d, v.P.cos_d, v.L.cells.chord[pos]);
+                    const uint16_t th = h16<BF16>(tau);
+                    const uint16_t tl = h16<BF16>(tau - f16<BF16>(th));
+                    if (KSTEPS == 1) {
+#pragma unroll
+                        for (int k = 0; k < 10; ++k) row[k] = h16<BF16>(m[k]);
+                        row[10] = th ^ 0x8000u;  // -tau_hi
+                        row[11] = tl ^ 0x8000u;  // -tau_lo
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 10; ++k) {
+                            const uint16_t hi = h16<BF16>(m[k]);
+                            const uint16_t lo = h16<BF16>(m[k] - f16<BF16>(hi));
+                            row[k] = hi;
+                            row[10 + k] = hi;
+                            row[20 + k] = lo;
+                        }
+                        row[30] = th ^ 0x8000u;
+                        row[31] = tl ^ 0x8000u;
+                    }
+                } else {  // absent cell: D = 1 for every pair
+                    row[KSTEPS == 1 ? 10 : 30] = h16<BF16>(1.f);
+                }
+#pragma unroll
+                for (int c = 0; c < K / 8; ++c) {
+                    uint4 w;
+                    w.x = (uint32_t)row[8 * c + 0] | ((uint32_t)row[8 * c + 1] << 16);
+                    w.y = (uint32_t)row[8 * c + 2] | ((uint32_t)row[8 * c + 3] << 16);
+                    w.z = (uint32_t)row[8 * c + 4] | ((uint32_t)row[8 * c + 5] << 16);
+                    w.w = (uint32_t)row[8 * c + 6] | ((uint32_t)row[8 * c + 7] << 16);
+                    *reinterpret_cast<uint4 *>(tile + tc_off(r, 8 * c)) = w;
+                }
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_full[ab]);
+            ++i;
+        }
+    } else {
+        // ------------------------------- epilogue ------------------------------
+        const int g = (warp - 4) >> 2;      // warpgroup
+        const int q = warp & 3;             // TMEM lane quarter this warp may access
+        const int row = 32 * q + lane;      // cell row of this thread
+        int64_t j = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+            ItemView v;
+            if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
+            const int64_t j0 = j;
+            j += v.ntiles;
+            // my tiles of this item: j0 + t with (j0 + t) % G == g
+            int t = (int)((g - (int)(j0 % G) + G) % G);
+            if (t >= v.ntiles) continue;
+            const int pos = v.W.cell_begin + row;
+            const bool valid = pos < v.ncell;
+            float tau = 0.f, band = -1.f;
+            if (valid) {
+                const float4 m0 = v.L.cells.m32[3 * pos], m1 = v.L.cells.m32[3 * pos + 1],
+                             m2 = v.L.cells.m32[3 * pos + 2];
+                const float m[10] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y};
+                tau = (float)tau_of(v.P.sin_d, v.P.cos_d, v.L.cells.chord[pos]);
+                band = fmaxf(cell_band<KSTEPS, BF16>(m), band_req);
+            }
+            int cnt = 0;
+            unsigned rechecked = 0, ambiguous = 0;
+            bool haveR = false;
+            float4 R0 = make_float4(0, 0, 0, 0), R1 = R0, R2 = R0;
+            const int64_t gbase = v.P.pool_off + v.W.pair_begin;
+            for (; t < v.ntiles; t += G) {
+                const int64_t jj = j0 + t;
+                const int as = (int)(jj % kNAcc);
+                const uint32_t uc = (uint32_t)(jj / kNAcc);
+                // warp-uniform outcome: every lane must reach the .sync.aligned tcgen05.ld below
+                if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[as], uc & 1u, abort_flag))) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(as * 128);
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + 32 * c, r);
+                    tmem_ld_wait(r);
+                    bool flag = false;
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        cnt += (int)(r[e] >> 31);
+                        flag |= fabsf(__uint_as_float(r[e])) <= band;
+                    }
+                    if (flag) {  // rare: re-check the flagged tests of this chunk
+                        if (!haveR) {
+                            R0 = v.L.cells.R32[3 * pos];
+                            R1 = v.L.cells.R32[3 * pos + 1];
+                            R2 = v.L.cells.R32[3 * pos + 2];
+                            haveR = true;
+                        }
+#pragma unroll 1
+                        for (int e = 0; e < 32; ++e) {
+                            const float d = __uint_as_float(r[e]);
+                            if (fabsf(d) <= band) {
+                                const int64_t gp = gbase + (int64_t)t * kPairTile + 32 * c + e;
+                                const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
+                                const float vv = recheck_v(R0, R1, R2, p0, p1);
+                                cnt += (int)(vv <= tau) - (int)(r[e] >> 31);
+                                ++rechecked;
+                                ambiguous += fabsf(vv - tau) <= kAmbig;
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[as]);
+            }
+            if (valid && cnt != 0) atomicAdd(&v.L.counts[pos], cnt);
+            const unsigned rc = __reduce_add_sync(0xffffffffu, rechecked);
+            const unsigned am = __reduce_add_sync(0xffffffffu, ambiguous);
+            if (lane == 0) {
+                if (rc) atomicAdd(&stats[v.W.prob].rechecked, (unsigned long long)rc);
+                if (am) atomicAdd(&stats[v.W.prob].ambiguous, (unsigned long long)am);
+            }
+        }
+    }
+
+    // ------------------------------- teardown -------------------------------
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        if (lane == 0) {
+            volatile int never = 0;
+            if (!mbar_wait(mma_done, 0, &never)) atomicExch(err_flag, 1);
+        }
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc512(tmem_base);
+    }
+}
+
+constexpr size_t kSmemBytes = 1024 + 2 * kTileBytesMax + kNB * kTileBytesMax + kGuard + 256;
+
+template <int G, int KSTEPS, bool BF16>
+cudaError_t prepare_t() {
+    return cudaFuncSetAttribute(vote_tc_kernel<G, KSTEPS, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmemBytes);
+}
+
+template <int G, int KSTEPS, bool BF16>
+cudaError_t launch_t(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
+                     int level_stride, int level, PairPool pool, ProbStats *stats, float band_req, int grid,
+                     int *err_flag, cudaStream_t s) {
+    vote_tc_kernel<G, KSTEPS, BF16><<<grid, 128 + 128 * G, kSmemBytes, s>>>(items, n_items, probs, lref, level_stride,
+                                                                           level, pool, stats, band_req, err_flag);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Sets the dynamic shared-memory limit of every variant (once, outside any
+// stream capture).
+cudaError_t prepare_vote_tc() {
+    cudaError_t e = cudaSuccess;
+    const cudaError_t r[8] = {prepare_t<2, 1, false>(), prepare_t<2, 1, true>(), prepare_t<2, 2, false>(),
+                              prepare_t<2, 2, true>(),  prepare_t<4, 1, false>(), prepare_t<4, 1, true>(),
+                              prepare_t<4, 2, false>(), prepare_t<4, 2, true>()};
+    for (cudaError_t x : r)
+        if (x != cudaSuccess) e = x;
+    return e;
+}
+
+int tc_epilogue_groups = 2;
+
+cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
+                           int level_stride, int level, PairPool pool, ProbStats *stats, int prec, float band_req,
+                           int grid_blocks, int *err_flag, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    const int grid = grid_blocks < n_items ? grid_blocks : n_items;
+    const bool g4 = tc_epilogue_groups == 4;
+#define RV_TC(G_, KS_, BF_) \
+    launch_t<G_, KS_, BF_>(items, n_items, probs, lref, level_stride, level, pool, stats, band_req, grid, err_flag, s)
+    switch (prec) {
+    case ROT_PREC_FP16: return g4 ? RV_TC(4, 1, false) : RV_TC(2, 1, false);
+    case ROT_PREC_BF16: return g4 ? RV_TC(4, 1, true) : RV_TC(2, 1, true);
+    case ROT_PREC_FP16X2: return g4 ? RV_TC(4, 2, false) : RV_TC(2, 2, false);
+    case ROT_PREC_BF16X2: return g4 ? RV_TC(4, 2, true) : RV_TC(2, 2, true);
+    default: return cudaErrorInvalidValue;
+    }
+#undef RV_TC
 }
 
 }  // namespace rv

@@ -229,7 +229,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
             const int64_t ct = (nc + cells_per_item - 1) / cells_per_item;
             work += ct * (int64_t)(align_up((size_t)pl.probs_h[k].n, kPairTile) / kPairTile);
         }
-        const int64_t target = 4LL * slots;
+        const int64_t target = (tck ? 16LL : 4LL) * slots;
         int64_t chunk = std::max<int64_t>(4, (work + target - 1) / target);  // pair tiles per item
         auto &items = pl.items_h[lev];
         for (int k = 0; k < P; ++k) {
@@ -284,11 +284,11 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     const size_t o_nc = reserve(sizeof(int32_t) * (size_t)P * S);
     const size_t o_stats = reserve(sizeof(ProbStats) * P);
     const size_t o_nkept = reserve(sizeof(int32_t) * (size_t)P * S);
+    const size_t o_err = reserve(sizeof(int) * 4);
     const size_t z1 = align_up(off, 256);
     const size_t o_kept = reserve(sizeof(int32_t) * (size_t)P * S * K);
     const size_t o_cand = reserve(sizeof(Cand) * ((size_t)P * pl.chunks_per_prob * K + (size_t)P * K));
     const size_t o_res = reserve(sizeof(rot_vote_result) * P);
-    const size_t o_err = reserve(sizeof(int) * 4);
     // child tables: P x max_levels x child_cap cells
     const size_t nchild = (size_t)P * std::max(1, max_levels) * child_cap;
     const size_t o_cq = reserve(sizeof(double4_32a) * nchild);

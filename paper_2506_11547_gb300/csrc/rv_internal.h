@@ -108,6 +108,9 @@ cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *pr
                            int level_stride, int level, PairPool pool, ProbStats *stats, int prec, float band_req,
                            int grid_blocks, int *err_flag, cudaStream_t s);
 
+// Once per process/device, outside stream capture: kernel attributes of the tensor-core vote.
+cudaError_t prepare_vote_tc();
+
 // Top-K phase 1 (per chunk of cells) and phase 2 (per problem merge) + children.
 cudaError_t launch_topk(const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride, int level,
                         int top_k, int rank_mode, int max_cells, Cand *cand, int chunks_per_prob,

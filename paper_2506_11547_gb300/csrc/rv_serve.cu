@@ -32,6 +32,13 @@ int Context::init(const rot_vote_config &c) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return ROT_VOTE_ECUDA;
     sm_count = prop.multiProcessorCount;
+    if (prop.major >= 10) {
+        const cudaError_t e = prepare_vote_tc();
+        if (e != cudaSuccess) {
+            last_error = std::string("setting tensor-core kernel attributes: ") + cudaGetErrorString(e);
+            return ROT_VOTE_ECUDA;
+        }
+    }
     if (c.cuda_stream) {
         stream = (cudaStream_t)c.cuda_stream;
         own_stream = false;

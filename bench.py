@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the precision-form comparison")
+    ap.add_argument("--only-solve", action="store_true",
+                    help="warm-up + timed solves only (a short, fixed launch sequence for profiler captures)")
     return ap.parse_args()
 
 
@@ -221,6 +223,15 @@ def main():
         ctx.solve_raw(arr, 1, out)
     res0 = rv.Result.of(out[0])
     tests_per_step = res0.tests
+    if args.only_solve:
+        for _ in range(args.steps):
+            ctx.solve_raw(arr, 1, out)
+        torch.cuda.synchronize()
+        if rank == 0:
+            r = rv.Result.of(out[0])
+            print(json.dumps({"only_solve": True, "workload": args.workload, "precision": args.precision,
+                              "status": r.status, "ms_gpu": r.ms_gpu, "tests": r.tests}))
+        return
 
     # ---- device-timed steps (inputs resident in HBM; L2 flushed before each) ----
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -312,6 +323,30 @@ def main():
                "sample": f"{m} random coarse cells x {p.n} pairs of this workload's level 0 ({dt:.1f} s, "
                          f"FP64 C oracle, threads over cells)"}
 
+    # ---- the precision forms on the same workload (device-timed the same way) ----
+    extra = None
+    if not args.no_extra and args.precision == "fp32":
+        extra = {}
+        for prec in ("fp16x2", "bf16x2", "fp16"):
+            cx = rv.Context(grid_n=grid_n, levels=levels, precision=prec, cuda_stream=stream.cuda_stream)
+            for _ in range(3):
+                cx.solve_raw(arr, 1, out)
+            ts = []
+            for _ in range(max(3, args.steps // 2)):
+                flush.zero_()
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                cx.solve_raw(arr, 1, out)
+                s1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(s0.elapsed_time(s1))
+            rr = rv.Result.of(out[0])
+            extra[prec] = {"value": tests_per_step / (sum(ts) / len(ts) / 1e3), "unit": UNIT,
+                           "ms_per_step": sum(ts) / len(ts), "rechecked": rr.rechecked,
+                           "same_result_as_fp32": bool(rr.best_cell == res0.best_cell and
+                                                       list(rr.q) == list(res0.q))}
+            cx.close()
+
     lat = per
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -327,6 +362,7 @@ def main():
         "gpu_launches": launches * args.steps,
         "roofline": roofline,
         "stage_ms": {f"{k[0]}:{k[1]}": v for k, v in sorted(stage_avg.items(), key=lambda x: -x[1])},
+        "precision_forms": extra,
         "clocks": clocks,
         "cpu_baseline": cpu,
         "result": {"status": res0.status, "angle_to_truth_rad": None, "rechecked": res0.rechecked,

@@ -89,7 +89,7 @@ typedef enum { ROT_RANK_EXCESS = 0, ROT_RANK_RAW = 1 } rot_vote_rank_mode;
 
 /* Context configuration.  Every field has a default; 0 selects it. */
 typedef struct {
-    int grid_n;               /* coarse cells per axis over [-1,1]^3; power of two in [2, 1024]; default 32 */
+    int grid_n;               /* coarse cells per axis over [-1,1]^3; power of two in [2, 256]; default 32 */
     int levels;               /* refinement levels (2x2x2 split of the kept cells); default 0 */
     int top_k;                /* cells kept per level; default 16, at most 64 */
     int precision;            /* rot_vote_precision; default ROT_PREC_FP32 */
@@ -104,6 +104,10 @@ typedef struct {
                                  repeated solves of the same shape; default 1; negative = off */
     int keep_trace;           /* 1 = keep per-level cell counts for rot_vote_level_trace; 2 = that and
                                  per-kernel timing for rot_vote_stage_times; default 0 */
+    int autotune;             /* 1 = on the first solve of each shape class (precision, size bucket), time
+                                 every vote tile-shape candidate on its coarse level and keep the fastest
+                                 (cached per context; appended to the file named by the environment
+                                 variable ROT_VOTE_TUNE_CACHE if set); default 1; negative = off */
 } rot_vote_config;
 
 /* One problem.  a, b: [n, 3] row-major float32 unit vectors (host or device).

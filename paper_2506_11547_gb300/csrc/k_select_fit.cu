@@ -10,19 +10,31 @@ namespace rv {
 namespace {
 
 // Total order of candidates: score descending, then linear index ascending.
+// The score is compared through an order-preserving 64-bit integer image of
+// the double (integer compares run on the ALU; GB300's FP64 pipe is narrow).
 struct Key {
-    double score;
+    uint64_t key;
     int64_t idx;
     int32_t pos;
 };
 
+__device__ __forceinline__ uint64_t order_key(double s) {
+    if (s == 0.0) s = 0.0;  // -0 and +0 compare equal as scores
+    const uint64_t b = (uint64_t)__double_as_longlong(s);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_score(uint64_t k) {
+    const uint64_t b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
 __device__ __forceinline__ bool better(const Key &a, const Key &b) {
-    return a.score > b.score || (a.score == b.score && a.idx < b.idx);
+    return a.key > b.key || (a.key == b.key && a.idx < b.idx);
 }
 
 __device__ __forceinline__ Key shfl_key(const Key &k, int src_lane_delta) {
     Key o;
-    o.score = __shfl_down_sync(0xffffffffu, k.score, src_lane_delta);
+    o.key = __shfl_down_sync(0xffffffffu, k.key, src_lane_delta);
     o.idx = __shfl_down_sync(0xffffffffu, k.idx, src_lane_delta);
     o.pos = __shfl_down_sync(0xffffffffu, k.pos, src_lane_delta);
     return o;
@@ -38,10 +50,10 @@ __device__ void block_select(const Key (&mine)[kPerThread], int k, Cand *out) {
     __shared__ Key wbest[kSelThreads / 32];
     __shared__ Key prev_s;
     Key prev;
-    prev.score = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    prev.key = ~0ull;  // above every score
     prev.idx = -1;
     prev.pos = -1;
-    const Key none = {-__longlong_as_double(0x7ff0000000000000LL), INT64_MAX, -1};
+    const Key none = {0ull, INT64_MAX, -1};
     for (int r = 0; r < k; ++r) {
         Key best = none;
 #pragma unroll
@@ -60,7 +72,7 @@ __device__ void block_select(const Key (&mine)[kPerThread], int k, Cand *out) {
                 if (better(wbest[w], b)) b = wbest[w];
             prev_s = b;
             Cand c;
-            c.score = b.score;
+            c.score = key_score(b.key);
             c.idx = b.idx;
             c.pos = b.pos;
             c.pad = 0;
@@ -95,12 +107,12 @@ __global__ void __launch_bounds__(kSelThreads) topk_phase1(const ProbRef *__rest
         const int c = c0 + (int)threadIdx.x + e * kSelThreads;
         if (c < ncell) {
             const int32_t cnt = L.counts[c];
-            const double t = tau_of(P.sin_d, P.cos_d, L.cells.chord[c]);
-            mine[e].score = rank_mode == ROT_RANK_RAW ? (double)cnt : dsub((double)cnt, dmul(nd, t));
+            const double t = rank_mode == ROT_RANK_RAW ? 0.0 : tau_cs(P.sin_d, P.cos_d, L.cells.trig[c]);
+            mine[e].key = order_key(rank_mode == ROT_RANK_RAW ? (double)cnt : dsub((double)cnt, dmul(nd, t)));
             mine[e].idx = L.cells.idx[c];
             mine[e].pos = c;
         } else {
-            mine[e].score = 0.0;
+            mine[e].key = 0ull;
             mine[e].idx = INT64_MAX;
             mine[e].pos = -1;
         }
@@ -147,7 +159,7 @@ __global__ void __launch_bounds__(kSelThreads) topk_phase2(const ProbRef *__rest
                 const int ci = base + (j - kMaxTopK);
                 c = ci < ncand ? src[ci] : Cand{0.0, -1, -1, 0};
             }
-            mine[e].score = c.score;
+            mine[e].key = c.pos >= 0 ? order_key(c.score) : 0ull;
             mine[e].idx = c.pos >= 0 ? c.idx : INT64_MAX;
             mine[e].pos = c.pos;
         }
@@ -183,10 +195,12 @@ __device__ void jacobi4(double A[4][4], double V[4][4]) {
     for (int r = 0; r < 4; ++r)
         for (int c = 0; c < 4; ++c) V[r][c] = r == c ? 1.0 : 0.0;
     for (int sweep = 0; sweep < 50; ++sweep) {
-        double off = 0.0;
-        for (int r = 0; r < 4; ++r)
+        double off = 0.0, dia = 0.0;
+        for (int r = 0; r < 4; ++r) {
+            dia = fma(A[r][r], A[r][r], dia);
             for (int c = r + 1; c < 4; ++c) off = fma(A[r][c], A[r][c], off);
-        if (off < 1e-300) break;
+        }
+        if (off <= 1e-40 * dia || off < 1e-300) break;
         for (int p = 0; p < 3; ++p) {
             for (int q = p + 1; q < 4; ++q) {
                 const double apq = A[p][q];
@@ -244,53 +258,119 @@ __device__ __forceinline__ void canonical(double q[4]) {
     }
 }
 
-// Adds S_i (FP64, from the float32 inputs) to acc[10].
-__device__ __forceinline__ void add_S(const float4 &p0, const float4 &p1, double acc[10]) {
-    const double a0 = p0.x, a1 = p0.y, a2 = p0.z, b0 = p0.w, b1 = p1.x, b2 = p1.y;
-    const double ab = a0 * b0 + a1 * b1 + a2 * b2;
-    acc[0] += 0.5 * (1.0 - ab);
-    acc[1] += 0.5 * (1.0 + ab - 2.0 * a0 * b0);
-    acc[2] += 0.5 * (1.0 + ab - 2.0 * a1 * b1);
-    acc[3] += 0.5 * (1.0 + ab - 2.0 * a2 * b2);
-    acc[4] += -0.5 * (a1 * b2 - a2 * b1);
-    acc[5] += -0.5 * (a2 * b0 - a0 * b2);
-    acc[6] += -0.5 * (a0 * b1 - a1 * b0);
-    acc[7] += -0.5 * (a0 * b1 + a1 * b0);
-    acc[8] += -0.5 * (a0 * b2 + a2 * b0);
-    acc[9] += -0.5 * (a1 * b2 + a2 * b1);
+// Sum of S_i over a set of m pairs from the attitude-profile matrix
+// B = sum_i b_i a_i^T (App. A: S_i = (I - M_i)/2 with
+// M_i = [[tr B_i, z_i^T], [z_i, B_i + B_i^T - tr(B_i) I]], B_i = b_i a_i^T,
+// z_i = a_i x b_i), so only 9 FP64 multiply-adds per member are needed.
+// u = [S00 S11 S22 S33 S01 S02 S03 S12 S13 S23] of the sum.
+__device__ __forceinline__ void sumS_from_B(const double B[9], double m, double u[10]) {
+    const double tr = B[0] + B[4] + B[8];
+    u[0] = 0.5 * (m - tr);
+    u[1] = 0.5 * (m - (2.0 * B[0] - tr));
+    u[2] = 0.5 * (m - (2.0 * B[4] - tr));
+    u[3] = 0.5 * (m - (2.0 * B[8] - tr));
+    u[4] = -0.5 * (B[7] - B[5]);  // z0 = B21 - B12 = (a x b)_x summed
+    u[5] = -0.5 * (B[2] - B[6]);  // z1 = B02 - B20
+    u[6] = -0.5 * (B[3] - B[1]);  // z2 = B10 - B01
+    u[7] = -0.5 * (B[1] + B[3]);
+    u[8] = -0.5 * (B[2] + B[6]);
+    u[9] = -0.5 * (B[5] + B[7]);
 }
 
-// Deterministic block sum of 10 doubles and two counters (fixed tree order).
-__device__ void block_sum(double acc[10], int &c1, int &c2, double out[10], int &o1, int &o2) {
-    __shared__ double wsum[kFitThreads / 32][10];
-    __shared__ int wc[kFitThreads / 32][2];
+constexpr int kFitPer = 8;                     // pairs per thread per chunk
+constexpr int kFitChunk = kFitThreads * kFitPer;
+
+// Deterministic block-wide exclusive scan of a small per-thread count.
+__device__ __forceinline__ int block_excl_scan(int v, int *total) {
+    __shared__ int wsum[kFitThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
 #pragma unroll
-    for (int k = 0; k < 10; ++k)
-        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
-    for (int off = 16; off > 0; off >>= 1) {
-        c1 += __shfl_down_sync(0xffffffffu, c1, off);
-        c2 += __shfl_down_sync(0xffffffffu, c2, off);
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
     }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int base = 0, tot = 0;
+    for (int k = 0; k < kFitThreads / 32; ++k) {
+        if (k < w) base += wsum[k];
+        tot += wsum[k];
+    }
+    __syncthreads();
+    *total = tot;
+    return base + x - v;
+}
+
+// One pass over the problem's pairs: membership by the FP32 re-check
+// (|b - R a|^2/4 - c <= thr), stored in mem[]; members compacted in a fixed
+// order and their b a^T summed in FP64.  Returns (in *m, *changed) block totals
+// and the 9 sums in B (thread 0).
+__device__ void fit_pass(const float4 *__restrict__ pr, uint8_t *mem, int64_t n, const float4 &R0, const float4 &R1,
+                         const float4 &R2, float thr, bool first, int *list, double B[9], int *m_out,
+                         int *chg_out) {
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int m = 0, chg = 0;
+    for (int64_t base = 0; base < n; base += kFitChunk) {
+        int mine[kFitPer];
+        int cnt = 0;
+#pragma unroll
+        for (int e = 0; e < kFitPer; ++e) {
+            const int64_t i = base + (int64_t)e * kFitThreads + threadIdx.x;
+            mine[e] = -1;
+            if (i < n) {
+                const bool in = recheck_v(R0, R1, R2, pr[2 * i], pr[2 * i + 1]) <= thr;
+                if (!first) chg += in != (mem[i] != 0);
+                mem[i] = in;
+                if (in) mine[cnt++] = (int)(i - base);
+            }
+        }
+        int tot;
+        const int off = block_excl_scan(cnt, &tot);
+#pragma unroll
+        for (int e = 0; e < kFitPer; ++e)
+            if (e < cnt) list[off + e] = mine[e];
+        __syncthreads();
+        for (int k = threadIdx.x; k < tot; k += kFitThreads) {
+            const int64_t i = base + list[k];
+            const float4 p0 = pr[2 * i], p1 = pr[2 * i + 1];
+            const double a0 = p0.x, a1 = p0.y, a2 = p0.z, b0 = p0.w, b1 = p1.x, b2 = p1.y;
+            acc[0] = fma(b0, a0, acc[0]);
+            acc[1] = fma(b0, a1, acc[1]);
+            acc[2] = fma(b0, a2, acc[2]);
+            acc[3] = fma(b1, a0, acc[3]);
+            acc[4] = fma(b1, a1, acc[4]);
+            acc[5] = fma(b1, a2, acc[5]);
+            acc[6] = fma(b2, a0, acc[6]);
+            acc[7] = fma(b2, a1, acc[7]);
+            acc[8] = fma(b2, a2, acc[8]);
+        }
+        m += tot;
+        __syncthreads();
+    }
+    // fixed-order reduction of the 9 sums and the change count
+    __shared__ double wsum[kFitThreads / 32][9];
+    __shared__ int wchg[kFitThreads / 32];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    for (int o = 16; o > 0; o >>= 1) chg += __shfl_down_sync(0xffffffffu, chg, o);
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
-        for (int k = 0; k < 10; ++k) wsum[w][k] = acc[k];
-        wc[w][0] = c1;
-        wc[w][1] = c2;
+        for (int k = 0; k < 9; ++k) wsum[w][k] = acc[k];
+        wchg[w] = chg;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 10; ++k) {
-            double s = 0.0;
-            for (int j = 0; j < kFitThreads / 32; ++j) s += wsum[j][k];
-            out[k] = s;
+        int c = 0;
+        for (int k = 0; k < 9; ++k) {
+            double t = 0.0;
+            for (int j = 0; j < kFitThreads / 32; ++j) t += wsum[j][k];
+            B[k] = t;
         }
-        int s1 = 0, s2 = 0;
-        for (int j = 0; j < kFitThreads / 32; ++j) {
-            s1 += wc[j][0];
-            s2 += wc[j][1];
-        }
-        o1 = s1;
-        o2 = s2;
+        for (int j = 0; j < kFitThreads / 32; ++j) c += wchg[j];
+        *m_out = m;
+        *chg_out = c;
     }
     __syncthreads();
 }
@@ -315,8 +395,9 @@ __global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restr
     const LevelRef L = lref[p * level_stride + last];
     const int wpos = kept_pos[(p * level_stride + last) * top_k];
     __shared__ double qs[4];
-    __shared__ double sums[10];
-    __shared__ int s_done, s_status, s_nin, s_refits;
+    __shared__ double Bs[9];
+    __shared__ int s_m, s_chg, s_done, s_status, s_nin, s_refits;
+    __shared__ int list[kFitChunk];
     if (wpos < 0) {  // no cell at the last level (cannot happen for valid inputs)
         if (threadIdx.x == 0) {
             rot_vote_result r = {};
@@ -328,35 +409,23 @@ __global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restr
     const int64_t n = P.n;
     const float4 *pr = pool.pr + 2 * P.pool_off;
     uint8_t *mem = member + P.pool_off;
-
     double qc[4];
     {
         const double4_32a q4 = L.cells.q[wpos];
         qc[0] = q4.x; qc[1] = q4.y; qc[2] = q4.z; qc[3] = q4.w;
     }
     // inliers of the winner: the voters of its cell (FP32 re-check decisions)
-    const float tau32 = (float)tau_of(P.sin_d, P.cos_d, L.cells.chord[wpos]);
+    const float tau32 = (float)tau_cs(P.sin_d, P.cos_d, L.cells.trig[wpos]);
     const float4 C0 = L.cells.R32[3 * wpos], C1 = L.cells.R32[3 * wpos + 1], C2 = L.cells.R32[3 * wpos + 2];
-    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    int cnt = 0, chg = 0;
-    for (int64_t i = threadIdx.x; i < n; i += kFitThreads) {
-        const float4 p0 = pr[2 * i], p1 = pr[2 * i + 1];
-        const bool in = recheck_v(C0, C1, C2, p0, p1) <= tau32;
-        mem[i] = in;
-        if (in) {
-            add_S(p0, p1, acc);
-            ++cnt;
-        }
-    }
-    int tot = 0, dummy = 0;
-    block_sum(acc, cnt, chg, sums, tot, dummy);
+    fit_pass(pr, mem, n, C0, C1, C2, tau32, true, list, Bs, &s_m, &s_chg);
     if (threadIdx.x == 0) {
         s_status = ROT_VOTE_OK;
         s_done = 0;
         s_refits = 0;
-        s_nin = tot;
-        double q[4];
-        if (tot < 2 || !smallest_eigvec(sums, q)) {
+        s_nin = s_m;
+        double u[10], q[4];
+        sumS_from_B(Bs, (double)s_m, u);
+        if (s_m < 2 || !smallest_eigvec(u, q)) {
             for (int k = 0; k < 4; ++k) q[k] = qc[k];
             s_status = ROT_VOTE_EDEGENERATE;
             s_done = 1;
@@ -369,28 +438,15 @@ __global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restr
         double q[4] = {qs[0], qs[1], qs[2], qs[3]};
         float4 R0, R1, R2;
         R32_of(q, R0, R1, R2);
-        for (int k = 0; k < 10; ++k) acc[k] = 0.0;
-        cnt = 0;
-        chg = 0;
-        for (int64_t i = threadIdx.x; i < n; i += kFitThreads) {
-            const float4 p0 = pr[2 * i], p1 = pr[2 * i + 1];
-            const bool in = recheck_v(R0, R1, R2, p0, p1) <= thr;
-            chg += in != (mem[i] != 0);
-            mem[i] = in;
-            if (in) {
-                add_S(p0, p1, acc);
-                ++cnt;
-            }
-        }
-        int m = 0, changed = 0;
-        block_sum(acc, cnt, chg, sums, m, changed);
+        fit_pass(pr, mem, n, R0, R1, R2, thr, false, list, Bs, &s_m, &s_chg);
         if (threadIdx.x == 0) {
-            double qn[4];
-            if (m < 2 || changed == 0 || !smallest_eigvec(sums, qn)) {
+            double u[10], qn[4];
+            sumS_from_B(Bs, (double)s_m, u);
+            if (s_m < 2 || s_chg == 0 || !smallest_eigvec(u, qn)) {
                 s_done = 1;
             } else {
                 for (int k = 0; k < 4; ++k) qs[k] = qn[k];
-                s_nin = m;
+                s_nin = s_m;
                 s_refits = t;
             }
         }

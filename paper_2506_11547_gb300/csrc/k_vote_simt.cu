@@ -31,7 +31,7 @@ constexpr int kTP = 128;     // pairs per shared-memory tile
 constexpr int kThreads = 128;
 
 template <int CPT>
-__global__ void __launch_bounds__(kThreads) vote_simt_kernel(const VoteItem *__restrict__ items, int n_items,
+__global__ void __launch_bounds__(kThreads, 4) vote_simt_kernel(const VoteItem *__restrict__ items, int n_items,
                                                              const ProbRef *__restrict__ probs,
                                                              const LevelRef *__restrict__ lref, int level_stride,
                                                              int level, PairPool pool, ProbStats *stats) {
@@ -43,21 +43,23 @@ __global__ void __launch_bounds__(kThreads) vote_simt_kernel(const VoteItem *__r
         const LevelRef L = lref[W.prob * level_stride + level];
         const int ncell = *L.ncells;
         if (W.cell_begin >= ncell) continue;
-
+        // the item's kSimtItemCells cells, CPT x kThreads at a time
+        const int cell_end = min(ncell, W.cell_begin + kSimtItemCells);
+      for (int sub = W.cell_begin; sub < cell_end; sub += CPT * kThreads) {
         float m[CPT][10], tau[CPT];
         int cnt[CPT];
         int pos[CPT];
 #pragma unroll
         for (int k = 0; k < CPT; ++k) {
-            pos[k] = W.cell_begin + (int)threadIdx.x + k * kThreads;
+            pos[k] = sub + (int)threadIdx.x + k * kThreads;
             cnt[k] = 0;
-            if (pos[k] < ncell) {
+            if (pos[k] < cell_end) {
                 const float4 m0 = L.cells.m32[3 * pos[k]], m1 = L.cells.m32[3 * pos[k] + 1],
                              m2 = L.cells.m32[3 * pos[k] + 2];
                 m[k][0] = m0.x; m[k][1] = m0.y; m[k][2] = m0.z; m[k][3] = m0.w;
                 m[k][4] = m1.x; m[k][5] = m1.y; m[k][6] = m1.z; m[k][7] = m1.w;
                 m[k][8] = m2.x; m[k][9] = m2.y;
-                tau[k] = (float)tau_of(P.sin_d, P.cos_d, L.cells.chord[pos[k]]);
+                tau[k] = (float)tau_cs(P.sin_d, P.cos_d, L.cells.trig[pos[k]]);
             } else {  // absent cell: d = 1 for every pair, never counted, never in the band
 #pragma unroll
                 for (int e = 0; e < 10; ++e) m[k][e] = 0.f;
@@ -124,19 +126,18 @@ __global__ void __launch_bounds__(kThreads) vote_simt_kernel(const VoteItem *__r
         }
 #pragma unroll
         for (int k = 0; k < CPT; ++k)
-            if (pos[k] < ncell && cnt[k] != 0) atomicAdd(&L.counts[pos[k]], cnt[k]);
+            if (pos[k] < cell_end && cnt[k] != 0) atomicAdd(&L.counts[pos[k]], cnt[k]);
         const unsigned rc = __reduce_add_sync(0xffffffffu, rechecked);
         const unsigned am = __reduce_add_sync(0xffffffffu, ambiguous);
         if ((threadIdx.x & 31) == 0) {
             if (rc) atomicAdd(&stats[W.prob].rechecked, (unsigned long long)rc);
             if (am) atomicAdd(&stats[W.prob].ambiguous, (unsigned long long)am);
         }
+      }
     }
 }
 
 }  // namespace
-
-int simt_cells_per_item(int cells_per_thread) { return cells_per_thread * kThreads; }
 
 cudaError_t launch_vote_simt(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                              int level_stride, int level, PairPool pool, ProbStats *stats, int cells_per_thread,

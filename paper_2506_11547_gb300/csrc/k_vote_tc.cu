@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     const float4 m0 = v.L.cells.m32[3 * pos], m1 = v.L.cells.m32[3 * pos + 1],
                                  m2 = v.L.cells.m32[3 * pos + 2];
                     const float m[10] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y};
-                    const float tau = (float)tau_of(v.P.sin_d, v.P.cos_d, v.L.cells.chord[pos]);
+                    const float tau = (float)tau_cs(v.P.sin_d, v.P.cos_d, v.L.cells.trig[pos]);
                     const uint16_t th = h16<BF16>(tau);
                     const uint16_t tl = h16<BF16>(tau - f16<BF16>(th));
                     if (KSTEPS == 1) {
@@ -414,13 +414,17 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 const float4 m0 = v.L.cells.m32[3 * pos], m1 = v.L.cells.m32[3 * pos + 1],
                              m2 = v.L.cells.m32[3 * pos + 2];
                 const float m[10] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y};
-                tau = (float)tau_of(v.P.sin_d, v.P.cos_d, v.L.cells.chord[pos]);
+                tau = (float)tau_cs(v.P.sin_d, v.P.cos_d, v.L.cells.trig[pos]);
                 band = fmaxf(cell_band<KSTEPS, BF16>(m), band_req);
             }
             int cnt = 0;
             unsigned rechecked = 0, ambiguous = 0;
-            bool haveR = false;
             float4 R0 = make_float4(0, 0, 0, 0), R1 = R0, R2 = R0;
+            if (valid) {  // the cell's rotation, for re-checks
+                R0 = v.L.cells.R32[3 * pos];
+                R1 = v.L.cells.R32[3 * pos + 1];
+                R2 = v.L.cells.R32[3 * pos + 2];
+            }
             const int64_t gbase = v.P.pool_off + v.W.pair_begin;
             for (; t < v.ntiles; t += G) {
                 const int64_t jj = j0 + t;
@@ -435,34 +439,39 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(as * 128);
 #pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
-                    uint32_t r[32];
+                for (int c = 0; c < 4; c += 2) {  // two 32-column loads per wait
+                    uint32_t r[32], r2[32];
                     tmem_ld32(taddr + 32 * c, r);
+                    tmem_ld32(taddr + 32 * c + 32, r2);
                     tmem_ld_wait(r);
-                    bool flag = false;
+                    tmem_ld_wait(r2);
+                    float mn = 3.0f;
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
-                        cnt += (int)(r[e] >> 31);
-                        flag |= fabsf(__uint_as_float(r[e])) <= band;
+                        cnt += (int)(r[e] >> 31) + (int)(r2[e] >> 31);
+                        mn = fminf(mn, fminf(fabsf(__uint_as_float(r[e])), fabsf(__uint_as_float(r2[e]))));
                     }
-                    if (flag) {  // rare: re-check the flagged tests of this chunk
-                        if (!haveR) {
-                            R0 = v.L.cells.R32[3 * pos];
-                            R1 = v.L.cells.R32[3 * pos + 1];
-                            R2 = v.L.cells.R32[3 * pos + 2];
-                            haveR = true;
-                        }
-#pragma unroll 1
+                    if (mn <= band) {  // rare: re-check the flagged tests of these 64 columns
+                        // flag and sign masks built with constant register indices only
+                        uint32_t f0 = 0, f1 = 0, s0 = 0, s1 = 0;
+#pragma unroll
                         for (int e = 0; e < 32; ++e) {
-                            const float d = __uint_as_float(r[e]);
-                            if (fabsf(d) <= band) {
-                                const int64_t gp = gbase + (int64_t)t * kPairTile + 32 * c + e;
-                                const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
-                                const float vv = recheck_v(R0, R1, R2, p0, p1);
-                                cnt += (int)(vv <= tau) - (int)(r[e] >> 31);
-                                ++rechecked;
-                                ambiguous += fabsf(vv - tau) <= kAmbig;
-                            }
+                            f0 |= (uint32_t)(fabsf(__uint_as_float(r[e])) <= band) << e;
+                            f1 |= (uint32_t)(fabsf(__uint_as_float(r2[e])) <= band) << e;
+                            s0 |= (r[e] >> 31) << e;
+                            s1 |= (r2[e] >> 31) << e;
+                        }
+                        uint64_t fm = ((uint64_t)f1 << 32) | f0;
+                        const uint64_t sm = ((uint64_t)s1 << 32) | s0;
+                        while (fm) {
+                            const int e = __ffsll((long long)fm) - 1;
+                            fm &= fm - 1;
+                            const int64_t gp = gbase + (int64_t)t * kPairTile + 32 * c + e;
+                            const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
+                            const float vv = recheck_v(R0, R1, R2, p0, p1);
+                            cnt += (int)(vv <= tau) - (int)((sm >> e) & 1ull);
+                            ++rechecked;
+                            ambiguous += fabsf(vv - tau) <= kAmbig;
                         }
                     }
                 }
@@ -525,14 +534,12 @@ cudaError_t prepare_vote_tc() {
     return e;
 }
 
-int tc_epilogue_groups = 2;
-
 cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                            int level_stride, int level, PairPool pool, ProbStats *stats, int prec, float band_req,
-                           int grid_blocks, int *err_flag, cudaStream_t s) {
+                           int epilogue_groups, int grid_blocks, int *err_flag, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
     const int grid = grid_blocks < n_items ? grid_blocks : n_items;
-    const bool g4 = tc_epilogue_groups == 4;
+    const bool g4 = epilogue_groups == 4;
 #define RV_TC(G_, KS_, BF_) \
     launch_t<G_, KS_, BF_>(items, n_items, probs, lref, level_stride, level, pool, stats, band_req, grid, err_flag, s)
     switch (prec) {

@@ -71,6 +71,7 @@ int Context::grid_table(int n, const GridTable **out) {
     g.n = n;
     g.ncells = total;
     const size_t bytes = align_up(sizeof(double4_32a) * total, 256) + align_up(sizeof(double) * total, 256) +
+                         align_up(sizeof(double2) * total, 256) +
                          align_up(sizeof(int64_t) * total, 256) + 2 * align_up(sizeof(float4) * 3 * total, 256) +
                          256 + align_up(sizeof(int4) * rows.size(), 256);
     if (bytes_held + bytes > budget) return fail(ROT_VOTE_ENOMEM, "grid table exceeds the device memory budget");
@@ -84,6 +85,7 @@ int Context::grid_table(int n, const GridTable **out) {
     };
     g.cells.q = (double4_32a *)take(sizeof(double4_32a) * total);
     g.cells.chord = (double *)take(sizeof(double) * total);
+    g.cells.trig = (double2 *)take(sizeof(double2) * total);
     g.cells.idx = (int64_t *)take(sizeof(int64_t) * total);
     g.cells.m32 = (float4 *)take(sizeof(float4) * 3 * total);
     g.cells.R32 = (float4 *)take(sizeof(float4) * 3 * total);
@@ -215,7 +217,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
 
     // level items
     const int tck = tc_k_of(pl.prec);
-    const int cells_per_item = tck ? kCellTile : simt_cpt * 128;
+    const int cells_per_item = tck ? kCellTile : kSimtItemCells;
     const int blocks_per_sm = tck ? 1 : 4;
     const int slots = sm_count * blocks_per_sm;
     pl.grid_blocks = slots;
@@ -293,6 +295,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     const size_t nchild = (size_t)P * std::max(1, max_levels) * child_cap;
     const size_t o_cq = reserve(sizeof(double4_32a) * nchild);
     const size_t o_cch = reserve(sizeof(double) * nchild);
+    const size_t o_ctr = reserve(sizeof(double2) * nchild);
     const size_t o_cidx = reserve(sizeof(int64_t) * nchild);
     const size_t o_cm = reserve(sizeof(float4) * 3 * nchild);
     const size_t o_cR = reserve(sizeof(float4) * 3 * nchild);
@@ -352,6 +355,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     CellSoA ch;
     ch.q = (double4_32a *)(B + o_cq);
     ch.chord = (double *)(B + o_cch);
+    ch.trig = (double2 *)(B + o_ctr);
     ch.idx = (int64_t *)(B + o_cidx);
     ch.m32 = (float4 *)(B + o_cm);
     ch.R32 = (float4 *)(B + o_cR);
@@ -368,6 +372,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
                 const size_t base = ((size_t)k * std::max(1, max_levels) + (lev - 1)) * child_cap;
                 L.cells.q = ch.q + base;
                 L.cells.chord = ch.chord + base;
+                L.cells.trig = ch.trig + base;
                 L.cells.idx = ch.idx + base;
                 L.cells.m32 = ch.m32 + 3 * base;
                 L.cells.R32 = ch.R32 + 3 * base;
@@ -382,8 +387,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     std::string sig;
     sig.reserve(64 + 24 * P);
     char buf[96];
-    snprintf(buf, sizeof buf, "%d|%d|%d|%d|%d|%d|%d|", P, pl.prec, K, cfg.rank_mode, cfg.refit_iters, simt_cpt,
-             (int)all_dev);
+    snprintf(buf, sizeof buf, "%d|%d|%d|%d|%d|%d|", P, pl.prec, K, cfg.rank_mode, cfg.refit_iters, (int)all_dev);
     sig += buf;
     for (int k = 0; k < P; ++k) {
         snprintf(buf, sizeof buf, "%lld,%d,%d;", (long long)pl.probs_h[k].n, gridn[k], levs[k]);
@@ -476,12 +480,7 @@ int Context::enqueue_pipeline(Wave &w) {
     for (int lev = 0; lev < S && e == cudaSuccess; ++lev) {
         const int nit = (int)pl.items_h[lev].size();
         mark(1, lev);
-        if (pl.pool.tc_k)
-            e = launch_vote_tc(pl.d_items[lev], nit, pl.d_probs, pl.d_lref, S, lev, pl.pool, pl.d_stats, pl.prec,
-                               cfg.recheck_band, pl.grid_blocks, pl.d_err, w.stream);
-        else
-            e = launch_vote_simt(pl.d_items[lev], nit, pl.d_probs, pl.d_lref, S, lev, pl.pool, pl.d_stats, simt_cpt,
-                                 pl.grid_blocks, w.stream);
+        e = launch_vote(w, lev, pl.variant);
         done();
         mark(2, lev);
         if (e == cudaSuccess)
@@ -506,9 +505,121 @@ int Context::enqueue_pipeline(Wave &w) {
     return ROT_VOTE_OK;
 }
 
+cudaError_t Context::launch_vote(Wave &w, int lev, int variant) {
+    Plan &pl = w.plan;
+    const int nit = (int)pl.items_h[lev].size();
+    if (pl.pool.tc_k)
+        return launch_vote_tc(pl.d_items[lev], nit, pl.d_probs, pl.d_lref, pl.stride, lev, pl.pool, pl.d_stats,
+                              pl.prec, cfg.recheck_band, variant, pl.grid_blocks, pl.d_err, w.stream);
+    return launch_vote_simt(pl.d_items[lev], nit, pl.d_probs, pl.d_lref, pl.stride, lev, pl.pool, pl.d_stats, variant,
+                            pl.grid_blocks, w.stream);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: the vote's tile shape (CUDA-core form: cells per thread;
+// tensor-core form: epilogue warpgroups) is chosen per shape class by timing
+// every candidate on the level-0 vote of the first solve in that class.
+// ---------------------------------------------------------------------------
+static int ilog2_64(int64_t x) {
+    int r = 0;
+    while (x > 1) {
+        x >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+std::string Context::tune_key(const Plan &pl) const {
+    int64_t tests0 = 0;
+    for (int k = 0; k < pl.nprob; ++k)
+        tests0 += (int64_t)pl.probs_h[k].n * (pl.lref_h[(size_t)k * pl.stride].cap);
+    char buf[96];
+    snprintf(buf, sizeof buf, "sm%d:prec%d:tests2^%d:probs2^%d", sm_count, pl.prec, ilog2_64(tests0),
+             ilog2_64(pl.nprob));
+    return buf;
+}
+
+static std::vector<int> candidates(int tc_k) { return tc_k ? std::vector<int>{2, 4} : std::vector<int>{4, 8}; }
+
+int Context::choose_variant(Wave &w) {
+    Plan &pl = w.plan;
+    const std::vector<int> cand = candidates(pl.pool.tc_k);
+    pl.variant = cand[pl.pool.tc_k ? 0 : 0];
+    if (cfg.autotune < 0) return ROT_VOTE_OK;
+    const std::string key = tune_key(pl);
+    auto it = tuned.find(key);
+    if (it != tuned.end()) {
+        pl.variant = it->second;
+        return ROT_VOTE_OK;
+    }
+    char *B = (char *)w.base;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    int best = cand[0];
+    for (int v : cand) {
+        float tot = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) {
+            cudaError_t e = cudaMemsetAsync(B + pl.zero_off, 0, pl.zero_bytes, w.stream);
+            if (e == cudaSuccess)
+                e = launch_pair_prep(pl.d_probs, pl.d_tiles, (int)pl.tiles_h.size(), pl.pool, pl.prec, pl.d_stats,
+                                     w.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, w.stream);
+            if (e == cudaSuccess) e = launch_vote(w, 0, v);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, w.stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(w.stream);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(e, "autotuning the vote");
+            }
+            if (rep > 0) tot += ms;
+        }
+        int err = 0;
+        cudaMemcpy(&err, pl.d_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (err) continue;  // a bounded wait expired: never choose this variant
+        if (tot < best_ms) {
+            best_ms = tot;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tuned[key] = best;
+    pl.variant = best;
+    save_tuning(key, best, best_ms / 2.f);
+    return ROT_VOTE_OK;
+}
+
+void Context::load_tuning() {
+    const char *path = getenv("ROT_VOTE_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char key[128];
+    int v;
+    float ms;
+    while (fscanf(f, "%127s %d %f", key, &v, &ms) == 3) tuned[key] = v;
+    fclose(f);
+}
+
+void Context::save_tuning(const std::string &key, int v, float ms) {
+    const char *path = getenv("ROT_VOTE_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %.4f\n", key.c_str(), v, ms);
+    fclose(f);
+}
+
 // Plans, uploads and launches a batch on wave w (asynchronous).
 int Context::launch_batch(Wave &w, const rot_vote_problem *p, const std::vector<int> &sel) {
     const std::string old_sig = w.plan.signature;
+    const int old_variant = w.plan.variant;
     const bool had_graph = w.graph_exec != nullptr;
     int rc = plan_batch(w, p, sel);
     if (rc != ROT_VOTE_OK) return rc;
@@ -516,6 +627,9 @@ int Context::launch_batch(Wave &w, const rot_vote_problem *p, const std::vector<
     if (rc != ROT_VOTE_OK) return fail(rc, "pinned result allocation failed");
     rc = upload(w, p, sel);
     if (rc != ROT_VOTE_OK) return rc;
+    rc = choose_variant(w);
+    if (rc != ROT_VOTE_OK) return rc;
+    if (w.plan.variant != old_variant) w.plan.signature += "|changed";
     cudaError_t e = cudaEventRecord(w.ev0, w.stream);
     if (e != cudaSuccess) return cuda_fail(e, "recording an event");
     const bool graphs = cfg.use_graphs > 0 && cfg.keep_trace < 2;
@@ -771,6 +885,7 @@ int rot_vote_create(const rot_vote_config *cfg_in, rot_vote_ctx **out) {
     if (c.device_mem_budget == 0) c.device_mem_budget = (size_t)16 << 30;
     if (c.max_inflight == 0) c.max_inflight = 256;
     if (c.use_graphs == 0) c.use_graphs = 1;
+    if (c.autotune == 0) c.autotune = 1;
     if (c.grid_n < 2 || c.grid_n > 256 || (c.grid_n & (c.grid_n - 1)) || c.levels < 0 || c.levels > kMaxLevels ||
         c.top_k < 1 || c.top_k > kMaxTopK || c.precision < 0 || c.precision > ROT_PREC_BF16X2 || c.rank_mode < 0 ||
         c.rank_mode > 1 || c.max_inflight < 1 || !(c.recheck_band >= 0.f))

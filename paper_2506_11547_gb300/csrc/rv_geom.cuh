@@ -31,6 +31,25 @@ __device__ __forceinline__ double tau_of(double sin_d, double cos_d, double chor
     return dmul(s, s);
 }
 
+// The delta-independent part of the threshold: cos r = 1 - 2x^2 and
+// sin r = 2x sqrt(1 - x^2) of r = 2 asin(x), x = min(1, chord/2).
+__device__ __forceinline__ double2 cell_trig(double chord) {
+    double x = ddiv(chord, 2.0);
+    if (x > 1.0) x = 1.0;
+    const double cr = dsub(1.0, dmul(dmul(2.0, x), x));
+    const double sr = dmul(dmul(2.0, x), dsqrt(dsub(1.0, dmul(x, x))));
+    return make_double2(cr, sr);
+}
+
+// tau = sin^2(delta + r) from the cell's (cos r, sin r): the same operations,
+// in the same order, as tau_of(), without its square root and division.
+__device__ __forceinline__ double tau_cs(double sin_d, double cos_d, double2 cs) {
+    const double cos_sum = dsub(dmul(cos_d, cs.x), dmul(sin_d, cs.y));
+    if (cos_sum <= 0.0) return 1.0;
+    const double s = dadd(dmul(sin_d, cs.x), dmul(cos_d, cs.y));
+    return dmul(s, s);
+}
+
 __device__ __forceinline__ double dist0(double lo, double hi) {
     if (lo > 0.0) return lo;
     if (hi < 0.0) return -hi;
@@ -145,6 +164,7 @@ __device__ __forceinline__ void write_cell(const CellSoAT &t, int64_t pos, int n
     cell_geom(n, ix, iy, iz, q, &chord);
     t.q[pos] = make_double4_32a(q[0], q[1], q[2], q[3]);
     t.chord[pos] = chord;
+    t.trig[pos] = cell_trig(chord);
     t.idx[pos] = (iz * (int64_t)n + iy) * (int64_t)n + ix;
     double m[10], R[9];
     monomials(q, m);

@@ -16,16 +16,19 @@ constexpr int kCellTile = 128;      // cells per tensor-core A tile (TMEM lanes)
 constexpr float kAmbig = 1e-6f;     // |v - tau| below this: the decision is reported ambiguous
 constexpr float kBandFP32 = 4e-6f;  // rigorous bound on |v_fast - v_exact| of the FP32 FMA form
 constexpr int kSelChunk = 4096;     // cells per top-K phase-1 block
+constexpr int kSimtItemCells = 1024; // cells per CUDA-core vote work item (any cells-per-thread variant)
 
 // Per-cell record of a level table (structure of arrays).
 //   q     FP64 centre quaternion (w, x, y, z)
 //   chord FP64 covering chord (r = 2 asin(chord / 2))
+//   trig  FP64 (cos r, sin r), so tau = sin^2(delta + r) costs no sqrt/div
 //   idx   linear cell index (iz*n + iy)*n + ix at the table's level
 //   m32   monomials [w2 x2 y2 z2 2wx 2wy 2wz 2xy 2xz 2yz] rounded to f32, + 2 pad (48 B)
 //   R32   rotation matrix of q rounded to f32, row-major, + 3 pad (48 B)
 struct CellSoA {
     double4_32a *q;
     double *chord;
+    double2 *trig;
     int64_t *idx;
     float4 *m32;  // 3 float4 per cell
     float4 *R32;  // 3 float4 per cell
@@ -106,7 +109,7 @@ cudaError_t launch_vote_simt(const VoteItem *items, int n_items, const ProbRef *
 // Vote, tcgen05 tensor-core form. prec: ROT_PREC_FP16 .. BF16X2.
 cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                            int level_stride, int level, PairPool pool, ProbStats *stats, int prec, float band_req,
-                           int grid_blocks, int *err_flag, cudaStream_t s);
+                           int epilogue_groups, int grid_blocks, int *err_flag, cudaStream_t s);
 
 // Once per process/device, outside stream capture: kernel attributes of the tensor-core vote.
 cudaError_t prepare_vote_tc();

@@ -20,7 +20,6 @@ namespace rv {
 
 size_t align_up(size_t x, size_t a);
 int check_problem(const rot_vote_problem &p, int grid_n, int levels, std::string *why);
-int simt_cells_per_item(int cells_per_thread);
 
 struct GridTable {
     int n = 0;
@@ -36,6 +35,7 @@ struct Plan {
     std::string signature;
     int nprob = 0, prec = 0, top_k = 16, stride = 1, max_level = 0;
     int chunks_per_prob = 1, grid_blocks = 1;
+    int variant = 0;  // vote tile shape: cells per thread (CUDA cores) or epilogue warpgroups (tensor cores)
     int64_t pool_pairs = 0, in_floats = 0;
     bool inputs_on_device = true;
     std::vector<ProbRef> probs_h;
@@ -104,7 +104,7 @@ class Context {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     size_t budget = 0, bytes_held = 0;
-    int simt_cpt = 4;
+    std::unordered_map<std::string, int> tuned;  // autotuner choices per shape class
     int test_fail_alloc = 0;
     // per-kernel profiling (keep_trace == 2)
     std::vector<cudaEvent_t> prof_ev;
@@ -136,6 +136,11 @@ class Context {
     int plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<int> &sel);
     int upload(Wave &w, const rot_vote_problem *p, const std::vector<int> &sel);
     int enqueue_pipeline(Wave &w);
+    cudaError_t launch_vote(Wave &w, int lev, int variant);
+    std::string tune_key(const Plan &pl) const;
+    int choose_variant(Wave &w);
+    void load_tuning();
+    void save_tuning(const std::string &key, int v, float ms);
     int launch_batch(Wave &w, const rot_vote_problem *p, const std::vector<int> &sel);
     int collect(Wave &w, const std::vector<int> &sel, rot_vote_result *out);
     int solve(const rot_vote_problem *p, int n, rot_vote_result *out);

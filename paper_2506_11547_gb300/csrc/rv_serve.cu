@@ -47,6 +47,7 @@ int Context::init(const rot_vote_config &c) {
         own_stream = true;
     }
     if (main_wave.init(stream, false) != ROT_VOTE_OK) return ROT_VOTE_ECUDA;
+    load_tuning();
     return ROT_VOTE_OK;
 }
 

@@ -27,7 +27,7 @@ class rot_vote_config(C.Structure):
     _fields_ = [("grid_n", C.c_int), ("levels", C.c_int), ("top_k", C.c_int), ("precision", C.c_int),
                 ("recheck_band", C.c_float), ("rank_mode", C.c_int), ("refit_iters", C.c_int),
                 ("device_mem_budget", C.c_size_t), ("max_inflight", C.c_int), ("cuda_stream", C.c_void_p),
-                ("use_graphs", C.c_int), ("keep_trace", C.c_int)]
+                ("use_graphs", C.c_int), ("keep_trace", C.c_int), ("autotune", C.c_int)]
 
 
 class rot_vote_problem(C.Structure):
@@ -144,14 +144,15 @@ class Context:
 
     def __init__(self, grid_n=0, levels=0, top_k=0, precision="fp32", recheck_band=0.0, rank_mode="excess",
                  refit_iters=0, device_mem_budget=0, max_inflight=0, cuda_stream=None, use_graphs=0,
-                 keep_trace=0):
+                 keep_trace=0, autotune=0):
         L = load()
         self._L = L
         cfg = rot_vote_config(int(grid_n), int(levels), int(top_k),
                               PREC[precision] if isinstance(precision, str) else int(precision),
                               float(recheck_band), RANK[rank_mode] if isinstance(rank_mode, str) else int(rank_mode),
                               int(refit_iters), int(device_mem_budget), int(max_inflight),
-                              C.c_void_p(cuda_stream) if cuda_stream else None, int(use_graphs), int(keep_trace))
+                              C.c_void_p(cuda_stream) if cuda_stream else None, int(use_graphs), int(keep_trace),
+                              int(autotune))
         h = C.c_void_p()
         rc = L.rot_vote_create(C.byref(cfg), C.byref(h))
         if rc != OK:

@@ -1,5 +1,6 @@
 // k_select_fit.cu -- ranking of the voted cells, top-K selection, and the
 // final fit (Eq. stack, Sec. 4.2) with its refit loop.
+#include <cooperative_groups.h>
 #include <float.h>
 
 #include "rv_geom.cuh"
@@ -189,65 +190,6 @@ __global__ void __launch_bounds__(kSelThreads) topk_phase2(const ProbRef *__rest
 // ---------------------------------------------------------------------------
 constexpr int kFitThreads = 512;
 
-// Cyclic Jacobi on a symmetric 4x4 (row-major, in place); eigenvectors in the
-// columns of V; returns eigenvalues unsorted on the diagonal of A.
-__device__ void jacobi4(double A[4][4], double V[4][4]) {
-    for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) V[r][c] = r == c ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 50; ++sweep) {
-        double off = 0.0, dia = 0.0;
-        for (int r = 0; r < 4; ++r) {
-            dia = fma(A[r][r], A[r][r], dia);
-            for (int c = r + 1; c < 4; ++c) off = fma(A[r][c], A[r][c], off);
-        }
-        if (off <= 1e-40 * dia || off < 1e-300) break;
-        for (int p = 0; p < 3; ++p) {
-            for (int q = p + 1; q < 4; ++q) {
-                const double apq = A[p][q];
-                if (apq == 0.0) continue;
-                const double th = (A[q][q] - A[p][p]) / (2.0 * apq);
-                const double t = copysign(1.0, th) / (fabs(th) + sqrt(fma(th, th, 1.0)));
-                const double c = rsqrt(fma(t, t, 1.0));
-                const double s = t * c;
-                for (int k = 0; k < 4; ++k) {
-                    const double x = A[k][p], y = A[k][q];
-                    A[k][p] = c * x - s * y;
-                    A[k][q] = s * x + c * y;
-                }
-                for (int k = 0; k < 4; ++k) {
-                    const double x = A[p][k], y = A[q][k];
-                    A[p][k] = c * x - s * y;
-                    A[q][k] = s * x + c * y;
-                }
-                for (int k = 0; k < 4; ++k) {
-                    const double x = V[k][p], y = V[k][q];
-                    V[k][p] = c * x - s * y;
-                    V[k][q] = s * x + c * y;
-                }
-            }
-        }
-    }
-}
-
-// Smallest eigenvector of the symmetric matrix with unique entries
-// u = [S00 S11 S22 S33 S01 S02 S03 S12 S13 S23]; returns false if the two
-// smallest eigenvalues are within 1e-12 * trace (no unique minimiser).
-__device__ bool smallest_eigvec(const double u[10], double q[4]) {
-    double A[4][4] = {{u[0], u[4], u[5], u[6]}, {u[4], u[1], u[7], u[8]}, {u[5], u[7], u[2], u[9]},
-                      {u[6], u[8], u[9], u[3]}};
-    const double tr = u[0] + u[1] + u[2] + u[3];
-    double V[4][4];
-    jacobi4(A, V);
-    int i0 = 0;
-    for (int k = 1; k < 4; ++k)
-        if (A[k][k] < A[i0][i0]) i0 = k;
-    double l1 = DBL_MAX;
-    for (int k = 0; k < 4; ++k)
-        if (k != i0 && A[k][k] < l1) l1 = A[k][k];
-    for (int r = 0; r < 4; ++r) q[r] = V[r][i0];
-    return (l1 - A[i0][i0]) > 1e-12 * tr;
-}
-
 __device__ __forceinline__ void canonical(double q[4]) {
     for (int k = 0; k < 4; ++k) {
         if (q[k] > 0.0) return;
@@ -277,8 +219,9 @@ __device__ __forceinline__ void sumS_from_B(const double B[9], double m, double 
     u[9] = -0.5 * (B[5] + B[7]);
 }
 
-constexpr int kFitPer = 8;                     // pairs per thread per chunk
-constexpr int kFitChunk = kFitThreads * kFitPer;
+constexpr int kFitPer = 8;                     // pairs per thread per slice
+constexpr int kFitSlice = kFitThreads * kFitPer;  // 4096 pairs: the unit of the fixed reduction order
+constexpr int kFitMaxCluster = 8;
 
 // Deterministic block-wide exclusive scan of a small per-thread count.
 __device__ __forceinline__ int block_excl_scan(int v, int *total) {
@@ -302,36 +245,38 @@ __device__ __forceinline__ int block_excl_scan(int v, int *total) {
     return base + x - v;
 }
 
-// One pass over the problem's pairs: membership by the FP32 re-check
-// (|b - R a|^2/4 - c <= thr), stored in mem[]; members compacted in a fixed
-// order and their b a^T summed in FP64.  Returns (in *m, *changed) block totals
-// and the 9 sums in B (thread 0).
-__device__ void fit_pass(const float4 *__restrict__ pr, uint8_t *mem, int64_t n, const float4 &R0, const float4 &R1,
-                         const float4 &R2, float thr, bool first, int *list, double B[9], int *m_out,
-                         int *chg_out) {
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    int m = 0, chg = 0;
-    for (int64_t base = 0; base < n; base += kFitChunk) {
-        int mine[kFitPer];
-        int cnt = 0;
+// One slice of a fit pass: membership by the FP32 re-check
+// (|b - R a|^2/4 - c <= thr) for pairs [base, base + kFitSlice), stored in
+// mem[]; members compacted in index order and their b a^T summed in FP64 by
+// warp 0 in a fixed order.  Writes the slice's 9 sums, member count and
+// changed count to part[0..10] (thread 0).  Depends only on the slice.
+__device__ void fit_slice(const float4 *__restrict__ pr, uint8_t *mem, int64_t n, int64_t base, const float4 &R0,
+                          const float4 &R1, const float4 &R2, float thr, bool first, int *list, double *part) {
+    int mine[kFitPer];
+    int cnt = 0, chg = 0;
 #pragma unroll
-        for (int e = 0; e < kFitPer; ++e) {
-            const int64_t i = base + (int64_t)e * kFitThreads + threadIdx.x;
-            mine[e] = -1;
-            if (i < n) {
-                const bool in = recheck_v(R0, R1, R2, pr[2 * i], pr[2 * i + 1]) <= thr;
-                if (!first) chg += in != (mem[i] != 0);
-                mem[i] = in;
-                if (in) mine[cnt++] = (int)(i - base);
-            }
+    for (int e = 0; e < kFitPer; ++e) {
+        const int64_t i = base + (int64_t)e * kFitThreads + threadIdx.x;
+        mine[e] = -1;
+        if (i < n) {
+            const bool in = recheck_v(R0, R1, R2, pr[2 * i], pr[2 * i + 1]) <= thr;
+            if (!first) chg += in != (mem[i] != 0);
+            mem[i] = in;
+            if (in) mine[cnt++] = (int)(i - base);
         }
-        int tot;
-        const int off = block_excl_scan(cnt, &tot);
+    }
+    __shared__ int wchg[kFitThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) chg += __shfl_down_sync(0xffffffffu, chg, o);
+    if ((threadIdx.x & 31) == 0) wchg[threadIdx.x >> 5] = chg;
+    int tot;
+    const int off = block_excl_scan(cnt, &tot);
 #pragma unroll
-        for (int e = 0; e < kFitPer; ++e)
-            if (e < cnt) list[off + e] = mine[e];
-        __syncthreads();
-        for (int k = threadIdx.x; k < tot; k += kFitThreads) {
+    for (int e = 0; e < kFitPer; ++e)
+        if (e < cnt) list[off + e] = mine[e];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = threadIdx.x; k < tot; k += 32) {
             const int64_t i = base + list[k];
             const float4 p0 = pr[2 * i], p1 = pr[2 * i + 1];
             const double a0 = p0.x, a1 = p0.y, a2 = p0.z, b0 = p0.w, b1 = p1.x, b2 = p1.y;
@@ -345,34 +290,69 @@ __device__ void fit_pass(const float4 *__restrict__ pr, uint8_t *mem, int64_t n,
             acc[7] = fma(b2, a1, acc[7]);
             acc[8] = fma(b2, a2, acc[8]);
         }
-        m += tot;
-        __syncthreads();
-    }
-    // fixed-order reduction of the 9 sums and the change count
-    __shared__ double wsum[kFitThreads / 32][9];
-    __shared__ int wchg[kFitThreads / 32];
+        if (tot > 0) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k)
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-    for (int o = 16; o > 0; o >>= 1) chg += __shfl_down_sync(0xffffffffu, chg, o);
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        for (int k = 0; k < 9; ++k) wsum[w][k] = acc[k];
-        wchg[w] = chg;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int c = 0;
-        for (int k = 0; k < 9; ++k) {
-            double t = 0.0;
-            for (int j = 0; j < kFitThreads / 32; ++j) t += wsum[j][k];
-            B[k] = t;
+            for (int k = 0; k < 9; ++k)
+                for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
         }
-        for (int j = 0; j < kFitThreads / 32; ++j) c += wchg[j];
-        *m_out = m;
-        *chg_out = c;
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 9; ++k) part[k] = tot > 0 ? acc[k] : 0.0;
+            part[9] = (double)tot;
+            int c = 0;
+            for (int j = 0; j < kFitThreads / 32; ++j) c += wchg[j];
+            part[10] = (double)c;
+        }
     }
     __syncthreads();
+}
+
+// Warp-cooperative cyclic Jacobi on a symmetric 4x4 held in shared memory
+// (FP64), accumulating rotations into V (which may start from a previous
+// eigenbasis).  Each rotation's tan(phi) is estimated in FP32; (c, s) are then
+// made orthogonal to FP64 precision (c = 1/sqrt(1 + t^2) by Newton steps), so
+// V stays orthogonal and every sweep shrinks the off-diagonal mass by ~1e-7.
+// Lanes 0..3 update row/column k = lane.  Called by one whole warp.
+__device__ void jacobi4_warp(double (*A)[4], double (*V)[4]) {
+    const int lane = threadIdx.x & 31, k = lane & 3;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int r = 0; r < 4; ++r) {
+            dia = fma(A[r][r], A[r][r], dia);
+            for (int c = r + 1; c < 4; ++c) off = fma(A[r][c], A[r][c], off);
+        }
+        if (off <= 1e-40 * dia || off < 1e-300) break;
+        for (int p = 0; p < 3; ++p) {
+            for (int q = p + 1; q < 4; ++q) {
+                const double apq = A[p][q];
+                if (apq == 0.0) continue;
+                const float th = ((float)A[q][q] - (float)A[p][p]) / (2.f * (float)apq);
+                float tf = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+                if (!(fabsf(tf) <= 1.f)) tf = 0.f;  // non-finite estimate: skip the rotation
+                const double t = (double)tf;
+                const double x = fma(t, t, 1.0);
+                double r = (double)rsqrtf((float)x);
+                r = r * fma(-0.5 * x, r * r, 1.5);
+                r = r * fma(-0.5 * x, r * r, 1.5);
+                const double c = r, s = t * r;
+                __syncwarp();
+                if (lane < 4) {  // A <- A J : columns p, q of row k
+                    const double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+                __syncwarp();
+                if (lane < 4) {  // A <- J^T A : rows p, q of column k
+                    const double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                __syncwarp();
+            }
+        }
+    }
 }
 
 __device__ __forceinline__ void R32_of(const double q[4], float4 &R0, float4 &R1, float4 &R2) {
@@ -383,77 +363,152 @@ __device__ __forceinline__ void R32_of(const double q[4], float4 &R0, float4 &R1
     R2 = make_float4((float)R[8], 0.f, 0.f, 0.f);
 }
 
+// Shared state of the fit, owned by the cluster's rank-0 CTA.
+struct FitShared {
+    double q[4];
+    int done, status, nin, refits;
+};
+
+// Fit of one problem per thread-block cluster (gridDim.x = problems x C):
+// the C CTAs split the problem's slices round-robin and write per-slice
+// partial sums to global memory; after a cluster barrier, rank 0 sums the
+// slices in index order, solves the 4x4 eigenproblem and publishes q in its
+// shared memory, which the other CTAs read through distributed shared memory.
+// The result is independent of C and of the other problems in the batch.
 __global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restrict__ probs,
                                                           const LevelRef *__restrict__ lref, int level_stride,
                                                           const int32_t *__restrict__ kept_pos, int top_k,
                                                           int refit_iters, PairPool pool, uint8_t *member,
+                                                          double *slice_part, const int64_t *slice_off,
                                                           const ProbStats *__restrict__ stats,
                                                           rot_vote_result *results) {
-    const int p = blockIdx.x;
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int p = blockIdx.x / C;
     const ProbRef P = probs[p];
     const int last = P.levels;
     const LevelRef L = lref[p * level_stride + last];
     const int wpos = kept_pos[(p * level_stride + last) * top_k];
-    __shared__ double qs[4];
-    __shared__ double Bs[9];
-    __shared__ int s_m, s_chg, s_done, s_status, s_nin, s_refits;
-    __shared__ int list[kFitChunk];
+    __shared__ FitShared sh;
+    __shared__ double As[4][4], Vs[4][4];
+    __shared__ double Btot[11];
+    __shared__ int list[kFitSlice];
+    FitShared *root = cluster.map_shared_rank(&sh, 0);
     if (wpos < 0) {  // no cell at the last level (cannot happen for valid inputs)
-        if (threadIdx.x == 0) {
+        if (rank == 0 && threadIdx.x == 0) {
             rot_vote_result r = {};
             r.status = ROT_VOTE_EDEGENERATE;
             results[p] = r;
         }
-        return;
+        return;  // uniform across the cluster
     }
     const int64_t n = P.n;
     const float4 *pr = pool.pr + 2 * P.pool_off;
     uint8_t *mem = member + P.pool_off;
+    double *part = slice_part + 11 * slice_off[p];
+    const int64_t nslices = (n + kFitSlice - 1) / kFitSlice;
     double qc[4];
     {
         const double4_32a q4 = L.cells.q[wpos];
         qc[0] = q4.x; qc[1] = q4.y; qc[2] = q4.z; qc[3] = q4.w;
     }
-    // inliers of the winner: the voters of its cell (FP32 re-check decisions)
-    const float tau32 = (float)tau_cs(P.sin_d, P.cos_d, L.cells.trig[wpos]);
-    const float4 C0 = L.cells.R32[3 * wpos], C1 = L.cells.R32[3 * wpos + 1], C2 = L.cells.R32[3 * wpos + 2];
-    fit_pass(pr, mem, n, C0, C1, C2, tau32, true, list, Bs, &s_m, &s_chg);
-    if (threadIdx.x == 0) {
-        s_status = ROT_VOTE_OK;
-        s_done = 0;
-        s_refits = 0;
-        s_nin = s_m;
-        double u[10], q[4];
-        sumS_from_B(Bs, (double)s_m, u);
-        if (s_m < 2 || !smallest_eigvec(u, q)) {
-            for (int k = 0; k < 4; ++k) q[k] = qc[k];
-            s_status = ROT_VOTE_EDEGENERATE;
-            s_done = 1;
-        }
-        for (int k = 0; k < 4; ++k) qs[k] = q[k];
-    }
-    __syncthreads();
-    const float thr = (float)(P.sin_d * P.sin_d);  // refit rule: q^T S_i q <= sin^2(delta)
-    for (int t = 1; t <= refit_iters && !s_done; ++t) {
-        double q[4] = {qs[0], qs[1], qs[2], qs[3]};
-        float4 R0, R1, R2;
-        R32_of(q, R0, R1, R2);
-        fit_pass(pr, mem, n, R0, R1, R2, thr, false, list, Bs, &s_m, &s_chg);
-        if (threadIdx.x == 0) {
-            double u[10], qn[4];
-            sumS_from_B(Bs, (double)s_m, u);
-            if (s_m < 2 || s_chg == 0 || !smallest_eigvec(u, qn)) {
-                s_done = 1;
-            } else {
-                for (int k = 0; k < 4; ++k) qs[k] = qn[k];
-                s_nin = s_m;
-                s_refits = t;
+    if (threadIdx.x < 16) Vs[threadIdx.x >> 2][threadIdx.x & 3] = (threadIdx.x >> 2) == (threadIdx.x & 3) ? 1.0 : 0.0;
+
+    // iteration 0: the voters of the winning cell (FP32 re-check decisions);
+    // iterations t >= 1: q_{t-1}^T S_i q_{t-1} <= sin^2(delta)
+    const float thr_refit = (float)(P.sin_d * P.sin_d);
+    float4 R0 = L.cells.R32[3 * wpos], R1 = L.cells.R32[3 * wpos + 1], R2 = L.cells.R32[3 * wpos + 2];
+    float thr = (float)tau_cs(P.sin_d, P.cos_d, L.cells.trig[wpos]);
+    for (int t = 0; t <= refit_iters; ++t) {
+        for (int64_t sl = rank; sl < nslices; sl += C)
+            fit_slice(pr, mem, n, sl * kFitSlice, R0, R1, R2, thr, t == 0, list, part + 11 * sl);
+        cluster.sync();  // every slice partial is written
+        if (rank == 0) {
+            if (threadIdx.x < 11) {  // slices summed in index order
+                double acc = 0.0;
+                for (int64_t sl = 0; sl < nslices; ++sl) acc += part[11 * sl + threadIdx.x];
+                Btot[threadIdx.x] = acc;
+            }
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                const int m = (int)Btot[9], chg = (int)Btot[10];
+                double u[10];
+                sumS_from_B(Btot, (double)m, u);
+                const double tr = u[0] + u[1] + u[2] + u[3];
+                bool stop = false, degenerate = false;
+                if (t == 0) {
+                    degenerate = m < 2;
+                } else {
+                    stop = m < 2 || chg == 0;
+                }
+                if (!stop && !degenerate) {
+                    // the sum in the current eigenbasis (warm start): A' = V^T A V, two 16-lane steps
+                    const double Ain[4][4] = {{u[0], u[4], u[5], u[6]}, {u[4], u[1], u[7], u[8]},
+                                              {u[5], u[7], u[2], u[9]}, {u[6], u[8], u[9], u[3]}};
+                    const int er = (threadIdx.x >> 2) & 3, ec = threadIdx.x & 3;
+                    double w = 0.0;
+                    if (threadIdx.x < 16)
+                        for (int a = 0; a < 4; ++a) w = fma(Ain[er][a], Vs[a][ec], w);  // W = A V
+                    __syncwarp();
+                    if (threadIdx.x < 16) As[er][ec] = w;
+                    __syncwarp();
+                    double x = 0.0;
+                    if (threadIdx.x < 16)
+                        for (int a = 0; a < 4; ++a) x = fma(Vs[a][er], As[a][ec], x);  // V^T W
+                    const double vsave = threadIdx.x < 16 ? Vs[er][ec] : 0.0;
+                    __syncwarp();
+                    if (threadIdx.x < 16) As[er][ec] = x;
+                    __syncwarp();
+                    jacobi4_warp(As, Vs);
+                    __syncwarp();
+                    // smallest and second-smallest eigenvalue
+                    int i0 = 0;
+                    for (int k = 1; k < 4; ++k)
+                        if (As[k][k] < As[i0][i0]) i0 = k;
+                    double l1 = DBL_MAX;
+                    for (int k = 0; k < 4; ++k)
+                        if (k != i0 && As[k][k] < l1) l1 = As[k][k];
+                    const bool gap_ok = (l1 - As[i0][i0]) > 1e-12 * tr;
+                    if (threadIdx.x == 0) {
+                        if (!gap_ok) {
+                            if (t == 0) degenerate = true;
+                            else stop = true;
+                        }
+                        if (!degenerate && !stop) {
+                            for (int r = 0; r < 4; ++r) sh.q[r] = Vs[r][i0];
+                            sh.nin = m;
+                            sh.refits = t;
+                        }
+                    }
+                    __syncwarp();
+                    if (!gap_ok && threadIdx.x < 16) Vs[er][ec] = vsave;  // keep the previous basis
+                }
+                if (threadIdx.x == 0) {
+                    if (t == 0) {
+                        sh.status = degenerate ? ROT_VOTE_EDEGENERATE : ROT_VOTE_OK;
+                        if (degenerate) {
+                            for (int r = 0; r < 4; ++r) sh.q[r] = qc[r];
+                            sh.nin = m;
+                            sh.refits = 0;
+                        }
+                        sh.done = degenerate || refit_iters == 0;
+                    } else {
+                        sh.done = stop || t == refit_iters;
+                    }
+                }
             }
         }
-        __syncthreads();
+        cluster.sync();  // rank 0 has published q / done
+        if (root->done) break;  // uniform: every CTA reads rank 0's flag
+        double q[4] = {root->q[0], root->q[1], root->q[2], root->q[3]};
+        R32_of(q, R0, R1, R2);
+        thr = thr_refit;
+        cluster.sync();  // rank 0's state is not rewritten before everyone has read it
     }
-    if (threadIdx.x == 0) {
-        double q[4] = {qs[0], qs[1], qs[2], qs[3]};
+    if (rank == 0 && threadIdx.x == 0) {
+        double q[4] = {sh.q[0], sh.q[1], sh.q[2], sh.q[3]};
         canonical(q);
         double R[9];
         quat_to_R(q, R);
@@ -461,18 +516,19 @@ __global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restr
         for (int k = 0; k < 4; ++k) r.q[k] = q[k];
         for (int k = 0; k < 9; ++k) r.R[k] = R[k];
         r.best_count = L.counts[wpos];
-        r.inliers = s_nin;
+        r.inliers = sh.nin;
         r.best_cell = L.cells.idx[wpos];
         r.best_level = last;
-        r.refits = s_refits;
+        r.refits = sh.refits;
         r.tests = (int64_t)stats[p].tests;
         r.rechecked = (int64_t)stats[p].rechecked;
         r.ambiguous = (int64_t)stats[p].ambiguous;
-        r.status = stats[p].invalid ? ROT_VOTE_EINVAL : s_status;
+        r.status = stats[p].invalid ? ROT_VOTE_EINVAL : sh.status;
         r.ms_gpu = 0.f;
         r.latency_ms = 0.f;
         results[p] = r;
     }
+    cluster.sync();  // rank 0's shared memory stays alive until every CTA is done reading it
 }
 
 }  // namespace
@@ -494,13 +550,28 @@ cudaError_t launch_topk(const ProbRef *probs, int nprob, const LevelRef *lref, i
     return cudaGetLastError();
 }
 
+int fit_slices(int64_t n) { return (int)((n + kFitSlice - 1) / kFitSlice); }
+
 cudaError_t launch_fit(const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride,
                        const int32_t *kept_pos, int top_k, int refit_iters, PairPool pool, uint8_t *member,
-                       const ProbStats *stats, rot_vote_result *results, cudaStream_t s) {
+                       double *slice_part, const int64_t *slice_off, int cluster, const ProbStats *stats,
+                       rot_vote_result *results, cudaStream_t s) {
     if (nprob <= 0) return cudaSuccess;
-    fit_kernel<<<nprob, kFitThreads, 0, s>>>(probs, lref, level_stride, kept_pos, top_k, refit_iters, pool, member,
-                                            stats, results);
-    return cudaGetLastError();
+    if (cluster < 1 || cluster > kFitMaxCluster) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)(nprob * cluster));
+    lc.blockDim = dim3(kFitThreads);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, fit_kernel, probs, lref, level_stride, kept_pos, top_k, refit_iters, pool, member,
+                              slice_part, slice_off, stats, results);
 }
 
 }  // namespace rv

@@ -154,6 +154,21 @@ __host__ __device__ constexpr uint32_t idesc_f16() {
     return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 }
 
+// cnt + (x >> 31) as an integer multiply-add: hi32(x * 2) + cnt (FMA pipe,
+// leaving the ALU pipe to the band check).
+__device__ __forceinline__ uint32_t add_sign(uint32_t cnt, uint32_t x) {
+    asm("mad.hi.u32 %0, %1, 2, %0;" : "+r"(cnt) : "r"(x));
+    return cnt;
+}
+// min(m, |x|, |y|) in one three-input minimum.
+__device__ __forceinline__ float min3_abs(float m, float x, float y) {
+    float r;
+    asm("{\n .reg .f32 ax, ay;\n abs.f32 ax, %2;\n abs.f32 ay, %3;\n min.f32 %0, %1, ax, ay;\n}"
+        : "=f"(r)
+        : "f"(m), "f"(x), "f"(y));
+    return r;
+}
+
 __device__ __forceinline__ int tc_off(int r, int k) { return (k >> 3) * 2048 + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
 
 template <bool BF16>
@@ -446,11 +461,13 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     tmem_ld_wait(r);
                     tmem_ld_wait(r2);
                     float mn = 3.0f;
+                    uint32_t c2 = 0;
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
-                        cnt += (int)(r[e] >> 31) + (int)(r2[e] >> 31);
-                        mn = fminf(mn, fminf(fabsf(__uint_as_float(r[e])), fabsf(__uint_as_float(r2[e]))));
+                        c2 = add_sign(add_sign(c2, r[e]), r2[e]);
+                        mn = min3_abs(mn, __uint_as_float(r[e]), __uint_as_float(r2[e]));
                     }
+                    cnt += (int)c2;
                     if (mn <= band) {  // rare: re-check the flagged tests of these 64 columns
                         // flag and sign masks built with constant register indices only
                         uint32_t f0 = 0, f1 = 0, s0 = 0, s1 = 0;

@@ -291,6 +291,19 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     const size_t o_kept = reserve(sizeof(int32_t) * (size_t)P * S * K);
     const size_t o_cand = reserve(sizeof(Cand) * ((size_t)P * pl.chunks_per_prob * K + (size_t)P * K));
     const size_t o_res = reserve(sizeof(rot_vote_result) * P);
+    // fit: per-slice partial sums (11 doubles per 4096-pair slice) and slice offsets
+    pl.slice_off_h.assign(P, 0);
+    int64_t nsl = 0, maxn = 0;
+    for (int k = 0; k < P; ++k) {
+        pl.slice_off_h[k] = nsl;
+        nsl += fit_slices(pl.probs_h[k].n);
+        maxn = std::max<int64_t>(maxn, pl.probs_h[k].n);
+    }
+    const size_t o_slice = reserve(sizeof(double) * 11 * (size_t)std::max<int64_t>(1, nsl));
+    const size_t o_sloff = reserve(sizeof(int64_t) * P);
+    // cluster size of the fit: enough CTAs for the largest problem's slices, power of two <= 8
+    pl.fit_cluster = 1;
+    while (pl.fit_cluster < 8 && (int64_t)pl.fit_cluster * 2 * 4096 < maxn) pl.fit_cluster *= 2;
     // child tables: P x max_levels x child_cap cells
     const size_t nchild = (size_t)P * std::max(1, max_levels) * child_cap;
     const size_t o_cq = reserve(sizeof(double4_32a) * nchild);
@@ -324,6 +337,8 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     pl.d_kept = (int32_t *)(B + o_kept);
     pl.d_cand = (Cand *)(B + o_cand);
     pl.d_res = (rot_vote_result *)(B + o_res);
+    pl.d_slice = (double *)(B + o_slice);
+    pl.d_sloff = (int64_t *)(B + o_sloff);
     pl.d_err = (int *)(B + o_err);
 
     // pair-prep tiles
@@ -403,7 +418,8 @@ int Context::upload(Wave &w, const rot_vote_problem *p, const std::vector<int> &
     const int P = pl.nprob, S = pl.stride;
     // descriptor block: probs, lref, items, tiles -> contiguous in the workspace?  They are
     // separate ranges; pack them into one pinned staging block and copy each range.
-    size_t hb = sizeof(ProbRef) * P + sizeof(LevelRef) * (size_t)P * S + sizeof(int2) * pl.tiles_h.size();
+    size_t hb = sizeof(ProbRef) * P + sizeof(LevelRef) * (size_t)P * S + sizeof(int2) * pl.tiles_h.size() +
+                sizeof(int64_t) * P + 16 * 8;
     for (int lev = 0; lev < S; ++lev) hb += sizeof(VoteItem) * pl.items_h[lev].size();
     int rc = w.ensure_pinned(hb + 4096);
     if (rc != ROT_VOTE_OK) return fail(rc, "pinned staging allocation failed");
@@ -421,6 +437,7 @@ int Context::upload(Wave &w, const rot_vote_problem *p, const std::vector<int> &
     for (int lev = 0; lev < S && e == cudaSuccess; ++lev)
         e = put(pl.d_items[lev], pl.items_h[lev].data(), sizeof(VoteItem) * pl.items_h[lev].size());
     if (e == cudaSuccess) e = put(pl.d_tiles, pl.tiles_h.data(), sizeof(int2) * pl.tiles_h.size());
+    if (e == cudaSuccess) e = put(pl.d_sloff, pl.slice_off_h.data(), sizeof(int64_t) * pl.slice_off_h.size());
     if (e != cudaSuccess) return cuda_fail(e, "uploading descriptors");
     if (!pl.inputs_on_device) {
         // host inputs: direct copies from pinned caller memory when few problems, else pack
@@ -495,8 +512,8 @@ int Context::enqueue_pipeline(Wave &w) {
     }
     mark(4, -1);
     if (e == cudaSuccess)
-        e = launch_fit(pl.d_probs, P, pl.d_lref, S, pl.d_kept, K, cfg.refit_iters, pl.pool, pl.d_member, pl.d_stats,
-                       pl.d_res, w.stream);
+        e = launch_fit(pl.d_probs, P, pl.d_lref, S, pl.d_kept, K, cfg.refit_iters, pl.pool, pl.d_member,
+                       pl.d_slice, pl.d_sloff, pl.fit_cluster, pl.d_stats, pl.d_res, w.stream);
     done();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(w.results_h, pl.d_res, sizeof(rot_vote_result) * P, cudaMemcpyDeviceToHost, w.stream);

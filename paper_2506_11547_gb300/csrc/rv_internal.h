@@ -123,8 +123,12 @@ cudaError_t launch_children(const ProbRef *probs, int nprob, const LevelRef *lre
                             int top_k, const int32_t *kept_pos, const int32_t *nkept, cudaStream_t s);
 
 // Fit: winner voters, FP64 sum of S_i, Jacobi, refit loop; writes results.
+// One thread-block cluster of `cluster` CTAs per problem; slice_part holds
+// 11 doubles per 4096-pair slice, problem p's slices starting at slice_off[p].
+int fit_slices(int64_t n);
 cudaError_t launch_fit(const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride,
                        const int32_t *kept_pos, int top_k, int refit_iters, PairPool pool, uint8_t *member,
-                       const ProbStats *stats, rot_vote_result *results, cudaStream_t s);
+                       double *slice_part, const int64_t *slice_off, int cluster, const ProbStats *stats,
+                       rot_vote_result *results, cudaStream_t s);
 
 }  // namespace rv

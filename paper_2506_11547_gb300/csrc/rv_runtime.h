@@ -43,6 +43,8 @@ struct Plan {
     std::vector<std::vector<VoteItem>> items_h;
     std::vector<int2> tiles_h;
     std::vector<int64_t> in_off;
+    std::vector<int64_t> slice_off_h;
+    int fit_cluster = 1;
     // device pointers (inside the wave's workspace)
     ProbRef *d_probs = nullptr;
     LevelRef *d_lref = nullptr;
@@ -56,6 +58,8 @@ struct Plan {
     ProbStats *d_stats = nullptr;
     Cand *d_cand = nullptr;
     rot_vote_result *d_res = nullptr;
+    double *d_slice = nullptr;
+    int64_t *d_sloff = nullptr;
     int *d_err = nullptr;
 };
 

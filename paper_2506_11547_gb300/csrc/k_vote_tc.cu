@@ -154,18 +154,17 @@ __host__ __device__ constexpr uint32_t idesc_f16() {
     return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-// cnt + (x >> 31) as an integer multiply-add: hi32(x * 2) + cnt (FMA pipe,
-// leaving the ALU pipe to the band check).
-__device__ __forceinline__ uint32_t add_sign(uint32_t cnt, uint32_t x) {
-    asm("mad.hi.u32 %0, %1, 2, %0;" : "+r"(cnt) : "r"(x));
+// cnt + (x >> 31) as an integer multiply-add hi32(x * two) + cnt with
+// two == 2 passed at run time, so it stays a multiply-add on the FMA pipe and
+// leaves the half-rate ALU pipe to the band check.
+__device__ __forceinline__ uint32_t add_sign(uint32_t cnt, uint32_t x, uint32_t two) {
+    asm("mad.hi.u32 %0, %1, %2, %0;" : "+r"(cnt) : "r"(x), "r"(two));
     return cnt;
 }
-// min(m, |x|, |y|) in one three-input minimum.
-__device__ __forceinline__ float min3_abs(float m, float x, float y) {
+// min(m, x, y) in one three-input minimum (inputs are squares, so no |.|).
+__device__ __forceinline__ float min3(float m, float x, float y) {
     float r;
-    asm("{\n .reg .f32 ax, ay;\n abs.f32 ax, %2;\n abs.f32 ay, %3;\n min.f32 %0, %1, ax, ay;\n}"
-        : "=f"(r)
-        : "f"(m), "f"(x), "f"(y));
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(m), "f"(x), "f"(y));
     return r;
 }
 
@@ -229,7 +228,7 @@ template <int G, int KSTEPS, bool BF16>
 __global__ void __launch_bounds__(128 + 128 * G, 1)
     vote_tc_kernel(const VoteItem *__restrict__ items, int n_items, const ProbRef *__restrict__ probs,
                    const LevelRef *__restrict__ lref, int level_stride, int level, PairPool pool, ProbStats *stats,
-                   float band_req, int *err_flag) {
+                   float band_req, int *err_flag, uint32_t two) {
     constexpr int kTileBytes = kPairTile * 16 * KSTEPS * 2;  // 128 rows x K x 2 B
     constexpr int K = 16 * KSTEPS;
     constexpr uint32_t IDESC = idesc_f16<BF16>();
@@ -432,6 +431,8 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 tau = (float)tau_cs(v.P.sin_d, v.P.cos_d, v.L.cells.trig[pos]);
                 band = fmaxf(cell_band<KSTEPS, BF16>(m), band_req);
             }
+            // D^2 <= band2 whenever |D| <= band (rounding of the square included)
+            const float band2 = band > 0.f ? band * band * 1.0001f : -1.f;
             int cnt = 0;
             unsigned rechecked = 0, ambiguous = 0;
             float4 R0 = make_float4(0, 0, 0, 0), R1 = R0, R2 = R0;
@@ -441,6 +442,38 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 R2 = v.L.cells.R32[3 * pos + 2];
             }
             const int64_t gbase = v.P.pool_off + v.W.pair_begin;
+            // counts the 32 values of one chunk (columns col0..col0+31 of tile t):
+            // sign bits with an integer multiply-add, the band by the minimum of D^2;
+            // flagged values (rare) get the FP32 re-check
+            auto chunk_count = [&](const uint32_t (&r)[32], int col0) {
+                float mn = 16.0f;  // min of D^2 (|D| <= 4)
+                uint32_t c2 = 0;
+#pragma unroll
+                for (int e = 0; e < 32; e += 2) {
+                    c2 = add_sign(add_sign(c2, r[e], two), r[e + 1], two);
+                    const float x = __uint_as_float(r[e]), y = __uint_as_float(r[e + 1]);
+                    mn = min3(mn, x * x, y * y);
+                }
+                cnt += (int)c2;
+                if (mn <= band2) {
+                    uint32_t fm = 0, sm = 0;  // flag and sign masks, constant register indices only
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        fm |= (uint32_t)(fabsf(__uint_as_float(r[e])) <= band) << e;
+                        sm |= (r[e] >> 31) << e;
+                    }
+                    while (fm) {
+                        const int e = __ffs((int)fm) - 1;
+                        fm &= fm - 1;
+                        const int64_t gp = gbase + (int64_t)t * kPairTile + col0 + e;
+                        const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
+                        const float vv = recheck_v(R0, R1, R2, p0, p1);
+                        cnt += (int)(vv <= tau) - (int)((sm >> e) & 1u);
+                        ++rechecked;
+                        ambiguous += fabsf(vv - tau) <= kAmbig;
+                    }
+                }
+            };
             for (; t < v.ntiles; t += G) {
                 const int64_t jj = j0 + t;
                 const int as = (int)(jj % kNAcc);
@@ -453,45 +486,21 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 }
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(as * 128);
-#pragma unroll 1
-                for (int c = 0; c < 4; c += 2) {  // two 32-column loads per wait
-                    uint32_t r[32], r2[32];
-                    tmem_ld32(taddr + 32 * c, r);
-                    tmem_ld32(taddr + 32 * c + 32, r2);
-                    tmem_ld_wait(r);
-                    tmem_ld_wait(r2);
-                    float mn = 3.0f;
-                    uint32_t c2 = 0;
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        c2 = add_sign(add_sign(c2, r[e]), r2[e]);
-                        mn = min3_abs(mn, __uint_as_float(r[e]), __uint_as_float(r2[e]));
-                    }
-                    cnt += (int)c2;
-                    if (mn <= band) {  // rare: re-check the flagged tests of these 64 columns
-                        // flag and sign masks built with constant register indices only
-                        uint32_t f0 = 0, f1 = 0, s0 = 0, s1 = 0;
-#pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            f0 |= (uint32_t)(fabsf(__uint_as_float(r[e])) <= band) << e;
-                            f1 |= (uint32_t)(fabsf(__uint_as_float(r2[e])) <= band) << e;
-                            s0 |= (r[e] >> 31) << e;
-                            s1 |= (r2[e] >> 31) << e;
-                        }
-                        uint64_t fm = ((uint64_t)f1 << 32) | f0;
-                        const uint64_t sm = ((uint64_t)s1 << 32) | s0;
-                        while (fm) {
-                            const int e = __ffsll((long long)fm) - 1;
-                            fm &= fm - 1;
-                            const int64_t gp = gbase + (int64_t)t * kPairTile + 32 * c + e;
-                            const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
-                            const float vv = recheck_v(R0, R1, R2, p0, p1);
-                            cnt += (int)(vv <= tau) - (int)((sm >> e) & 1ull);
-                            ++rechecked;
-                            ambiguous += fabsf(vv - tau) <= kAmbig;
-                        }
-                    }
-                }
+                // software pipeline over the tile's four 32-column chunks: the load
+                // of chunk c+1 is in flight while chunk c is counted
+                uint32_t ra[32], rb[32];
+                tmem_ld32(taddr, ra);
+                tmem_ld_wait(ra);
+                tmem_ld32(taddr + 32, rb);
+                chunk_count(ra, 0);
+                tmem_ld_wait(rb);
+                tmem_ld32(taddr + 64, ra);
+                chunk_count(rb, 32);
+                tmem_ld_wait(ra);
+                tmem_ld32(taddr + 96, rb);
+                chunk_count(ra, 64);
+                tmem_ld_wait(rb);
+                chunk_count(rb, 96);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acc_empty[as]);
@@ -533,7 +542,7 @@ cudaError_t launch_t(const VoteItem *items, int n_items, const ProbRef *probs, c
                      int level_stride, int level, PairPool pool, ProbStats *stats, float band_req, int grid,
                      int *err_flag, cudaStream_t s) {
     vote_tc_kernel<G, KSTEPS, BF16><<<grid, 128 + 128 * G, kSmemBytes, s>>>(items, n_items, probs, lref, level_stride,
-                                                                           level, pool, stats, band_req, err_flag);
+                                                                           level, pool, stats, band_req, err_flag, 2u);
     return cudaGetLastError();
 }
 

@@ -132,8 +132,9 @@ __global__ void pair_prep_kernel(const ProbRef *__restrict__ probs, const int2 *
         p0 = make_float4(a0, a1, a2, b0);
         p1 = make_float4(b1, b2, 0.25f * ((na + nb) - 2.f), 0.f);
     }
-#pragma unroll
-    for (int q = 0; q < 5; ++q) pool.s32[5 * g + q] = make_float4(s[2 * q], s[2 * q], s[2 * q + 1], s[2 * q + 1]);
+    pool.s32[3 * g + 0] = make_float4(s[0], s[1], s[2], s[3]);
+    pool.s32[3 * g + 1] = make_float4(s[4], s[5], s[6], s[7]);
+    pool.s32[3 * g + 2] = make_float4(s[8], s[9], 0.f, 0.f);
     pool.pr[2 * g + 0] = p0;
     pool.pr[2 * g + 1] = p1;
     if (tc_prec != ROT_PREC_FP32 && pool.tcb) {

@@ -2,13 +2,10 @@
 //
 // For cell c and pair i the test is v = m(q_c) . s_i <= tau_c (q^T S_i q as a
 // 10-term dot product of the cell's monomials and the pair's S entries).  Each
-// thread owns CPT cells, taken two at a time: their monomials are packed as
-// (m_k(c0), m_k(c1)) pairs and every pair's S entries are stored duplicated,
-// (s_k, s_k), so one packed fma.rn.f32x2 advances two tests.  The block
-// streams the item's pairs through shared memory with cp.async double
-// buffering; d = fma-chain(m, s, -tau), count += signbit(d).  Each lane of the
-// packed FMA rounds exactly like a scalar fmaf, so the arithmetic is the FP32
-// FMA chain of the plain form.
+// thread owns CPT cells (their monomials and thresholds live in registers);
+// the block streams the item's pairs through shared memory with cp.async
+// double buffering, and every thread tests its cells against each pair:
+// d = fma-chain(m, s, -tau), count += signbit(d).
 //
 // Exactness: |d - (v - tau)_exact| <= kBandFP32 (input rounding of m, s, tau
 // plus ten FMA roundings, with |m|_1 <= 4 and sum |m_k s_k| <= 1.9).  Tests
@@ -30,30 +27,15 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Two IEEE FP32 fused multiply-adds in one instruction.
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-    unsigned long long ra, rb, rc, rd;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
-    float2 d;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
-    return d;
-}
-
 constexpr int kTP = 128;     // pairs per shared-memory tile
 constexpr int kThreads = 128;
-constexpr int kS4 = 5;       // float4 per pair: (s0 s0 s1 s1) ... (s8 s8 s9 s9)
 
 template <int CPT>
 __global__ void __launch_bounds__(kThreads, 4) vote_simt_kernel(const VoteItem *__restrict__ items, int n_items,
-                                                                const ProbRef *__restrict__ probs,
-                                                                const LevelRef *__restrict__ lref, int level_stride,
-                                                                int level, PairPool pool, ProbStats *stats) {
-    static_assert(CPT % 2 == 0, "cells are processed two at a time");
-    constexpr int H = CPT / 2;
-    __shared__ __align__(16) float4 sh[2][kTP * kS4];
+                                                             const ProbRef *__restrict__ probs,
+                                                             const LevelRef *__restrict__ lref, int level_stride,
+                                                             int level, PairPool pool, ProbStats *stats) {
+    __shared__ __align__(16) float4 sh[2][kTP * 3];
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const VoteItem W = items[it];
         const ProbRef P = probs[W.prob];
@@ -63,106 +45,95 @@ __global__ void __launch_bounds__(kThreads, 4) vote_simt_kernel(const VoteItem *
         if (W.cell_begin >= ncell) continue;
         // the item's kSimtItemCells cells, CPT x kThreads at a time
         const int cell_end = min(ncell, W.cell_begin + kSimtItemCells);
-        for (int sub = W.cell_begin; sub < cell_end; sub += CPT * kThreads) {
-            float2 m[H][10], tau0[H];
-            float tau[CPT];
-            int cnt[CPT];
-            int pos[CPT];
+      for (int sub = W.cell_begin; sub < cell_end; sub += CPT * kThreads) {
+        float m[CPT][10], tau[CPT];
+        int cnt[CPT];
+        int pos[CPT];
 #pragma unroll
-            for (int k = 0; k < CPT; ++k) {
-                pos[k] = sub + (int)threadIdx.x + k * kThreads;
-                cnt[k] = 0;
-                float mk[10];
-                if (pos[k] < cell_end) {
-                    const float4 m0 = L.cells.m32[3 * pos[k]], m1 = L.cells.m32[3 * pos[k] + 1],
-                                 m2 = L.cells.m32[3 * pos[k] + 2];
-                    mk[0] = m0.x; mk[1] = m0.y; mk[2] = m0.z; mk[3] = m0.w;
-                    mk[4] = m1.x; mk[5] = m1.y; mk[6] = m1.z; mk[7] = m1.w;
-                    mk[8] = m2.x; mk[9] = m2.y;
-                    tau[k] = (float)tau_cs(P.sin_d, P.cos_d, L.cells.trig[pos[k]]);
-                } else {  // absent cell: d = 1 for every pair, never counted, never in the band
+        for (int k = 0; k < CPT; ++k) {
+            pos[k] = sub + (int)threadIdx.x + k * kThreads;
+            cnt[k] = 0;
+            if (pos[k] < cell_end) {
+                const float4 m0 = L.cells.m32[3 * pos[k]], m1 = L.cells.m32[3 * pos[k] + 1],
+                             m2 = L.cells.m32[3 * pos[k] + 2];
+                m[k][0] = m0.x; m[k][1] = m0.y; m[k][2] = m0.z; m[k][3] = m0.w;
+                m[k][4] = m1.x; m[k][5] = m1.y; m[k][6] = m1.z; m[k][7] = m1.w;
+                m[k][8] = m2.x; m[k][9] = m2.y;
+                tau[k] = (float)tau_cs(P.sin_d, P.cos_d, L.cells.trig[pos[k]]);
+            } else {  // absent cell: d = 1 for every pair, never counted, never in the band
 #pragma unroll
-                    for (int e = 0; e < 10; ++e) mk[e] = 0.f;
-                    tau[k] = -1.f;
-                }
-#pragma unroll
-                for (int e = 0; e < 10; ++e) {
-                    if (k & 1) m[k >> 1][e].y = mk[e];
-                    else m[k >> 1][e].x = mk[e];
-                }
+                for (int e = 0; e < 10; ++e) m[k][e] = 0.f;
+                tau[k] = -1.f;
             }
-#pragma unroll
-            for (int h = 0; h < H; ++h) tau0[h] = make_float2(-tau[2 * h], -tau[2 * h + 1]);
+        }
+        const int64_t g0 = P.pool_off + W.pair_begin;
+        const int npairs = W.pair_end - W.pair_begin;        // multiple of kTP (pool padding)
+        const int ntiles = (npairs + kTP - 1) / kTP;
+        const float4 *src = pool.s32 + 3 * g0;
+        unsigned rechecked = 0, ambiguous = 0;
 
-            const int64_t g0 = P.pool_off + W.pair_begin;
-            const int npairs = W.pair_end - W.pair_begin;  // multiple of kTP (pool padding)
-            const int ntiles = (npairs + kTP - 1) / kTP;
-            const float4 *src = pool.s32 + kS4 * g0;
-            unsigned rechecked = 0, ambiguous = 0;
-
-            auto load_tile = [&](int buf, int t) {
-                const float4 *gsrc = src + (int64_t)t * kTP * kS4;
-                for (int e = threadIdx.x; e < kTP * kS4; e += kThreads) cp_async16(&sh[buf][e], gsrc + e);
-            };
-            load_tile(0, 0);
+        auto load_tile = [&](int buf, int t) {
+            const float4 *gsrc = src + (int64_t)t * kTP * 3;
+            for (int e = threadIdx.x; e < kTP * 3; e += kThreads) cp_async16(&sh[buf][e], gsrc + e);
+        };
+        load_tile(0, 0);
+        cp_async_commit();
+        for (int t = 0; t < ntiles; ++t) {
+            if (t + 1 < ntiles) load_tile((t + 1) & 1, t + 1);
             cp_async_commit();
-            for (int t = 0; t < ntiles; ++t) {
-                if (t + 1 < ntiles) load_tile((t + 1) & 1, t + 1);
-                cp_async_commit();
-                cp_async_wait<1>();
-                __syncthreads();
-                const float4 *S = sh[t & 1];
+            cp_async_wait<1>();
+            __syncthreads();
+            const float4 *S = sh[t & 1];
 #pragma unroll 2
-                for (int j = 0; j < kTP; ++j) {
-                    float2 s2[10];
+            for (int j = 0; j < kTP; ++j) {
+                const float4 s0 = S[3 * j], s1 = S[3 * j + 1], s2 = S[3 * j + 2];
+                float d[CPT];
+                bool flag = false;
 #pragma unroll
-                    for (int q = 0; q < kS4; ++q) {
-                        const float4 v4 = S[kS4 * j + q];
-                        s2[2 * q] = make_float2(v4.x, v4.y);
-                        s2[2 * q + 1] = make_float2(v4.z, v4.w);
-                    }
-                    float d[CPT];
-                    float mn = 3.0f;
+                for (int k = 0; k < CPT; ++k) {
+                    float x = fmaf(m[k][0], s0.x, -tau[k]);
+                    x = fmaf(m[k][1], s0.y, x);
+                    x = fmaf(m[k][2], s0.z, x);
+                    x = fmaf(m[k][3], s0.w, x);
+                    x = fmaf(m[k][4], s1.x, x);
+                    x = fmaf(m[k][5], s1.y, x);
+                    x = fmaf(m[k][6], s1.z, x);
+                    x = fmaf(m[k][7], s1.w, x);
+                    x = fmaf(m[k][8], s2.x, x);
+                    x = fmaf(m[k][9], s2.y, x);
+                    d[k] = x;
+                    cnt[k] += (int)(__float_as_uint(x) >> 31);
+                    flag |= fabsf(x) <= kBandFP32;
+                }
+                if (flag) {  // rare: re-check the flagged tests of this pair
+                    const int64_t gp = g0 + (int64_t)t * kTP + j;
+                    const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
 #pragma unroll
-                    for (int h = 0; h < H; ++h) {
-                        float2 x = ffma2(m[h][0], s2[0], tau0[h]);
-#pragma unroll
-                        for (int e = 1; e < 10; ++e) x = ffma2(m[h][e], s2[e], x);
-                        d[2 * h] = x.x;
-                        d[2 * h + 1] = x.y;
-                        cnt[2 * h] += (int)(__float_as_uint(x.x) >> 31);
-                        cnt[2 * h + 1] += (int)(__float_as_uint(x.y) >> 31);
-                        mn = fminf(mn, fminf(fabsf(x.x), fabsf(x.y)));
-                    }
-                    if (mn <= kBandFP32) {  // rare: re-check the flagged tests of this pair
-                        const int64_t gp = g0 + (int64_t)t * kTP + j;
-                        const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
-#pragma unroll
-                        for (int k = 0; k < CPT; ++k) {
-                            if (fabsf(d[k]) <= kBandFP32) {
-                                const float4 R0 = L.cells.R32[3 * pos[k]], R1 = L.cells.R32[3 * pos[k] + 1],
-                                             R2 = L.cells.R32[3 * pos[k] + 2];
-                                const float v = recheck_v(R0, R1, R2, p0, p1);
-                                const int vote = v <= tau[k];
-                                cnt[k] += vote - (int)(__float_as_uint(d[k]) >> 31);
-                                ++rechecked;
-                                ambiguous += fabsf(v - tau[k]) <= kAmbig;
-                            }
+                    for (int k = 0; k < CPT; ++k) {
+                        if (fabsf(d[k]) <= kBandFP32) {
+                            const float4 R0 = L.cells.R32[3 * pos[k]], R1 = L.cells.R32[3 * pos[k] + 1],
+                                         R2 = L.cells.R32[3 * pos[k] + 2];
+                            const float v = recheck_v(R0, R1, R2, p0, p1);
+                            const int vote = v <= tau[k];
+                            cnt[k] += vote - (int)(__float_as_uint(d[k]) >> 31);
+                            ++rechecked;
+                            ambiguous += fabsf(v - tau[k]) <= kAmbig;
                         }
                     }
                 }
-                __syncthreads();
             }
-#pragma unroll
-            for (int k = 0; k < CPT; ++k)
-                if (pos[k] < cell_end && cnt[k] != 0) atomicAdd(&L.counts[pos[k]], cnt[k]);
-            const unsigned rc = __reduce_add_sync(0xffffffffu, rechecked);
-            const unsigned am = __reduce_add_sync(0xffffffffu, ambiguous);
-            if ((threadIdx.x & 31) == 0) {
-                if (rc) atomicAdd(&stats[W.prob].rechecked, (unsigned long long)rc);
-                if (am) atomicAdd(&stats[W.prob].ambiguous, (unsigned long long)am);
-            }
+            __syncthreads();
         }
+#pragma unroll
+        for (int k = 0; k < CPT; ++k)
+            if (pos[k] < cell_end && cnt[k] != 0) atomicAdd(&L.counts[pos[k]], cnt[k]);
+        const unsigned rc = __reduce_add_sync(0xffffffffu, rechecked);
+        const unsigned am = __reduce_add_sync(0xffffffffu, ambiguous);
+        if ((threadIdx.x & 31) == 0) {
+            if (rc) atomicAdd(&stats[W.prob].rechecked, (unsigned long long)rc);
+            if (am) atomicAdd(&stats[W.prob].ambiguous, (unsigned long long)am);
+        }
+      }
     }
 }
 

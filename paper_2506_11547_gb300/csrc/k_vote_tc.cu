@@ -161,10 +161,12 @@ __device__ __forceinline__ uint32_t add_sign(uint32_t cnt, uint32_t x, uint32_t 
     asm("mad.hi.u32 %0, %1, %2, %0;" : "+r"(cnt) : "r"(x), "r"(two));
     return cnt;
 }
-// min(m, x, y) in one three-input minimum (inputs are squares, so no |.|).
-__device__ __forceinline__ float min3(float m, float x, float y) {
+// min(m, |x|, |y|) in one three-input minimum.
+__device__ __forceinline__ float min3_abs(float m, float x, float y) {
     float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(m), "f"(x), "f"(y));
+    asm("{\n .reg .f32 ax, ay;\n abs.f32 ax, %2;\n abs.f32 ay, %3;\n min.f32 %0, %1, ax, ay;\n}"
+        : "=f"(r)
+        : "f"(m), "f"(x), "f"(y));
     return r;
 }
 
@@ -222,6 +224,80 @@ __device__ __forceinline__ bool load_item(const VoteItem *items, int it, const P
     if (v.W.cell_begin >= v.ncell) return false;
     v.ntiles = (v.W.pair_end - v.W.pair_begin) / kPairTile;
     return v.ntiles > 0;
+}
+
+// Warps 2-3: the A tile (128 cells x K, 16-bit) of every work item, double
+// buffered; a cold role kept out of line so the epilogue keeps its registers.
+template <int KSTEPS, bool BF16>
+__device__ __noinline__ void build_a_tiles(const VoteItem *__restrict__ items, int n_items,
+                                           const ProbRef *__restrict__ probs, const LevelRef *__restrict__ lref,
+                                           int level_stride, int level, uint8_t *sA, uint64_t *a_full,
+                                           uint64_t *a_empty, volatile int *abort_flag, int *err_flag, int warp,
+                                           int lane) {
+    constexpr int K = 16 * KSTEPS;
+    const int r0 = (warp - 2) * 64 + lane;
+    int i = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        ItemView v;
+        if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
+        const int ab = i & 1;
+        const uint32_t ua = (uint32_t)(i >> 1);
+        // warp-uniform outcome of the bounded wait
+        if (!__all_sync(0xffffffffu, mbar_wait(&a_empty[ab], (ua & 1u) ^ 1u, abort_flag))) {
+            *abort_flag = 1;
+            atomicExch(err_flag, 1);
+            break;
+        }
+        uint8_t *tile = sA + ab * kTileBytesMax;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = r0 + 32 * h;
+            const int pos = v.W.cell_begin + r;
+            uint16_t row[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) row[k] = 0;
+            if (pos < v.ncell) {
+                const float4 m0 = v.L.cells.m32[3 * pos], m1 = v.L.cells.m32[3 * pos + 1],
+                             m2 = v.L.cells.m32[3 * pos + 2];
+                const float m[10] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y};
+                const float tau = (float)tau_cs(v.P.sin_d, v.P.cos_d, v.L.cells.trig[pos]);
+                const uint16_t th = h16<BF16>(tau);
+                const uint16_t tl = h16<BF16>(tau - f16<BF16>(th));
+                if (KSTEPS == 1) {
+#pragma unroll
+                    for (int k = 0; k < 10; ++k) row[k] = h16<BF16>(m[k]);
+                    row[10] = th ^ 0x8000u;  // -tau_hi
+                    row[11] = tl ^ 0x8000u;  // -tau_lo
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 10; ++k) {
+                        const uint16_t hi = h16<BF16>(m[k]);
+                        const uint16_t lo = h16<BF16>(m[k] - f16<BF16>(hi));
+                        row[k] = hi;
+                        row[10 + k] = hi;
+                        row[20 + k] = lo;
+                    }
+                    row[30] = th ^ 0x8000u;
+                    row[31] = tl ^ 0x8000u;
+                }
+            } else {  // absent cell: D = 1 for every pair
+                row[KSTEPS == 1 ? 10 : 30] = h16<BF16>(1.f);
+            }
+#pragma unroll
+            for (int c = 0; c < K / 8; ++c) {
+                uint4 w;
+                w.x = (uint32_t)row[8 * c + 0] | ((uint32_t)row[8 * c + 1] << 16);
+                w.y = (uint32_t)row[8 * c + 2] | ((uint32_t)row[8 * c + 3] << 16);
+                w.z = (uint32_t)row[8 * c + 4] | ((uint32_t)row[8 * c + 5] << 16);
+                w.w = (uint32_t)row[8 * c + 6] | ((uint32_t)row[8 * c + 7] << 16);
+                *reinterpret_cast<uint4 *>(tile + tc_off(r, 8 * c)) = w;
+            }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a_full[ab]);
+        ++i;
+    }
 }
 
 template <int G, int KSTEPS, bool BF16>
@@ -344,68 +420,8 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
         }
     } else if (warp < 4) {
         // ---------------------------- A-tile builder ---------------------------
-        const int r0 = (warp - 2) * 64 + lane;
-        int i = 0;
-        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-            ItemView v;
-            if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
-            const int ab = i & 1;
-            const uint32_t ua = (uint32_t)(i >> 1);
-            // warp-uniform outcome of the bounded wait
-            if (!__all_sync(0xffffffffu, mbar_wait(&a_empty[ab], (ua & 1u) ^ 1u, abort_flag))) {
-                fail();
-                break;
-            }
-            uint8_t *tile = sA + ab * kTileBytesMax;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = r0 + 32 * h;
-                const int pos = v.W.cell_begin + r;
-                uint16_t row[32];
-#pragma unroll
-                for (int k = 0; k < 32; ++k) row[k] = 0;
-                if (pos < v.ncell) {
-                    const float4 m0 = v.L.cells.m32[3 * pos], m1 = v.L.cells.m32[3 * pos + 1],
-                                 m2 = v.L.cells.m32[3 * pos + 2];
-                    const float m[10] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y};
-                    const float tau = (float)tau_cs(v.P.sin_d, v.P.cos_d, v.L.cells.trig[pos]);
-                    const uint16_t th = h16<BF16>(tau);
-                    const uint16_t tl = h16<BF16>(tau - f16<BF16>(th));
-                    if (KSTEPS == 1) {
-#pragma unroll
-                        for (int k = 0; k < 10; ++k) row[k] = h16<BF16>(m[k]);
-                        row[10] = th ^ 0x8000u;  // -tau_hi
-                        row[11] = tl ^ 0x8000u;  // -tau_lo
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 10; ++k) {
-                            const uint16_t hi = h16<BF16>(m[k]);
-                            const uint16_t lo = h16<BF16>(m[k] - f16<BF16>(hi));
-                            row[k] = hi;
-                            row[10 + k] = hi;
-                            row[20 + k] = lo;
-                        }
-                        row[30] = th ^ 0x8000u;
-                        row[31] = tl ^ 0x8000u;
-                    }
-                } else {  // absent cell: D = 1 for every pair
-                    row[KSTEPS == 1 ? 10 : 30] = h16<BF16>(1.f);
-                }
-#pragma unroll
-                for (int c = 0; c < K / 8; ++c) {
-                    uint4 w;
-                    w.x = (uint32_t)row[8 * c + 0] | ((uint32_t)row[8 * c + 1] << 16);
-                    w.y = (uint32_t)row[8 * c + 2] | ((uint32_t)row[8 * c + 3] << 16);
-                    w.z = (uint32_t)row[8 * c + 4] | ((uint32_t)row[8 * c + 5] << 16);
-                    w.w = (uint32_t)row[8 * c + 6] | ((uint32_t)row[8 * c + 7] << 16);
-                    *reinterpret_cast<uint4 *>(tile + tc_off(r, 8 * c)) = w;
-                }
-            }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&a_full[ab]);
-            ++i;
-        }
+        build_a_tiles<KSTEPS, BF16>(items, n_items, probs, lref, level_stride, level, sA, a_full, a_empty, abort_flag,
+                                    err_flag, warp, lane);
     } else {
         // ------------------------------- epilogue ------------------------------
         const int g = (warp - 4) >> 2;      // warpgroup
@@ -431,8 +447,6 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 tau = (float)tau_cs(v.P.sin_d, v.P.cos_d, v.L.cells.trig[pos]);
                 band = fmaxf(cell_band<KSTEPS, BF16>(m), band_req);
             }
-            // D^2 <= band2 whenever |D| <= band (rounding of the square included)
-            const float band2 = band > 0.f ? band * band * 1.0001f : -1.f;
             int cnt = 0;
             unsigned rechecked = 0, ambiguous = 0;
             float4 R0 = make_float4(0, 0, 0, 0), R1 = R0, R2 = R0;
@@ -446,16 +460,26 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
             // sign bits with an integer multiply-add, the band by the minimum of D^2;
             // flagged values (rare) get the FP32 re-check
             auto chunk_count = [&](const uint32_t (&r)[32], int col0) {
-                float mn = 16.0f;  // min of D^2 (|D| <= 4)
-                uint32_t c2 = 0;
+                // four independent chains each, so consecutive instructions do not wait on one another
+                float m0 = 4.f, m1 = 4.f, m2 = 4.f, m3 = 4.f;  // min |D| (|D| <= 4)
+                uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
 #pragma unroll
-                for (int e = 0; e < 32; e += 2) {
-                    c2 = add_sign(add_sign(c2, r[e], two), r[e + 1], two);
-                    const float x = __uint_as_float(r[e]), y = __uint_as_float(r[e + 1]);
-                    mn = min3(mn, x * x, y * y);
+                for (int e = 0; e < 32; e += 8) {
+                    c0 = add_sign(c0, r[e], two);
+                    c1 = add_sign(c1, r[e + 1], two);
+                    c2 = add_sign(c2, r[e + 2], two);
+                    c3 = add_sign(c3, r[e + 3], two);
+                    c0 = add_sign(c0, r[e + 4], two);
+                    c1 = add_sign(c1, r[e + 5], two);
+                    c2 = add_sign(c2, r[e + 6], two);
+                    c3 = add_sign(c3, r[e + 7], two);
+                    m0 = min3_abs(m0, __uint_as_float(r[e]), __uint_as_float(r[e + 1]));
+                    m1 = min3_abs(m1, __uint_as_float(r[e + 2]), __uint_as_float(r[e + 3]));
+                    m2 = min3_abs(m2, __uint_as_float(r[e + 4]), __uint_as_float(r[e + 5]));
+                    m3 = min3_abs(m3, __uint_as_float(r[e + 6]), __uint_as_float(r[e + 7]));
                 }
-                cnt += (int)c2;
-                if (mn <= band2) {
+                cnt += (int)(c0 + c1 + c2 + c3);
+                if (fminf(fminf(m0, m1), fminf(m2, m3)) <= band) {
                     uint32_t fm = 0, sm = 0;  // flag and sign masks, constant register indices only
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
@@ -488,19 +512,29 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(as * 128);
                 // software pipeline over the tile's four 32-column chunks: the load
                 // of chunk c+1 is in flight while chunk c is counted
-                uint32_t ra[32], rb[32];
-                tmem_ld32(taddr, ra);
-                tmem_ld_wait(ra);
-                tmem_ld32(taddr + 32, rb);
-                chunk_count(ra, 0);
-                tmem_ld_wait(rb);
-                tmem_ld32(taddr + 64, ra);
-                chunk_count(rb, 32);
-                tmem_ld_wait(ra);
-                tmem_ld32(taddr + 96, rb);
-                chunk_count(ra, 64);
-                tmem_ld_wait(rb);
-                chunk_count(rb, 96);
+                if (G <= 2) {
+                    uint32_t ra[32], rb[32];
+                    tmem_ld32(taddr, ra);
+                    tmem_ld_wait(ra);
+                    tmem_ld32(taddr + 32, rb);
+                    chunk_count(ra, 0);
+                    tmem_ld_wait(rb);
+                    tmem_ld32(taddr + 64, ra);
+                    chunk_count(rb, 32);
+                    tmem_ld_wait(ra);
+                    tmem_ld32(taddr + 96, rb);
+                    chunk_count(ra, 64);
+                    tmem_ld_wait(rb);
+                    chunk_count(rb, 96);
+                } else {  // four warps per SMSP hide the load latency; one buffer keeps registers low
+#pragma unroll 1
+                    for (int c = 0; c < 4; ++c) {
+                        uint32_t ra[32];
+                        tmem_ld32(taddr + 32 * c, ra);
+                        tmem_ld_wait(ra);
+                        chunk_count(ra, 32 * c);
+                    }
+                }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acc_empty[as]);

@@ -268,7 +268,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     std::vector<size_t> o_items(S);
     for (int lev = 0; lev < S; ++lev) o_items[lev] = reserve(sizeof(VoteItem) * std::max<size_t>(1, pl.items_h[lev].size()));
     const size_t o_in = reserve(sizeof(float) * (size_t)pl.in_floats * 2);
-    const size_t o_s32 = reserve(sizeof(float4) * 5 * (size_t)pool);
+    const size_t o_s32 = reserve(sizeof(float4) * 3 * (size_t)pool);
     const size_t o_pr = reserve(sizeof(float4) * 2 * (size_t)pool);
     const size_t o_tcb = tck ? reserve((size_t)pool * tck * 2) : 0;
     const size_t o_member = reserve((size_t)pool);

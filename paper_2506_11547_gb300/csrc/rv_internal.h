@@ -82,8 +82,7 @@ struct Cand {
 };
 
 // Pair pool: one record per pair, padded to kPairTile per problem.
-//   s32  [P][5] float4: S entries [S00 S11 S22 S33 S01 S02 S03 S12 S13 S23], each twice
-//        ((s0 s0 s1 s1) (s2 s2 s3 s3) ...) for the packed f32x2 vote
+//   s32  [P][3] float4: S entries [S00 S11 S22 S33 S01 S02 S03 S12 S13 S23] + 2 pad
 //   pr   [P][2] float4: a0 a1 a2 b0 | b1 b2 c 0, c = (|a|^2 + |b|^2 - 2)/4
 //   tcb  tensor-core operand tiles (16-bit), layout described in k_vote_tc.cu
 struct PairPool {

@@ -16,12 +16,14 @@
 //   warp 0      lane 0 streams 128-pair B tiles global -> shared with the bulk
 //               copy engine (cp.async.bulk + mbarrier complete_tx), kNB stages
 //   warp 1      allocates 512 TMEM columns; lane 0 issues tcgen05.mma
-//               (M = 128 cells, N = 128 pairs, K = 16 per instruction) into
-//               one of kNAcc accumulator stages and commits to mbarriers
+//               (M = 128 cells, N = 64 pairs, K = 16 per instruction), each
+//               half of a B tile into one of 8 accumulator stages of 64
+//               columns, and commits to mbarriers
 //   warps 2-3   build the 128-row A tile of each work item in shared memory
 //               (double buffered)
-//   warps 4..   G epilogue warpgroups; tile j belongs to warpgroup j % G and
-//               accumulator stage j % kNAcc; each thread owns one TMEM lane =
+//   warps 4..   G epilogue warpgroups; 64-pair unit u belongs to warpgroup
+//               u % G and accumulator stage u % 8 (so every warpgroup has at
+//               least two stages in flight); each thread owns one TMEM lane =
 //               one cell, reads 32 columns per tcgen05.ld
 // Every mbarrier wait is bounded (2 s or 2^24 polls): on expiry the CTA sets
 // *err_flag, stops all roles, waits (bounded) for its own copies and MMAs,
@@ -41,7 +43,8 @@ namespace rv {
 namespace {
 
 constexpr int kNB = 6;           // B stages
-constexpr int kNAcc = 4;         // accumulator stages x 128 TMEM columns = 512
+constexpr int kNAcc = 8;         // accumulator stages x 64 TMEM columns = 512
+constexpr int kUnit = 64;        // pairs per accumulator stage (half a 128-pair B tile)
 constexpr int kTileBytesMax = 8192;
 constexpr int kGuard = 64 * 1024;  // slack after the operand tiles; also keeps one CTA per SM (> 116 KB)
 constexpr uint64_t kWaitNs = 2000000000ull;
@@ -148,10 +151,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
            (1ull << 46);
 }
 // Instruction descriptor of kind::f16: D = F32, A = B = F16 (0) or BF16 (1),
-// both K-major, N = 128 (>> 3 at bit 17), M = 128 (>> 4 at bit 24).
+// both K-major, N = 64 (>> 3 at bit 17), M = 128 (>> 4 at bit 24).
 template <bool BF16>
 __host__ __device__ constexpr uint32_t idesc_f16() {
-    return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((uint32_t)(kUnit >> 3) << 17) |
+           ((128u >> 4) << 24);
 }
 
 // cnt + (x >> 31) as an integer multiply-add hi32(x * two) + cnt with
@@ -394,23 +398,35 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 }
                 tc_fence_after();
                 const uint32_t a_addr = smem_u32(sA + ab * kTileBytesMax);
-                for (int t = 0; t < v.ntiles; ++t, ++j) {
-                    const int bs = (int)(j % kNB), as = (int)(j % kNAcc);
-                    const uint32_t ub = (uint32_t)(j / kNB), uc = (uint32_t)(j / kNAcc);
-                    if (!mbar_wait(&b_full[bs], ub & 1u, abort_flag) ||
-                        !mbar_wait(&acc_empty[as], (uc & 1u) ^ 1u, abort_flag)) {
+                for (int t = 0; t < v.ntiles && ok; ++t, ++j) {
+                    const int bs = (int)(j % kNB);
+                    const uint32_t ub = (uint32_t)(j / kNB);
+                    if (!mbar_wait(&b_full[bs], ub & 1u, abort_flag)) {
                         fail();
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
                     const uint32_t b_addr = smem_u32(sB + bs * kTileBytesMax);
-                    const uint32_t d_tmem = tmem_base + (uint32_t)(as * 128);
 #pragma unroll
-                    for (int k = 0; k < KSTEPS; ++k)
-                        mma_f16(d_tmem, sdesc(a_addr + k * 4096), sdesc(b_addr + k * 4096), IDESC, k > 0 ? 1u : 0u);
+                    for (int h = 0; h < 2; ++h) {  // pairs 0-63 and 64-127: 8 row groups of 128 B each
+                        const int64_t u = 2 * j + h;
+                        const int as = (int)(u % kNAcc);
+                        const uint32_t uc = (uint32_t)(u / kNAcc);
+                        if (!mbar_wait(&acc_empty[as], (uc & 1u) ^ 1u, abort_flag)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d_tmem = tmem_base + (uint32_t)(as * kUnit);
+#pragma unroll
+                        for (int k = 0; k < KSTEPS; ++k)
+                            mma_f16(d_tmem, sdesc(a_addr + k * 4096), sdesc(b_addr + h * 1024 + k * 4096), IDESC,
+                                    k > 0 ? 1u : 0u);
+                        mma_commit(&acc_full[as]);
+                    }
+                    if (!ok) break;
                     mma_commit(&b_empty[bs]);
-                    mma_commit(&acc_full[as]);
                 }
                 if (!ok) break;
                 mma_commit(&a_empty[ab]);
@@ -432,11 +448,12 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             ItemView v;
             if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
-            const int64_t j0 = j;
+            const int64_t j0 = 2 * j;  // first 64-pair unit of the item
+            const int nunits = 2 * v.ntiles;
             j += v.ntiles;
-            // my tiles of this item: j0 + t with (j0 + t) % G == g
+            // my units of this item: j0 + t with (j0 + t) % G == g
             int t = (int)((g - (int)(j0 % G) + G) % G);
-            if (t >= v.ntiles) continue;
+            if (t >= nunits) continue;
             const int pos = v.W.cell_begin + row;
             const bool valid = pos < v.ncell;
             float tau = 0.f, band = -1.f;
@@ -489,7 +506,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     while (fm) {
                         const int e = __ffs((int)fm) - 1;
                         fm &= fm - 1;
-                        const int64_t gp = gbase + (int64_t)t * kPairTile + col0 + e;
+                        const int64_t gp = gbase + (int64_t)t * kUnit + col0 + e;
                         const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
                         const float vv = recheck_v(R0, R1, R2, p0, p1);
                         cnt += (int)(vv <= tau) - (int)((sm >> e) & 1u);
@@ -498,7 +515,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     }
                 }
             };
-            for (; t < v.ntiles; t += G) {
+            for (; t < nunits; t += G) {
                 const int64_t jj = j0 + t;
                 const int as = (int)(jj % kNAcc);
                 const uint32_t uc = (uint32_t)(jj / kNAcc);
@@ -509,26 +526,18 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(as * 128);
-                // software pipeline over the tile's four 32-column chunks: the load
-                // of chunk c+1 is in flight while chunk c is counted
-                if (G <= 2) {
+                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(as * kUnit);
+                if (G <= 2) {  // the load of the second chunk is in flight while the first is counted
                     uint32_t ra[32], rb[32];
                     tmem_ld32(taddr, ra);
                     tmem_ld_wait(ra);
                     tmem_ld32(taddr + 32, rb);
                     chunk_count(ra, 0);
                     tmem_ld_wait(rb);
-                    tmem_ld32(taddr + 64, ra);
                     chunk_count(rb, 32);
-                    tmem_ld_wait(ra);
-                    tmem_ld32(taddr + 96, rb);
-                    chunk_count(ra, 64);
-                    tmem_ld_wait(rb);
-                    chunk_count(rb, 96);
                 } else {  // four warps per SMSP hide the load latency; one buffer keeps registers low
 #pragma unroll 1
-                    for (int c = 0; c < 4; ++c) {
+                    for (int c = 0; c < 2; ++c) {
                         uint32_t ra[32];
                         tmem_ld32(taddr + 32 * c, ra);
                         tmem_ld_wait(ra);
@@ -563,7 +572,9 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     }
 }
 
-constexpr size_t kSmemBytes = 1024 + 2 * kTileBytesMax + kNB * kTileBytesMax + kGuard + 256;
+// 1024 B alignment slack + A (2 stages) + B (kNB stages) + guard + barriers and flags (< 1 KB)
+constexpr size_t kSmemBytes = 1024 + 2 * kTileBytesMax + kNB * kTileBytesMax + kGuard + 1024;
+static_assert((2 * kNB + 2 * kNAcc + 5) * 8 + 8 <= 1024, "barrier area");
 
 template <int G, int KSTEPS, bool BF16>
 cudaError_t prepare_t() {

@@ -71,8 +71,7 @@ __device__ __forceinline__ uint64_t gtimer() {
 }
 // Bounded wait for the phase of parity `parity` to complete.  Returns false
 // when the CTA was aborted or the wait expired.
-__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    if (mbar_try_wait(bar, parity)) return true;
+__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
     const uint64_t t0 = gtimer();
     for (uint32_t it = 1; it < kWaitPolls; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
@@ -82,6 +81,9 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile 
         }
     }
     return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, abort_flag);
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                                     err_flag, warp, lane);
     } else {
         // ------------------------------- epilogue ------------------------------
-        const int g = (warp - 4) >> 2;      // warpgroup
+        const int g = (warp - 4) >> 2;      // warpgroup (0 .. G-1)
         const int q = warp & 3;             // TMEM lane quarter this warp may access
         const int row = 32 * q + lane;      // cell row of this thread
         int64_t j = 0;
@@ -597,9 +599,10 @@ cudaError_t launch_t(const VoteItem *items, int n_items, const ProbRef *probs, c
 // stream capture).
 cudaError_t prepare_vote_tc() {
     cudaError_t e = cudaSuccess;
-    const cudaError_t r[8] = {prepare_t<2, 1, false>(), prepare_t<2, 1, true>(), prepare_t<2, 2, false>(),
-                              prepare_t<2, 2, true>(),  prepare_t<4, 1, false>(), prepare_t<4, 1, true>(),
-                              prepare_t<4, 2, false>(), prepare_t<4, 2, true>()};
+    const cudaError_t r[12] = {prepare_t<2, 1, false>(), prepare_t<2, 1, true>(), prepare_t<2, 2, false>(),
+                               prepare_t<2, 2, true>(),  prepare_t<4, 1, false>(), prepare_t<4, 1, true>(),
+                               prepare_t<4, 2, false>(), prepare_t<4, 2, true>(),  prepare_t<6, 1, false>(),
+                               prepare_t<6, 1, true>(),  prepare_t<6, 2, false>(), prepare_t<6, 2, true>()};
     for (cudaError_t x : r)
         if (x != cudaSuccess) e = x;
     return e;
@@ -610,16 +613,18 @@ cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *pr
                            int epilogue_groups, int grid_blocks, int *err_flag, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
     const int grid = grid_blocks < n_items ? grid_blocks : n_items;
-    const bool g4 = epilogue_groups == 4;
 #define RV_TC(G_, KS_, BF_) \
     launch_t<G_, KS_, BF_>(items, n_items, probs, lref, level_stride, level, pool, stats, band_req, grid, err_flag, s)
+#define RV_TC_G(KS_, BF_) \
+    (epilogue_groups == 6 ? RV_TC(6, KS_, BF_) : epilogue_groups == 4 ? RV_TC(4, KS_, BF_) : RV_TC(2, KS_, BF_))
     switch (prec) {
-    case ROT_PREC_FP16: return g4 ? RV_TC(4, 1, false) : RV_TC(2, 1, false);
-    case ROT_PREC_BF16: return g4 ? RV_TC(4, 1, true) : RV_TC(2, 1, true);
-    case ROT_PREC_FP16X2: return g4 ? RV_TC(4, 2, false) : RV_TC(2, 2, false);
-    case ROT_PREC_BF16X2: return g4 ? RV_TC(4, 2, true) : RV_TC(2, 2, true);
+    case ROT_PREC_FP16: return RV_TC_G(1, false);
+    case ROT_PREC_BF16: return RV_TC_G(1, true);
+    case ROT_PREC_FP16X2: return RV_TC_G(2, false);
+    case ROT_PREC_BF16X2: return RV_TC_G(2, true);
     default: return cudaErrorInvalidValue;
     }
+#undef RV_TC_G
 #undef RV_TC
 }
 

@@ -47,6 +47,15 @@ constexpr int kNAcc = 8;         // accumulator stages x 64 TMEM columns = 512
 constexpr int kUnit = 64;        // pairs per accumulator stage (half a 128-pair B tile)
 constexpr int kTileBytesMax = 8192;
 constexpr int kGuard = 64 * 1024;  // slack after the operand tiles; also keeps one CTA per SM (> 116 KB)
+// Deferred re-check state, per epilogue warp / warpgroup (after the barriers):
+//   queue   kQCap entries {pair offset in the item, lane | sign << 5} per warp
+//   rows    R (9), tau, band, pad per cell row, per warpgroup
+//   corr    count correction per cell row, per warpgroup
+constexpr int kQCap = 64;
+constexpr int kMaxG = 6;
+constexpr size_t kQueueBytes = (size_t)4 * kMaxG * kQCap * 8;
+constexpr size_t kRowBytes = (size_t)kMaxG * 128 * 12 * 4;
+constexpr size_t kCorrBytes = (size_t)kMaxG * 128 * 4;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint32_t kWaitPolls = 1u << 24;
 
@@ -323,6 +332,10 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     uint64_t *a_full = acc_empty + kNAcc, *a_empty = a_full + 2, *mma_done = a_empty + 2;
     uint32_t *tmem_slot = (uint32_t *)(mma_done + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    uint8_t *rq = (uint8_t *)bars + 1024;  // deferred re-check state
+    uint2 *q_all = (uint2 *)rq;
+    float *rows_all = (float *)(rq + kQueueBytes);
+    int *corr_all = (int *)(rq + kQueueBytes + kRowBytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -468,17 +481,47 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
             }
             int cnt = 0;
             unsigned rechecked = 0, ambiguous = 0;
-            float4 R0 = make_float4(0, 0, 0, 0), R1 = R0, R2 = R0;
-            if (valid) {  // the cell's rotation, for re-checks
-                R0 = v.L.cells.R32[3 * pos];
-                R1 = v.L.cells.R32[3 * pos + 1];
-                R2 = v.L.cells.R32[3 * pos + 2];
+            uint2 *qw = q_all + (size_t)(warp - 4) * kQCap;  // this warp's queue
+            float *rows = rows_all + (size_t)g * 128 * 12;   // this warpgroup's row table
+            int *corr = corr_all + g * 128;
+            {  // the cell's rotation and threshold, for re-checks of this row by any lane of the warp
+                float4 R0 = make_float4(0, 0, 0, 0), R1 = R0, R2 = R0;
+                if (valid) {
+                    R0 = v.L.cells.R32[3 * pos];
+                    R1 = v.L.cells.R32[3 * pos + 1];
+                    R2 = v.L.cells.R32[3 * pos + 2];
+                }
+                float4 *rr = reinterpret_cast<float4 *>(rows + row * 12);
+                rr[0] = R0;
+                rr[1] = R1;
+                rr[2] = make_float4(R2.x, tau, 0.f, 0.f);
+                corr[row] = 0;
             }
+            __syncwarp();
+            int qn = 0;  // entries in this warp's queue (warp-uniform)
             const int64_t gbase = v.P.pool_off + v.W.pair_begin;
+            // drains the queue: one entry per lane, loads issued in parallel
+            auto flush = [&]() {
+                for (int k = lane; k < qn; k += 32) {
+                    const uint2 en = qw[k];
+                    const int rrow = 32 * q + (int)(en.y & 31u);
+                    const float4 *rr = reinterpret_cast<const float4 *>(rows + rrow * 12);
+                    const float4 R0 = rr[0], R1 = rr[1], R2x = rr[2];
+                    const float rtau = R2x.y;
+                    const int64_t gp = gbase + (int64_t)en.x;
+                    const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
+                    const float vv = recheck_v(R0, R1, make_float4(R2x.x, 0.f, 0.f, 0.f), p0, p1);
+                    atomicAdd(&corr[rrow], (int)(vv <= rtau) - (int)(en.y >> 5));
+                    ++rechecked;
+                    ambiguous += fabsf(vv - rtau) <= kAmbig;
+                }
+                __syncwarp();
+                qn = 0;
+            };
             // counts the 32 values of one chunk (columns col0..col0+31 of tile t):
             // sign bits with an integer multiply-add, the band by the minimum of D^2;
             // flagged values (rare) get the FP32 re-check
-            auto chunk_count = [&](const uint32_t (&r)[32], int col0) {
+            auto chunk_count = [&](const uint32_t (&r)[32], int col0, int unit_off) {
                 // four independent chains each, so consecutive instructions do not wait on one another
                 float m0 = 4.f, m1 = 4.f, m2 = 4.f, m3 = 4.f;  // min |D| (|D| <= 4)
                 uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
@@ -498,22 +541,30 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     m3 = min3_abs(m3, __uint_as_float(r[e + 6]), __uint_as_float(r[e + 7]));
                 }
                 cnt += (int)(c0 + c1 + c2 + c3);
-                if (fminf(fminf(m0, m1), fminf(m2, m3)) <= band) {
+                const bool hit = fminf(fminf(m0, m1), fminf(m2, m3)) <= band;
+                if (__any_sync(0xffffffffu, hit)) {  // rare: queue the flagged tests (warp-uniform branch)
                     uint32_t fm = 0, sm = 0;  // flag and sign masks, constant register indices only
+                    if (hit) {
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        fm |= (uint32_t)(fabsf(__uint_as_float(r[e])) <= band) << e;
-                        sm |= (r[e] >> 31) << e;
+                        for (int e = 0; e < 32; ++e) {
+                            fm |= (uint32_t)(fabsf(__uint_as_float(r[e])) <= band) << e;
+                            sm |= (r[e] >> 31) << e;
+                        }
                     }
-                    while (fm) {
-                        const int e = __ffs((int)fm) - 1;
-                        fm &= fm - 1;
-                        const int64_t gp = gbase + (int64_t)t * kUnit + col0 + e;
-                        const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
-                        const float vv = recheck_v(R0, R1, R2, p0, p1);
-                        cnt += (int)(vv <= tau) - (int)((sm >> e) & 1u);
-                        ++rechecked;
-                        ambiguous += fabsf(vv - tau) <= kAmbig;
+                    const uint32_t lt = (1u << lane) - 1u;
+                    for (;;) {
+                        const bool has = fm != 0;
+                        const uint32_t bal = __ballot_sync(0xffffffffu, has);
+                        if (bal == 0) break;
+                        if (has) {
+                            const int e = __ffs((int)fm) - 1;
+                            fm &= fm - 1;
+                            qw[qn + __popc(bal & lt)] =
+                                make_uint2((uint32_t)(unit_off + col0 + e), (uint32_t)lane | (((sm >> e) & 1u) << 5));
+                        }
+                        qn += __popc(bal);
+                        __syncwarp();
+                        if (qn > kQCap - 32) flush();
                     }
                 }
             };
@@ -534,22 +585,24 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     tmem_ld32(taddr, ra);
                     tmem_ld_wait(ra);
                     tmem_ld32(taddr + 32, rb);
-                    chunk_count(ra, 0);
+                    chunk_count(ra, 0, t * kUnit);
                     tmem_ld_wait(rb);
-                    chunk_count(rb, 32);
+                    chunk_count(rb, 32, t * kUnit);
                 } else {  // four warps per SMSP hide the load latency; one buffer keeps registers low
 #pragma unroll 1
                     for (int c = 0; c < 2; ++c) {
                         uint32_t ra[32];
                         tmem_ld32(taddr + 32 * c, ra);
                         tmem_ld_wait(ra);
-                        chunk_count(ra, 32 * c);
+                        chunk_count(ra, 32 * c, t * kUnit);
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acc_empty[as]);
             }
+            if (qn > 0) flush();
+            cnt += corr[row];
             if (valid && cnt != 0) atomicAdd(&v.L.counts[pos], cnt);
             const unsigned rc = __reduce_add_sync(0xffffffffu, rechecked);
             const unsigned am = __reduce_add_sync(0xffffffffu, ambiguous);
@@ -574,8 +627,9 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     }
 }
 
-// 1024 B alignment slack + A (2 stages) + B (kNB stages) + guard + barriers and flags (< 1 KB)
-constexpr size_t kSmemBytes = 1024 + 2 * kTileBytesMax + kNB * kTileBytesMax + kGuard + 1024;
+// 1024 B alignment slack + A (2 stages) + B (kNB stages) + guard + barriers and flags (< 1 KB) + re-check state
+constexpr size_t kSmemBytes =
+    1024 + 2 * kTileBytesMax + kNB * kTileBytesMax + kGuard + 1024 + kQueueBytes + kRowBytes + kCorrBytes;
 static_assert((2 * kNB + 2 * kNAcc + 5) * 8 + 8 <= 1024, "barrier area");
 
 template <int G, int KSTEPS, bool BF16>

@@ -56,11 +56,13 @@ __device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float x) { return _
 __device__ __forceinline__ float from16(__half x) { return __half2float(x); }
 __device__ __forceinline__ float from16(__nv_bfloat16 x) { return __bfloat162float(x); }
 
-// Byte offset of element (row r, column k) of a 128-row, K-column operand tile
-// in the canonical no-swizzle K-major layout: 8x(16 B) core matrices stored
-// contiguously; core matrices consecutive in the row direction are 128 B apart
-// (SBO), consecutive in K are 128*16 = 2048 B apart (LBO).
-__device__ __forceinline__ int tc_off(int r, int k) { return (k >> 3) * 2048 + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+// Byte offset of element (row r, column k) of a kPairTile-row, K-column operand
+// tile in the canonical no-swizzle K-major layout: 8x(16 B) core matrices
+// stored contiguously; core matrices consecutive in the row direction are 128 B
+// apart (SBO), consecutive in K are kPairTile*16 B apart (LBO).
+__device__ __forceinline__ int tc_off(int r, int k) {
+    return (k >> 3) * (kPairTile * 16) + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
 
 template <typename T16>
 __device__ __forceinline__ void write_tc_row(uint8_t *tile, int r, int K, const float s[10], bool pad) {

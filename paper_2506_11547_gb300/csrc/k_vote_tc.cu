@@ -13,25 +13,27 @@
 // is below 7e-7, so every decision with |v - tau| > 1e-6 is the FP64 one.
 //
 // One persistent CTA per SM:
-//   warp 0      lane 0 streams 128-pair B tiles global -> shared with the bulk
+//   warp 0      lane 0 streams 256-pair B tiles global -> shared with the bulk
 //               copy engine (cp.async.bulk + mbarrier complete_tx), kNB stages
 //   warp 1      allocates 512 TMEM columns; lane 0 issues tcgen05.mma
-//               (M = 128 cells, N = 64 pairs, K = 16 per instruction), each
-//               half of a B tile into one of 8 accumulator stages of 64
-//               columns, and commits to mbarriers
+//               (M = 128 cells, N = 256 pairs, K = 16 per instruction) into one
+//               of two accumulator stages of 256 columns, commits to mbarriers
 //   warps 2-3   build the 128-row A tile of each work item in shared memory
 //               (double buffered)
-//   warps 4..   G epilogue warpgroups; 64-pair unit u belongs to warpgroup
-//               u % G and accumulator stage u % 8 (so every warpgroup has at
-//               least two stages in flight); each thread owns one TMEM lane =
-//               one cell, reads 32 columns per tcgen05.ld
+//   warps 4..   G epilogue warpgroups: warpgroups g = s, s+2, ... drain stage s,
+//               each a 256/(G/2)-column slice; each thread owns one TMEM lane
+//               = one cell and reads 32 columns per tcgen05.ld.  Tests inside
+//               the band go to a per-warp shared-memory queue that is drained
+//               32 at a time (one lane per test), so no warp waits on one
+//               global load per flagged test.
 // Every mbarrier wait is bounded (2 s or 2^24 polls): on expiry the CTA sets
 // *err_flag, stops all roles, waits (bounded) for its own copies and MMAs,
 // frees its TMEM and returns.
 //
 // Operand tiles use the canonical no-swizzle K-major layout: 8 rows x 16 B
 // core matrices stored contiguously (128 B); SBO = 128 B between 8-row
-// groups, LBO = 2048 B between the 8-column halves of a K = 16 slice.
+// groups; LBO = rows x 16 B between the 8-column halves of a K = 16 slice
+// (2048 B for the 128-row A tile, 4096 B for the 256-row B tile).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -42,20 +44,28 @@ namespace rv {
 
 namespace {
 
-constexpr int kNB = 6;           // B stages
-constexpr int kNAcc = 8;         // accumulator stages x 64 TMEM columns = 512
-constexpr int kUnit = 64;        // pairs per accumulator stage (half a 128-pair B tile)
-constexpr int kTileBytesMax = 8192;
-constexpr int kGuard = 64 * 1024;  // slack after the operand tiles; also keeps one CTA per SM (> 116 KB)
+constexpr int kNB = 5;                         // B stages
+constexpr int kNAcc = 2;                       // accumulator stages x 256 TMEM columns = 512
+constexpr int kUnit = kPairTile;               // pairs per accumulator stage = MMA N
+constexpr int kATileBytesMax = 128 * 32 * 2;   // 128 rows x K = 32 x 2 B
+constexpr int kBTileBytesMax = kUnit * 32 * 2; // 256 rows x K = 32 x 2 B
+constexpr int kALbo = 128 * 16, kBLbo = kUnit * 16;
 // Deferred re-check state, per epilogue warp / warpgroup (after the barriers):
 //   queue   kQCap entries {pair offset in the item, lane | sign << 5} per warp
-//   rows    R (9), tau, band, pad per cell row, per warpgroup
+//   rows    R (9), tau, pad per cell row, per warpgroup
 //   corr    count correction per cell row, per warpgroup
 constexpr int kQCap = 64;
-constexpr int kMaxG = 6;
+constexpr int kMaxG = 4;
 constexpr size_t kQueueBytes = (size_t)4 * kMaxG * kQCap * 8;
 constexpr size_t kRowBytes = (size_t)kMaxG * 128 * 12 * 4;
 constexpr size_t kCorrBytes = (size_t)kMaxG * 128 * 4;
+constexpr size_t kBarBytes = 1024;
+// 1024 B alignment slack + A (2 stages) + B (kNB stages) + barriers/flags + re-check state.
+// Over 116 KB, so one CTA per SM (each holds all 512 TMEM columns).
+constexpr size_t kSmemBytes =
+    1024 + 2 * kATileBytesMax + kNB * kBTileBytesMax + kBarBytes + kQueueBytes + kRowBytes + kCorrBytes;
+static_assert(kSmemBytes > 116 * 1024 && kSmemBytes <= 227 * 1024, "shared memory budget");
+static_assert((2 * kNB + 2 * kNAcc + 5) * 8 + 8 <= (int)kBarBytes, "barrier area");
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint32_t kWaitPolls = 1u << 24;
 
@@ -156,17 +166,31 @@ __device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
                  : "memory");
 }
 
-// Shared-memory matrix descriptor, canonical K-major layout without swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(2048u >> 4) << 16) | ((uint64_t)(128u >> 4) << 32) |
+// Shared-memory matrix descriptor, canonical K-major layout without swizzle:
+// start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO = 128 B >> 4 (32-45), version 1 (46).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(128u >> 4) << 32) |
            (1ull << 46);
 }
-// Instruction descriptor of kind::f16: D = F32, A = B = F16 (0) or BF16 (1),
-// both K-major, N = 64 (>> 3 at bit 17), M = 128 (>> 4 at bit 24).
+// Instruction descriptor of kind::f16: D = F32 (bit 4), A = B = F16 (0) or
+// BF16 (1) at bits 7 and 10, both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 template <bool BF16>
 __host__ __device__ constexpr uint32_t idesc_f16() {
     return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((uint32_t)(kUnit >> 3) << 17) |
            ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ int a_off(int r, int k) { return (k >> 3) * kALbo + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+template <bool BF16>
+__device__ __forceinline__ uint16_t h16(float x) {
+    if (BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    return __half_as_ushort(__float2half_rn(x));
+}
+template <bool BF16>
+__device__ __forceinline__ float f16(uint16_t x) {
+    if (BF16) return __bfloat162float(__ushort_as_bfloat16(x));
+    return __half2float(__ushort_as_half(x));
 }
 
 // cnt + (x >> 31) as an integer multiply-add hi32(x * two) + cnt with
@@ -183,19 +207,6 @@ __device__ __forceinline__ float min3_abs(float m, float x, float y) {
         : "=f"(r)
         : "f"(m), "f"(x), "f"(y));
     return r;
-}
-
-__device__ __forceinline__ int tc_off(int r, int k) { return (k >> 3) * 2048 + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
-
-template <bool BF16>
-__device__ __forceinline__ uint16_t h16(float x) {
-    if (BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-    return __half_as_ushort(__float2half_rn(x));
-}
-template <bool BF16>
-__device__ __forceinline__ float f16(uint16_t x) {
-    if (BF16) return __bfloat162float(__ushort_as_bfloat16(x));
-    return __half2float(__ushort_as_half(x));
 }
 
 // Rigorous per-cell bound on |D - (v - tau)| (see the file comment).
@@ -263,7 +274,7 @@ __device__ __noinline__ void build_a_tiles(const VoteItem *__restrict__ items, i
             atomicExch(err_flag, 1);
             break;
         }
-        uint8_t *tile = sA + ab * kTileBytesMax;
+        uint8_t *tile = sA + ab * kATileBytesMax;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int r = r0 + 32 * h;
@@ -305,7 +316,7 @@ __device__ __noinline__ void build_a_tiles(const VoteItem *__restrict__ items, i
                 w.y = (uint32_t)row[8 * c + 2] | ((uint32_t)row[8 * c + 3] << 16);
                 w.z = (uint32_t)row[8 * c + 4] | ((uint32_t)row[8 * c + 5] << 16);
                 w.w = (uint32_t)row[8 * c + 6] | ((uint32_t)row[8 * c + 7] << 16);
-                *reinterpret_cast<uint4 *>(tile + tc_off(r, 8 * c)) = w;
+                *reinterpret_cast<uint4 *>(tile + a_off(r, 8 * c)) = w;
             }
         }
         fence_proxy_async_smem();
@@ -320,19 +331,21 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     vote_tc_kernel(const VoteItem *__restrict__ items, int n_items, const ProbRef *__restrict__ probs,
                    const LevelRef *__restrict__ lref, int level_stride, int level, PairPool pool, ProbStats *stats,
                    float band_req, int *err_flag, uint32_t two) {
-    constexpr int kTileBytes = kPairTile * 16 * KSTEPS * 2;  // 128 rows x K x 2 B
-    constexpr int K = 16 * KSTEPS;
+    static_assert(G == 2 || G == 4, "epilogue warpgroups split the two accumulator stages evenly");
+    constexpr int kTileBytes = kUnit * 16 * KSTEPS * 2;  // 256 rows x K x 2 B
     constexpr uint32_t IDESC = idesc_f16<BF16>();
+    constexpr int kPerStage = G / 2;           // warpgroups draining each stage
+    constexpr int kCols = kUnit / kPerStage;   // columns per warpgroup per unit
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = smem;                                   // 2 x kTileBytesMax
-    uint8_t *sB = smem + 2 * kTileBytesMax;               // kNB x kTileBytesMax
-    uint64_t *bars = (uint64_t *)(sB + kNB * kTileBytesMax + kGuard);
+    uint8_t *sA = smem;                          // 2 x kATileBytesMax
+    uint8_t *sB = smem + 2 * kATileBytesMax;     // kNB x kBTileBytesMax
+    uint64_t *bars = (uint64_t *)(sB + kNB * kBTileBytesMax);
     uint64_t *b_full = bars, *b_empty = bars + kNB, *acc_full = bars + 2 * kNB, *acc_empty = acc_full + kNAcc;
     uint64_t *a_full = acc_empty + kNAcc, *a_empty = a_full + 2, *mma_done = a_empty + 2;
     uint32_t *tmem_slot = (uint32_t *)(mma_done + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-    uint8_t *rq = (uint8_t *)bars + 1024;  // deferred re-check state
+    uint8_t *rq = (uint8_t *)bars + kBarBytes;  // deferred re-check state
     uint2 *q_all = (uint2 *)rq;
     float *rows_all = (float *)(rq + kQueueBytes);
     int *corr_all = (int *)(rq + kQueueBytes + kRowBytes);
@@ -345,7 +358,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
         }
         for (int s = 0; s < kNAcc; ++s) {
             mbar_init(&acc_full[s], 1);
-            mbar_init(&acc_empty[s], 4);
+            mbar_init(&acc_empty[s], 4 * kPerStage);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&a_full[s], 2);
@@ -385,7 +398,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                         break;
                     }
                     mbar_arrive_expect_tx(&b_full[bs], kTileBytes);
-                    bulk_g2s(sB + bs * kTileBytesMax, src + (int64_t)t * kTileBytes, kTileBytes, &b_full[bs]);
+                    bulk_g2s(sB + bs * kBTileBytesMax, src + (int64_t)t * kTileBytes, kTileBytes, &b_full[bs]);
                 }
             }
             // drain: the last issued copy of each stage has completed before exit
@@ -412,36 +425,25 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a_addr = smem_u32(sA + ab * kTileBytesMax);
-                for (int t = 0; t < v.ntiles && ok; ++t, ++j) {
-                    const int bs = (int)(j % kNB);
-                    const uint32_t ub = (uint32_t)(j / kNB);
-                    if (!mbar_wait(&b_full[bs], ub & 1u, abort_flag)) {
+                const uint32_t a_addr = smem_u32(sA + ab * kATileBytesMax);
+                for (int t = 0; t < v.ntiles; ++t, ++j) {
+                    const int bs = (int)(j % kNB), as = (int)(j % kNAcc);
+                    const uint32_t ub = (uint32_t)(j / kNB), uc = (uint32_t)(j / kNAcc);
+                    if (!mbar_wait(&b_full[bs], ub & 1u, abort_flag) ||
+                        !mbar_wait(&acc_empty[as], (uc & 1u) ^ 1u, abort_flag)) {
                         fail();
                         ok = false;
                         break;
                     }
-                    const uint32_t b_addr = smem_u32(sB + bs * kTileBytesMax);
+                    tc_fence_after();
+                    const uint32_t b_addr = smem_u32(sB + bs * kBTileBytesMax);
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(as * kUnit);
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {  // pairs 0-63 and 64-127: 8 row groups of 128 B each
-                        const int64_t u = 2 * j + h;
-                        const int as = (int)(u % kNAcc);
-                        const uint32_t uc = (uint32_t)(u / kNAcc);
-                        if (!mbar_wait(&acc_empty[as], (uc & 1u) ^ 1u, abort_flag)) {
-                            fail();
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t d_tmem = tmem_base + (uint32_t)(as * kUnit);
-#pragma unroll
-                        for (int k = 0; k < KSTEPS; ++k)
-                            mma_f16(d_tmem, sdesc(a_addr + k * 4096), sdesc(b_addr + h * 1024 + k * 4096), IDESC,
-                                    k > 0 ? 1u : 0u);
-                        mma_commit(&acc_full[as]);
-                    }
-                    if (!ok) break;
+                    for (int k = 0; k < KSTEPS; ++k)
+                        mma_f16(d_tmem, sdesc(a_addr + k * 2 * kALbo, kALbo), sdesc(b_addr + k * 2 * kBLbo, kBLbo),
+                                IDESC, k > 0 ? 1u : 0u);
                     mma_commit(&b_empty[bs]);
+                    mma_commit(&acc_full[as]);
                 }
                 if (!ok) break;
                 mma_commit(&a_empty[ab]);
@@ -455,20 +457,24 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                                     err_flag, warp, lane);
     } else {
         // ------------------------------- epilogue ------------------------------
-        const int g = (warp - 4) >> 2;      // warpgroup (0 .. G-1)
-        const int q = warp & 3;             // TMEM lane quarter this warp may access
-        const int row = 32 * q + lane;      // cell row of this thread
+        const int g = (warp - 4) >> 2;        // warpgroup (0 .. G-1)
+        const int stage = g & 1;              // the accumulator stage it drains
+        const int col0 = (g >> 1) * kCols;    // its column slice of each unit
+        const int q = warp & 3;               // TMEM lane quarter this warp may access
+        const int row = 32 * q + lane;        // cell row of this thread
+        uint2 *qw = q_all + (size_t)(warp - 4) * kQCap;  // this warp's re-check queue
+        float *rows = rows_all + (size_t)g * 128 * 12;   // this warpgroup's row table
+        int *corr = corr_all + g * 128;
         int64_t j = 0;
         bool ok = true;
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             ItemView v;
             if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
-            const int64_t j0 = 2 * j;  // first 64-pair unit of the item
-            const int nunits = 2 * v.ntiles;
+            const int64_t j0 = j;
             j += v.ntiles;
-            // my units of this item: j0 + t with (j0 + t) % G == g
-            int t = (int)((g - (int)(j0 % G) + G) % G);
-            if (t >= nunits) continue;
+            // my units of this item: j0 + t with (j0 + t) % 2 == stage
+            int t = (int)(((int64_t)stage - (j0 & 1) + 2) & 1);
+            if (t >= v.ntiles) continue;
             const int pos = v.W.cell_begin + row;
             const bool valid = pos < v.ncell;
             float tau = 0.f, band = -1.f;
@@ -481,9 +487,6 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
             }
             int cnt = 0;
             unsigned rechecked = 0, ambiguous = 0;
-            uint2 *qw = q_all + (size_t)(warp - 4) * kQCap;  // this warp's queue
-            float *rows = rows_all + (size_t)g * 128 * 12;   // this warpgroup's row table
-            int *corr = corr_all + g * 128;
             {  // the cell's rotation and threshold, for re-checks of this row by any lane of the warp
                 float4 R0 = make_float4(0, 0, 0, 0), R1 = R0, R2 = R0;
                 if (valid) {
@@ -518,10 +521,10 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 __syncwarp();
                 qn = 0;
             };
-            // counts the 32 values of one chunk (columns col0..col0+31 of tile t):
-            // sign bits with an integer multiply-add, the band by the minimum of D^2;
-            // flagged values (rare) get the FP32 re-check
-            auto chunk_count = [&](const uint32_t (&r)[32], int col0, int unit_off) {
+            // counts the 32 values of one chunk at pair offset poff in the item:
+            // sign bits with an integer multiply-add, the band by the minimum of
+            // |D|; flagged values (rare) are queued for the FP32 re-check
+            auto chunk_count = [&](const uint32_t (&r)[32], int poff) {
                 // four independent chains each, so consecutive instructions do not wait on one another
                 float m0 = 4.f, m1 = 4.f, m2 = 4.f, m3 = 4.f;  // min |D| (|D| <= 4)
                 uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
@@ -560,7 +563,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                             const int e = __ffs((int)fm) - 1;
                             fm &= fm - 1;
                             qw[qn + __popc(bal & lt)] =
-                                make_uint2((uint32_t)(unit_off + col0 + e), (uint32_t)lane | (((sm >> e) & 1u) << 5));
+                                make_uint2((uint32_t)(poff + e), (uint32_t)lane | (((sm >> e) & 1u) << 5));
                         }
                         qn += __popc(bal);
                         __syncwarp();
@@ -568,38 +571,35 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     }
                 }
             };
-            for (; t < nunits; t += G) {
+            for (; t < v.ntiles; t += 2) {
                 const int64_t jj = j0 + t;
-                const int as = (int)(jj % kNAcc);
                 const uint32_t uc = (uint32_t)(jj / kNAcc);
                 // warp-uniform outcome: every lane must reach the .sync.aligned tcgen05.ld below
-                if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[as], uc & 1u, abort_flag))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[stage], uc & 1u, abort_flag))) {
                     fail();
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(as * kUnit);
-                if (G <= 2) {  // the load of the second chunk is in flight while the first is counted
-                    uint32_t ra[32], rb[32];
-                    tmem_ld32(taddr, ra);
-                    tmem_ld_wait(ra);
-                    tmem_ld32(taddr + 32, rb);
-                    chunk_count(ra, 0, t * kUnit);
-                    tmem_ld_wait(rb);
-                    chunk_count(rb, 32, t * kUnit);
-                } else {  // four warps per SMSP hide the load latency; one buffer keeps registers low
+                const uint32_t taddr =
+                    tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(stage * kUnit + col0);
+                const int pbase = t * kUnit + col0;
+                // two-deep pipeline over 32-column chunks: chunk c+1 loads while chunk c is counted
+                uint32_t ra[32], rb[32];
+                tmem_ld32(taddr, ra);
+                tmem_ld_wait(ra);
 #pragma unroll 1
-                    for (int c = 0; c < 2; ++c) {
-                        uint32_t ra[32];
-                        tmem_ld32(taddr + 32 * c, ra);
-                        tmem_ld_wait(ra);
-                        chunk_count(ra, 32 * c, t * kUnit);
-                    }
+                for (int c = 0; c < kCols; c += 64) {
+                    tmem_ld32(taddr + c + 32, rb);
+                    chunk_count(ra, pbase + c);
+                    tmem_ld_wait(rb);
+                    if (c + 64 < kCols) tmem_ld32(taddr + c + 64, ra);
+                    chunk_count(rb, pbase + c + 32);
+                    if (c + 64 < kCols) tmem_ld_wait(ra);
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&acc_empty[as]);
+                if (lane == 0) mbar_arrive(&acc_empty[stage]);
             }
             if (qn > 0) flush();
             cnt += corr[row];
@@ -627,11 +627,6 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     }
 }
 
-// 1024 B alignment slack + A (2 stages) + B (kNB stages) + guard + barriers and flags (< 1 KB) + re-check state
-constexpr size_t kSmemBytes =
-    1024 + 2 * kTileBytesMax + kNB * kTileBytesMax + kGuard + 1024 + kQueueBytes + kRowBytes + kCorrBytes;
-static_assert((2 * kNB + 2 * kNAcc + 5) * 8 + 8 <= 1024, "barrier area");
-
 template <int G, int KSTEPS, bool BF16>
 cudaError_t prepare_t() {
     return cudaFuncSetAttribute(vote_tc_kernel<G, KSTEPS, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -653,10 +648,9 @@ cudaError_t launch_t(const VoteItem *items, int n_items, const ProbRef *probs, c
 // stream capture).
 cudaError_t prepare_vote_tc() {
     cudaError_t e = cudaSuccess;
-    const cudaError_t r[12] = {prepare_t<2, 1, false>(), prepare_t<2, 1, true>(), prepare_t<2, 2, false>(),
-                               prepare_t<2, 2, true>(),  prepare_t<4, 1, false>(), prepare_t<4, 1, true>(),
-                               prepare_t<4, 2, false>(), prepare_t<4, 2, true>(),  prepare_t<6, 1, false>(),
-                               prepare_t<6, 1, true>(),  prepare_t<6, 2, false>(), prepare_t<6, 2, true>()};
+    const cudaError_t r[8] = {prepare_t<2, 1, false>(), prepare_t<2, 1, true>(), prepare_t<2, 2, false>(),
+                              prepare_t<2, 2, true>(),  prepare_t<4, 1, false>(), prepare_t<4, 1, true>(),
+                              prepare_t<4, 2, false>(), prepare_t<4, 2, true>()};
     for (cudaError_t x : r)
         if (x != cudaSuccess) e = x;
     return e;
@@ -669,8 +663,7 @@ cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *pr
     const int grid = grid_blocks < n_items ? grid_blocks : n_items;
 #define RV_TC(G_, KS_, BF_) \
     launch_t<G_, KS_, BF_>(items, n_items, probs, lref, level_stride, level, pool, stats, band_req, grid, err_flag, s)
-#define RV_TC_G(KS_, BF_) \
-    (epilogue_groups == 6 ? RV_TC(6, KS_, BF_) : epilogue_groups == 4 ? RV_TC(4, KS_, BF_) : RV_TC(2, KS_, BF_))
+#define RV_TC_G(KS_, BF_) (epilogue_groups == 4 ? RV_TC(4, KS_, BF_) : RV_TC(2, KS_, BF_))
     switch (prec) {
     case ROT_PREC_FP16: return RV_TC_G(1, false);
     case ROT_PREC_BF16: return RV_TC_G(1, true);

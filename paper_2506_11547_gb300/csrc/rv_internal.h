@@ -11,7 +11,7 @@ namespace rv {
 
 constexpr int kMaxLevels = 12;      // refinement levels per problem
 constexpr int kMaxTopK = 64;
-constexpr int kPairTile = 128;      // pairs per pool tile (tensor-core B tile rows)
+constexpr int kPairTile = 256;      // pairs per pool tile (tensor-core B tile rows = MMA N)
 constexpr int kCellTile = 128;      // cells per tensor-core A tile (TMEM lanes)
 constexpr float kAmbig = 1e-6f;     // |v - tau| below this: the decision is reported ambiguous
 constexpr float kBandFP32 = 4e-6f;  // rigorous bound on |v_fast - v_exact| of the FP32 FMA form

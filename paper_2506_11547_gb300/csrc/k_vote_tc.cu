@@ -16,13 +16,15 @@
 //   warp 0      lane 0 streams 256-pair B tiles global -> shared with the bulk
 //               copy engine (cp.async.bulk + mbarrier complete_tx), kNB stages
 //   warp 1      allocates 512 TMEM columns; lane 0 issues tcgen05.mma
-//               (M = 128 cells, N = 256 pairs, K = 16 per instruction) into one
-//               of two accumulator stages of 256 columns, commits to mbarriers
+//               (M = 128 cells, N = 128 pairs, K = 16 per instruction), each
+//               half of a B tile into one of four accumulator stages of 128
+//               columns, and commits to mbarriers
 //   warps 2-3   build the 128-row A tile of each work item in shared memory
 //               (double buffered)
-//   warps 4..   G epilogue warpgroups: warpgroups g = s, s+2, ... drain stage s,
-//               each a 256/(G/2)-column slice; each thread owns one TMEM lane
-//               = one cell and reads 32 columns per tcgen05.ld.  Tests inside
+//   warps 4..   G epilogue warpgroups: 128-pair unit u goes to stage u % 4
+//               and warpgroup u % G (with G = 2 each warpgroup has two stages
+//               in flight); each thread owns one TMEM lane = one cell and
+//               reads 32 columns per tcgen05.ld.  Tests inside
 //               the band go to a per-warp shared-memory queue that is drained
 //               32 at a time (one lane per test), so no warp waits on one
 //               global load per flagged test.
@@ -45,11 +47,11 @@ namespace rv {
 namespace {
 
 constexpr int kNB = 5;                         // B stages
-constexpr int kNAcc = 2;                       // accumulator stages x 256 TMEM columns = 512
-constexpr int kUnit = kPairTile;               // pairs per accumulator stage = MMA N
+constexpr int kNAcc = 4;                       // accumulator stages x 128 TMEM columns = 512
+constexpr int kUnit = 128;                     // pairs per accumulator stage = MMA N (half a B tile)
 constexpr int kATileBytesMax = 128 * 32 * 2;   // 128 rows x K = 32 x 2 B
-constexpr int kBTileBytesMax = kUnit * 32 * 2; // 256 rows x K = 32 x 2 B
-constexpr int kALbo = 128 * 16, kBLbo = kUnit * 16;
+constexpr int kBTileBytesMax = kPairTile * 32 * 2; // 256 rows x K = 32 x 2 B
+constexpr int kALbo = 128 * 16, kBLbo = kPairTile * 16;
 // Deferred re-check state, per epilogue warp / warpgroup (after the barriers):
 //   queue   kQCap entries {pair offset in the item, lane | sign << 5} per warp
 //   rows    R (9), tau, pad per cell row, per warpgroup
@@ -331,11 +333,9 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     vote_tc_kernel(const VoteItem *__restrict__ items, int n_items, const ProbRef *__restrict__ probs,
                    const LevelRef *__restrict__ lref, int level_stride, int level, PairPool pool, ProbStats *stats,
                    float band_req, int *err_flag, uint32_t two) {
-    static_assert(G == 2 || G == 4, "epilogue warpgroups split the two accumulator stages evenly");
-    constexpr int kTileBytes = kUnit * 16 * KSTEPS * 2;  // 256 rows x K x 2 B
+    static_assert(G == 2 || G == 4, "every accumulator stage belongs to one warpgroup");
+    constexpr int kTileBytes = kPairTile * 16 * KSTEPS * 2;  // 256 rows x K x 2 B
     constexpr uint32_t IDESC = idesc_f16<BF16>();
-    constexpr int kPerStage = G / 2;           // warpgroups draining each stage
-    constexpr int kCols = kUnit / kPerStage;   // columns per warpgroup per unit
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;                          // 2 x kATileBytesMax
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
         }
         for (int s = 0; s < kNAcc; ++s) {
             mbar_init(&acc_full[s], 1);
-            mbar_init(&acc_empty[s], 4 * kPerStage);
+            mbar_init(&acc_empty[s], 4);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&a_full[s], 2);
@@ -426,24 +426,35 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 }
                 tc_fence_after();
                 const uint32_t a_addr = smem_u32(sA + ab * kATileBytesMax);
-                for (int t = 0; t < v.ntiles; ++t, ++j) {
-                    const int bs = (int)(j % kNB), as = (int)(j % kNAcc);
-                    const uint32_t ub = (uint32_t)(j / kNB), uc = (uint32_t)(j / kNAcc);
-                    if (!mbar_wait(&b_full[bs], ub & 1u, abort_flag) ||
-                        !mbar_wait(&acc_empty[as], (uc & 1u) ^ 1u, abort_flag)) {
+                for (int t = 0; t < v.ntiles && ok; ++t, ++j) {
+                    const int bs = (int)(j % kNB);
+                    const uint32_t ub = (uint32_t)(j / kNB);
+                    if (!mbar_wait(&b_full[bs], ub & 1u, abort_flag)) {
                         fail();
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
                     const uint32_t b_addr = smem_u32(sB + bs * kBTileBytesMax);
-                    const uint32_t d_tmem = tmem_base + (uint32_t)(as * kUnit);
 #pragma unroll
-                    for (int k = 0; k < KSTEPS; ++k)
-                        mma_f16(d_tmem, sdesc(a_addr + k * 2 * kALbo, kALbo), sdesc(b_addr + k * 2 * kBLbo, kBLbo),
-                                IDESC, k > 0 ? 1u : 0u);
+                    for (int h = 0; h < 2; ++h) {  // pairs 0-127 and 128-255: 16 row groups of 128 B each
+                        const int64_t u = 2 * j + h;
+                        const int as = (int)(u % kNAcc);
+                        const uint32_t uc = (uint32_t)(u / kNAcc);
+                        if (!mbar_wait(&acc_empty[as], (uc & 1u) ^ 1u, abort_flag)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d_tmem = tmem_base + (uint32_t)(as * kUnit);
+#pragma unroll
+                        for (int k = 0; k < KSTEPS; ++k)
+                            mma_f16(d_tmem, sdesc(a_addr + k * 2 * kALbo, kALbo),
+                                    sdesc(b_addr + h * 2048 + k * 2 * kBLbo, kBLbo), IDESC, k > 0 ? 1u : 0u);
+                        mma_commit(&acc_full[as]);
+                    }
+                    if (!ok) break;
                     mma_commit(&b_empty[bs]);
-                    mma_commit(&acc_full[as]);
                 }
                 if (!ok) break;
                 mma_commit(&a_empty[ab]);
@@ -458,8 +469,6 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     } else {
         // ------------------------------- epilogue ------------------------------
         const int g = (warp - 4) >> 2;        // warpgroup (0 .. G-1)
-        const int stage = g & 1;              // the accumulator stage it drains
-        const int col0 = (g >> 1) * kCols;    // its column slice of each unit
         const int q = warp & 3;               // TMEM lane quarter this warp may access
         const int row = 32 * q + lane;        // cell row of this thread
         uint2 *qw = q_all + (size_t)(warp - 4) * kQCap;  // this warp's re-check queue
@@ -470,11 +479,12 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             ItemView v;
             if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
-            const int64_t j0 = j;
+            const int64_t j0 = 2 * j;  // first 128-pair unit of the item
+            const int nunits = 2 * v.ntiles;
             j += v.ntiles;
-            // my units of this item: j0 + t with (j0 + t) % 2 == stage
-            int t = (int)(((int64_t)stage - (j0 & 1) + 2) & 1);
-            if (t >= v.ntiles) continue;
+            // my units of this item: j0 + t with (j0 + t) % G == g
+            int t = (int)(((int64_t)g - j0 % G + G) % G);
+            if (t >= nunits) continue;
             const int pos = v.W.cell_begin + row;
             const bool valid = pos < v.ncell;
             float tau = 0.f, band = -1.f;
@@ -571,8 +581,9 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     }
                 }
             };
-            for (; t < v.ntiles; t += 2) {
+            for (; t < nunits; t += G) {
                 const int64_t jj = j0 + t;
+                const int stage = (int)(jj % kNAcc);
                 const uint32_t uc = (uint32_t)(jj / kNAcc);
                 // warp-uniform outcome: every lane must reach the .sync.aligned tcgen05.ld below
                 if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[stage], uc & 1u, abort_flag))) {
@@ -581,22 +592,22 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t taddr =
-                    tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(stage * kUnit + col0);
-                const int pbase = t * kUnit + col0;
+                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(stage * kUnit);
+                const int pbase = t * kUnit;
                 // two-deep pipeline over 32-column chunks: chunk c+1 loads while chunk c is counted
                 uint32_t ra[32], rb[32];
                 tmem_ld32(taddr, ra);
                 tmem_ld_wait(ra);
-#pragma unroll 1
-                for (int c = 0; c < kCols; c += 64) {
-                    tmem_ld32(taddr + c + 32, rb);
-                    chunk_count(ra, pbase + c);
-                    tmem_ld_wait(rb);
-                    if (c + 64 < kCols) tmem_ld32(taddr + c + 64, ra);
-                    chunk_count(rb, pbase + c + 32);
-                    if (c + 64 < kCols) tmem_ld_wait(ra);
-                }
+                tmem_ld32(taddr + 32, rb);
+                chunk_count(ra, pbase);
+                tmem_ld_wait(rb);
+                tmem_ld32(taddr + 64, ra);
+                chunk_count(rb, pbase + 32);
+                tmem_ld_wait(ra);
+                tmem_ld32(taddr + 96, rb);
+                chunk_count(ra, pbase + 64);
+                tmem_ld_wait(rb);
+                chunk_count(rb, pbase + 96);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acc_empty[stage]);

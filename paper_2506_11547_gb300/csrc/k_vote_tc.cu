@@ -57,7 +57,7 @@ constexpr int kALbo = 128 * 16, kBLbo = kPairTile * 16;
 //   rows    R (9), tau, pad per cell row, per warpgroup
 //   corr    count correction per cell row, per warpgroup
 constexpr int kQCap = 64;
-constexpr int kMaxG = 4;
+constexpr int kMaxG = 6;
 constexpr size_t kQueueBytes = (size_t)4 * kMaxG * kQCap * 8;
 constexpr size_t kRowBytes = (size_t)kMaxG * 128 * 12 * 4;
 constexpr size_t kCorrBytes = (size_t)kMaxG * 128 * 4;
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     vote_tc_kernel(const VoteItem *__restrict__ items, int n_items, const ProbRef *__restrict__ probs,
                    const LevelRef *__restrict__ lref, int level_stride, int level, PairPool pool, ProbStats *stats,
                    float band_req, int *err_flag, uint32_t two) {
-    static_assert(G == 2 || G == 4, "every accumulator stage belongs to one warpgroup");
+    static_assert(G >= 1 && G <= kMaxG, "epilogue warpgroups");
     constexpr int kTileBytes = kPairTile * 16 * KSTEPS * 2;  // 256 rows x K x 2 B
     constexpr uint32_t IDESC = idesc_f16<BF16>();
     extern __shared__ uint8_t smem_raw[];
@@ -535,25 +535,19 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
             // sign bits with an integer multiply-add, the band by the minimum of
             // |D|; flagged values (rare) are queued for the FP32 re-check
             auto chunk_count = [&](const uint32_t (&r)[32], int poff) {
-                // four independent chains each, so consecutive instructions do not wait on one another
+                // independent chains (8 counts, 4 minima), so consecutive instructions do not wait on one another
                 float m0 = 4.f, m1 = 4.f, m2 = 4.f, m3 = 4.f;  // min |D| (|D| <= 4)
-                uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+                uint32_t c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
                 for (int e = 0; e < 32; e += 8) {
-                    c0 = add_sign(c0, r[e], two);
-                    c1 = add_sign(c1, r[e + 1], two);
-                    c2 = add_sign(c2, r[e + 2], two);
-                    c3 = add_sign(c3, r[e + 3], two);
-                    c0 = add_sign(c0, r[e + 4], two);
-                    c1 = add_sign(c1, r[e + 5], two);
-                    c2 = add_sign(c2, r[e + 6], two);
-                    c3 = add_sign(c3, r[e + 7], two);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) c[k] = add_sign(c[k], r[e + k], two);
                     m0 = min3_abs(m0, __uint_as_float(r[e]), __uint_as_float(r[e + 1]));
                     m1 = min3_abs(m1, __uint_as_float(r[e + 2]), __uint_as_float(r[e + 3]));
                     m2 = min3_abs(m2, __uint_as_float(r[e + 4]), __uint_as_float(r[e + 5]));
                     m3 = min3_abs(m3, __uint_as_float(r[e + 6]), __uint_as_float(r[e + 7]));
                 }
-                cnt += (int)(c0 + c1 + c2 + c3);
+                cnt += (int)(((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7])));
                 const bool hit = fminf(fminf(m0, m1), fminf(m2, m3)) <= band;
                 if (__any_sync(0xffffffffu, hit)) {  // rare: queue the flagged tests (warp-uniform branch)
                     uint32_t fm = 0, sm = 0;  // flag and sign masks, constant register indices only
@@ -594,20 +588,15 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(stage * kUnit);
                 const int pbase = t * kUnit;
-                // two-deep pipeline over 32-column chunks: chunk c+1 loads while chunk c is counted
-                uint32_t ra[32], rb[32];
-                tmem_ld32(taddr, ra);
-                tmem_ld_wait(ra);
-                tmem_ld32(taddr + 32, rb);
-                chunk_count(ra, pbase);
-                tmem_ld_wait(rb);
-                tmem_ld32(taddr + 64, ra);
-                chunk_count(rb, pbase + 32);
-                tmem_ld_wait(ra);
-                tmem_ld32(taddr + 96, rb);
-                chunk_count(ra, pbase + 64);
-                tmem_ld_wait(rb);
-                chunk_count(rb, pbase + 96);
+                // one 32-column chunk at a time (a TMEM load and wait cost ~30 cycles;
+                // the other warps on the sub-partition cover it)
+#pragma unroll 1
+                for (int c = 0; c < kUnit; c += 32) {
+                    uint32_t ra[32];
+                    tmem_ld32(taddr + c, ra);
+                    tmem_ld_wait(ra);
+                    chunk_count(ra, pbase + c);
+                }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acc_empty[stage]);
@@ -659,9 +648,10 @@ cudaError_t launch_t(const VoteItem *items, int n_items, const ProbRef *probs, c
 // stream capture).
 cudaError_t prepare_vote_tc() {
     cudaError_t e = cudaSuccess;
-    const cudaError_t r[8] = {prepare_t<2, 1, false>(), prepare_t<2, 1, true>(), prepare_t<2, 2, false>(),
-                              prepare_t<2, 2, true>(),  prepare_t<4, 1, false>(), prepare_t<4, 1, true>(),
-                              prepare_t<4, 2, false>(), prepare_t<4, 2, true>()};
+    const cudaError_t r[12] = {prepare_t<2, 1, false>(), prepare_t<2, 1, true>(), prepare_t<2, 2, false>(),
+                               prepare_t<2, 2, true>(),  prepare_t<4, 1, false>(), prepare_t<4, 1, true>(),
+                               prepare_t<4, 2, false>(), prepare_t<4, 2, true>(),  prepare_t<6, 1, false>(),
+                               prepare_t<6, 1, true>(),  prepare_t<6, 2, false>(), prepare_t<6, 2, true>()};
     for (cudaError_t x : r)
         if (x != cudaSuccess) e = x;
     return e;
@@ -674,7 +664,8 @@ cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *pr
     const int grid = grid_blocks < n_items ? grid_blocks : n_items;
 #define RV_TC(G_, KS_, BF_) \
     launch_t<G_, KS_, BF_>(items, n_items, probs, lref, level_stride, level, pool, stats, band_req, grid, err_flag, s)
-#define RV_TC_G(KS_, BF_) (epilogue_groups == 4 ? RV_TC(4, KS_, BF_) : RV_TC(2, KS_, BF_))
+#define RV_TC_G(KS_, BF_) \
+    (epilogue_groups == 6 ? RV_TC(6, KS_, BF_) : epilogue_groups == 4 ? RV_TC(4, KS_, BF_) : RV_TC(2, KS_, BF_))
     switch (prec) {
     case ROT_PREC_FP16: return RV_TC_G(1, false);
     case ROT_PREC_BF16: return RV_TC_G(1, true);

@@ -556,7 +556,7 @@ std::string Context::tune_key(const Plan &pl) const {
     return buf;
 }
 
-static std::vector<int> candidates(int tc_k) { return tc_k ? std::vector<int>{2, 4} : std::vector<int>{4, 8}; }
+static std::vector<int> candidates(int tc_k) { return tc_k ? std::vector<int>{2, 4, 6} : std::vector<int>{4, 8}; }
 
 int Context::choose_variant(Wave &w) {
     Plan &pl = w.plan;

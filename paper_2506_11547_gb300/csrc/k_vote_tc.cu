@@ -57,7 +57,7 @@ constexpr int kALbo = 128 * 16, kBLbo = kPairTile * 16;
 //   rows    R (9), tau, pad per cell row, per warpgroup
 //   corr    count correction per cell row, per warpgroup
 constexpr int kQCap = 64;
-constexpr int kMaxG = 6;
+constexpr int kMaxG = 4;
 constexpr size_t kQueueBytes = (size_t)4 * kMaxG * kQCap * 8;
 constexpr size_t kRowBytes = (size_t)kMaxG * 128 * 12 * 4;
 constexpr size_t kCorrBytes = (size_t)kMaxG * 128 * 4;
@@ -333,7 +333,10 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     vote_tc_kernel(const VoteItem *__restrict__ items, int n_items, const ProbRef *__restrict__ probs,
                    const LevelRef *__restrict__ lref, int level_stride, int level, PairPool pool, ProbStats *stats,
                    float band_req, int *err_flag, uint32_t two) {
-    static_assert(G >= 1 && G <= kMaxG, "epilogue warpgroups");
+    // Each warpgroup must own fixed stages and drain them in order: if G did not
+    // divide kNAcc, a warpgroup could wait on phase k+1 of a stage whose phase k
+    // is still pending, which an mbarrier parity wait cannot tell apart.
+    static_assert(G >= 1 && G <= kMaxG && kNAcc % G == 0, "epilogue warpgroups must divide the stages");
     constexpr int kTileBytes = kPairTile * 16 * KSTEPS * 2;  // 256 rows x K x 2 B
     constexpr uint32_t IDESC = idesc_f16<BF16>();
     extern __shared__ uint8_t smem_raw[];
@@ -648,10 +651,9 @@ cudaError_t launch_t(const VoteItem *items, int n_items, const ProbRef *probs, c
 // stream capture).
 cudaError_t prepare_vote_tc() {
     cudaError_t e = cudaSuccess;
-    const cudaError_t r[12] = {prepare_t<2, 1, false>(), prepare_t<2, 1, true>(), prepare_t<2, 2, false>(),
-                               prepare_t<2, 2, true>(),  prepare_t<4, 1, false>(), prepare_t<4, 1, true>(),
-                               prepare_t<4, 2, false>(), prepare_t<4, 2, true>(),  prepare_t<6, 1, false>(),
-                               prepare_t<6, 1, true>(),  prepare_t<6, 2, false>(), prepare_t<6, 2, true>()};
+    const cudaError_t r[8] = {prepare_t<2, 1, false>(), prepare_t<2, 1, true>(), prepare_t<2, 2, false>(),
+                              prepare_t<2, 2, true>(),  prepare_t<4, 1, false>(), prepare_t<4, 1, true>(),
+                              prepare_t<4, 2, false>(), prepare_t<4, 2, true>()};
     for (cudaError_t x : r)
         if (x != cudaSuccess) e = x;
     return e;
@@ -664,8 +666,7 @@ cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *pr
     const int grid = grid_blocks < n_items ? grid_blocks : n_items;
 #define RV_TC(G_, KS_, BF_) \
     launch_t<G_, KS_, BF_>(items, n_items, probs, lref, level_stride, level, pool, stats, band_req, grid, err_flag, s)
-#define RV_TC_G(KS_, BF_) \
-    (epilogue_groups == 6 ? RV_TC(6, KS_, BF_) : epilogue_groups == 4 ? RV_TC(4, KS_, BF_) : RV_TC(2, KS_, BF_))
+#define RV_TC_G(KS_, BF_) (epilogue_groups == 4 ? RV_TC(4, KS_, BF_) : RV_TC(2, KS_, BF_))
     switch (prec) {
     case ROT_PREC_FP16: return RV_TC_G(1, false);
     case ROT_PREC_BF16: return RV_TC_G(1, true);

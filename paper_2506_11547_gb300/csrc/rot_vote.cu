@@ -556,7 +556,7 @@ std::string Context::tune_key(const Plan &pl) const {
     return buf;
 }
 
-static std::vector<int> candidates(int tc_k) { return tc_k ? std::vector<int>{2, 4, 6} : std::vector<int>{4, 8}; }
+static std::vector<int> candidates(int tc_k) { return tc_k ? std::vector<int>{2, 4} : std::vector<int>{4, 8}; }
 
 int Context::choose_variant(Wave &w) {
     Plan &pl = w.plan;
@@ -598,7 +598,11 @@ int Context::choose_variant(Wave &w) {
         }
         int err = 0;
         cudaMemcpy(&err, pl.d_err, sizeof(int), cudaMemcpyDeviceToHost);
-        if (err) continue;  // a bounded wait expired: never choose this variant
+        if (err) {  // a bounded device-side wait expired: report it, never choose silently
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(ROT_VOTE_ETIMEDOUT, "a bounded device-side wait gave up while autotuning the vote");
+        }
         if (tot < best_ms) {
             best_ms = tot;
             best = v;

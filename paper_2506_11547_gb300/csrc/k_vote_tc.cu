@@ -12,22 +12,29 @@
 // are re-evaluated with the FP32 re-check |b - R_c a|^2/4 - c_i, whose error
 // is below 7e-7, so every decision with |v - tau| > 1e-6 is the FP64 one.
 //
-// One persistent CTA per SM:
+// One persistent CTA per SM.  The MMA unit is U = 256 or 128 pairs (N of one
+// tcgen05.mma) and TMEM holds 512 / U accumulator stages of U columns:
 //   warp 0      lane 0 streams 256-pair B tiles global -> shared with the bulk
 //               copy engine (cp.async.bulk + mbarrier complete_tx), kNB stages
 //   warp 1      allocates 512 TMEM columns; lane 0 issues tcgen05.mma
-//               (M = 128 cells, N = 128 pairs, K = 16 per instruction), each
-//               half of a B tile into one of four accumulator stages of 128
-//               columns, and commits to mbarriers
+//               (M = 128 cells, N = U pairs, K = 16 per instruction), each
+//               U-pair unit of a B tile into the next accumulator stage, and
+//               commits to mbarriers
 //   warps 2-3   build the 128-row A tile of each work item in shared memory
 //               (double buffered)
-//   warps 4..   G epilogue warpgroups: 128-pair unit u goes to stage u % 4
-//               and warpgroup u % G (with G = 2 each warpgroup has two stages
-//               in flight); each thread owns one TMEM lane = one cell and
-//               reads 32 columns per tcgen05.ld.  Tests inside
-//               the band go to a per-warp shared-memory queue that is drained
+//   warps 4..   G epilogue warpgroups; warpgroup g drains columns
+//               [g U/G, (g+1) U/G) of every unit in turn, so each has all
+//               stages in flight; each thread owns one TMEM lane = one cell and
+//               reads 16 or 32 columns per tcgen05.ld, double-buffered so the
+//               next load is in flight while it counts the current one: sign
+//               bits two per byte permute and the minimum of |D| two values per
+//               three-input minimum, with no warp vote per chunk.  Once per unit
+//               the warp votes on its chunks holding a value within the band
+//               (rare), reloads those from the stage it still holds and queues
+//               their tests in a per-warp shared-memory queue that is drained
 //               32 at a time (one lane per test), so no warp waits on one
 //               global load per flagged test.
+// The autotuner picks U, G and the chunk width per workload.
 // Every mbarrier wait is bounded (2 s or 2^24 polls): on expiry the CTA sets
 // *err_flag, stops all roles, waits (bounded) for its own copies and MMAs,
 // frees its TMEM and returns.
@@ -47,8 +54,7 @@ namespace rv {
 namespace {
 
 constexpr int kNB = 5;                         // B stages
-constexpr int kNAcc = 4;                       // accumulator stages x 128 TMEM columns = 512
-constexpr int kUnit = 128;                     // pairs per accumulator stage = MMA N (half a B tile)
+constexpr int kMaxAcc = 4;                     // accumulator stages (512 TMEM columns / unit width)
 constexpr int kATileBytesMax = 128 * 32 * 2;   // 128 rows x K = 32 x 2 B
 constexpr int kBTileBytesMax = kPairTile * 32 * 2; // 256 rows x K = 32 x 2 B
 constexpr int kALbo = 128 * 16, kBLbo = kPairTile * 16;
@@ -67,7 +73,7 @@ constexpr size_t kBarBytes = 1024;
 constexpr size_t kSmemBytes =
     1024 + 2 * kATileBytesMax + kNB * kBTileBytesMax + kBarBytes + kQueueBytes + kRowBytes + kCorrBytes;
 static_assert(kSmemBytes > 116 * 1024 && kSmemBytes <= 227 * 1024, "shared memory budget");
-static_assert((2 * kNB + 2 * kNAcc + 5) * 8 + 8 <= (int)kBarBytes, "barrier area");
+static_assert((2 * kNB + 2 * kMaxAcc + 5) * 8 + 8 <= (int)kBarBytes, "barrier area");
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint32_t kWaitPolls = 1u << 24;
 
@@ -144,29 +150,37 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                      smem_u32(bar))
                  : "memory");
 }
-// 32 consecutive 32-bit TMEM columns of this thread's lane; the wait binds the
-// registers so no use is scheduled before the data has arrived.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// N (16 or 32) consecutive 32-bit TMEM columns of this thread's lane; the
+// wait (for all of the thread's outstanding loads) binds the registers, so no
+// use is scheduled before the data has arrived.
+#define RV_R4(b) "=r"(r[b]), "=r"(r[b + 1]), "=r"(r[b + 2]), "=r"(r[b + 3])
+#define RV_W4(b) "+r"(r[b]), "+r"(r[b + 1]), "+r"(r[b + 2]), "+r"(r[b + 3])
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                 "[%16];\n"
+                 : RV_R4(0), RV_R4(4), RV_R4(8), RV_R4(12)
+                 : "r"(taddr)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
         "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : RV_R4(0), RV_R4(4), RV_R4(8), RV_R4(12), RV_R4(16), RV_R4(20), RV_R4(24), RV_R4(28)
         : "r"(taddr)
         : "memory");
 }
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" : RV_W4(0), RV_W4(4), RV_W4(8), RV_W4(12) : : "memory");
+}
 __device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
-                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 : RV_W4(0), RV_W4(4), RV_W4(8), RV_W4(12), RV_W4(16), RV_W4(20), RV_W4(24), RV_W4(28)
                  :
                  : "memory");
 }
+#undef RV_R4
+#undef RV_W4
 
 // Shared-memory matrix descriptor, canonical K-major layout without swizzle:
 // start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO = 128 B >> 4 (32-45), version 1 (46).
@@ -176,9 +190,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo) {
 }
 // Instruction descriptor of kind::f16: D = F32 (bit 4), A = B = F16 (0) or
 // BF16 (1) at bits 7 and 10, both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-template <bool BF16>
+template <bool BF16, int N>
 __host__ __device__ constexpr uint32_t idesc_f16() {
-    return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((uint32_t)(kUnit >> 3) << 17) |
+    return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
            ((128u >> 4) << 24);
 }
 
@@ -195,19 +209,23 @@ __device__ __forceinline__ float f16(uint16_t x) {
     return __half2float(__ushort_as_half(x));
 }
 
-// cnt + (x >> 31) as an integer multiply-add hi32(x * two) + cnt with
-// two == 2 passed at run time, so it stays a multiply-add on the FMA pipe and
-// leaves the half-rate ALU pipe to the band check.
-__device__ __forceinline__ uint32_t add_sign(uint32_t cnt, uint32_t x, uint32_t two) {
-    asm("mad.hi.u32 %0, %1, %2, %0;" : "+r"(cnt) : "r"(x), "r"(two));
-    return cnt;
+// Sign bytes of two FP32 values, each twice: bytes [s(a), s(b), s(a), s(b)] with
+// s(x) = 0xFF if x's sign bit is set, else 0 (byte permute with sign replication).
+__device__ __forceinline__ uint32_t sign_bytes2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, 0xFBFB;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
 }
-// min(m, |x|, |y|) in one three-input minimum.
+// Number of set sign bits among the 2k values whose sign_bytes2 words sum (mod 2^32)
+// to t, for k <= 63: t = 255 X with X = sum_i n_i 256^i (n_i <= 63 the count in
+// byte i, each value counted twice); 255 is odd, so X = t 255^-1 mod 2^32, and its
+// byte sum 2 (n_0 + n_1) is the top byte of X 0x01010101.  0xFBFCFDFF is
+// 255^-1 0x01010101 mod 2^32.
+__device__ __forceinline__ int sign_count(uint32_t t) { return (int)((t * 0xFBFCFDFFu) >> 25); }
+// min(m, |x|, |y|) (three-input minimum).
 __device__ __forceinline__ float min3_abs(float m, float x, float y) {
     float r;
-    asm("{\n .reg .f32 ax, ay;\n abs.f32 ax, %2;\n abs.f32 ay, %3;\n min.f32 %0, %1, ax, ay;\n}"
-        : "=f"(r)
-        : "f"(m), "f"(x), "f"(y));
+    asm("min.abs.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(m), "f"(x), "f"(y));
     return r;
 }
 
@@ -328,17 +346,22 @@ __device__ __noinline__ void build_a_tiles(const VoteItem *__restrict__ items, i
     }
 }
 
-template <int G, int KSTEPS, bool BF16>
+template <int G, int KSTEPS, bool BF16, int CH, int U>
 __global__ void __launch_bounds__(128 + 128 * G, 1)
     vote_tc_kernel(const VoteItem *__restrict__ items, int n_items, const ProbRef *__restrict__ probs,
                    const LevelRef *__restrict__ lref, int level_stride, int level, PairPool pool, ProbStats *stats,
-                   float band_req, int *err_flag, uint32_t two) {
-    // Each warpgroup must own fixed stages and drain them in order: if G did not
-    // divide kNAcc, a warpgroup could wait on phase k+1 of a stage whose phase k
-    // is still pending, which an mbarrier parity wait cannot tell apart.
-    static_assert(G >= 1 && G <= kMaxG && kNAcc % G == 0, "epilogue warpgroups must divide the stages");
+                   float band_req, int *err_flag) {
+    // Every warpgroup drains every stage, in unit order, so no wait ever runs
+    // more than one phase ahead of its stage (an mbarrier parity wait could not
+    // tell phase k+1 from a pending phase k).
+    constexpr int kNAcc = 512 / U;     // accumulator stages of U columns
+    constexpr int kUPT = kPairTile / U;  // units (MMAs of N = U) per B tile
+    static_assert((U == 128 || U == 256) && kNAcc <= kMaxAcc, "unit width");
+    static_assert(G >= 1 && G <= kMaxG && U % (32 * G) == 0, "epilogue warpgroups");
+    constexpr int kCols = U / G;  // columns of each unit per warpgroup
+    static_assert((CH == 16 || CH == 32) && (kCols == CH || kCols % (2 * CH) == 0), "TMEM chunks");
     constexpr int kTileBytes = kPairTile * 16 * KSTEPS * 2;  // 256 rows x K x 2 B
-    constexpr uint32_t IDESC = idesc_f16<BF16>();
+    constexpr uint32_t IDESC = idesc_f16<BF16, U>();
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;                          // 2 x kATileBytesMax
@@ -361,7 +384,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
         }
         for (int s = 0; s < kNAcc; ++s) {
             mbar_init(&acc_full[s], 1);
-            mbar_init(&acc_empty[s], 4);
+            mbar_init(&acc_empty[s], 4 * G);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&a_full[s], 2);
@@ -439,8 +462,8 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     }
                     const uint32_t b_addr = smem_u32(sB + bs * kBTileBytesMax);
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {  // pairs 0-127 and 128-255: 16 row groups of 128 B each
-                        const int64_t u = 2 * j + h;
+                    for (int h = 0; h < kUPT; ++h) {  // rows [h U, (h+1) U) of the B tile: U / 8 groups of 128 B
+                        const int64_t u = kUPT * j + h;
                         const int as = (int)(u % kNAcc);
                         const uint32_t uc = (uint32_t)(u / kNAcc);
                         if (!mbar_wait(&acc_empty[as], (uc & 1u) ^ 1u, abort_flag)) {
@@ -449,11 +472,11 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t d_tmem = tmem_base + (uint32_t)(as * kUnit);
+                        const uint32_t d_tmem = tmem_base + (uint32_t)(as * U);
 #pragma unroll
                         for (int k = 0; k < KSTEPS; ++k)
                             mma_f16(d_tmem, sdesc(a_addr + k * 2 * kALbo, kALbo),
-                                    sdesc(b_addr + h * 2048 + k * 2 * kBLbo, kBLbo), IDESC, k > 0 ? 1u : 0u);
+                                    sdesc(b_addr + h * (U / 8) * 128 + k * 2 * kBLbo, kBLbo), IDESC, k > 0 ? 1u : 0u);
                         mma_commit(&acc_full[as]);
                     }
                     if (!ok) break;
@@ -482,12 +505,9 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             ItemView v;
             if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
-            const int64_t j0 = 2 * j;  // first 128-pair unit of the item
-            const int nunits = 2 * v.ntiles;
-            j += v.ntiles;
-            // my units of this item: j0 + t with (j0 + t) % G == g
-            int t = (int)(((int64_t)g - j0 % G + G) % G);
-            if (t >= nunits) continue;
+            const int64_t j0 = j;  // first unit of the item
+            const int nunits = kUPT * v.ntiles;
+            j += nunits;
             const int pos = v.W.cell_begin + row;
             const bool valid = pos < v.ncell;
             float tau = 0.f, band = -1.f;
@@ -534,51 +554,53 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 __syncwarp();
                 qn = 0;
             };
-            // counts the 32 values of one chunk at pair offset poff in the item:
-            // sign bits with an integer multiply-add, the band by the minimum of
-            // |D|; flagged values (rare) are queued for the FP32 re-check
-            auto chunk_count = [&](const uint32_t (&r)[32], int poff) {
-                // independent chains (8 counts, 4 minima), so consecutive instructions do not wait on one another
+            // counts the CH values of one chunk: sign bits (D < 0) two per byte
+            // permute, summed two words per add; returns whether the chunk holds a
+            // value within the band (minimum of |D|, two values per three-input
+            // minimum).  No warp vote here, so consecutive chunks overlap.
+            auto chunk_count = [&](const uint32_t(&r)[CH]) -> uint32_t {
+                uint32_t t0 = 0, t1 = 0;
                 float m0 = 4.f, m1 = 4.f, m2 = 4.f, m3 = 4.f;  // min |D| (|D| <= 4)
-                uint32_t c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
-                for (int e = 0; e < 32; e += 8) {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) c[k] = add_sign(c[k], r[e + k], two);
+                for (int e = 0; e < CH; e += 8) {
+                    t0 = t0 + sign_bytes2(r[e], r[e + 1]) + sign_bytes2(r[e + 2], r[e + 3]);
+                    t1 = t1 + sign_bytes2(r[e + 4], r[e + 5]) + sign_bytes2(r[e + 6], r[e + 7]);
                     m0 = min3_abs(m0, __uint_as_float(r[e]), __uint_as_float(r[e + 1]));
                     m1 = min3_abs(m1, __uint_as_float(r[e + 2]), __uint_as_float(r[e + 3]));
                     m2 = min3_abs(m2, __uint_as_float(r[e + 4]), __uint_as_float(r[e + 5]));
                     m3 = min3_abs(m3, __uint_as_float(r[e + 6]), __uint_as_float(r[e + 7]));
                 }
-                cnt += (int)(((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7])));
-                const bool hit = fminf(fminf(m0, m1), fminf(m2, m3)) <= band;
-                if (__any_sync(0xffffffffu, hit)) {  // rare: queue the flagged tests (warp-uniform branch)
-                    uint32_t fm = 0, sm = 0;  // flag and sign masks, constant register indices only
-                    if (hit) {
+                cnt += sign_count(t0 + t1);
+                return fminf(fminf(m0, m1), fminf(m2, m3)) <= band ? 1u : 0u;
+            };
+            // queues the tests within the band of one chunk (pair offset poff in
+            // the item) for the FP32 re-check; hit: this lane's chunk holds one
+            auto chunk_queue = [&](const uint32_t(&r)[CH], int poff, bool hit) {
+                uint32_t fm = 0, sm = 0;  // flag and sign masks, constant register indices only
+                if (hit) {
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            fm |= (uint32_t)(fabsf(__uint_as_float(r[e])) <= band) << e;
-                            sm |= (r[e] >> 31) << e;
-                        }
-                    }
-                    const uint32_t lt = (1u << lane) - 1u;
-                    for (;;) {
-                        const bool has = fm != 0;
-                        const uint32_t bal = __ballot_sync(0xffffffffu, has);
-                        if (bal == 0) break;
-                        if (has) {
-                            const int e = __ffs((int)fm) - 1;
-                            fm &= fm - 1;
-                            qw[qn + __popc(bal & lt)] =
-                                make_uint2((uint32_t)(poff + e), (uint32_t)lane | (((sm >> e) & 1u) << 5));
-                        }
-                        qn += __popc(bal);
-                        __syncwarp();
-                        if (qn > kQCap - 32) flush();
+                    for (int e = 0; e < CH; ++e) {
+                        fm |= (uint32_t)(fabsf(__uint_as_float(r[e])) <= band) << e;
+                        sm |= (r[e] >> 31) << e;
                     }
                 }
+                const uint32_t lt = (1u << lane) - 1u;
+                for (;;) {
+                    const bool has = fm != 0;
+                    const uint32_t bal = __ballot_sync(0xffffffffu, has);
+                    if (bal == 0) break;
+                    if (has) {
+                        const int e = __ffs((int)fm) - 1;
+                        fm &= fm - 1;
+                        qw[qn + __popc(bal & lt)] =
+                            make_uint2((uint32_t)(poff + e), (uint32_t)lane | (((sm >> e) & 1u) << 5));
+                    }
+                    qn += __popc(bal);
+                    __syncwarp();
+                    if (qn > kQCap - 32) flush();
+                }
             };
-            for (; t < nunits; t += G) {
+            for (int t = 0; t < nunits; ++t) {
                 const int64_t jj = j0 + t;
                 const int stage = (int)(jj % kNAcc);
                 const uint32_t uc = (uint32_t)(jj / kNAcc);
@@ -589,16 +611,36 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(stage * kUnit);
-                const int pbase = t * kUnit;
-                // one 32-column chunk at a time (a TMEM load and wait cost ~30 cycles;
-                // the other warps on the sub-partition cover it)
+                const uint32_t taddr =
+                    tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(stage * U + g * kCols);
+                const int pbase = t * U + g * kCols;
+                // CH-column chunks, double-buffered: the load of the next chunk is in
+                // flight while this one is counted
+                uint32_t ra[CH], rb[CH];
+                uint32_t hm = 0;  // bit c: this lane's chunk c holds a value within the band
+                tmem_ld(taddr, ra);
+                tmem_ld_wait(ra);
+                if constexpr (kCols == CH) {
+                    hm = chunk_count(ra);
+                } else {
 #pragma unroll 1
-                for (int c = 0; c < kUnit; c += 32) {
-                    uint32_t ra[32];
-                    tmem_ld32(taddr + c, ra);
+                    for (int c = 0; c < kCols / CH; c += 2) {
+                        tmem_ld(taddr + (c + 1) * CH, rb);
+                        hm |= chunk_count(ra) << c;
+                        tmem_ld_wait(rb);
+                        const bool more = c + 2 < kCols / CH;
+                        if (more) tmem_ld(taddr + (c + 2) * CH, ra);
+                        hm |= chunk_count(rb) << (c + 1);
+                        if (more) tmem_ld_wait(ra);
+                    }
+                }
+                // rare (one warp vote per unit): reload the flagged chunks from the
+                // stage, still held, and queue their tests within the band
+                for (uint32_t any = __reduce_or_sync(0xffffffffu, hm); any != 0; any &= any - 1) {
+                    const int c = __ffs((int)any) - 1;
+                    tmem_ld(taddr + c * CH, ra);
                     tmem_ld_wait(ra);
-                    chunk_count(ra, pbase + c);
+                    chunk_queue(ra, pbase + c * CH, (hm >> c) & 1u);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -630,19 +672,42 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     }
 }
 
-template <int G, int KSTEPS, bool BF16>
+template <int G, int KSTEPS, bool BF16, int CH, int U>
 cudaError_t prepare_t() {
-    return cudaFuncSetAttribute(vote_tc_kernel<G, KSTEPS, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(vote_tc_kernel<G, KSTEPS, BF16, CH, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kSmemBytes);
 }
 
-template <int G, int KSTEPS, bool BF16>
-cudaError_t launch_t(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
+// The tile shapes the autotuner chooses from: variant = G (epilogue warpgroups)
+// + 10 if the TMEM chunks are 16 columns wide (else 32) + 100 if the MMA unit
+// is 128 pairs wide (four accumulator stages; else 256 pairs and two stages).
+#define RV_TC_VARIANTS(X) X(2, 32, 256, 2) X(4, 32, 256, 4) X(2, 16, 256, 12) X(4, 16, 256, 14) \
+    X(2, 32, 128, 102) X(4, 32, 128, 104) X(2, 16, 128, 112) X(4, 16, 128, 114)
+
+template <int KSTEPS, bool BF16>
+cudaError_t prepare_all() {
+    cudaError_t e = cudaSuccess, x;
+#define RV_PREP(G_, CH_, U_, V_) \
+    if ((x = prepare_t<G_, KSTEPS, BF16, CH_, U_>()) != cudaSuccess) e = x;
+    RV_TC_VARIANTS(RV_PREP)
+#undef RV_PREP
+    return e;
+}
+
+template <int KSTEPS, bool BF16>
+cudaError_t launch_v(int variant, const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                      int level_stride, int level, PairPool pool, ProbStats *stats, float band_req, int grid,
                      int *err_flag, cudaStream_t s) {
-    vote_tc_kernel<G, KSTEPS, BF16><<<grid, 128 + 128 * G, kSmemBytes, s>>>(items, n_items, probs, lref, level_stride,
-                                                                           level, pool, stats, band_req, err_flag, 2u);
-    return cudaGetLastError();
+    switch (variant) {
+#define RV_CASE(G_, CH_, U_, V_)                                                                             \
+    case V_:                                                                                                 \
+        vote_tc_kernel<G_, KSTEPS, BF16, CH_, U_><<<grid, 128 + 128 * G_, kSmemBytes, s>>>(                  \
+            items, n_items, probs, lref, level_stride, level, pool, stats, band_req, err_flag);              \
+        return cudaGetLastError();
+        RV_TC_VARIANTS(RV_CASE)
+#undef RV_CASE
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -650,23 +715,21 @@ cudaError_t launch_t(const VoteItem *items, int n_items, const ProbRef *probs, c
 // Sets the dynamic shared-memory limit of every variant (once, outside any
 // stream capture).
 cudaError_t prepare_vote_tc() {
-    cudaError_t e = cudaSuccess;
-    const cudaError_t r[8] = {prepare_t<2, 1, false>(), prepare_t<2, 1, true>(), prepare_t<2, 2, false>(),
-                              prepare_t<2, 2, true>(),  prepare_t<4, 1, false>(), prepare_t<4, 1, true>(),
-                              prepare_t<4, 2, false>(), prepare_t<4, 2, true>()};
+    const cudaError_t r[4] = {prepare_all<1, false>(), prepare_all<1, true>(), prepare_all<2, false>(),
+                              prepare_all<2, true>()};
     for (cudaError_t x : r)
-        if (x != cudaSuccess) e = x;
-    return e;
+        if (x != cudaSuccess) return x;
+    return cudaSuccess;
 }
 
 cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                            int level_stride, int level, PairPool pool, ProbStats *stats, int prec, float band_req,
-                           int epilogue_groups, int grid_blocks, int *err_flag, cudaStream_t s) {
+                           int variant, int grid_blocks, int *err_flag, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
     const int grid = grid_blocks < n_items ? grid_blocks : n_items;
-#define RV_TC(G_, KS_, BF_) \
-    launch_t<G_, KS_, BF_>(items, n_items, probs, lref, level_stride, level, pool, stats, band_req, grid, err_flag, s)
-#define RV_TC_G(KS_, BF_) (epilogue_groups == 4 ? RV_TC(4, KS_, BF_) : RV_TC(2, KS_, BF_))
+#define RV_TC_G(KS_, BF_) \
+    launch_v<KS_, BF_>(variant, items, n_items, probs, lref, level_stride, level, pool, stats, band_req, grid, \
+                       err_flag, s)
     switch (prec) {
     case ROT_PREC_FP16: return RV_TC_G(1, false);
     case ROT_PREC_BF16: return RV_TC_G(1, true);
@@ -675,7 +738,6 @@ cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *pr
     default: return cudaErrorInvalidValue;
     }
 #undef RV_TC_G
-#undef RV_TC
 }
 
 }  // namespace rv

@@ -556,7 +556,11 @@ std::string Context::tune_key(const Plan &pl) const {
     return buf;
 }
 
-static std::vector<int> candidates(int tc_k) { return tc_k ? std::vector<int>{2, 4} : std::vector<int>{4, 8}; }
+// CUDA-core form: cells per thread; tensor-core form: epilogue warpgroups, +10 for
+// 16-column TMEM chunks, +100 for 128-pair MMA units (four accumulator stages)
+static std::vector<int> candidates(int tc_k) {
+    return tc_k ? std::vector<int>{2, 4, 12, 14, 102, 104, 112, 114} : std::vector<int>{4, 8};
+}
 
 int Context::choose_variant(Wave &w) {
     Plan &pl = w.plan;

@@ -65,7 +65,8 @@ typedef enum {
     ROT_VOTE_EAGAIN = -4,       /* rot_vote_submit: admission queue full */
     ROT_VOTE_ETIMEDOUT = -5,    /* a bounded device-side wait gave up */
     ROT_VOTE_EDEGENERATE = -6,  /* fit degenerate: < 2 inliers or a repeated smallest eigenvalue */
-    ROT_VOTE_ENOTFOUND = -7     /* rot_vote_poll: unknown or already collected ticket */
+    ROT_VOTE_ENOTFOUND = -7,    /* rot_vote_poll: unknown or already collected ticket */
+    ROT_VOTE_ETOOLARGE = -8     /* rot_vote_count_cells_static: n or ncells above its static limits */
 } rot_vote_status;
 
 /* Arithmetic of the dominant (cell, pair) contraction.  All modes give the
@@ -187,6 +188,52 @@ void rot_vote_destroy(rot_vote_ctx *ctx);
 
 /* Text of the last error on ctx ("" if none); valid until the next call on ctx. */
 const char *rot_vote_last_error(const rot_vote_ctx *ctx);
+
+/* ---- Allocation-free vote (the paper has no counterpart: a deployment aid) ----
+ *
+ * rot_vote_count_cells_static counts, for each of ncells caller-given cells of
+ * the grid_n^3 grid (linear index (iz*grid_n + iy)*grid_n + ix), how many of
+ * the n pairs vote for it: the same FP32 CUDA-core vote, with the same exact
+ * counts, as a context's solve in ROT_PREC_FP32.  It allocates no device
+ * memory and calls no allocating library routine: its pair pool, cell table
+ * and work lists live in one file-scope static device array of
+ * ROT_VOTE_STATIC_SCRATCH_BYTES that every GPU which loads the library holds
+ * until the process exits.  It is for callers that cannot allocate device
+ * memory: code running inside a framework whose caching allocator owns the
+ * device's memory (a cudaMalloc behind its back can fail or fragment it), and
+ * per-frame real-time loops that cannot take the device-wide synchronisation
+ * of cudaFree.
+ *
+ * Arguments
+ *   a, b    device (or managed) float32 [n][3], unit vectors, b_i ~ R a_i
+ *   n       2 <= n <= ROT_VOTE_STATIC_MAX_PAIRS
+ *   delta   inlier angle threshold, 0 < delta < pi/2 (rounded to float, as in
+ *           rot_vote_problem)
+ *   grid_n  grid side, a power of two in [2, 2^20]
+ *   cells   device int64 [ncells] linear cell indices; each cell's box must
+ *           meet the unit ball (a cell of the level table)
+ *   ncells  1 <= ncells <= ROT_VOTE_STATIC_MAX_CELLS
+ *   counts  device int32 [ncells], written (the call zeroes it first)
+ *   cuda_stream  cudaStream_t to run on (NULL = the legacy default stream)
+ * The call runs on the current device and returns after the counts are
+ * written (it synchronises cuda_stream).  The caller owns every buffer.
+ *
+ * Returns OK; ETOOLARGE (n or ncells above the limits, nothing launched);
+ * EINVAL (bad argument, a pointer that is not device memory, a non-unit or
+ * non-finite input vector, or a cell index outside the level table -- counts
+ * are then unspecified); ECUDA.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the one array and leaves its contents behind;
+ * each call rewrites everything it reads before reading it.  Calls whose work
+ * overlaps on the GPU (other host threads, other streams) race on the array:
+ * serialise them. */
+#define ROT_VOTE_STATIC_SCRATCH_BYTES (4 << 20)
+#define ROT_VOTE_STATIC_MAX_PAIRS 32768
+#define ROT_VOTE_STATIC_MAX_CELLS 8192
+int rot_vote_count_cells_static(const float *a, const float *b, int64_t n, double delta, int grid_n,
+                                const int64_t *cells, int32_t ncells, int32_t *counts, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "librot_vote.so")
 
-OK, PENDING, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEDOUT, EDEGENERATE, ENOTFOUND = 0, 1, -1, -2, -3, -4, -5, -6, -7
+OK, PENDING, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEDOUT, EDEGENERATE, ENOTFOUND, ETOOLARGE = 0, 1, -1, -2, -3, -4, -5, -6, -7, -8
+STATIC_SCRATCH_BYTES, STATIC_MAX_PAIRS, STATIC_MAX_CELLS = 4 << 20, 32768, 8192
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2, "fp16x2": 3, "bf16x2": 4}
 RANK = {"excess": 0, "raw": 1}
 
@@ -51,7 +52,7 @@ STAGE_KIND = {0: "pair_prep", 1: "vote", 2: "topk", 3: "children", 4: "fit"}
 _lib = None
 
 EXPORTS = ("rot_vote_create", "rot_vote_solve", "rot_vote_submit", "rot_vote_poll", "rot_vote_level_trace",
-           "rot_vote_stage_times", "rot_vote_destroy", "rot_vote_last_error")
+           "rot_vote_stage_times", "rot_vote_destroy", "rot_vote_last_error", "rot_vote_count_cells_static")
 
 
 def load(path: str = LIB_PATH):
@@ -79,6 +80,9 @@ def load(path: str = LIB_PATH):
     L.rot_vote_destroy.restype = None
     L.rot_vote_last_error.argtypes = [C.c_void_p]
     L.rot_vote_last_error.restype = C.c_char_p
+    L.rot_vote_count_cells_static.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, C.c_void_p,
+                                              C.c_int32, C.c_void_p, C.c_void_p]
+    L.rot_vote_count_cells_static.restype = C.c_int
     _lib = L
     return L
 
@@ -239,3 +243,15 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def count_cells_static(a, b, delta: float, grid_n: int, cells, counts, cuda_stream: int = 0) -> int:
+    """rot_vote_count_cells_static: vote counts of the listed cells into `counts`
+    with no device allocation.  a, b: device float32 [n, 3]; cells: device int64
+    [ncells]; counts: device int32 [ncells].  Returns the rot_vote status."""
+    for t, dt in ((a, "torch.float32"), (b, "torch.float32"), (cells, "torch.int64"), (counts, "torch.int32")):
+        if str(t.dtype) != dt or not t.is_contiguous():
+            raise TypeError(f"expected a contiguous {dt} device tensor")
+    return int(load().rot_vote_count_cells_static(a.data_ptr(), b.data_ptr(), int(a.shape[0]), float(delta),
+                                                  int(grid_n), cells.data_ptr(), int(cells.shape[0]),
+                                                  counts.data_ptr(), int(cuda_stream) or None))

@@ -30,6 +30,12 @@
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
  * arithmetic is the written sequence of IEEE double operations).
+ *
+ * Pins (tests/test_oracle_pins.py): steps 1-7 and the fit of a given inlier
+ * set are each checked against the paper's closed forms, brute force, an
+ * independent lattice count or numpy/SVD.  Parity unpinned: the refit
+ * iteration of step 8 (its delta-only inlier rule and stopping rule) has no
+ * check beyond noise-free recovery of the true rotation.
  */
 #include <math.h>
 #include <pthread.h>

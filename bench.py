@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--no-extra", action="store_true", help="skip the precision-form comparison")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the precision-form, batched and serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--only-solve", action="store_true",
                     help="warm-up + timed solves only (a short, fixed launch sequence for profiler captures)")
     return ap.parse_args()
@@ -153,6 +155,124 @@ def cpu_oracle_rate(p, grid_n, seconds: float, threads: int):
     oracle.vote_cells(p.a, p.b, float(np.float32(p.delta)), grid_n, cells[order[:m]], nthreads=threads)
     dt = time.perf_counter() - t0
     return m * p.n / dt, m, dt
+
+
+def bench_batched(rv, synth, torch, stream, flush, launches: int = 3):
+    """4096 independent problems (N log-uniform in [50, 2e4], outliers U[0.5, 0.95],
+    sigma U[0.001, 0.02], delta = 3 sigma; 32^3 + 2 levels) in one rot_vote_solve
+    call: one pass of the pipeline over all of them, replayed from a CUDA graph."""
+    probs = synth.batched_problems(4096)
+    dev = [(torch.from_numpy(p.a).cuda(), torch.from_numpy(p.b).cuda()) for p in probs]
+    P = len(probs)
+    arr = (rv.rot_vote_problem * P)()
+    keep = []
+    for k, p in enumerate(probs):
+        arr[k], kk = rv.problem(dev[k][0], dev[k][1], p.delta)
+        keep.append(kk)
+    out = (rv.rot_vote_result * P)()
+    res = {}
+    for prec in ("fp16x2", "fp32"):
+        ctx = rv.Context(grid_n=32, levels=2, precision=prec, cuda_stream=stream.cuda_stream)
+        for _ in range(2):  # autotune + graph capture, then a replay
+            ctx.solve_raw(arr, P, out)
+        ts = []
+        for _ in range(launches):
+            flush.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            ctx.solve_raw(arr, P, out)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(s0.elapsed_time(s1))
+        ctx.close()
+        ms = sum(ts) / len(ts)
+        tests = sum(int(out[k].tests) for k in range(P))
+        res[prec] = {"value": tests / (ms / 1e3), "unit": "cell-correspondence tests/s",
+                     "rotations_per_s": P / (ms / 1e3), "ms_per_call": ms, "problems": P,
+                     "tests_per_call": tests, "status_ok": sum(int(out[k].status == 0) for k in range(P)),
+                     "degenerate": sum(int(out[k].status == -6) for k in range(P))}
+    res["workload"] = ("4096 problems, N log-uniform [50, 2e4] (sum N = %d), outliers U[0.5, 0.95], "
+                       "sigma U[0.001, 0.02], delta = 3 sigma; 32^3 + 2 levels; one call (CUDA graph replay)"
+                       % sum(p.n for p in probs))
+    return res
+
+
+def bench_serving(rv, synth, torch, seconds: float, rate_hz: float = 2000.0, distinct: int = 512):
+    """Poisson arrivals at rate_hz (N log-uniform [100, 1e5], outliers U[0.8, 0.99],
+    sigma 0.01, delta 0.03; 32^3 + 2 levels, FP16 hi/lo form) through
+    rot_vote_submit / rot_vote_poll while earlier requests run; `distinct`
+    generated problems are cycled."""
+    import numpy as np
+    t_arr, probs = synth.serving_stream(distinct, rate_hz=rate_hz)
+    gaps = np.diff(t_arr, prepend=0.0)
+    dev = [(torch.from_numpy(p.a).cuda(), torch.from_numpy(p.b).cuda(), p.delta) for p in probs]
+    ctx = rv.Context(grid_n=32, levels=2, precision="fp16x2", max_inflight=256)
+    # warm-up at the same rate for 1 s (tuning, workspace growth), then the timed stream
+    due = time.perf_counter()
+    warm = []
+    for k in range(int(rate_hz)):
+        due += gaps[k % distinct]
+        while time.perf_counter() < due:
+            pass
+        t = ctx.submit(*dev[k % distinct])
+        if t > 0:
+            warm.append(t)
+    for t in warm:
+        while ctx.poll(t, timeout_us=10000) is None:
+            pass
+    total = int(seconds * rate_hz)
+    lat, tests, done_t = [], [0], []
+    tickets, refused = [], [0]
+    lock = threading.Lock()
+    finished = threading.Event()
+
+    def poller():
+        pending = []
+        while True:
+            with lock:
+                pending.extend(tickets)
+                tickets.clear()
+            if not pending and finished.is_set():
+                return
+            keep_p = []
+            for t in pending:
+                r = ctx.poll(t, timeout_us=0)
+                if r is None:
+                    keep_p.append(t)
+                else:
+                    lat.append(r.latency_ms)
+                    tests[0] += r.tests
+                    done_t.append(time.perf_counter())
+            pending = keep_p
+            time.sleep(0.0002)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    due = t0
+    for k in range(total):
+        due += gaps[k % distinct] if k else 0.0
+        while time.perf_counter() < due:
+            pass
+        t = ctx.submit(*dev[k % distinct])
+        if t < 0:
+            refused[0] += 1
+        else:
+            with lock:
+                tickets.append(t)
+    t_sub = time.perf_counter() - t0
+    finished.set()
+    th.join()
+    ctx.close()
+    span = max(done_t) - t0
+    return {"rotations_per_s": len(lat) / span, "offered_per_s": total / t_sub,
+            "tests_per_s": tests[0] / span, "unit": "rotations/s",
+            "latency_ms": {"p50": percentile(lat, 50), "p90": percentile(lat, 90), "p99": percentile(lat, 99),
+                           "max": max(lat)},
+            "completed": len(lat), "refused_eagain": refused[0],
+            "workload": ("Poisson %.0f/s for %.1f s; N log-uniform [100, 1e5], outliers U[0.8, 0.99], sigma 0.01, "
+                         "delta 0.03; 32^3 + 2 levels; fp16x2; %d distinct problems cycled; after a 1 s warm-up at the same "
+                         "rate; latency = submit to result ready (library clock)" % (rate_hz, seconds, distinct))}
 
 
 def run_reference(args):
@@ -347,6 +467,11 @@ def main():
                                                        list(rr.q) == list(res0.q))}
             cx.close()
 
+    batched = serving = None
+    if not args.no_extra and ws == 1:
+        batched = bench_batched(rv, synth, torch, stream, flush)
+        serving = bench_serving(rv, synth, torch, args.serve_seconds)
+
     lat = per
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -363,6 +488,8 @@ def main():
         "roofline": roofline,
         "stage_ms": {f"{k[0]}:{k[1]}": v for k, v in sorted(stage_avg.items(), key=lambda x: -x[1])},
         "precision_forms": extra,
+        "batched": batched,
+        "serving": serving,
         "clocks": clocks,
         "cpu_baseline": cpu,
         "result": {"status": res0.status, "angle_to_truth_rad": None, "rechecked": res0.rechecked,

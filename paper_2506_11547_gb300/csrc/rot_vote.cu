@@ -562,16 +562,42 @@ static std::vector<int> candidates(int tc_k) {
     return tc_k ? std::vector<int>{2, 4, 12, 14, 102, 104, 112, 114} : std::vector<int>{4, 8};
 }
 
-int Context::choose_variant(Wave &w) {
+// The tuned variant of the bucket nearest to `key` (same SM count and
+// precision; distance in the two log2 size coordinates), or -1 if none.
+int Context::nearest_tuned(const std::string &key) const {
+    int sm = 0, prec = 0, te = 0, pe = 0;
+    if (sscanf(key.c_str(), "sm%d:prec%d:tests2^%d:probs2^%d", &sm, &prec, &te, &pe) != 4) return -1;
+    int best = -1, best_d = 1 << 30;
+    for (const auto &kv : tuned) {
+        int sm2 = 0, prec2 = 0, te2 = 0, pe2 = 0;
+        if (sscanf(kv.first.c_str(), "sm%d:prec%d:tests2^%d:probs2^%d", &sm2, &prec2, &te2, &pe2) != 4) continue;
+        if (sm2 != sm || prec2 != prec) continue;
+        const int d = std::abs(te2 - te) + std::abs(pe2 - pe);
+        if (d < best_d) {
+            best_d = d;
+            best = kv.second;
+        }
+    }
+    return best;
+}
+
+int Context::choose_variant(Wave &w, bool serving) {
     Plan &pl = w.plan;
     const std::vector<int> cand = candidates(pl.pool.tc_k);
-    pl.variant = cand[pl.pool.tc_k ? 0 : 0];
+    pl.variant = cand[0];
     if (cfg.autotune < 0) return ROT_VOTE_OK;
     const std::string key = tune_key(pl);
     auto it = tuned.find(key);
     if (it != tuned.end()) {
         pl.variant = it->second;
         return ROT_VOTE_OK;
+    }
+    if (serving) {  // never stall the serving scheduler on a new size bucket once one is tuned
+        const int near = nearest_tuned(key);
+        if (near >= 0) {
+            pl.variant = near;
+            return ROT_VOTE_OK;
+        }
     }
     char *B = (char *)w.base;
     cudaEvent_t e0, e1;
@@ -642,7 +668,7 @@ void Context::save_tuning(const std::string &key, int v, float ms) {
 }
 
 // Plans, uploads and launches a batch on wave w (asynchronous).
-int Context::launch_batch(Wave &w, const rot_vote_problem *p, const std::vector<int> &sel) {
+int Context::launch_batch(Wave &w, const rot_vote_problem *p, const std::vector<int> &sel, bool serving) {
     const std::string old_sig = w.plan.signature;
     const int old_variant = w.plan.variant;
     const bool had_graph = w.graph_exec != nullptr;
@@ -652,7 +678,7 @@ int Context::launch_batch(Wave &w, const rot_vote_problem *p, const std::vector<
     if (rc != ROT_VOTE_OK) return fail(rc, "pinned result allocation failed");
     rc = upload(w, p, sel);
     if (rc != ROT_VOTE_OK) return rc;
-    rc = choose_variant(w);
+    rc = choose_variant(w, serving);
     if (rc != ROT_VOTE_OK) return rc;
     if (w.plan.variant != old_variant) w.plan.signature += "|changed";
     cudaError_t e = cudaEventRecord(w.ev0, w.stream);
@@ -711,7 +737,7 @@ int Context::collect(Wave &w, const std::vector<int> &sel, rot_vote_result *out)
 // ---------------------------------------------------------------------------
 int Wave::ensure(size_t bytes, Context &ctx) {
     if (bytes <= cap) return ROT_VOTE_OK;
-    const size_t want = std::max(bytes, cap + cap / 2);
+    const size_t want = std::max(bytes, 2 * cap);  // geometric growth: few reallocations
     if (ctx.bytes_held - cap + want > ctx.budget) {
         if (ctx.bytes_held - cap + bytes > ctx.budget) {
             ctx.last_error = "workspace exceeds the device memory budget";

@@ -142,10 +142,11 @@ class Context {
     int enqueue_pipeline(Wave &w);
     cudaError_t launch_vote(Wave &w, int lev, int variant);
     std::string tune_key(const Plan &pl) const;
-    int choose_variant(Wave &w);
+    int choose_variant(Wave &w, bool serving);
+    int nearest_tuned(const std::string &key) const;
     void load_tuning();
     void save_tuning(const std::string &key, int v, float ms);
-    int launch_batch(Wave &w, const rot_vote_problem *p, const std::vector<int> &sel);
+    int launch_batch(Wave &w, const rot_vote_problem *p, const std::vector<int> &sel, bool serving = false);
     int collect(Wave &w, const std::vector<int> &sel, rot_vote_result *out);
     int solve(const rot_vote_problem *p, int n, rot_vote_result *out);
     int level_trace(int problem, int level, int64_t *idx, int32_t *count, int64_t cap, int64_t *ncells,

@@ -173,7 +173,7 @@ void Context::sched_loop() {
                 for (int k = 0; k < take; ++k) sel[k] = k;
                 const int saved_graphs = cfg.use_graphs;
                 cfg.use_graphs = -1;  // every serving batch has its own shape: launch directly
-                rc = launch_batch(w, probs.data(), sel);
+                rc = launch_batch(w, probs.data(), sel, true);
                 cfg.use_graphs = saved_graphs;
                 if (rc != ROT_VOTE_ENOMEM) break;
                 take /= 2;  // memory-based admission: admit fewer and retry

@@ -1,0 +1,95 @@
+"""Serving (rot_vote_submit / rot_vote_poll): continuous batching on several
+overlapping waves.  Each result must be the same when the problem is solved
+alone and when it runs in the mix; the queue bound answers EAGAIN; poll has
+PENDING / ENOTFOUND semantics; invalid problems are rejected at submit."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2506_11547_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+from paper_2506_11547_gb300 import rot_vote as rv  # noqa: E402
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _same(r, s):
+    return (np.array_equal(r.q, s.q) and r.best_cell == s.best_cell and r.best_count == s.best_count
+            and r.inliers == s.inliers and r.tests == s.tests and r.rechecked == s.rechecked
+            and r.status == s.status)
+
+
+def _drain(ctx, tickets, timeout_s=120.0):
+    out = {}
+    t_end = time.time() + timeout_s
+    while len(out) < len(tickets) and time.time() < t_end:
+        for t in tickets:
+            if t not in out:
+                r = ctx.poll(t, timeout_us=2000)
+                if r is not None:
+                    out[t] = r
+    assert len(out) == len(tickets), "serving did not finish in time"
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp16x2", "fp32"])
+def test_serving_result_same_alone_and_in_the_mix(prec):
+    rng = np.random.default_rng(11)
+    ns = np.exp(rng.uniform(np.log(60), np.log(8000), size=40)).astype(int)
+    probs = [synth.make_problem(int(n), rho=float(rng.uniform(0.5, 0.95)), sigma=0.01, delta=0.03,
+                                seed=500 + k) for k, n in enumerate(ns)]
+    args = [(_dev(p.a), _dev(p.b), p.delta) for p in probs]
+    with rv.Context(grid_n=16, levels=2, precision=prec, max_inflight=8) as ctx:
+        # burst: later problems are queued while earlier waves are on the device
+        tickets = [ctx.submit(*x) for x in args]
+        assert all(t > 0 for t in tickets)
+        mixed = _drain(ctx, tickets)
+    with rv.Context(grid_n=16, levels=2, precision=prec) as ctx:
+        alone = [ctx.solve([x])[0] for x in args]
+    for t, ra in zip(tickets, alone):
+        rm = mixed[t]
+        assert rm.latency_ms > 0
+        assert _same(rm, ra)
+
+
+def test_serving_queue_bound_and_poll_semantics():
+    p = synth.make_problem(2000, rho=0.9, sigma=0.01, delta=0.03, seed=77)
+    x = (_dev(p.a), _dev(p.b), p.delta)
+    with rv.Context(grid_n=16, levels=1, precision="fp32", max_inflight=1) as ctx:
+        tickets, refused = [], 0
+        for _ in range(64):  # the admission queue holds max_inflight * 8 problems
+            t = ctx.submit(*x)
+            if t < 0:
+                refused += 1
+            else:
+                tickets.append(t)
+        assert refused > 0
+        with pytest.raises(rv.RotVoteError) as e:
+            ctx.poll(max(tickets) + 1000)
+        assert e.value.code == rv.ENOTFOUND
+        res = _drain(ctx, tickets)
+        assert all(r.status == rv.OK for r in res.values())
+        assert len({tuple(r.q) for r in res.values()}) == 1  # same problem, same answer
+        with pytest.raises(rv.RotVoteError) as e:  # a collected ticket is released
+            ctx.poll(tickets[0])
+        assert e.value.code == rv.ENOTFOUND
+
+
+def test_serving_rejects_invalid_problem_at_submit():
+    p = synth.make_problem(100, rho=0.5, sigma=0.01, delta=0.03, seed=3)
+    with rv.Context(grid_n=16, levels=0) as ctx:
+        with pytest.raises(rv.RotVoteError) as e:
+            ctx.submit(_dev(p.a[:1]), _dev(p.b[:1]), p.delta)  # n < 2
+        assert e.value.code == rv.EINVAL
+        with pytest.raises(rv.RotVoteError) as e:
+            ctx.submit(_dev(p.a), _dev(p.b), 2.0)  # delta outside (0, pi/2)
+        assert e.value.code == rv.EINVAL

@@ -108,7 +108,13 @@ typedef struct {
     int autotune;             /* 1 = on the first solve of each shape class (precision, size bucket), time
                                  every vote tile-shape candidate on its coarse level and keep the fastest
                                  (cached per context; appended to the file named by the environment
-                                 variable ROT_VOTE_TUNE_CACHE if set); default 1; negative = off */
+                                 variable ROT_VOTE_TUNE_CACHE if set); default 1; negative = off
+                                 (a fixed default shape); >= 2 = always use the tile shape with this
+                                 code (tests, diagnostics): FP32 form 4, 8 (scalar kernel, cells per
+                                 thread) or 102, 104 (packed f32x2 kernel); tensor-core forms 2, 4
+                                 (epilogue warpgroups) + 10 (16-column TMEM chunks) + 100 (128-pair
+                                 MMA units), i.e. 2, 4, 12, 14, 102, 104, 112, 114.  A code that
+                                 does not exist for the precision fails the solve with EINVAL. */
 } rot_vote_config;
 
 /* One problem.  a, b: [n, 3] row-major float32 unit vectors (host or device).

@@ -139,6 +139,14 @@ __global__ void pair_prep_kernel(const ProbRef *__restrict__ probs, const int2 *
     pool.s32[3 * g + 2] = make_float4(s[8], s[9], 0.f, 0.f);
     pool.pr[2 * g + 0] = p0;
     pool.pr[2 * g + 1] = p1;
+    if (pool.s2x) {  // pair-interleaved copy for the packed FP32 vote
+        float *x = reinterpret_cast<float *>(pool.s2x + (g >> 1) * 5);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            x[4 * k + (g & 1)] = s[2 * k];
+            x[4 * k + 2 + (g & 1)] = s[2 * k + 1];
+        }
+    }
     if (tc_prec != ROT_PREC_FP32 && pool.tcb) {
         const int K = pool.tc_k;
         uint8_t *tile = reinterpret_cast<uint8_t *>(pool.tcb) + (g / kPairTile) * (int64_t)(kPairTile * K * 2);

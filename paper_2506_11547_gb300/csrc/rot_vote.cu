@@ -271,6 +271,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     const size_t o_s32 = reserve(sizeof(float4) * 3 * (size_t)pool);
     const size_t o_pr = reserve(sizeof(float4) * 2 * (size_t)pool);
     const size_t o_tcb = tck ? reserve((size_t)pool * tck * 2) : 0;
+    const size_t o_s2x = tck ? 0 : reserve(sizeof(float4) * 5 * (size_t)(pool / 2));
     const size_t o_member = reserve((size_t)pool);
     const size_t o_tiles = reserve(sizeof(int2) * (size_t)(pool / kPairTile + 1));
     // zeroed region: counts, child counts, stats, nkept
@@ -325,6 +326,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     pl.pool.pr = (float4 *)(B + o_pr);
     pl.pool.tcb = tck ? (void *)(B + o_tcb) : nullptr;
     pl.pool.tc_k = tck;
+    pl.pool.s2x = tck ? nullptr : (float4 *)(B + o_s2x);
     pl.d_member = (uint8_t *)(B + o_member);
     pl.d_tiles = (int2 *)(B + o_tiles);
     pl.zero_off = z0;
@@ -556,10 +558,10 @@ std::string Context::tune_key(const Plan &pl) const {
     return buf;
 }
 
-// CUDA-core form: cells per thread; tensor-core form: epilogue warpgroups, +10 for
+// CUDA-core form: cells per thread, +100 for the packed f32x2 kernel; tensor-core form: epilogue warpgroups, +10 for
 // 16-column TMEM chunks, +100 for 128-pair MMA units (four accumulator stages)
 static std::vector<int> candidates(int tc_k) {
-    return tc_k ? std::vector<int>{2, 4, 12, 14, 102, 104, 112, 114} : std::vector<int>{4, 8};
+    return tc_k ? std::vector<int>{2, 4, 12, 14, 102, 104, 112, 114} : std::vector<int>{102, 104, 4, 8};
 }
 
 // The tuned variant of the bucket nearest to `key` (same SM count and
@@ -586,6 +588,12 @@ int Context::choose_variant(Wave &w, bool serving) {
     const std::vector<int> cand = candidates(pl.pool.tc_k);
     pl.variant = cand[0];
     if (cfg.autotune < 0) return ROT_VOTE_OK;
+    if (cfg.autotune >= 2) {  // a forced tile shape
+        if (std::find(cand.begin(), cand.end(), cfg.autotune) == cand.end())
+            return fail(ROT_VOTE_EINVAL, "autotune names a tile shape that does not exist for this precision");
+        pl.variant = cfg.autotune;
+        return ROT_VOTE_OK;
+    }
     const std::string key = tune_key(pl);
     auto it = tuned.find(key);
     if (it != tuned.end()) {

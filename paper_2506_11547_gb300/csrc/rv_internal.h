@@ -90,6 +90,9 @@ struct PairPool {
     float4 *pr;
     void *tcb;
     int tc_k;  // 16 or 32 (0 if absent)
+    // [P/2][5] float4, pairs (i, i+1) interleaved for the packed FP32 vote:
+    // float4 k of pair-pair j = (s_2k(2j), s_2k(2j+1), s_2k+1(2j), s_2k+1(2j+1)); null if absent
+    float4 *s2x = nullptr;
 };
 
 // ---- launchers (each returns cudaGetLastError() of its launch) ----
@@ -101,9 +104,10 @@ cudaError_t launch_build_level0(const int4 *rows, int nrows, int n, int64_t ncel
 cudaError_t launch_pair_prep(const ProbRef *probs, const int2 *tiles, int ntiles, PairPool pool, int tc_prec,
                              ProbStats *stats, cudaStream_t s);
 
-// Vote, CUDA-core FP32 form.
+// Vote, CUDA-core FP32 form.  variant: cells per thread (4 or 8) of the scalar
+// kernel, or 100 + cells per thread (2 or 4) of the packed f32x2 kernel (needs pool.s2x).
 cudaError_t launch_vote_simt(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
-                             int level_stride, int level, PairPool pool, ProbStats *stats, int cells_per_thread,
+                             int level_stride, int level, PairPool pool, ProbStats *stats, int variant,
                              int grid_blocks, cudaStream_t s);
 
 // Vote, tcgen05 tensor-core form. prec: ROT_PREC_FP16 .. BF16X2; variant = epilogue

@@ -48,11 +48,11 @@ def check_kept(gpu_kept, lev, n_pairs):
     assert np.allclose(np.sort(ws), np.sort(gs), atol=1e-9) and np.max(np.abs(ws - gs)) < 1e-9 + 2 * lev["amb"].max()
 
 
-def run_both(p, grid_n, levels, precision="fp32", top_k=16, rank_mode="excess", refit=8, device=True):
+def run_both(p, grid_n, levels, precision="fp32", top_k=16, rank_mode="excess", refit=8, device=True, shape=0):
     import oracle
     a, b = (dev(p.a), dev(p.b)) if device else (p.a, p.b)
     with rv.Context(grid_n=grid_n, levels=levels, top_k=top_k, precision=precision, rank_mode=rank_mode,
-                    refit_iters=refit if refit else -1, keep_trace=1) as ctx:
+                    refit_iters=refit if refit else -1, keep_trace=1, autotune=shape) as ctx:
         r = ctx.solve([(a, b, p.delta)])[0]
         tr = [ctx.level_trace(0, lev) for lev in range(levels + 1)]
     o = oracle.solve(p.a, p.b, f32(p.delta), grid_n=grid_n, levels=levels, top_k=top_k,
@@ -84,6 +84,27 @@ def test_multilevel_every_level():
     p = synth.make_problem(3000, rho=0.9, sigma=0.01, delta=0.03, seed=77)
     r, tr, o = run_both(p, 16, 3)
     assert_parity(p, r, tr, o, 3)
+
+
+FP32_SHAPES = [4, 8, 102, 104]  # scalar kernel (cells per thread), packed f32x2 kernel (100 + cells per thread)
+
+
+@pytest.mark.parametrize("shape", FP32_SHAPES)
+def test_every_fp32_tile_shape(shape):
+    p = synth.make_problem(3001, rho=0.9, sigma=0.01, delta=0.03, seed=78)
+    r, tr, o = run_both(p, 16, 2, shape=shape)
+    assert_parity(p, r, tr, o, 2)
+    q = synth.make_problem(257, rho=0.5, sigma=0.01, delta=0.05, seed=79)  # ragged: padded pair tile
+    r, tr, o = run_both(q, 8, 1, shape=shape)
+    assert_parity(q, r, tr, o, 1)
+
+
+def test_unknown_tile_shape_is_rejected():
+    p = synth.make_problem(300, rho=0.5, sigma=0.01, delta=0.05, seed=80)
+    with rv.Context(grid_n=8, levels=0, autotune=12) as ctx:  # 12 exists only for the tensor-core forms
+        with pytest.raises(rv.RotVoteError) as e:
+            ctx.solve([(dev(p.a), dev(p.b), p.delta)])
+        assert e.value.code == rv.EINVAL
 
 
 @pytest.mark.parametrize("n", [2, 3, 127, 128, 129, 257, 1000])

@@ -63,6 +63,26 @@ def test_tc_counts_identical_to_fp32_form(prec):
     assert np.array_equal(r32.q, rtc.q) and r32.inliers == rtc.inliers
 
 
+TC_SHAPES = [2, 4, 12, 14, 102, 104, 112, 114]
+
+
+@pytest.mark.parametrize("shape", TC_SHAPES)
+def test_every_tc_tile_shape_counts_identical_to_fp32(shape):
+    p = synth.make_problem(9000, rho=0.95, sigma=0.01, delta=0.03, seed=22)
+    out = {}
+    for pr, sh in (("fp32", 4), ("fp16x2", shape), ("bf16", shape)):
+        with rv.Context(grid_n=16, levels=2, precision=pr, keep_trace=1, autotune=sh) as ctx:
+            r = ctx.solve([(dev(p.a), dev(p.b), p.delta)])[0]
+            out[pr] = (r, [ctx.level_trace(0, lev) for lev in range(3)])
+    r32, t32 = out["fp32"]
+    for pr in ("fp16x2", "bf16"):
+        rr, tt = out[pr]
+        for lev in range(3):
+            assert np.array_equal(t32[lev][1], tt[lev][1])
+            assert np.array_equal(t32[lev][2], tt[lev][2])
+        assert np.array_equal(r32.q, rr.q)
+
+
 @pytest.mark.parametrize("prec", ["fp16x2", "bf16x2"])
 def test_tc_batched_equals_alone(prec):
     probs = [synth.make_problem(n, rho=0.8, sigma=0.01, delta=d, seed=s)

@@ -52,6 +52,27 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_max(x: float, dist, device) -> float:
+    """Maximum of x over the ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step: float, steps: int, world: int, max_elapsed_s: float) -> float:
+    """Weak scaling: every rank runs `steps` steps of its own problem of the same
+    shape; the job rate is all ranks' units over the slowest rank's time."""
+    return units_per_step * steps * world / max_elapsed_s
+
+
+def rank_problem(synth, workload: str, rank: int):
+    """Rank r solves its own seeded instance (rep = r) of the workload's shape."""
+    return synth.config_problem(workload, rep=rank)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -329,7 +350,7 @@ def main():
     from paper_2506_11547_gb300 import synth
 
     # weak scaling: each rank solves its own problem instance of the same shape
-    p, grid_n, levels = synth.config_problem(args.workload, rep=rank)
+    p, grid_n, levels = rank_problem(synth, args.workload, rank)
     a_d = torch.from_numpy(p.a).to(dev)
     b_d = torch.from_numpy(p.b).to(dev)
     stream = torch.cuda.current_stream()
@@ -368,13 +389,8 @@ def main():
     if dist:
         dist.barrier()
     per = [s.elapsed_time(e) for s, e in evs]
-    elapsed = sum(per)
-    if dist:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    total_tests = tests_per_step * args.steps * ws
-    value = total_tests / (elapsed / 1e3)
+    elapsed = reduce_max(sum(per), dist, dev)
+    value = whole_job_rate(tests_per_step, args.steps, ws, elapsed / 1e3)
     ms_per_step = elapsed / args.steps
     clocks = clk.summary()
 
@@ -391,12 +407,8 @@ def main():
         t0 = time.perf_counter()
         ctx.solve_raw(arr_h, 1, out)  # blocking: H2D, pipeline, D2H of the result
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_t)
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = tests_per_step * args.steps * ws / e2e_s
+    e2e_s = reduce_max(sum(e2e_t), dist, dev)
+    e2e_value = whole_job_rate(tests_per_step, args.steps, ws, e2e_s)
     h2d = 2 * p.n * 3 * 4
     d2h = ctypes.sizeof(rv.rot_vote_result) + 4  # result struct + device error word
 

@@ -73,7 +73,7 @@ constexpr size_t kBarBytes = 1024;
 constexpr size_t kSmemBytes =
     1024 + 2 * kATileBytesMax + kNB * kBTileBytesMax + kBarBytes + kQueueBytes + kRowBytes + kCorrBytes;
 static_assert(kSmemBytes > 116 * 1024 && kSmemBytes <= 227 * 1024, "shared memory budget");
-static_assert((2 * kNB + 2 * kMaxAcc + 5) * 8 + 8 <= (int)kBarBytes, "barrier area");
+static_assert((2 * kNB + 2 * kMaxAcc + 5) * 8 + 8 + 16 <= (int)kBarBytes, "barrier area");
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint32_t kWaitPolls = 1u << 24;
 
@@ -96,21 +96,29 @@ __device__ __forceinline__ uint64_t gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// Control block of the bounded waits: `abort` is set by any role that gives up;
+// `limit_ns` bounds one wait (kWaitNs, or 1 ms in the wait-expiry test mode).
+struct WaitCtl {
+    volatile int abort;
+    int pad;
+    uint64_t limit_ns;
+};
+
 // Bounded wait for the phase of parity `parity` to complete.  Returns false
 // when the CTA was aborted or the wait expired.
-__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    const uint64_t t0 = gtimer();
+__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, WaitCtl *w) {
+    const uint64_t t0 = gtimer(), lim = w->limit_ns;
     for (uint32_t it = 1; it < kWaitPolls; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 31) == 0) {
-            if (*abort_flag) return false;
-            if (gtimer() - t0 > kWaitNs) return false;
+            if (w->abort) return false;
+            if (gtimer() - t0 > lim) return false;
         }
     }
     return false;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, abort_flag);
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, WaitCtl *w) {
+    return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, w);
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
@@ -278,7 +286,7 @@ template <int KSTEPS, bool BF16>
 __device__ __noinline__ void build_a_tiles(const VoteItem *__restrict__ items, int n_items,
                                            const ProbRef *__restrict__ probs, const LevelRef *__restrict__ lref,
                                            int level_stride, int level, uint8_t *sA, uint64_t *a_full,
-                                           uint64_t *a_empty, volatile int *abort_flag, int *err_flag, int warp,
+                                           uint64_t *a_empty, WaitCtl *wctl, int *err_flag, int warp,
                                            int lane) {
     constexpr int K = 16 * KSTEPS;
     const int r0 = (warp - 2) * 64 + lane;
@@ -289,8 +297,8 @@ __device__ __noinline__ void build_a_tiles(const VoteItem *__restrict__ items, i
         const int ab = i & 1;
         const uint32_t ua = (uint32_t)(i >> 1);
         // warp-uniform outcome of the bounded wait
-        if (!__all_sync(0xffffffffu, mbar_wait(&a_empty[ab], (ua & 1u) ^ 1u, abort_flag))) {
-            *abort_flag = 1;
+        if (!__all_sync(0xffffffffu, mbar_wait(&a_empty[ab], (ua & 1u) ^ 1u, wctl))) {
+            wctl->abort = 1;
             atomicExch(err_flag, 1);
             break;
         }
@@ -350,7 +358,7 @@ template <int G, int KSTEPS, bool BF16, int CH, int U>
 __global__ void __launch_bounds__(128 + 128 * G, 1)
     vote_tc_kernel(const VoteItem *__restrict__ items, int n_items, const ProbRef *__restrict__ probs,
                    const LevelRef *__restrict__ lref, int level_stride, int level, PairPool pool, ProbStats *stats,
-                   float band_req, int *err_flag) {
+                   float band_req, int *err_flag, uint64_t wait_ns, int test_stall) {
     // Every warpgroup drains every stage, in unit order, so no wait ever runs
     // more than one phase ahead of its stage (an mbarrier parity wait could not
     // tell phase k+1 from a pending phase k).
@@ -370,7 +378,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     uint64_t *b_full = bars, *b_empty = bars + kNB, *acc_full = bars + 2 * kNB, *acc_empty = acc_full + kNAcc;
     uint64_t *a_full = acc_empty + kNAcc, *a_empty = a_full + 2, *mma_done = a_empty + 2;
     uint32_t *tmem_slot = (uint32_t *)(mma_done + 1);
-    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    WaitCtl *wctl = (WaitCtl *)(tmem_slot + 2);  // 8-byte aligned
     uint8_t *rq = (uint8_t *)bars + kBarBytes;  // deferred re-check state
     uint2 *q_all = (uint2 *)rq;
     float *rows_all = (float *)(rq + kQueueBytes);
@@ -391,7 +399,8 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
             mbar_init(&a_empty[s], 1);
         }
         mbar_init(mma_done, 1);
-        *abort_flag = 0;
+        wctl->abort = 0;
+        wctl->limit_ns = wait_ns;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 1) tmem_alloc512(tmem_slot);
@@ -401,7 +410,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     const uint32_t tmem_base = *tmem_slot;
 
     auto fail = [&]() {
-        *abort_flag = 1;
+        wctl->abort = 1;
         atomicExch(err_flag, 1);
     };
 
@@ -418,21 +427,22 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 for (int t = 0; t < v.ntiles; ++t, ++j) {
                     const int bs = (int)(j % kNB);
                     const uint32_t u = (uint32_t)(j / kNB);
-                    if (!mbar_wait(&b_empty[bs], (u & 1u) ^ 1u, abort_flag)) {
+                    if (!mbar_wait(&b_empty[bs], (u & 1u) ^ 1u, wctl)) {
                         fail();
                         ok = false;
                         break;
                     }
+                    if (test_stall) continue;  // wait-expiry test: the copy never arrives
                     mbar_arrive_expect_tx(&b_full[bs], kTileBytes);
                     bulk_g2s(sB + bs * kBTileBytesMax, src + (int64_t)t * kTileBytes, kTileBytes, &b_full[bs]);
                 }
             }
             // drain: the last issued copy of each stage has completed before exit
-            for (int64_t jj = j - 1; jj >= 0 && jj >= j - kNB; --jj) {
+            WaitCtl drain{0, 0, kWaitNs};
+            for (int64_t jj = j - 1; !test_stall && jj >= 0 && jj >= j - kNB; --jj) {
                 const int bs = (int)(jj % kNB);
                 const uint32_t u = (uint32_t)(jj / kNB);
-                volatile int never = 0;
-                if (!mbar_wait(&b_full[bs], u & 1u, &never)) atomicExch(err_flag, 1);
+                if (!mbar_wait(&b_full[bs], u & 1u, &drain)) atomicExch(err_flag, 1);
             }
         }
     } else if (warp == 1) {
@@ -446,7 +456,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
                 const int ab = i & 1;
                 const uint32_t ua = (uint32_t)(i >> 1);
-                if (!mbar_wait(&a_full[ab], ua & 1u, abort_flag)) {
+                if (!mbar_wait(&a_full[ab], ua & 1u, wctl)) {
                     fail();
                     break;
                 }
@@ -455,7 +465,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 for (int t = 0; t < v.ntiles && ok; ++t, ++j) {
                     const int bs = (int)(j % kNB);
                     const uint32_t ub = (uint32_t)(j / kNB);
-                    if (!mbar_wait(&b_full[bs], ub & 1u, abort_flag)) {
+                    if (!mbar_wait(&b_full[bs], ub & 1u, wctl)) {
                         fail();
                         ok = false;
                         break;
@@ -466,7 +476,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                         const int64_t u = kUPT * j + h;
                         const int as = (int)(u % kNAcc);
                         const uint32_t uc = (uint32_t)(u / kNAcc);
-                        if (!mbar_wait(&acc_empty[as], (uc & 1u) ^ 1u, abort_flag)) {
+                        if (!mbar_wait(&acc_empty[as], (uc & 1u) ^ 1u, wctl)) {
                             fail();
                             ok = false;
                             break;
@@ -490,7 +500,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
         }
     } else if (warp < 4) {
         // ---------------------------- A-tile builder ---------------------------
-        build_a_tiles<KSTEPS, BF16>(items, n_items, probs, lref, level_stride, level, sA, a_full, a_empty, abort_flag,
+        build_a_tiles<KSTEPS, BF16>(items, n_items, probs, lref, level_stride, level, sA, a_full, a_empty, wctl,
                                     err_flag, warp, lane);
     } else {
         // ------------------------------- epilogue ------------------------------
@@ -605,7 +615,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 const int stage = (int)(jj % kNAcc);
                 const uint32_t uc = (uint32_t)(jj / kNAcc);
                 // warp-uniform outcome: every lane must reach the .sync.aligned tcgen05.ld below
-                if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[stage], uc & 1u, abort_flag))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[stage], uc & 1u, wctl))) {
                     fail();
                     ok = false;
                     break;
@@ -663,8 +673,8 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     __syncthreads();
     if (warp == 1) {
         if (lane == 0) {
-            volatile int never = 0;
-            if (!mbar_wait(mma_done, 0, &never)) atomicExch(err_flag, 1);
+            WaitCtl done_ctl{0, 0, kWaitNs};
+            if (!mbar_wait(mma_done, 0, &done_ctl)) atomicExch(err_flag, 1);
         }
         __syncwarp();
         tc_fence_after();
@@ -697,12 +707,13 @@ cudaError_t prepare_all() {
 template <int KSTEPS, bool BF16>
 cudaError_t launch_v(int variant, const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                      int level_stride, int level, PairPool pool, ProbStats *stats, float band_req, int grid,
-                     int *err_flag, cudaStream_t s) {
+                     int *err_flag, int test_stall, cudaStream_t s) {
     switch (variant) {
 #define RV_CASE(G_, CH_, U_, V_)                                                                             \
     case V_:                                                                                                 \
         vote_tc_kernel<G_, KSTEPS, BF16, CH_, U_><<<grid, 128 + 128 * G_, kSmemBytes, s>>>(                  \
-            items, n_items, probs, lref, level_stride, level, pool, stats, band_req, err_flag);              \
+            items, n_items, probs, lref, level_stride, level, pool, stats, band_req, err_flag,               \
+            test_stall ? 1000000ull : kWaitNs, test_stall);                                                   \
         return cudaGetLastError();
         RV_TC_VARIANTS(RV_CASE)
 #undef RV_CASE
@@ -724,12 +735,12 @@ cudaError_t prepare_vote_tc() {
 
 cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                            int level_stride, int level, PairPool pool, ProbStats *stats, int prec, float band_req,
-                           int variant, int grid_blocks, int *err_flag, cudaStream_t s) {
+                           int variant, int grid_blocks, int *err_flag, int test_stall, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
     const int grid = grid_blocks < n_items ? grid_blocks : n_items;
 #define RV_TC_G(KS_, BF_) \
     launch_v<KS_, BF_>(variant, items, n_items, probs, lref, level_stride, level, pool, stats, band_req, grid, \
-                       err_flag, s)
+                       err_flag, test_stall, s)
     switch (prec) {
     case ROT_PREC_FP16: return RV_TC_G(1, false);
     case ROT_PREC_BF16: return RV_TC_G(1, true);

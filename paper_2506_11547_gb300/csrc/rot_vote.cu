@@ -529,7 +529,7 @@ cudaError_t Context::launch_vote(Wave &w, int lev, int variant) {
     const int nit = (int)pl.items_h[lev].size();
     if (pl.pool.tc_k)
         return launch_vote_tc(pl.d_items[lev], nit, pl.d_probs, pl.d_lref, pl.stride, lev, pl.pool, pl.d_stats,
-                              pl.prec, cfg.recheck_band, variant, pl.grid_blocks, pl.d_err, w.stream);
+                              pl.prec, cfg.recheck_band, variant, pl.grid_blocks, pl.d_err, w.stall, w.stream);
     return launch_vote_simt(pl.d_items[lev], nit, pl.d_probs, pl.d_lref, pl.stride, lev, pl.pool, pl.d_stats, variant,
                             pl.grid_blocks, w.stream);
 }
@@ -688,10 +688,12 @@ int Context::launch_batch(Wave &w, const rot_vote_problem *p, const std::vector<
     if (rc != ROT_VOTE_OK) return rc;
     rc = choose_variant(w, serving);
     if (rc != ROT_VOTE_OK) return rc;
+    w.stall = test_stall > 0 ? 1 : 0;
+    if (test_stall > 0) --test_stall;
     if (w.plan.variant != old_variant) w.plan.signature += "|changed";
     cudaError_t e = cudaEventRecord(w.ev0, w.stream);
     if (e != cudaSuccess) return cuda_fail(e, "recording an event");
-    const bool graphs = cfg.use_graphs > 0 && cfg.keep_trace < 2;
+    const bool graphs = cfg.use_graphs > 0 && cfg.keep_trace < 2 && !w.stall;
     if (graphs) {
         if (!(had_graph && old_sig == w.plan.signature && w.graph_base == w.base)) {
             if (w.graph_exec) {

@@ -113,9 +113,13 @@ cudaError_t launch_vote_simt(const VoteItem *items, int n_items, const ProbRef *
 // Vote, tcgen05 tensor-core form. prec: ROT_PREC_FP16 .. BF16X2; variant = epilogue
 // warpgroups (2 or 4), plus 10 for 16-column instead of 32-column TMEM chunks, plus
 // 100 for 128-pair MMA units in four accumulator stages (else 256 pairs, two stages).
+// Every device wait is bounded (2 s); on expiry *err_flag is set and the kernel
+// returns.  test_stall != 0 (fault-injection tests only): the producer issues no
+// copies and each wait is bounded by 1 ms, so the kernel must report through
+// *err_flag and leave the context usable.
 cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                            int level_stride, int level, PairPool pool, ProbStats *stats, int prec, float band_req,
-                           int variant, int grid_blocks, int *err_flag, cudaStream_t s);
+                           int variant, int grid_blocks, int *err_flag, int test_stall, cudaStream_t s);
 
 // Once per process/device, outside stream capture: kernel attributes of the tensor-core vote.
 cudaError_t prepare_vote_tc();

@@ -84,6 +84,7 @@ struct Wave {
     Plan plan;
     // serving bookkeeping
     bool busy = false;
+    int stall = 0;  // fault injection for this batch (see Context::test_stall)
     std::vector<uint64_t> tickets;
     std::vector<double> t_submit;
 
@@ -109,7 +110,9 @@ class Context {
     bool own_stream = false;
     size_t budget = 0, bytes_held = 0;
     std::unordered_map<std::string, int> tuned;  // autotuner choices per shape class
-    int test_fail_alloc = 0;
+    int test_fail_alloc = 0;  // fault injection: the k-th workspace allocation fails (ROT_VOTE_TEST_FAIL_ALLOC=k)
+    int test_stall = 0;       // fault injection: in the next k solves the tensor-core copies never arrive and
+                              // device waits are bounded by 1 ms (ROT_VOTE_TEST_STALL=k)
     // per-kernel profiling (keep_trace == 2)
     std::vector<cudaEvent_t> prof_ev;
     std::vector<rot_vote_stage> prof;

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "rv_runtime.h"
@@ -48,6 +49,9 @@ int Context::init(const rot_vote_config &c) {
     }
     if (main_wave.init(stream, false) != ROT_VOTE_OK) return ROT_VOTE_ECUDA;
     load_tuning();
+    // fault-injection hooks for the failure tests (never set in normal use)
+    if (const char *e = getenv("ROT_VOTE_TEST_FAIL_ALLOC")) test_fail_alloc = atoi(e);
+    if (const char *e = getenv("ROT_VOTE_TEST_STALL")) test_stall = atoi(e);
     return ROT_VOTE_OK;
 }
 

@@ -38,7 +38,7 @@ FLOPS_PER_TEST = 20.0  # 10 multiply-adds of the (cell monomials . pair S entrie
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32")
@@ -107,6 +107,10 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.time() + 3.0  # start timing only once the sampler is producing samples
+            while not self.lines and time.time() < t_end:
+                time.sleep(0.01)
+            self.skip = len(self.lines)  # samples taken before the timed region
         except Exception:
             self.proc = None
         return self
@@ -126,7 +130,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[getattr(self, "skip", 0):] or self.lines[-1:]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 8:
                 continue

@@ -38,15 +38,35 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 constexpr int kTP = 128;     // pairs per shared-memory tile
+
+// Next work item of this CTA: from the atomic counter if there is one (CTAs
+// take items as they finish, so no CTA is left with a long tail), else in
+// grid-stride order.  Block-uniform; every thread must call it.
+__device__ __forceinline__ int next_item(int *counter, int &stride_it, int *s_item) {
+    if (!counter) {
+        const int it = stride_it;
+        stride_it += gridDim.x;
+        return it;
+    }
+    if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = *s_item;
+    __syncthreads();  // every thread has read the slot before it is reused
+    return it;
+}
 constexpr int kThreads = 128;
 
 template <int CPT>
 __global__ void __launch_bounds__(kThreads, 4) vote_simt_kernel(const VoteItem *__restrict__ items, int n_items,
                                                              const ProbRef *__restrict__ probs,
                                                              const LevelRef *__restrict__ lref, int level_stride,
-                                                             int level, PairPool pool, ProbStats *stats) {
+                                                             int level, PairPool pool, ProbStats *stats,
+                                                             int *item_counter) {
     __shared__ __align__(16) float4 sh[2][kTP * 3];
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    __shared__ int s_item;
+    int stride_it = blockIdx.x;
+    for (int it = next_item(item_counter, stride_it, &s_item); it < n_items;
+         it = next_item(item_counter, stride_it, &s_item)) {
         const VoteItem W = items[it];
         const ProbRef P = probs[W.prob];
         if (level > P.levels) continue;  // uniform across the block
@@ -178,9 +198,13 @@ template <int CPT>
 __global__ void __launch_bounds__(kThreads, 4) vote_simt2_kernel(const VoteItem *__restrict__ items, int n_items,
                                                               const ProbRef *__restrict__ probs,
                                                               const LevelRef *__restrict__ lref, int level_stride,
-                                                              int level, PairPool pool, ProbStats *stats) {
+                                                              int level, PairPool pool, ProbStats *stats,
+                                                              int *item_counter) {
     __shared__ __align__(16) float4 sh[2][kPP * 5];
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    __shared__ int s_item;
+    int stride_it = blockIdx.x;
+    for (int it = next_item(item_counter, stride_it, &s_item); it < n_items;
+         it = next_item(item_counter, stride_it, &s_item)) {
         const VoteItem W = items[it];
         const ProbRef P = probs[W.prob];
         if (level > P.levels) continue;  // uniform across the block
@@ -327,16 +351,16 @@ __global__ void __launch_bounds__(kThreads, 4) vote_simt2_kernel(const VoteItem 
 
 cudaError_t launch_vote_simt(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                              int level_stride, int level, PairPool pool, ProbStats *stats, int variant,
-                             int grid_blocks, cudaStream_t s) {
+                             int grid_blocks, int *item_counter, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
     const int grid = grid_blocks < n_items ? grid_blocks : n_items;
     if (variant > 100 && !pool.s2x) return cudaErrorInvalidValue;
     switch (variant) {
-    case 102: vote_simt2_kernel<2><<<grid, kThreads, 0, s>>>(items, n_items, probs, lref, level_stride, level, pool, stats); break;
-    case 104: vote_simt2_kernel<4><<<grid, kThreads, 0, s>>>(items, n_items, probs, lref, level_stride, level, pool, stats); break;
-    case 2: vote_simt_kernel<2><<<grid, kThreads, 0, s>>>(items, n_items, probs, lref, level_stride, level, pool, stats); break;
-    case 4: vote_simt_kernel<4><<<grid, kThreads, 0, s>>>(items, n_items, probs, lref, level_stride, level, pool, stats); break;
-    case 8: vote_simt_kernel<8><<<grid, kThreads, 0, s>>>(items, n_items, probs, lref, level_stride, level, pool, stats); break;
+    case 102: vote_simt2_kernel<2><<<grid, kThreads, 0, s>>>(items, n_items, probs, lref, level_stride, level, pool, stats, item_counter); break;
+    case 104: vote_simt2_kernel<4><<<grid, kThreads, 0, s>>>(items, n_items, probs, lref, level_stride, level, pool, stats, item_counter); break;
+    case 2: vote_simt_kernel<2><<<grid, kThreads, 0, s>>>(items, n_items, probs, lref, level_stride, level, pool, stats, item_counter); break;
+    case 4: vote_simt_kernel<4><<<grid, kThreads, 0, s>>>(items, n_items, probs, lref, level_stride, level, pool, stats, item_counter); break;
+    case 8: vote_simt_kernel<8><<<grid, kThreads, 0, s>>>(items, n_items, probs, lref, level_stride, level, pool, stats, item_counter); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -231,20 +231,23 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
             const int64_t ct = (nc + cells_per_item - 1) / cells_per_item;
             work += ct * (int64_t)(align_up((size_t)pl.probs_h[k].n, kPairTile) / kPairTile);
         }
-        const int64_t target = (tck ? 16LL : 4LL) * slots;
-        int64_t chunk = std::max<int64_t>(4, (work + target - 1) / target);  // pair tiles per item
+        // tensor-core form: ~16 items per persistent CTA, taken in grid-stride order;
+        // CUDA-core form: ~16 items per resident CTA, handed out by an atomic counter
+        const int64_t target = 16LL * slots;
+        const int64_t chunk = std::max<int64_t>(4, (work + target - 1) / target);  // pair tiles per item
         auto &items = pl.items_h[lev];
         for (int k = 0; k < P; ++k) {
             if (lev > levs[k]) continue;
             const int64_t nc = lev == 0 ? gt[k]->ncells : child_cap;
             const int64_t ptiles = align_up((size_t)pl.probs_h[k].n, kPairTile) / kPairTile;
+            const int64_t nch = (ptiles + chunk - 1) / chunk;  // balanced: chunk sizes differ by <= 1 tile
             for (int64_t c0 = 0; c0 < nc; c0 += cells_per_item)
-                for (int64_t t0 = 0; t0 < ptiles; t0 += chunk) {
+                for (int64_t q = 0; q < nch; ++q) {
                     VoteItem it;
                     it.prob = k;
                     it.cell_begin = (int32_t)c0;
-                    it.pair_begin = (int32_t)(t0 * kPairTile);
-                    it.pair_end = (int32_t)(std::min(ptiles, t0 + chunk) * kPairTile);
+                    it.pair_begin = (int32_t)(ptiles * q / nch * kPairTile);
+                    it.pair_end = (int32_t)(ptiles * (q + 1) / nch * kPairTile);
                     items.push_back(it);
                 }
         }
@@ -288,6 +291,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     const size_t o_stats = reserve(sizeof(ProbStats) * P);
     const size_t o_nkept = reserve(sizeof(int32_t) * (size_t)P * S);
     const size_t o_err = reserve(sizeof(int) * 4);
+    const size_t o_ictr = reserve(sizeof(int) * (size_t)S);  // per-level work-item counters (CUDA-core vote)
     const size_t z1 = align_up(off, 256);
     const size_t o_kept = reserve(sizeof(int32_t) * (size_t)P * S * K);
     const size_t o_cand = reserve(sizeof(Cand) * ((size_t)P * pl.chunks_per_prob * K + (size_t)P * K));
@@ -342,6 +346,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     pl.d_slice = (double *)(B + o_slice);
     pl.d_sloff = (int64_t *)(B + o_sloff);
     pl.d_err = (int *)(B + o_err);
+    pl.d_ictr = (int *)(B + o_ictr);
 
     // pair-prep tiles
     pl.tiles_h.clear();
@@ -531,7 +536,7 @@ cudaError_t Context::launch_vote(Wave &w, int lev, int variant) {
         return launch_vote_tc(pl.d_items[lev], nit, pl.d_probs, pl.d_lref, pl.stride, lev, pl.pool, pl.d_stats,
                               pl.prec, cfg.recheck_band, variant, pl.grid_blocks, pl.d_err, w.stall, w.stream);
     return launch_vote_simt(pl.d_items[lev], nit, pl.d_probs, pl.d_lref, pl.stride, lev, pl.pool, pl.d_stats, variant,
-                            pl.grid_blocks, w.stream);
+                            pl.grid_blocks, pl.d_ictr + lev, w.stream);
 }
 
 // ---------------------------------------------------------------------------

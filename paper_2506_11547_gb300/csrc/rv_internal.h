@@ -106,9 +106,11 @@ cudaError_t launch_pair_prep(const ProbRef *probs, const int2 *tiles, int ntiles
 
 // Vote, CUDA-core FP32 form.  variant: cells per thread (4 or 8) of the scalar
 // kernel, or 100 + cells per thread (2 or 4) of the packed f32x2 kernel (needs pool.s2x).
+// item_counter: a zeroed int through which CTAs take work items dynamically; null =
+// items in grid-stride order.
 cudaError_t launch_vote_simt(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                              int level_stride, int level, PairPool pool, ProbStats *stats, int variant,
-                             int grid_blocks, cudaStream_t s);
+                             int grid_blocks, int *item_counter, cudaStream_t s);
 
 // Vote, tcgen05 tensor-core form. prec: ROT_PREC_FP16 .. BF16X2; variant = epilogue
 // warpgroups (2 or 4), plus 10 for 16-column instead of 32-column TMEM chunks, plus

@@ -61,6 +61,7 @@ struct Plan {
     double *d_slice = nullptr;
     int64_t *d_sloff = nullptr;
     int *d_err = nullptr;
+    int *d_ictr = nullptr;  // per-level work-item counters of the CUDA-core vote (zeroed per solve)
 };
 
 class Context;

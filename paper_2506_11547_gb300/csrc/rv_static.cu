@@ -228,7 +228,7 @@ extern "C" int rot_vote_count_cells_static(const float *a, const float *b, int64
                              stats, s);
     if (e == cudaSuccess)
         e = launch_vote_simt(reinterpret_cast<const VoteItem *>(base + kOffItems), A.nitems, probs, lref, 1, 0, pool,
-                             stats, 4, A.nitems, s);
+                             stats, 4, A.nitems, nullptr, s);
     // header slots back to the host: ProbStats.invalid and the bad-cell flag
     unsigned char hdr[1024];
     if (e == cudaSuccess) e = cudaMemcpyAsync(hdr, base, sizeof hdr, cudaMemcpyDeviceToHost, s);

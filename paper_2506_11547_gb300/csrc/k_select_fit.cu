@@ -306,53 +306,115 @@ __device__ void fit_slice(const float4 *__restrict__ pr, uint8_t *mem, int64_t n
     __syncthreads();
 }
 
-// Warp-cooperative cyclic Jacobi on a symmetric 4x4 held in shared memory
-// (FP64), accumulating rotations into V (which may start from a previous
-// eigenbasis).  Each rotation's tan(phi) is estimated in FP32; (c, s) are then
-// made orthogonal to FP64 precision (c = 1/sqrt(1 + t^2) by Newton steps), so
-// V stays orthogonal and every sweep shrinks the off-diagonal mass by ~1e-7.
-// Lanes 0..3 update row/column k = lane.  Called by one whole warp.
-__device__ void jacobi4_warp(double (*A)[4], double (*V)[4]) {
-    const int lane = threadIdx.x & 31, k = lane & 3;
-    for (int sweep = 0; sweep < 12; ++sweep) {
-        double off = 0.0, dia = 0.0;
+// Cyclic Jacobi in FP32 on a symmetric 4x4 (one thread, registers): returns
+// an orthogonal basis V (columns = eigenvectors) accurate to ~1e-7 relative.
+__device__ void jacobi4_f32(float A[4][4], float V[4][4]) {
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) V[r][c] = r == c ? 1.f : 0.f;
+    for (int sweep = 0; sweep < 10; ++sweep) {
+        float off = 0.f, dia = 0.f;
         for (int r = 0; r < 4; ++r) {
-            dia = fma(A[r][r], A[r][r], dia);
-            for (int c = r + 1; c < 4; ++c) off = fma(A[r][c], A[r][c], off);
+            dia = fmaf(A[r][r], A[r][r], dia);
+            for (int c = r + 1; c < 4; ++c) off = fmaf(A[r][c], A[r][c], off);
         }
-        if (off <= 1e-40 * dia || off < 1e-300) break;
+        if (!(off > 1e-14f * dia) || off < 1e-37f) break;
+#pragma unroll
         for (int p = 0; p < 3; ++p) {
+#pragma unroll
             for (int q = p + 1; q < 4; ++q) {
-                const double apq = A[p][q];
-                if (apq == 0.0) continue;
-                const float th = ((float)A[q][q] - (float)A[p][p]) / (2.f * (float)apq);
-                float tf = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
-                if (!(fabsf(tf) <= 1.f)) tf = 0.f;  // non-finite estimate: skip the rotation
-                const double t = (double)tf;
-                const double x = fma(t, t, 1.0);
-                double r = (double)rsqrtf((float)x);
-                r = r * fma(-0.5 * x, r * r, 1.5);
-                r = r * fma(-0.5 * x, r * r, 1.5);
-                const double c = r, s = t * r;
-                __syncwarp();
-                if (lane < 4) {  // A <- A J : columns p, q of row k
-                    const double akp = A[k][p], akq = A[k][q];
-                    A[k][p] = c * akp - s * akq;
-                    A[k][q] = s * akp + c * akq;
-                    const double vkp = V[k][p], vkq = V[k][q];
-                    V[k][p] = c * vkp - s * vkq;
-                    V[k][q] = s * vkp + c * vkq;
+                const float apq = A[p][q];
+                if (apq == 0.f) continue;
+                const float th = (A[q][q] - A[p][p]) / (2.f * apq);
+                float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+                if (!(fabsf(t) <= 1.f)) t = 0.f;
+                const float c = rsqrtf(fmaf(t, t, 1.f)), sn = t * c;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {  // A <- A J, V <- V J
+                    const float akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - sn * akq;
+                    A[k][q] = sn * akp + c * akq;
+                    const float vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + c * vkq;
                 }
-                __syncwarp();
-                if (lane < 4) {  // A <- J^T A : rows p, q of column k
-                    const double apk = A[p][k], aqk = A[q][k];
-                    A[p][k] = c * apk - s * aqk;
-                    A[q][k] = s * apk + c * aqk;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {  // A <- J^T A
+                    const float apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - sn * aqk;
+                    A[q][k] = sn * apk + c * aqk;
                 }
-                __syncwarp();
             }
         }
     }
+}
+
+// Smallest eigenpair of the symmetric 4x4 A (FP64, in shared memory), called
+// by one whole warp.  An FP32 Jacobi gives the basis u_0..u_3 (~1e-7); lane j
+// < 4 then takes the FP64 Rayleigh quotient lam_j = u_j^T A u_j / u_j^T u_j
+// (second-order accurate, ~1e-14 relative), and the smallest vector v gets two
+// FP64 first-order corrections v += sum_{j != i0} u_j (u_j^T r) / ((lam_i0 -
+// lam_j) u_j^T u_j), r = A v - (v^T A v / v^T v) v, which bring it to ~1e-14.
+// Writes q (unit, on every lane) and returns whether the gap between the two
+// smallest eigenvalues exceeds 1e-12 tr(A) (else q is the uncorrected u_i0).
+__device__ bool eig4_smallest(const double (*A)[4], float (*Vs)[4], double q[4]) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        float A32[4][4], V[4][4];
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) A32[r][c] = (float)A[r][c];
+        jacobi4_f32(A32, V);
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) Vs[r][c] = V[r][c];
+    }
+    __syncwarp();
+    const int j = lane & 3;
+    double u[4], Au[4];
+    for (int r = 0; r < 4; ++r) u[r] = (double)Vs[r][j];
+    for (int r = 0; r < 4; ++r) Au[r] = fma(A[r][0], u[0], fma(A[r][1], u[1], fma(A[r][2], u[2], A[r][3] * u[3])));
+    const double uu = fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], u[3] * u[3])));
+    const double uAu = fma(u[0], Au[0], fma(u[1], Au[1], fma(u[2], Au[2], u[3] * Au[3])));
+    const double lam = uAu / uu;
+    double lams[4];
+    for (int k = 0; k < 4; ++k) lams[k] = __shfl_sync(0xffffffffu, lam, k);
+    int i0 = 0;
+    for (int k = 1; k < 4; ++k)
+        if (lams[k] < lams[i0]) i0 = k;
+    double l1 = DBL_MAX;
+    for (int k = 0; k < 4; ++k)
+        if (k != i0 && lams[k] < l1) l1 = lams[k];
+    const double tr = A[0][0] + A[1][1] + A[2][2] + A[3][3];
+    const bool gap_ok = (l1 - lams[i0]) > 1e-12 * tr;
+    double v[4];
+    for (int r = 0; r < 4; ++r) v[r] = __shfl_sync(0xffffffffu, u[r], i0);
+    if (gap_ok) {
+        const double inv_uu = 1.0 / uu;  // lane j: 1 / u_j^T u_j
+        for (int round = 0; round < 2; ++round) {
+            double Av[4];
+            for (int r = 0; r < 4; ++r) Av[r] = fma(A[r][0], v[0], fma(A[r][1], v[1], fma(A[r][2], v[2], A[r][3] * v[3])));
+            const double vv = fma(v[0], v[0], fma(v[1], v[1], fma(v[2], v[2], v[3] * v[3])));
+            const double vAv = fma(v[0], Av[0], fma(v[1], Av[1], fma(v[2], Av[2], v[3] * Av[3])));
+            const double mu = vAv / vv;
+            double res[4];
+            for (int r = 0; r < 4; ++r) res[r] = fma(-mu, v[r], Av[r]);
+            // lane j != i0: coefficient of u_j (the gap keeps the denominator away from 0)
+            double coef = 0.0;
+            if (j != i0) {
+                const double ur = fma(u[0], res[0], fma(u[1], res[1], fma(u[2], res[2], u[3] * res[3])));
+                coef = ur * inv_uu / (mu - lams[j]);
+            }
+            double cf[4];
+            for (int k = 0; k < 4; ++k) cf[k] = __shfl_sync(0xffffffffu, coef, k);
+            for (int r = 0; r < 4; ++r) {
+                double d = 0.0;
+                for (int k = 0; k < 4; ++k) d = fma(cf[k], (double)Vs[r][k], d);
+                v[r] += d;
+            }
+        }
+    }
+    const double n2 = fma(v[0], v[0], fma(v[1], v[1], fma(v[2], v[2], v[3] * v[3])));
+    const double inv = 1.0 / sqrt(n2);
+    for (int r = 0; r < 4; ++r) q[r] = v[r] * inv;
+    return gap_ok;
 }
 
 __device__ __forceinline__ void R32_of(const double q[4], float4 &R0, float4 &R1, float4 &R2) {
@@ -392,7 +454,8 @@ __global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restr
     const LevelRef L = lref[p * level_stride + last];
     const int wpos = kept_pos[(p * level_stride + last) * top_k];
     __shared__ FitShared sh;
-    __shared__ double As[4][4], Vs[4][4];
+    __shared__ double As[4][4];
+    __shared__ float Vf[4][4];
     __shared__ double Btot[11];
     __shared__ int list[kFitSlice];
     FitShared *root = cluster.map_shared_rank(&sh, 0);
@@ -414,7 +477,6 @@ __global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restr
         const double4_32a q4 = L.cells.q[wpos];
         qc[0] = q4.x; qc[1] = q4.y; qc[2] = q4.z; qc[3] = q4.w;
     }
-    if (threadIdx.x < 16) Vs[threadIdx.x >> 2][threadIdx.x & 3] = (threadIdx.x >> 2) == (threadIdx.x & 3) ? 1.0 : 0.0;
 
     // iteration 0: the voters of the winning cell (FP32 re-check decisions);
     // iterations t >= 1: q_{t-1}^T S_i q_{t-1} <= sin^2(delta)
@@ -436,7 +498,6 @@ __global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restr
                 const int m = (int)Btot[9], chg = (int)Btot[10];
                 double u[10];
                 sumS_from_B(Btot, (double)m, u);
-                const double tr = u[0] + u[1] + u[2] + u[3];
                 bool stop = false, degenerate = false;
                 if (t == 0) {
                     degenerate = m < 2;
@@ -444,46 +505,24 @@ __global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restr
                     stop = m < 2 || chg == 0;
                 }
                 if (!stop && !degenerate) {
-                    // the sum in the current eigenbasis (warm start): A' = V^T A V, two 16-lane steps
                     const double Ain[4][4] = {{u[0], u[4], u[5], u[6]}, {u[4], u[1], u[7], u[8]},
                                               {u[5], u[7], u[2], u[9]}, {u[6], u[8], u[9], u[3]}};
-                    const int er = (threadIdx.x >> 2) & 3, ec = threadIdx.x & 3;
-                    double w = 0.0;
-                    if (threadIdx.x < 16)
-                        for (int a = 0; a < 4; ++a) w = fma(Ain[er][a], Vs[a][ec], w);  // W = A V
+                    if (threadIdx.x < 16) As[threadIdx.x >> 2][threadIdx.x & 3] = Ain[threadIdx.x >> 2][threadIdx.x & 3];
                     __syncwarp();
-                    if (threadIdx.x < 16) As[er][ec] = w;
-                    __syncwarp();
-                    double x = 0.0;
-                    if (threadIdx.x < 16)
-                        for (int a = 0; a < 4; ++a) x = fma(Vs[a][er], As[a][ec], x);  // V^T W
-                    const double vsave = threadIdx.x < 16 ? Vs[er][ec] : 0.0;
-                    __syncwarp();
-                    if (threadIdx.x < 16) As[er][ec] = x;
-                    __syncwarp();
-                    jacobi4_warp(As, Vs);
-                    __syncwarp();
-                    // smallest and second-smallest eigenvalue
-                    int i0 = 0;
-                    for (int k = 1; k < 4; ++k)
-                        if (As[k][k] < As[i0][i0]) i0 = k;
-                    double l1 = DBL_MAX;
-                    for (int k = 0; k < 4; ++k)
-                        if (k != i0 && As[k][k] < l1) l1 = As[k][k];
-                    const bool gap_ok = (l1 - As[i0][i0]) > 1e-12 * tr;
+                    double qn[4];
+                    const bool gap_ok = eig4_smallest(As, Vf, qn);
                     if (threadIdx.x == 0) {
                         if (!gap_ok) {
                             if (t == 0) degenerate = true;
                             else stop = true;
                         }
                         if (!degenerate && !stop) {
-                            for (int r = 0; r < 4; ++r) sh.q[r] = Vs[r][i0];
+                            for (int r = 0; r < 4; ++r) sh.q[r] = qn[r];
                             sh.nin = m;
                             sh.refits = t;
                         }
                     }
                     __syncwarp();
-                    if (!gap_ok && threadIdx.x < 16) Vs[er][ec] = vsave;  // keep the previous basis
                 }
                 if (threadIdx.x == 0) {
                     if (t == 0) {

@@ -178,8 +178,9 @@ int rot_vote_level_trace(rot_vote_ctx *ctx, int problem, int level, int64_t *idx
 /* Diagnostic: device time of each kernel launch of the last rot_vote_solve on
  * a context created with keep_trace = 2.  Such a context launches the
  * pipeline stage by stage (no CUDA graph) with a pair of CUDA events on its
- * stream around every kernel.  kind: 0 pair step, 1 vote, 2 top-K, 3
- * children, 4 fit; level: the level (-1 for pair step and fit).
+ * stream around every kernel (a stage may be two kernels).  kind: 0 pair step,
+ * 1 vote, 2 top-K with the next level's children, 4 fit (3 is unused); level:
+ * the level (-1 for pair step and fit).
  * Writes up to cap entries and their total count.  Returns OK or EINVAL. */
 typedef struct {
     int32_t kind;

@@ -89,6 +89,45 @@ __device__ void block_select(const Key (&mine)[kPerThread], int k, Cand *out) {
     }
 }
 
+// Children of one problem's kept cells: the octants of each kept cell at the
+// next level that meet the ball, written to the next level's table in (rank,
+// octant) order (an ordered block-wide compaction, 8 candidates per kept cell).
+// Called by the whole block; keep[0..nk) are the kept cells in rank order.
+__device__ void block_children(const LevelRef &L, const LevelRef &C, const Cand *keep, int nk) {
+    __shared__ int warp_tot[32];
+    __shared__ int s_base;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    const int nw = (int)(blockDim.x >> 5), lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t n = L.n_side;
+    for (int t0 = 0; t0 < 8 * nk; t0 += blockDim.x) {
+        const int t = t0 + (int)threadIdx.x, r = t >> 3, o = t & 7;
+        bool ex = false;
+        int64_t cx = 0, cy = 0, cz = 0;
+        if (r < nk) {
+            const int64_t pidx = L.cells.idx[keep[r].pos];
+            const int64_t ix = pidx % n, iy = (pidx / n) % n, iz = pidx / (n * n);
+            cx = 2 * ix + (o & 1);
+            cy = 2 * iy + ((o >> 1) & 1);
+            cz = 2 * iz + (o >> 2);
+            ex = cell_exists(2 * L.n_side, cx, cy, cz);
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, ex);
+        if (lane == 0) warp_tot[w] = __popc(ball);
+        __syncthreads();
+        int base = s_base, tot = 0;
+        for (int k = 0; k < nw; ++k) {
+            if (k < w) base += warp_tot[k];
+            tot += warp_tot[k];
+        }
+        if (ex) write_cell(C.cells, base + __popc(ball & ((1u << lane) - 1u)), 2 * L.n_side, cx, cy, cz);
+        __syncthreads();
+        if (threadIdx.x == 0) s_base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *const_cast<int32_t *>(C.ncells) = s_base;
+}
+
 // Phase 1: block (chunk, problem) ranks kSelChunk cells of one level.
 __global__ void __launch_bounds__(kSelThreads) topk_phase1(const ProbRef *__restrict__ probs,
                                                            const LevelRef *__restrict__ lref, int level_stride,
@@ -183,6 +222,54 @@ __global__ void __launch_bounds__(kSelThreads) topk_phase2(const ProbRef *__rest
         nkept[p * level_stride + level] = nkeep;
         atomicAdd(&stats[p].tests, (unsigned long long)ncell * (unsigned long long)P.n);
     }
+    if (level < P.levels) block_children(L, lref[p * level_stride + level + 1], keep, nkeep);  // uniform
+}
+
+// Ranking of a level of at most kSelChunk cells (the refinement levels): one
+// block per problem selects the top K and writes the next level's children.
+__global__ void __launch_bounds__(kSelThreads) select_small_kernel(const ProbRef *__restrict__ probs,
+                                                                   const LevelRef *__restrict__ lref,
+                                                                   int level_stride, int level, int top_k,
+                                                                   int rank_mode, int32_t *kept_pos, int32_t *nkept,
+                                                                   ProbStats *stats) {
+    const int p = blockIdx.x;
+    const ProbRef P = probs[p];
+    if (level > P.levels) return;
+    const LevelRef L = lref[p * level_stride + level];
+    const int ncell = min(*L.ncells, kSelChunk);
+    Key mine[kPerThread];
+    const double nd = (double)P.n;
+#pragma unroll
+    for (int e = 0; e < kPerThread; ++e) {
+        const int c = (int)threadIdx.x + e * kSelThreads;
+        if (c < ncell) {
+            const int32_t cnt = L.counts[c];
+            const double t = rank_mode == ROT_RANK_RAW ? 0.0 : tau_cs(P.sin_d, P.cos_d, L.cells.trig[c]);
+            mine[e].key = order_key(rank_mode == ROT_RANK_RAW ? (double)cnt : dsub((double)cnt, dmul(nd, t)));
+            mine[e].idx = L.cells.idx[c];
+            mine[e].pos = c;
+        } else {
+            mine[e].key = 0ull;
+            mine[e].idx = INT64_MAX;
+            mine[e].pos = -1;
+        }
+    }
+    __shared__ Cand sel[kMaxTopK];
+    __shared__ int nsel;
+    block_select(mine, top_k, sel);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nk = 0;
+        for (int r = 0; r < top_k; ++r) {
+            kept_pos[(p * level_stride + level) * top_k + r] = sel[r].pos;
+            nk += sel[r].pos >= 0;
+        }
+        nkept[p * level_stride + level] = nk;
+        nsel = nk;
+        atomicAdd(&stats[p].tests, (unsigned long long)ncell * (unsigned long long)P.n);
+    }
+    __syncthreads();
+    if (level < P.levels) block_children(L, lref[p * level_stride + level + 1], sel, nsel);
 }
 
 // ---------------------------------------------------------------------------
@@ -586,6 +673,15 @@ cudaError_t launch_topk(const ProbRef *probs, int nprob, const LevelRef *lref, i
     Cand *scratch = cand + (int64_t)nprob * chunks_per_prob * top_k;
     topk_phase2<<<nprob, kSelThreads, 0, s>>>(probs, lref, level_stride, level, top_k, cand, chunks_per_prob,
                                               kept_pos, nkept, stats, scratch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_small(const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride, int level,
+                                int top_k, int rank_mode, int32_t *kept_pos, int32_t *nkept, ProbStats *stats,
+                                cudaStream_t s) {
+    if (nprob <= 0) return cudaSuccess;
+    select_small_kernel<<<nprob, kSelThreads, 0, s>>>(probs, lref, level_stride, level, top_k, rank_mode, kept_pos,
+                                                      nkept, stats);
     return cudaGetLastError();
 }
 

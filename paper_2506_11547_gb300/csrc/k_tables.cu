@@ -1,5 +1,6 @@
-// k_tables.cu -- level tables (coarse grid, children of kept cells) and the
-// pair step (S_i entries, re-check records, tensor-core operand tiles).
+// k_tables.cu -- the coarse level table and the pair step (S_i entries,
+// re-check records, tensor-core operand tiles).  The children of kept cells are
+// written by the ranking kernels (k_select_fit.cu).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -162,55 +163,6 @@ cudaError_t launch_pair_prep(const ProbRef *probs, const int2 *tiles, int ntiles
                                    ProbStats *stats, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     pair_prep_kernel<<<ntiles, kPairTile, 0, s>>>(probs, tiles, ntiles, pool, tc_prec, stats);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Children: the 8 octants (dz, dy, dx) of each kept cell, in (rank, octant)
-// order, that meet the ball, written as the next level's table.
-// ---------------------------------------------------------------------------
-__global__ void children_kernel(const ProbRef *__restrict__ probs, const LevelRef *__restrict__ lref,
-                                int level_stride, int level, int top_k, const int32_t *__restrict__ kept_pos,
-                                const int32_t *__restrict__ nkept) {
-    const int p = blockIdx.x;
-    if (level >= probs[p].levels) return;
-    const LevelRef L = lref[p * level_stride + level];
-    const LevelRef C = lref[p * level_stride + level + 1];
-    const int nk = nkept[p * level_stride + level];
-    const int t = threadIdx.x;  // blockDim = 8 * top_k rounded up to whole warps (<= 512)
-    const int r = t >> 3, o = t & 7;
-    bool ex = false;
-    int64_t cx = 0, cy = 0, cz = 0;
-    if (r < nk) {
-        const int32_t ppos = kept_pos[(p * level_stride + level) * top_k + r];
-        const int64_t pidx = L.cells.idx[ppos];
-        const int64_t n = L.n_side;
-        const int64_t ix = pidx % n, iy = (pidx / n) % n, iz = pidx / (n * n);
-        cx = 2 * ix + (o & 1);
-        cy = 2 * iy + ((o >> 1) & 1);
-        cz = 2 * iz + (o >> 2);
-        ex = cell_exists(2 * L.n_side, cx, cy, cz);
-    }
-    // ordered compaction (block-wide exclusive scan over t)
-    __shared__ int warp_tot[16];
-    const unsigned ball = __ballot_sync(0xffffffffu, ex);
-    const int lane = t & 31, w = t >> 5;
-    if (lane == 0) warp_tot[w] = __popc(ball);
-    __syncthreads();
-    int base = 0, tot = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-        if (k < w) base += warp_tot[k];
-        tot += warp_tot[k];
-    }
-    const int pos = base + __popc(ball & ((1u << lane) - 1u));
-    if (ex) write_cell(C.cells, pos, 2 * L.n_side, cx, cy, cz);
-    if (t == 0) *const_cast<int32_t *>(C.ncells) = tot;
-}
-
-cudaError_t launch_children(const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride, int level,
-                            int top_k, const int32_t *kept_pos, const int32_t *nkept, cudaStream_t s) {
-    const int bs = ((8 * top_k + 31) / 32) * 32;  // whole warps (the compaction uses full-warp ballots)
-    children_kernel<<<nprob, bs, 0, s>>>(probs, lref, level_stride, level, top_k, kept_pos, nkept);
     return cudaGetLastError();
 }
 

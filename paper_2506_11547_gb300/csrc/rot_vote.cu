@@ -4,7 +4,7 @@
 // buffer layout inside one device workspace), its descriptors are uploaded
 // with one copy, and the device pipeline runs on one stream:
 //
-//   pair step -> for each level: vote, top-K, children -> fit -> results
+//   pair step -> for each level: vote, top-K (+ the next level's children) -> fit -> results
 //
 // The pipeline of a given shape is captured once in a CUDA graph and
 // replayed by later solves of the same shape (only the descriptors change).
@@ -501,21 +501,27 @@ int Context::enqueue_pipeline(Wave &w) {
     if (e == cudaSuccess)
         e = launch_pair_prep(pl.d_probs, pl.d_tiles, (int)pl.tiles_h.size(), pl.pool, pl.prec, pl.d_stats, w.stream);
     done();
+    // coarse level: the cell-major vote and the two-phase top-K; refinement
+    // levels (<= 8 top_k cells per problem): the pair-major vote and a one-block
+    // top-K.  Each ranking step also writes the next level's children.
     for (int lev = 0; lev < S && e == cudaSuccess; ++lev) {
-        const int nit = (int)pl.items_h[lev].size();
         mark(1, lev);
-        e = launch_vote(w, lev, pl.variant);
+        if (lev == 0)
+            e = launch_vote(w, lev, pl.variant);
+        else
+            e = launch_vote_small(pl.d_probs, pl.d_tiles, (int)pl.tiles_h.size(), pl.d_lref, S, lev, pl.pool,
+                                  pl.d_stats, w.stream);
         done();
         mark(2, lev);
-        if (e == cudaSuccess)
-            e = launch_topk(pl.d_probs, P, pl.d_lref, S, lev, K, cfg.rank_mode, 0, pl.d_cand, pl.chunks_per_prob,
-                            pl.d_kept, pl.d_nkept, pl.d_stats, w.stream);
-        done();
-        if (e == cudaSuccess && lev < pl.max_level) {
-            mark(3, lev);
-            e = launch_children(pl.d_probs, P, pl.d_lref, S, lev, K, pl.d_kept, pl.d_nkept, w.stream);
-            done();
+        if (e == cudaSuccess) {
+            if (lev == 0)
+                e = launch_topk(pl.d_probs, P, pl.d_lref, S, lev, K, cfg.rank_mode, 0, pl.d_cand,
+                                pl.chunks_per_prob, pl.d_kept, pl.d_nkept, pl.d_stats, w.stream);
+            else
+                e = launch_select_small(pl.d_probs, P, pl.d_lref, S, lev, K, cfg.rank_mode, pl.d_kept, pl.d_nkept,
+                                        pl.d_stats, w.stream);
         }
+        done();
     }
     mark(4, -1);
     if (e == cudaSuccess)

@@ -131,8 +131,19 @@ cudaError_t launch_topk(const ProbRef *probs, int nprob, const LevelRef *lref, i
                         int top_k, int rank_mode, int max_cells, Cand *cand, int chunks_per_prob,
                         int32_t *kept_pos, int32_t *nkept, ProbStats *stats, cudaStream_t s);
 
-cudaError_t launch_children(const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride, int level,
-                            int top_k, const int32_t *kept_pos, const int32_t *nkept, cudaStream_t s);
+// Phase 2 also writes the next level's children (the 8 octants of each kept cell
+// that meet the ball) when the problem has a next level.
+
+// Refinement levels (at most kSelChunk cells per problem): top-K and children in
+// one block per problem.
+cudaError_t launch_select_small(const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride, int level,
+                                int top_k, int rank_mode, int32_t *kept_pos, int32_t *nkept, ProbStats *stats,
+                                cudaStream_t s);
+
+// Vote of a refinement level, pair-major (one block per 256-pair tile of the
+// pair step's tile list); FP32 chain + FP32 re-check, exact counts in every form.
+cudaError_t launch_vote_small(const ProbRef *probs, const int2 *tiles, int ntiles, const LevelRef *lref,
+                              int level_stride, int level, PairPool pool, ProbStats *stats, cudaStream_t s);
 
 // Fit: winner voters, FP64 sum of S_i, Jacobi, refit loop; writes results.
 // One thread-block cluster of `cluster` CTAs per problem; slice_part holds

@@ -32,7 +32,7 @@ WORKLOAD = "fp32_n1e5_64L3"
 WORKLOAD_DESC = ("N=1e5 float32 unit pairs, 99% uniform outliers, inlier noise sigma=0.01, delta=0.03 rad; "
                  "64^3 coarse grid over the vector-part ball (146,864 cells) + 3 levels of 2x2x2 "
                  "subdivision of the top-16 cells; exact counts, EXCESS ranking, FP64 fit with 8 refits")
-FLOPS_PER_TEST = 20.0  # 10 multiply-adds of the (cell monomials . pair S entries) contraction
+FLOPS_PER_TEST = 20.0  # algorithmic: 10 multiply-adds of the (cell monomials . pair S entries) contraction
 
 
 def parse():
@@ -448,6 +448,7 @@ def main():
         roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": None, "kernel": f"{dom[0]} level {dom[1]}", "kernel_ms": stage_avg[dom],
                     "flops_per_test": FLOPS_PER_TEST, "tests_per_launch": tests_dom, "peak_source": note,
+                    "executed_fma_per_test": 9 if args.precision == "fp32" else None,
                     "share_of_step": stage_avg[dom] / sum(stage_avg.values())}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----

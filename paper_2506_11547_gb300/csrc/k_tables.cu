@@ -135,18 +135,25 @@ __global__ void pair_prep_kernel(const ProbRef *__restrict__ probs, const int2 *
         p0 = make_float4(a0, a1, a2, b0);
         p1 = make_float4(b1, b2, 0.25f * ((na + nb) - 2.f), 0.f);
     }
-    pool.s32[3 * g + 0] = make_float4(s[0], s[1], s[2], s[3]);
-    pool.s32[3 * g + 1] = make_float4(s[4], s[5], s[6], s[7]);
-    pool.s32[3 * g + 2] = make_float4(s[8], s[9], 0.f, 0.f);
+    // the FP32 form's operand P = b a^T (each product rounded once; 0 for padding pairs)
+    float pp[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+        const float bv[3] = {p0.w, p1.x, p1.y}, av[3] = {p0.x, p0.y, p0.z};
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) pp[3 * j + k] = bv[j] * av[k];
+    }
+    pool.p32[3 * g + 0] = make_float4(pp[0], pp[1], pp[2], pp[3]);
+    pool.p32[3 * g + 1] = make_float4(pp[4], pp[5], pp[6], pp[7]);
+    pool.p32[3 * g + 2] = make_float4(pp[8], 0.f, 0.f, 0.f);
     pool.pr[2 * g + 0] = p0;
     pool.pr[2 * g + 1] = p1;
-    if (pool.s2x) {  // pair-interleaved copy for the packed FP32 vote
-        float *x = reinterpret_cast<float *>(pool.s2x + (g >> 1) * 5);
+    if (pool.p2x) {  // pair-interleaved copy for the packed FP32 vote
+        float *x = reinterpret_cast<float *>(pool.p2x + (g >> 1) * 5);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            x[4 * k + (g & 1)] = s[2 * k];
-            x[4 * k + 2 + (g & 1)] = s[2 * k + 1];
-        }
+        for (int t = 0; t < 9; ++t) x[4 * (t >> 1) + 2 * (t & 1) + (g & 1)] = pp[t];
+        x[18 + (g & 1)] = 0.f;
     }
     if (tc_prec != ROT_PREC_FP32 && pool.tcb) {
         const int K = pool.tc_k;

@@ -271,10 +271,10 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     std::vector<size_t> o_items(S);
     for (int lev = 0; lev < S; ++lev) o_items[lev] = reserve(sizeof(VoteItem) * std::max<size_t>(1, pl.items_h[lev].size()));
     const size_t o_in = reserve(sizeof(float) * (size_t)pl.in_floats * 2);
-    const size_t o_s32 = reserve(sizeof(float4) * 3 * (size_t)pool);
+    const size_t o_p32 = reserve(sizeof(float4) * 3 * (size_t)pool);
     const size_t o_pr = reserve(sizeof(float4) * 2 * (size_t)pool);
     const size_t o_tcb = tck ? reserve((size_t)pool * tck * 2) : 0;
-    const size_t o_s2x = tck ? 0 : reserve(sizeof(float4) * 5 * (size_t)(pool / 2));
+    const size_t o_p2x = tck ? 0 : reserve(sizeof(float4) * 5 * (size_t)(pool / 2));
     const size_t o_member = reserve((size_t)pool);
     const size_t o_tiles = reserve(sizeof(int2) * (size_t)(pool / kPairTile + 1));
     // zeroed region: counts, child counts, stats, nkept
@@ -326,11 +326,11 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     pl.d_items.resize(S);
     for (int lev = 0; lev < S; ++lev) pl.d_items[lev] = (VoteItem *)(B + o_items[lev]);
     pl.d_in = (float *)(B + o_in);
-    pl.pool.s32 = (float4 *)(B + o_s32);
+    pl.pool.p32 = (float4 *)(B + o_p32);
     pl.pool.pr = (float4 *)(B + o_pr);
     pl.pool.tcb = tck ? (void *)(B + o_tcb) : nullptr;
     pl.pool.tc_k = tck;
-    pl.pool.s2x = tck ? nullptr : (float4 *)(B + o_s2x);
+    pl.pool.p2x = tck ? nullptr : (float4 *)(B + o_p2x);
     pl.d_member = (uint8_t *)(B + o_member);
     pl.d_tiles = (int2 *)(B + o_tiles);
     pl.zero_off = z0;

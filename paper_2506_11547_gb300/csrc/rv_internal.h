@@ -14,7 +14,7 @@ constexpr int kMaxTopK = 64;
 constexpr int kPairTile = 256;      // pairs per pool tile (tensor-core B tile rows = MMA N)
 constexpr int kCellTile = 128;      // cells per tensor-core A tile (TMEM lanes)
 constexpr float kAmbig = 1e-6f;     // |v - tau| below this: the decision is reported ambiguous
-constexpr float kBandFP32 = 4e-6f;  // rigorous bound on |v_fast - v_exact| of the FP32 FMA form
+constexpr float kBandR = 5e-6f;     // FP32 form: |d| band, d = fma-chain(-R_c, b a^T, 1 - 2 tau) ~ 2 (v - tau)
 constexpr int kSelChunk = 4096;     // cells per top-K phase-1 block
 constexpr int kSimtItemCells = 1024; // cells per CUDA-core vote work item (any cells-per-thread variant)
 
@@ -82,17 +82,19 @@ struct Cand {
 };
 
 // Pair pool: one record per pair, padded to kPairTile per problem.
-//   s32  [P][3] float4: S entries [S00 S11 S22 S33 S01 S02 S03 S12 S13 S23] + 2 pad
+//   p32  [P][3] float4: P = b a^T row-major [b0a0 b0a1 b0a2 b1a0 b1a1 b1a2 b2a0 b2a1 b2a2] + 3 pad
+//        (padding pairs: 0), the FP32 form's operand (q^T S q = (1 - b^T R(q) a) / 2, App. A)
 //   pr   [P][2] float4: a0 a1 a2 b0 | b1 b2 c 0, c = (|a|^2 + |b|^2 - 2)/4
-//   tcb  tensor-core operand tiles (16-bit), layout described in k_vote_tc.cu
+//   tcb  tensor-core operand tiles (16-bit S entries), layout described in k_vote_tc.cu
 struct PairPool {
-    float4 *s32;
+    float4 *p32;
     float4 *pr;
     void *tcb;
     int tc_k;  // 16 or 32 (0 if absent)
-    // [P/2][5] float4, pairs (i, i+1) interleaved for the packed FP32 vote:
-    // float4 k of pair-pair j = (s_2k(2j), s_2k(2j+1), s_2k+1(2j), s_2k+1(2j+1)); null if absent
-    float4 *s2x = nullptr;
+    // [P/2][5] float4, pairs (i, i+1) interleaved for the packed FP32 vote: float4 k < 4 of
+    // pair-pair j = (P_2k(2j), P_2k(2j+1), P_2k+1(2j), P_2k+1(2j+1)), float4 4 = (P_8(2j),
+    // P_8(2j+1), 0, 0); null if absent
+    float4 *p2x = nullptr;
 };
 
 // ---- launchers (each returns cudaGetLastError() of its launch) ----
@@ -105,7 +107,7 @@ cudaError_t launch_pair_prep(const ProbRef *probs, const int2 *tiles, int ntiles
                              ProbStats *stats, cudaStream_t s);
 
 // Vote, CUDA-core FP32 form.  variant: cells per thread (4 or 8) of the scalar
-// kernel, or 100 + cells per thread (2 or 4) of the packed f32x2 kernel (needs pool.s2x).
+// kernel, or 100 + cells per thread (2 or 4) of the packed f32x2 kernel (needs pool.p2x).
 // item_counter: a zeroed int through which CTAs take work items dynamically; null =
 // items in grid-stride order.
 cudaError_t launch_vote_simt(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,

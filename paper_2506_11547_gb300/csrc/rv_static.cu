@@ -219,7 +219,7 @@ extern "C" int rot_vote_count_cells_static(const float *a, const float *b, int64
     LevelRef *lref = reinterpret_cast<LevelRef *>(base + kOffLevel);
     ProbStats *stats = reinterpret_cast<ProbStats *>(base + kOffStats);
     PairPool pool;
-    pool.s32 = reinterpret_cast<float4 *>(base + kOffS32);
+    pool.p32 = reinterpret_cast<float4 *>(base + kOffS32);
     pool.pr = reinterpret_cast<float4 *>(base + kOffPr);
     pool.tcb = nullptr;
     pool.tc_k = 0;

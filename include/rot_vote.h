@@ -111,7 +111,8 @@ typedef struct {
                                  variable ROT_VOTE_TUNE_CACHE if set); default 1; negative = off
                                  (a fixed default shape); >= 2 = always use the tile shape with this
                                  code (tests, diagnostics): FP32 form 4, 8 (scalar kernel, cells per
-                                 thread) or 102, 104 (packed f32x2 kernel); tensor-core forms 2, 4
+                                 thread) or 102, 104, 114, 124 (packed f32x2 kernel; 114 / 124 with 5 /
+                                 6 CTAs per SM); tensor-core forms 2, 4
                                  (epilogue warpgroups) + 10 (16-column TMEM chunks) + 100 (128-pair
                                  MMA units), i.e. 2, 4, 12, 14, 102, 104, 112, 114.  A code that
                                  does not exist for the precision fails the solve with EINVAL. */

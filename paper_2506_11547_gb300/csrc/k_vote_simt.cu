@@ -206,8 +206,8 @@ __device__ __forceinline__ float min3_abs(float m, float x, float y) {
 
 constexpr int kPP = kTP / 2;  // pair-pairs per shared-memory tile (5 float4 each)
 
-template <int CPT>
-__global__ void __launch_bounds__(kThreads, 4) vote_simt2_kernel(const VoteItem *__restrict__ items, int n_items,
+template <int CPT, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) vote_simt2_kernel(const VoteItem *__restrict__ items, int n_items,
                                                               const ProbRef *__restrict__ probs,
                                                               const LevelRef *__restrict__ lref, int level_stride,
                                                               int level, PairPool pool, ProbStats *stats,
@@ -365,13 +365,17 @@ cudaError_t launch_vote_simt(const VoteItem *items, int n_items, const ProbRef *
     if (n_items <= 0) return cudaSuccess;
     const int grid = grid_blocks < n_items ? grid_blocks : n_items;
     if (variant > 100 && !pool.p2x) return cudaErrorInvalidValue;
-#define RV_SIMT(K_, CPT_) \
-    K_<CPT_><<<grid, kThreads, 0, s>>>(items, n_items, probs, lref, level_stride, level, pool, stats, item_counter)
+    // grid_blocks assumes 4 resident CTAs per SM; the packed shapes 114 / 124 fit 5 / 6
+    const int g5 = min(n_items, grid_blocks / 4 * 5), g6 = min(n_items, grid_blocks / 4 * 6);
+#define RV_SIMT(G_, ...) \
+    __VA_ARGS__<<<G_, kThreads, 0, s>>>(items, n_items, probs, lref, level_stride, level, pool, stats, item_counter)
     switch (variant) {
-    case 4: RV_SIMT(vote_simt_kernel, 4); break;
-    case 8: RV_SIMT(vote_simt_kernel, 8); break;
-    case 102: RV_SIMT(vote_simt2_kernel, 2); break;
-    case 104: RV_SIMT(vote_simt2_kernel, 4); break;
+    case 4: RV_SIMT(grid, vote_simt_kernel<4>); break;
+    case 8: RV_SIMT(grid, vote_simt_kernel<8>); break;
+    case 102: RV_SIMT(grid, vote_simt2_kernel<2, 4>); break;
+    case 104: RV_SIMT(grid, vote_simt2_kernel<4, 4>); break;
+    case 114: RV_SIMT(g5, vote_simt2_kernel<4, 5>); break;
+    case 124: RV_SIMT(g6, vote_simt2_kernel<4, 6>); break;
     default: return cudaErrorInvalidValue;
     }
 #undef RV_SIMT

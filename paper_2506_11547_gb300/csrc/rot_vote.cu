@@ -569,10 +569,10 @@ std::string Context::tune_key(const Plan &pl) const {
     return buf;
 }
 
-// CUDA-core form: cells per thread, +100 for the packed f32x2 kernel; tensor-core form: epilogue warpgroups, +10 for
+// CUDA-core form: cells per thread, +100 for the packed f32x2 kernel (+10 / +20: 5 / 6 CTAs per SM); tensor-core form: epilogue warpgroups, +10 for
 // 16-column TMEM chunks, +100 for 128-pair MMA units (four accumulator stages)
 static std::vector<int> candidates(int tc_k) {
-    return tc_k ? std::vector<int>{2, 4, 12, 14, 102, 104, 112, 114} : std::vector<int>{102, 104, 4, 8};
+    return tc_k ? std::vector<int>{2, 4, 12, 14, 102, 104, 112, 114} : std::vector<int>{124, 114, 104, 102, 4, 8};
 }
 
 // The tuned variant of the bucket nearest to `key` (same SM count and

@@ -107,7 +107,8 @@ cudaError_t launch_pair_prep(const ProbRef *probs, const int2 *tiles, int ntiles
                              ProbStats *stats, cudaStream_t s);
 
 // Vote, CUDA-core FP32 form.  variant: cells per thread (4 or 8) of the scalar
-// kernel, or 100 + cells per thread (2 or 4) of the packed f32x2 kernel (needs pool.p2x).
+// kernel, or 100 + cells per thread (2 or 4) of the packed f32x2 kernel (needs pool.p2x),
+// + 10 / + 20 for 5 / 6 resident CTAs per SM (codes 114, 124).
 // item_counter: a zeroed int through which CTAs take work items dynamically; null =
 // items in grid-stride order.
 cudaError_t launch_vote_simt(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,

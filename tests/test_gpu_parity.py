@@ -86,7 +86,7 @@ def test_multilevel_every_level():
     assert_parity(p, r, tr, o, 3)
 
 
-FP32_SHAPES = [4, 8, 102, 104]  # scalar kernel (cells per thread), packed f32x2 kernel (100 + cells per thread)
+FP32_SHAPES = [4, 8, 102, 104, 114, 124]  # scalar (cells per thread); packed f32x2 (100 + cells per thread, +10/+20 occupancy)
 
 
 @pytest.mark.parametrize("shape", FP32_SHAPES)

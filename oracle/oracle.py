@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = [
     "lib", "pair_M", "pair_S", "quad", "quat_to_R", "cell_exists", "cell_geom", "tau",
     "level_cells", "vote_cells", "rank", "jacobi4", "canonical", "solve", "OracleResult",
-    "AMBIG", "cell_of_point", "fit_cell",
+    "AMBIG", "cell_of_point", "fit_cell", "alg1_basis", "alg1_cell", "alg1_table", "alg1",
 ]
 
 AMBIG = 1e-6
@@ -73,6 +73,15 @@ def lib():
         L.rvo_fit_cell.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int64, C.c_int,
                                    C.POINTER(_Result)]
         L.rvo_fit_cell.restype = C.c_int
+        L.rvo_alg1_basis.argtypes = [_f32p, _f32p, _f64p, _f64p]
+        L.rvo_alg1_basis.restype = C.c_int
+        L.rvo_alg1_cell.argtypes = [_f64p, _f64p, C.c_double, C.c_double, C.c_int]
+        L.rvo_alg1_cell.restype = C.c_int64
+        L.rvo_alg1_table.argtypes = [C.c_int, _f64p]
+        L.rvo_alg1_table.restype = None
+        L.rvo_alg1.argtypes = [_f32p, _f32p, C.c_int64, _f64p, C.c_int, C.c_int, _i32p, C.POINTER(C.c_int64),
+                               C.POINTER(C.c_int32), _f64p]
+        L.rvo_alg1.restype = C.c_int64
         _lib = L
     return _lib
 
@@ -248,3 +257,37 @@ def fit_cell(a, b, delta: float, n_side: int, idx: int, refit_iters: int = 8) ->
 
 def default_threads() -> int:
     return max(1, (os.cpu_count() or 1))
+
+
+# ---- Alg. 1 (Sec. 4.3.2): sampled circles, stereographic projection, counting grid ----
+
+def alg1_basis(a, b):
+    """(ok, q_b1, q_b2) of pair (a, b) (Sec. 4.1)."""
+    q1 = np.zeros(4)
+    q2 = np.zeros(4)
+    ok = lib().rvo_alg1_basis(_v3(a), _v3(b), q1, q2)
+    return bool(ok), q1, q2
+
+
+def alg1_cell(q1, q2, cj: float, sj: float, n: int) -> int:
+    return int(lib().rvo_alg1_cell(np.ascontiguousarray(q1, dtype=np.float64), np.ascontiguousarray(q2, dtype=np.float64),
+                                   float(cj), float(sj), int(n)))
+
+
+def alg1_table(J: int) -> np.ndarray:
+    """[J, 2] (cos(alpha_j / 2), sin(alpha_j / 2)), alpha_j = -pi + 2 pi j / J."""
+    cs = np.zeros(2 * J)
+    lib().rvo_alg1_table(int(J), cs)
+    return cs.reshape(J, 2)
+
+
+def alg1(a, b, J: int, n: int):
+    """Alg. 1 on one problem: (acc [n^3] int32, best_idx, best_count, q, samples cast)."""
+    a, b = _f32_pairs(a, b)
+    cs = np.ascontiguousarray(alg1_table(J).reshape(-1))
+    acc = np.zeros(int(n) ** 3, dtype=np.int32)
+    bi = C.c_int64()
+    bc = C.c_int32()
+    q = np.zeros(4)
+    cast = lib().rvo_alg1(a.reshape(-1), b.reshape(-1), a.shape[0], cs, int(J), int(n), acc, C.byref(bi), C.byref(bc), q)
+    return acc, int(bi.value), int(bc.value), q, int(cast)

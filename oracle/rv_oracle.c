@@ -28,6 +28,10 @@
  *                     Q^T Q of Eq. (stack), Sec. 4.2; refit with the
  *                     delta-only inlier rule.
  *
+ * and, separately, the paper's own Alg. 1 (Sec. 4.3.2): circle samples,
+ * stereographic projection (Sec. 4.3.1), a counting grid over [-1,1]^3 and
+ * its argmax (rvo_alg1*).
+ *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
  * arithmetic is the written sequence of IEEE double operations).
  *
@@ -43,6 +47,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#define RVO_PI 3.14159265358979323846 /* the double nearest pi */
 #define RVO_AMBIG 1e-6 /* |v - tau| <= this: the (cell, pair) decision is reported ambiguous */
 
 enum { RVO_OK = 0, RVO_EINVAL = -1, RVO_EDEGENERATE = -6 };
@@ -607,4 +612,107 @@ int rvo_fit_cell(const float *a, const float *b, int64_t n, double delta, int n_
     const int status = fit_from_cell(S, n, sin(delta), cos(delta), n_side, idx, refit_iters, res);
     free(S);
     return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Alg. 1 (Sec. 4.3.2): the paper's own voting -- every quaternion    */
+/* circle sampled at J angles, each sample stereographically          */
+/* projected (Sec. 4.3.1) and counted in a grid over [-1,1]^3.        */
+/* ------------------------------------------------------------------ */
+
+/* Orthonormal basis (q_b1, q_b2) of the circle of pair (a, b), Sec. 4.1:
+ * q_b1 is the quaternion of the minimal rotation R_a^b, written with the
+ * half-angle identities w = cos(theta/2) = sqrt((1 + a.b)/2) and
+ * sin(theta/2) c = (a x b) / (2 w) (no trigonometry, no normalisation of
+ * a x b); q_b2 = [-b.v, w b + b x v] with v the vector part of q_b1.
+ * Returns 0 when a = -b exactly (w = 0: no circle is defined; such a pair
+ * casts no vote).  Every operation is a separate IEEE double operation. */
+int rvo_alg1_basis(const float a32[3], const float b32[3], double q1[4], double q2[4]) {
+    const double a0 = a32[0], a1 = a32[1], a2 = a32[2], b0 = b32[0], b1 = b32[1], b2 = b32[2];
+    const double c = (a0 * b0 + a1 * b1) + a2 * b2;
+    const double w = sqrt((1.0 + c) * 0.5);
+    if (!(w > 0.0)) return 0;
+    const double w2 = 2.0 * w;
+    const double vx = (a1 * b2 - a2 * b1) / w2, vy = (a2 * b0 - a0 * b2) / w2, vz = (a0 * b1 - a1 * b0) / w2;
+    q1[0] = w;
+    q1[1] = vx;
+    q1[2] = vy;
+    q1[3] = vz;
+    const double bv = (b0 * vx + b1 * vy) + b2 * vz;
+    q2[0] = -bv;
+    q2[1] = w * b0 + (b1 * vz - b2 * vy);
+    q2[2] = w * b1 + (b2 * vx - b0 * vz);
+    q2[3] = w * b2 + (b0 * vy - b1 * vx);
+    return 1;
+}
+
+/* Sample q(alpha_j) = q_b1 cos(alpha_j/2) + q_b2 sin(alpha_j/2), taken with
+ * the sign that puts it in the q3 <= 0 half (q and -q are one rotation; that
+ * half projects into the unit ball), projected p = (q0, q1, q2) / (1 - q3)
+ * (Sec. 4.3.1), and located in the n^3 grid over [-1,1]^3:
+ * i_k = floor((p_k + 1) n/2) clamped to [0, n-1].  Returns the linear index
+ * (iz n + iy) n + ix. */
+int64_t rvo_alg1_cell(const double q1[4], const double q2[4], double cj, double sj, int n) {
+    double q[4];
+    for (int k = 0; k < 4; ++k) q[k] = q1[k] * cj + q2[k] * sj;
+    if (q[3] > 0.0)
+        for (int k = 0; k < 4; ++k) q[k] = -q[k];
+    const double den = 1.0 - q[3];
+    const double half = 0.5 * (double)n;
+    int64_t i[3];
+    for (int k = 0; k < 3; ++k) {
+        const double x = (q[k] / den + 1.0) * half;
+        int64_t v = (int64_t)floor(x);
+        if (v < 0) v = 0;
+        if (v > n - 1) v = n - 1;
+        i[k] = v;
+    }
+    return (i[2] * n + i[1]) * n + i[0];
+}
+
+/* The whole of Alg. 1 for one problem: acc[n^3] (zeroed here) gets one count
+ * per sample; the winner is the largest count, ties to the smallest index; q
+ * is the inverse projection of the winner's centre
+ * p* = -1 + (i + 1/2) 2/n: q = [2 p*, |p*|^2 - 1] / (1 + |p*|^2), canonical
+ * sign.  cs holds (cos(alpha_j/2), sin(alpha_j/2)) for j < J.  Returns the
+ * number of samples cast. */
+int64_t rvo_alg1(const float *a, const float *b, int64_t n_pairs, const double *cs, int J, int n, int32_t *acc,
+                 int64_t *best_idx, int32_t *best_count, double q[4]) {
+    const int64_t cells = (int64_t)n * n * n;
+    memset(acc, 0, sizeof(int32_t) * (size_t)cells);
+    int64_t cast = 0;
+    for (int64_t i = 0; i < n_pairs; ++i) {
+        double q1[4], q2[4];
+        if (!rvo_alg1_basis(a + 3 * i, b + 3 * i, q1, q2)) continue;
+        for (int j = 0; j < J; ++j) {
+            ++acc[rvo_alg1_cell(q1, q2, cs[2 * j], cs[2 * j + 1], n)];
+            ++cast;
+        }
+    }
+    int64_t bi = 0;
+    for (int64_t c = 1; c < cells; ++c)
+        if (acc[c] > acc[bi]) bi = c;
+    *best_idx = bi;
+    *best_count = acc[bi];
+    const int64_t ix = bi % n, iy = (bi / n) % n, iz = bi / ((int64_t)n * n);
+    const double h = 2.0 / (double)n;
+    const double p[3] = {-1.0 + ((double)ix + 0.5) * h, -1.0 + ((double)iy + 0.5) * h, -1.0 + ((double)iz + 0.5) * h};
+    const double pp = (p[0] * p[0] + p[1] * p[1]) + p[2] * p[2];
+    const double den = 1.0 + pp;
+    q[0] = (2.0 * p[0]) / den;
+    q[1] = (2.0 * p[1]) / den;
+    q[2] = (2.0 * p[2]) / den;
+    q[3] = (pp - 1.0) / den;
+    rvo_canonical(q);
+    return cast;
+}
+
+/* (cos(alpha_j/2), sin(alpha_j/2)) for alpha_j = -pi + 2 pi j / J, j < J: the
+ * uniform discretisation of [-pi, pi) of Alg. 1. */
+void rvo_alg1_table(int J, double *cs) {
+    for (int j = 0; j < J; ++j) {
+        const double alpha = -RVO_PI + (2.0 * RVO_PI * (double)j) / (double)J;
+        cs[2 * j] = cos(alpha / 2.0);
+        cs[2 * j + 1] = sin(alpha / 2.0);
+    }
 }

@@ -222,6 +222,74 @@ def bench_batched(rv, synth, torch, stream, flush, launches: int = 3):
     return res
 
 
+def bench_alg1(rv, synth, torch, stream, flush, peaks, reps: int = 5):
+    """Alg. 1 (Sec. 4.3.2) at the paper's default resolution (1/180: a 360^3
+    accumulator) and J = 180, on 1e5 and 1e6 pairs with 99% outliers.  Device
+    time per solve (inputs resident, L2 flushed before each), the end-to-end
+    call with pinned host inputs, and each stage's time from a profiled run."""
+    res = {}
+    for n, sigma, seed in ((100000, 0.01, 2301), (1000000, 0.005, 2302)):
+        p = synth.make_problem(n, 0.99, sigma, 0.03, seed=seed)
+        a_d, b_d = torch.from_numpy(p.a).cuda(), torch.from_numpy(p.b).cuda()
+        a_h, b_h = torch.from_numpy(p.a).pin_memory(), torch.from_numpy(p.b).pin_memory()
+        arr = (rv.rot_vote_alg1_problem * 1)(rv.rot_vote_alg1_problem(a_d.data_ptr(), b_d.data_ptr(), n, 180, 360,
+                                                                        None))
+        arr_h = (rv.rot_vote_alg1_problem * 1)(rv.rot_vote_alg1_problem(a_h.data_ptr(), b_h.data_ptr(), n, 180, 360,
+                                                                          None))
+        out = (rv.rot_vote_alg1_result * 1)()
+        ctx = rv.Context(cuda_stream=stream.cuda_stream)
+        for _ in range(3):
+            ctx.alg1_raw(arr, 1, out)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            ctx.alg1_raw(arr, 1, out)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(s0.elapsed_time(s1))
+        r = rv.Alg1Result.of(out[0])
+        e2e = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.alg1_raw(arr_h, 1, out)
+            e2e.append(time.perf_counter() - t0)
+        ctx.close()
+        prof = rv.Context(cuda_stream=stream.cuda_stream, keep_trace=2)
+        st = {}
+        for k in range(4):
+            flush.zero_()
+            prof.alg1_raw(arr, 1, out)
+            if k:
+                for kind, _, ms in prof.stage_times():
+                    st.setdefault(kind, []).append(ms)
+        prof.close()
+        st = {k: sum(v) / len(v) for k, v in st.items()}
+        ms = sum(ts) / len(ts)
+        cells = 360 ** 3
+        acc_bytes = 4 * cells
+        res[f"n{n}"] = {
+            "ms_per_solve": ms, "samples_per_s": r.samples_cast / (ms / 1e3), "rotations_per_s": 1e3 / ms,
+            "e2e_ms": 1e3 * sum(e2e) / len(e2e), "samples_cast": r.samples_cast, "rechecked": r.rechecked,
+            "best_count": r.best_count, "angle_to_truth_rad": _angle(r.q, p.q_true), "status": r.status,
+            "stage_ms": st,
+            # the accumulator pass: 4 n^3 bytes read per argmax launch, 4 n^3 written per zeroing
+            "argmax_gbs": acc_bytes / (st["alg1_argmax"] / 1e3) / 1e9 if st.get("alg1_argmax") else None,
+            "zero_gbs": acc_bytes / (st["alg1_zero"] / 1e3) / 1e9 if st.get("alg1_zero") else None,
+            "hbm_peak_gbs": peaks.get("hbm_gbs"),
+            "vote_samples_per_s": r.samples_cast / (st["alg1_vote"] / 1e3) if st.get("alg1_vote") else None,
+            "paper_s": 0.04 if n == 100000 else 0.5,
+            "paper_note": ("RTX 4080, Python + CuPy, 1e5 pairs (Table I); context only" if n == 100000 else
+                           "the paper's bound for 1e6 pairs (Sec. 1, abstract); context only"),
+        }
+    res["workload"] = ("Alg. 1: J = 180 samples per circle, 360^3 accumulator over [-1,1]^3 (resolution 1/180), "
+                       "99% outliers; one problem per call")
+    return res
+
+
 def bench_serving(rv, synth, torch, seconds: float, rate_hz: float = 2000.0, distinct: int = 512):
     """Poisson arrivals at rate_hz (N log-uniform [100, 1e5], outliers U[0.8, 0.99],
     sigma 0.01, delta 0.03; 32^3 + 2 levels, FP16 hi/lo form) through
@@ -484,10 +552,11 @@ def main():
                                                        list(rr.q) == list(res0.q))}
             cx.close()
 
-    batched = serving = None
+    batched = serving = alg1 = None
     if not args.no_extra and ws == 1:
         batched = bench_batched(rv, synth, torch, stream, flush)
         serving = bench_serving(rv, synth, torch, args.serve_seconds)
+        alg1 = bench_alg1(rv, synth, torch, stream, flush, peaks)
 
     lat = per
     line = {
@@ -507,6 +576,7 @@ def main():
         "precision_forms": extra,
         "batched": batched,
         "serving": serving,
+        "alg1": alg1,
         "clocks": clocks,
         "cpu_baseline": cpu,
         "result": {"status": res0.status, "angle_to_truth_rad": None, "rechecked": res0.rechecked,

@@ -176,12 +176,14 @@ int rot_vote_poll(rot_vote_ctx *ctx, uint64_t ticket, rot_vote_result *out, int 
 int rot_vote_level_trace(rot_vote_ctx *ctx, int problem, int level, int64_t *idx, int32_t *count,
                          int64_t cap, int64_t *ncells, int64_t *kept_idx, int32_t *nkept);
 
-/* Diagnostic: device time of each kernel launch of the last rot_vote_solve on
+/* Diagnostic: device time of each kernel launch of the last rot_vote_solve (or rot_vote_alg1) on
  * a context created with keep_trace = 2.  Such a context launches the
  * pipeline stage by stage (no CUDA graph) with a pair of CUDA events on its
  * stream around every kernel (a stage may be two kernels).  kind: 0 pair step,
  * 1 vote, 2 top-K with the next level's children, 4 fit (3 is unused); level:
- * the level (-1 for pair step and fit).
+ * the level (-1 for pair step and fit).  After rot_vote_alg1 the entries are
+ * the stages of its last problem: kind 5 accumulator zeroing and circle
+ * bases, 6 sampling vote, 7 argmax and result (level -1).
  * Writes up to cap entries and their total count.  Returns OK or EINVAL. */
 typedef struct {
     int32_t kind;
@@ -242,6 +244,64 @@ const char *rot_vote_last_error(const rot_vote_ctx *ctx);
 #define ROT_VOTE_STATIC_MAX_CELLS 8192
 int rot_vote_count_cells_static(const float *a, const float *b, int64_t n, double delta, int grid_n,
                                 const int64_t *cells, int32_t ncells, int32_t *counts, void *cuda_stream);
+
+/* ---- Alg. 1: the paper's own voting by sampled circles (Sec. 4.3.2) ----
+ *
+ * For every pair the circle of rotations taking a_i to b_i (Sec. 4.1) is
+ *   q(alpha) = q_b1 cos(alpha/2) + q_b2 sin(alpha/2),
+ * with q_b1 the quaternion of the minimal rotation from a to b, written with
+ * the half-angle identities
+ *   w = sqrt((1 + a.b)/2),  q_b1 = (w, (a x b) / (2 w)),
+ * and q_b2 = (-b.v, w b + b x v), v the vector part of q_b1 (q_b2 = [0, b] q_b1:
+ * the half turn about b after the minimal rotation).  Alg. 1 samples alpha_j = -pi + 2 pi j / J,
+ * j = 0 .. J-1, takes each sample with the sign that gives q3 <= 0 (q and -q
+ * are one rotation; Sec. 4.3.1), projects it stereographically,
+ *   p = (q0, q1, q2) / (1 - q3),            a point of the closed unit ball,
+ * and counts it in the cell i_k = clamp(floor((p_k + 1) n / 2), 0, n - 1) of
+ * an n^3 accumulator over [-1, 1]^3, linear index (i2 n + i1) n + i0.  The
+ * winner is the largest count (ties: the smallest index); the rotation is
+ * the inverse projection of the winner's centre p* = -1 + (i + 1/2) 2/n,
+ *   q = (2 p*, |p*|^2 - 1) / (1 + |p*|^2),
+ * with the sign w > 0 (w = 0: the first nonzero component > 0).
+ *
+ * The cell of every sample is the cell that the same formulas give in IEEE
+ * double arithmetic, operation by operation in the order written above
+ * (products a_k b_k formed from the float32 inputs; (cos, sin)(alpha_j / 2)
+ * from the host C library).  The device evaluates each sample in FP32 and
+ * repeats it in FP64 when the FP32 result lies within a proven error bound
+ * (times a safety factor) of a cell boundary or of q3 = 0; the accumulator is
+ * therefore exact.  A pair with a = -b (w = 0, no circle) casts no sample.
+ */
+typedef struct {
+    const float *a;         /* [n,3] row-major float32 unit vectors, host or device memory; */
+    const float *b;         /*   validity as in rot_vote_problem */
+    int64_t n;              /* pairs, 2 <= n <= 2^30 */
+    int samples;            /* J, samples per circle, 1 <= J <= 65536; 0 = 180 */
+    int accum_side;         /* n of the n^3 accumulator, 2 <= n <= 1024; 0 = 360 */
+    int32_t *accumulator;   /* optional (NULL: not returned): host or device int32 [n^3], receives the
+                               counts in linear-index order; owned by the caller */
+} rot_vote_alg1_problem;
+
+typedef struct {
+    double q[4];            /* rotation of the winning cell, canonical sign */
+    double R[9];            /* its rotation matrix, row-major */
+    int32_t best_count;     /* count of the winning cell */
+    int32_t status;         /* rot_vote_status of this problem */
+    int64_t best_cell;      /* linear index of the winning cell */
+    int64_t samples_cast;   /* J x (pairs with a circle) */
+    int64_t rechecked;      /* samples whose cell the device decided in FP64 */
+    float ms_gpu;           /* device time of this problem (accumulator zeroing to result) */
+    float pad;
+} rot_vote_alg1_result;
+
+/* Run Alg. 1 on n_problems problems, one after another on the context's
+ * stream (each needs its own n^3 accumulator; the context keeps one, of
+ * 4 n^3 bytes, inside config.device_mem_budget), and block until out[] is
+ * written.  Returns OK when the call ran (per-problem status in
+ * out[k].status: OK, or EINVAL for bad arguments or inputs -- non-finite
+ * or non-unit vectors -- with the rest of out[k] unspecified), or ENOMEM /
+ * ECUDA / EINVAL when it could not run at all. */
+int rot_vote_alg1(rot_vote_ctx *ctx, const rot_vote_alg1_problem *p, int n_problems, rot_vote_alg1_result *out);
 
 #ifdef __cplusplus
 }

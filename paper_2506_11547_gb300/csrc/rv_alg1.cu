@@ -1,0 +1,541 @@
+// rv_alg1.cu -- Alg. 1 (Sec. 4.3.2), the paper's own voting: every pair's
+// circle of rotations (Sec. 4.1) sampled at J angles, each sample projected
+// stereographically (Sec. 4.3.1) and counted in an n^3 accumulator over
+// [-1, 1]^3, then the argmax and the inverse projection of its centre.
+//
+// Launches per problem, on the context's stream:
+//   alg1_prep_kernel    zeroes the accumulator (4 n^3 bytes) and writes each
+//             pair's circle basis: FP64 (the IEEE operation sequence of the
+//             formulas) and its FP32 rounding
+//   alg1_vote_kernel    persistent; the N J samples in FP32, 32 consecutive
+//             samples per warp instruction (coalesced angle-table reads), four
+//             independent samples per thread, one atomic add each.  Samples
+//             that need FP64 go to a per-warp shared-memory queue that the
+//             warp empties 32 at a time, so FP64 work runs in full warps
+//   alg1_argmax_kernel  (count, -index) maximum over the accumulator; the
+//             last block to finish writes the result (inverse projection,
+//             canonical sign, rotation matrix)
+//
+// Exactness.  A sample's cell is floor of x_k = (p_k + 1) n/2.  The FP32
+// evaluation below differs from the FP64 one by at most 1.1e-6 (n/2) cells
+// (error analysis at kEdgeRel); a sample whose FP32 x_k lies within
+// kEdgeRel (n/2) of an integer, or whose FP32 q3 lies within kQ3Guard of 0
+// (the sign choice), is evaluated again in FP64, operation for operation as
+// the formulas are written, so every count equals the FP64 count.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rv_geom.cuh"
+#include "rv_runtime.h"
+
+namespace rv {
+
+namespace {
+
+constexpr int kA1Threads = 256;
+constexpr int kA1Warps = kA1Threads / 32;
+constexpr int kA1U = 4;         // samples per thread per round of the vote
+constexpr int kWarpQ = 256;     // deferred FP64 samples per warp (emptied when above kWarpQ - 32 kA1U)
+// FP32 error bound, with u = 2^-24 and basis norms within 1e-3 of 1 (pairs
+// outside that take the FP64 path for every sample):
+//   q_k  = fma(q1_k, c, q2_k s) from FP32-rounded q1, q2, c, s:  <= 6u  (3.6e-7)
+//   den  = 1 + |q3| >= 1:                                        <= 8u
+//   p_k  = q_k * rcp(den):                                       <= 9.6e-7
+//   x_k  = fma(p_k, n/2, n/2):                                   <= 1.1e-6 (n/2)
+// kEdgeRel is 7x that bound; kQ3Guard is 11x the bound on q3.
+constexpr float kEdgeRel = 8e-6f;
+constexpr float kQ3Guard = 4e-6f;
+constexpr double kNormGuard = 1e-3;
+// q1f.x (= w > 0 for a circle) doubles as the pair's flag:
+constexpr float kNoCircle = -1.f;  // invalid input or a = -b
+constexpr float kFp64Only = -2.f;  // basis norms outside 1 +- kNormGuard: every sample in FP64
+
+struct A1Hdr {
+    unsigned long long best_key;   // (count << 32) | (0xffffffff - index): max = argmax, ties to the smallest index
+    unsigned long long cast;       // samples cast
+    unsigned long long rechecked;  // samples evaluated in FP64
+    int32_t invalid;               // an input vector failed validation
+    uint32_t blocks_done;          // argmax blocks finished (the last one writes the result)
+    rot_vote_alg1_result res;
+};
+static_assert(sizeof(A1Hdr) <= 256, "header slot");
+
+// q_b1, q_b2 of pair (a, b) (Sec. 4.1), each value the written sequence of
+// IEEE double operations.  False when w = 0 (a = -b: no circle).
+__device__ __forceinline__ bool alg1_basis(double a0, double a1, double a2, double b0, double b1, double b2,
+                                           double q1[4], double q2[4]) {
+    const double c = dadd(dadd(dmul(a0, b0), dmul(a1, b1)), dmul(a2, b2));
+    const double w = dsqrt(dmul(dadd(1.0, c), 0.5));
+    if (!(w > 0.0)) return false;
+    const double w2 = dmul(2.0, w);
+    const double vx = ddiv(dsub(dmul(a1, b2), dmul(a2, b1)), w2);
+    const double vy = ddiv(dsub(dmul(a2, b0), dmul(a0, b2)), w2);
+    const double vz = ddiv(dsub(dmul(a0, b1), dmul(a1, b0)), w2);
+    q1[0] = w;
+    q1[1] = vx;
+    q1[2] = vy;
+    q1[3] = vz;
+    const double bv = dadd(dadd(dmul(b0, vx), dmul(b1, vy)), dmul(b2, vz));
+    q2[0] = -bv;
+    q2[1] = dadd(dmul(w, b0), dsub(dmul(b1, vz), dmul(b2, vy)));
+    q2[2] = dadd(dmul(w, b1), dsub(dmul(b2, vx), dmul(b0, vz)));
+    q2[3] = dadd(dmul(w, b2), dsub(dmul(b0, vy), dmul(b1, vx)));
+    return true;
+}
+
+// The cell of sample (c, s) = (cos, sin)(alpha_j / 2) in FP64: q = q1 c + q2 s,
+// the sign with q3 <= 0, p = q_012 / (1 - q3), i_k = clamp(floor((p_k + 1) n/2)).
+__device__ __forceinline__ int alg1_cell64(const double q1[4], const double q2[4], double c, double s, int n,
+                                           double half) {
+    double q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = dadd(dmul(q1[k], c), dmul(q2[k], s));
+    if (q[3] > 0.0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = -q[k];
+    const double den = dsub(1.0, q[3]);
+    int i[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double x = dmul(dadd(ddiv(q[k], den), 1.0), half);
+        long long v = (long long)floor(x);
+        v = v < 0 ? 0 : (v > n - 1 ? n - 1 : v);
+        i[k] = (int)v;
+    }
+    return (i[2] * n + i[1]) * n + i[0];
+}
+
+// Zeroes acc[0, cells) (if zero) and writes every pair's basis: q1f, q2f the
+// FP32 roundings of q_b1, q_b2 (q1f.x = kNoCircle / kFp64Only flags the
+// pair), qd[4 i .. 4 i + 3] = q_b1, q_b2 in FP64.
+__global__ void __launch_bounds__(kA1Threads) alg1_prep_kernel(const float *__restrict__ a,
+                                                               const float *__restrict__ b, int64_t n,
+                                                               float4 *__restrict__ q1f, float4 *__restrict__ q2f,
+                                                               double2 *__restrict__ qd, int32_t *__restrict__ acc,
+                                                               int64_t cells, int zero, int J, A1Hdr *hdr) {
+    const int64_t T = (int64_t)gridDim.x * kA1Threads;
+    const int64_t g = (int64_t)blockIdx.x * kA1Threads + threadIdx.x;
+    if (zero) {
+        int4 *v = reinterpret_cast<int4 *>(acc);
+        const int64_t nvec = cells >> 2;
+        for (int64_t k = g; k < nvec; k += T) v[k] = make_int4(0, 0, 0, 0);
+        for (int64_t r = (nvec << 2) + g; r < cells; r += T) acc[r] = 0;
+    }
+    unsigned circles = 0;
+    for (int64_t i = g; i < n; i += T) {
+        const float a0 = a[3 * i], a1 = a[3 * i + 1], a2 = a[3 * i + 2];
+        const float b0 = b[3 * i], b1 = b[3 * i + 1], b2 = b[3 * i + 2];
+        const float na = fmaf(a0, a0, fmaf(a1, a1, a2 * a2));
+        const float nb = fmaf(b0, b0, fmaf(b1, b1, b2 * b2));
+        const bool ok = isfinite(a0) && isfinite(a1) && isfinite(a2) && isfinite(b0) && isfinite(b1) &&
+                        isfinite(b2) && fabsf(na - 1.f) <= 1e-5f && fabsf(nb - 1.f) <= 1e-5f;
+        double q1[4] = {0.0, 0.0, 0.0, 0.0}, q2[4] = {0.0, 0.0, 0.0, 0.0};
+        float4 A = make_float4(kNoCircle, 0.f, 0.f, 0.f), B = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!ok) {
+            atomicOr(&hdr->invalid, 1);
+        } else if (alg1_basis(a0, a1, a2, b0, b1, b2, q1, q2)) {
+            const double n1 = q1[0] * q1[0] + q1[1] * q1[1] + q1[2] * q1[2] + q1[3] * q1[3];
+            const double n2 = q2[0] * q2[0] + q2[1] * q2[1] + q2[2] * q2[2] + q2[3] * q2[3];
+            A = make_float4((float)q1[0], (float)q1[1], (float)q1[2], (float)q1[3]);  // w >= 2^-27: A.x > 0
+            B = make_float4((float)q2[0], (float)q2[1], (float)q2[2], (float)q2[3]);
+            if (!(fabs(n1 - 1.0) <= kNormGuard && fabs(n2 - 1.0) <= kNormGuard)) A.x = kFp64Only;
+            ++circles;
+        }
+        q1f[i] = A;
+        q2f[i] = B;
+        qd[4 * i + 0] = make_double2(q1[0], q1[1]);
+        qd[4 * i + 1] = make_double2(q1[2], q1[3]);
+        qd[4 * i + 2] = make_double2(q2[0], q2[1]);
+        qd[4 * i + 3] = make_double2(q2[2], q2[3]);
+    }
+    const unsigned cw = __reduce_add_sync(0xffffffffu, circles);
+    if ((threadIdx.x & 31) == 0 && cw) atomicAdd(&hdr->cast, (unsigned long long)cw * (unsigned long long)J);
+}
+
+// A warp's queued samples (pair << 16 | angle), 32 per pass, in FP64.
+__device__ __forceinline__ void alg1_drain(const unsigned long long *wq, int qn, const double2 *__restrict__ qd,
+                                           const double2 *__restrict__ t64, int side, double hd,
+                                           int32_t *__restrict__ acc, int lane) {
+    for (int k = lane; k < qn; k += 32) {
+        const unsigned long long e = wq[k];
+        const int64_t i = (int64_t)(e >> 16);
+        const int jj = (int)(e & 0xffffull);
+        const double2 u0 = qd[4 * i], u1 = qd[4 * i + 1], u2 = qd[4 * i + 2], u3 = qd[4 * i + 3];
+        const double q1[4] = {u0.x, u0.y, u1.x, u1.y}, q2[4] = {u2.x, u2.y, u3.x, u3.y};
+        const double2 cs = t64[jj];
+        atomicAdd(&acc[alg1_cell64(q1, q2, cs.x, cs.y, side, hd)], 1);
+    }
+}
+
+// Sample s in [0, N J) is (pair s / J, angle s % J).  Warp w takes the 32 kA1U
+// samples from w 32 kA1U on, lane l the samples w 32 kA1U + 32 k + l, then
+// moves on by the whole grid's share (adv_p pairs, adv_j angles).
+__global__ void __launch_bounds__(kA1Threads) alg1_vote_kernel(const float4 *__restrict__ q1f,
+                                                               const float4 *__restrict__ q2f,
+                                                               const double2 *__restrict__ qd,
+                                                               const float2 *__restrict__ t32,
+                                                               const double2 *__restrict__ t64, int J, int side,
+                                                               int32_t *__restrict__ acc, A1Hdr *hdr, int64_t total,
+                                                               int64_t adv_p, int adv_j) {
+    __shared__ unsigned long long queue[kA1Warps][kWarpQ];
+    const int lane = threadIdx.x & 31;
+    unsigned long long *wq = queue[threadIdx.x >> 5];
+    const int64_t w = (int64_t)blockIdx.x * kA1Warps + (threadIdx.x >> 5);
+    const int64_t stride = (int64_t)gridDim.x * kA1Warps * 32 * kA1U;
+    const float hf = 0.5f * (float)side;
+    const double hd = 0.5 * (double)side;
+    const float tol = hf * kEdgeRel;
+    const int p32 = 32 / J, j32 = 32 % J;
+    int64_t base = w * 32 * kA1U;
+    int64_t pair = (base + lane) / J;
+    int j = (int)(base + lane - pair * J);
+    int qn = 0;  // the warp's queue length (the same in every lane)
+    unsigned queued = 0;
+    for (; base < total; base += stride) {
+        int64_t pp = pair;
+        int jj = j;
+#pragma unroll
+        for (int k = 0; k < kA1U; ++k) {
+            bool slow = false;
+            if (base + 32 * k + lane < total) {
+                const float4 A = __ldg(&q1f[pp]);
+                if (A.x > 0.f) {
+                    const float4 B = __ldg(&q2f[pp]);
+                    const float2 cs = __ldg(&t32[jj]);
+                    const float q0 = fmaf(A.x, cs.x, B.x * cs.y);
+                    const float q1 = fmaf(A.y, cs.x, B.y * cs.y);
+                    const float q2 = fmaf(A.z, cs.x, B.z * cs.y);
+                    const float q3 = fmaf(A.w, cs.x, B.w * cs.y);
+                    // the sign with q3 <= 0 makes 1 - q3 = 1 + |q3| either way
+                    const float r = copysignf(__frcp_rn(1.f + fabsf(q3)), -q3);
+                    const float x0 = fmaf(q0 * r, hf, hf), x1 = fmaf(q1 * r, hf, hf), x2 = fmaf(q2 * r, hf, hf);
+                    const float f0 = floorf(x0), f1 = floorf(x1), f2 = floorf(x2);
+                    const float e0 = x0 - f0, e1 = x1 - f1, e2 = x2 - f2;  // exact
+                    const float e = fminf(fminf(fminf(e0, 1.f - e0), fminf(e1, 1.f - e1)), fminf(e2, 1.f - e2));
+                    if (fabsf(q3) <= kQ3Guard || e <= tol) {
+                        slow = true;
+                    } else {
+                        const int i0 = min(max((int)f0, 0), side - 1);
+                        const int i1 = min(max((int)f1, 0), side - 1);
+                        const int i2 = min(max((int)f2, 0), side - 1);
+                        atomicAdd(&acc[(i2 * side + i1) * side + i0], 1);
+                    }
+                } else {
+                    slow = A.x == kFp64Only;
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, slow);
+            if (slow) wq[qn + __popc(m & ((1u << lane) - 1u))] = ((unsigned long long)pp << 16) | (unsigned)jj;
+            qn += __popc(m);
+            jj += j32;
+            pp += p32;
+            if (jj >= J) {
+                jj -= J;
+                ++pp;
+            }
+        }
+        if (qn > kWarpQ - 32 * kA1U) {
+            __syncwarp();
+            alg1_drain(wq, qn, qd, t64, side, hd, acc, lane);
+            queued += qn;
+            qn = 0;
+            __syncwarp();
+        }
+        pair += adv_p;
+        j += adv_j;
+        if (j >= J) {
+            j -= J;
+            ++pair;
+        }
+    }
+    __syncwarp();
+    alg1_drain(wq, qn, qd, t64, side, hd, acc, lane);
+    queued += qn;
+    if (lane == 0 && queued) atomicAdd(&hdr->rechecked, (unsigned long long)queued);
+}
+
+__device__ __forceinline__ unsigned long long a1_key(int count, uint32_t idx) {
+    return ((unsigned long long)(uint32_t)count << 32) | (unsigned long long)(0xffffffffu - idx);
+}
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long x, unsigned long long y) {
+    return x > y ? x : y;
+}
+
+constexpr int kArgThreads = 256;
+
+__global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(const int32_t *__restrict__ acc, int side,
+                                                                  A1Hdr *hdr) {
+    const int64_t cells = (int64_t)side * side * side;
+    const int64_t nvec = cells >> 2;
+    const int4 *v = reinterpret_cast<const int4 *>(acc);
+    unsigned long long best = 0;
+    const int64_t stride = (int64_t)gridDim.x * kArgThreads;
+    int64_t k = (int64_t)blockIdx.x * kArgThreads + threadIdx.x;
+    for (; k + 3 * stride < nvec; k += 4 * stride) {  // four independent 16-byte loads in flight
+        int4 c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = __ldcs(v + k + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t i = (uint32_t)((k + u * stride) << 2);
+            best = umax64(best, a1_key(c[u].x, i));
+            best = umax64(best, a1_key(c[u].y, i + 1));
+            best = umax64(best, a1_key(c[u].z, i + 2));
+            best = umax64(best, a1_key(c[u].w, i + 3));
+        }
+    }
+    for (; k < nvec; k += stride) {
+        const int4 c = __ldcs(v + k);
+        const uint32_t i = (uint32_t)(k << 2);
+        best = umax64(best, a1_key(c.x, i));
+        best = umax64(best, a1_key(c.y, i + 1));
+        best = umax64(best, a1_key(c.z, i + 2));
+        best = umax64(best, a1_key(c.w, i + 3));
+    }
+    for (int64_t r = (nvec << 2) + (int64_t)blockIdx.x * kArgThreads + threadIdx.x; r < cells; r += stride)
+        best = umax64(best, a1_key(acc[r], (uint32_t)r));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, o));
+    __shared__ unsigned long long wbest[kArgThreads / 32];
+    __shared__ bool last;
+    if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kArgThreads / 32; ++w) best = umax64(best, wbest[w]);
+        atomicMax(&hdr->best_key, best);
+        __threadfence();
+        last = atomicAdd(&hdr->blocks_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    // The last block: every block's maximum is in best_key.  Inverse projection
+    // of the winner's centre p* = -1 + (i + 1/2) 2/n (Sec. 4.3.1):
+    // q = (2 p*, |p*|^2 - 1) / (1 + |p*|^2).
+    __threadfence();
+    const unsigned long long key = atomicAdd(&hdr->best_key, 0ull);
+    const uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffull);
+    const int64_t n = side;
+    const int64_t ix = idx % n, iy = (idx / n) % n, iz = idx / (n * n);
+    const double h = ddiv(2.0, (double)side);
+    const double p[3] = {dadd(-1.0, dmul(dadd((double)ix, 0.5), h)), dadd(-1.0, dmul(dadd((double)iy, 0.5), h)),
+                         dadd(-1.0, dmul(dadd((double)iz, 0.5), h))};
+    const double pp = dadd(dadd(dmul(p[0], p[0]), dmul(p[1], p[1])), dmul(p[2], p[2]));
+    const double den = dadd(1.0, pp);
+    double q[4] = {ddiv(dmul(2.0, p[0]), den), ddiv(dmul(2.0, p[1]), den), ddiv(dmul(2.0, p[2]), den),
+                   ddiv(dsub(pp, 1.0), den)};
+    for (int c = 0; c < 4; ++c) {  // sign: w > 0, else the first nonzero component > 0
+        if (q[c] > 0.0) break;
+        if (q[c] < 0.0) {
+            for (int m = 0; m < 4; ++m) q[m] = -q[m];
+            break;
+        }
+    }
+    double R[9];
+    quat_to_R(q, R);
+    rot_vote_alg1_result &res = hdr->res;
+    for (int c = 0; c < 4; ++c) res.q[c] = q[c];
+    for (int c = 0; c < 9; ++c) res.R[c] = R[c];
+    res.best_count = (int32_t)(key >> 32);
+    res.status = hdr->invalid ? ROT_VOTE_EINVAL : ROT_VOTE_OK;
+    res.best_cell = idx;
+    res.samples_cast = (int64_t)hdr->cast;
+    res.rechecked = (int64_t)hdr->rechecked;
+    res.ms_gpu = 0.f;
+    res.pad = 0.f;
+}
+
+constexpr int64_t kA1MaxPairs = (int64_t)1 << 30;
+constexpr int kA1MaxSamples = 65536;
+constexpr int kA1MaxSide = 1024;
+
+bool a1_on_device(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+void Context::alg1_release() {
+    if (a1_mem) {
+        cudaStreamSynchronize(stream);
+        cudaFree(a1_mem);
+        bytes_held -= a1_cap;
+    }
+    a1_mem = nullptr;
+    a1_cap = 0;
+    a1_J = 0;
+    if (a1_hdr_h) cudaFreeHost(a1_hdr_h);
+    a1_hdr_h = nullptr;
+    for (auto &e : a1_ev)
+        if (e) cudaEventDestroy(e);
+    a1_ev[0] = a1_ev[1] = nullptr;
+}
+
+int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *out) {
+    if (!a1_hdr_h && cudaMallocHost(&a1_hdr_h, 256) != cudaSuccess) {
+        cudaGetLastError();
+        a1_hdr_h = nullptr;
+        return fail(ROT_VOTE_ENOMEM, "pinned header allocation failed");
+    }
+    for (auto &ev : a1_ev)
+        if (!ev && cudaEventCreate(&ev) != cudaSuccess) {
+            ev = nullptr;
+            return fail(ROT_VOTE_ECUDA, "creating events");
+        }
+    for (int k = 0; k < np; ++k) {
+        rot_vote_alg1_result &r = out[k];
+        memset(&r, 0, sizeof r);
+        const rot_vote_alg1_problem &P = p[k];
+        const int J = P.samples == 0 ? 180 : P.samples;
+        const int side = P.accum_side == 0 ? 360 : P.accum_side;
+        if (!P.a || !P.b || P.n < 2 || P.n > kA1MaxPairs || J < 1 || J > kA1MaxSamples || side < 2 ||
+            side > kA1MaxSide) {
+            r.status = ROT_VOTE_EINVAL;
+            last_error = "alg1 problem " + std::to_string(k) + ": bad argument";
+            continue;
+        }
+        const bool dev_in = a1_on_device(P.a) && a1_on_device(P.b);
+        const int64_t cells = (int64_t)side * side * side;
+        // layout: header | accumulator | FP32 angle table | FP64 angle table | FP32 basis (2 x 16 B per pair) |
+        //         FP64 basis (64 B per pair) | staged inputs
+        const size_t off_acc = 256;
+        const size_t off_t32 = align_up(off_acc + sizeof(int32_t) * (size_t)cells, 256);
+        const size_t off_t64 = align_up(off_t32 + sizeof(float2) * J, 256);
+        const size_t off_q1f = align_up(off_t64 + sizeof(double2) * J, 256);
+        const size_t off_q2f = align_up(off_q1f + sizeof(float4) * (size_t)P.n, 256);
+        const size_t off_qd = align_up(off_q2f + sizeof(float4) * (size_t)P.n, 256);
+        const size_t off_in = align_up(off_qd + 4 * sizeof(double2) * (size_t)P.n, 256);
+        const size_t in_bytes = dev_in ? 0 : align_up(sizeof(float) * 3 * (size_t)P.n, 256);
+        const size_t need = off_in + 2 * in_bytes;
+        if (need > a1_cap) {
+            cudaStreamSynchronize(stream);
+            if (a1_mem) {
+                cudaFree(a1_mem);
+                bytes_held -= a1_cap;
+            }
+            a1_mem = nullptr;
+            a1_cap = 0;
+            a1_J = 0;
+            if (bytes_held + need > budget) return fail(ROT_VOTE_ENOMEM, "alg1 workspace exceeds the device memory budget");
+            if (cudaMalloc(&a1_mem, need) != cudaSuccess) {
+                cudaGetLastError();
+                a1_mem = nullptr;
+                return fail(ROT_VOTE_ENOMEM, "cudaMalloc of the alg1 workspace failed");
+            }
+            a1_cap = need;
+            bytes_held += need;
+        }
+        unsigned char *base = static_cast<unsigned char *>(a1_mem);
+        A1Hdr *hdr = reinterpret_cast<A1Hdr *>(base);
+        float2 *t32 = reinterpret_cast<float2 *>(base + off_t32);
+        double2 *t64 = reinterpret_cast<double2 *>(base + off_t64);
+        int32_t *acc = reinterpret_cast<int32_t *>(base + off_acc);
+        cudaError_t e = cudaSuccess;
+        if (a1_J != J || a1_toff != off_t32) {
+            // (cos, sin)(alpha_j / 2), alpha_j = -pi + 2 pi j / J: the uniform samples of [-pi, pi) of Alg. 1
+            std::vector<double2> h64(J);
+            std::vector<float2> h32(J);
+            for (int jj = 0; jj < J; ++jj) {
+                const double alpha = -M_PI + (2.0 * M_PI * (double)jj) / (double)J;
+                h64[jj] = make_double2(cos(alpha / 2.0), sin(alpha / 2.0));
+                h32[jj] = make_float2((float)h64[jj].x, (float)h64[jj].y);
+            }
+            e = cudaMemcpyAsync(t64, h64.data(), sizeof(double2) * J, cudaMemcpyHostToDevice, stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(t32, h32.data(), sizeof(float2) * J, cudaMemcpyHostToDevice, stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // the host vectors die here
+            if (e != cudaSuccess) return cuda_fail(e, "uploading the alg1 angle table");
+            a1_J = J;
+            a1_toff = off_t32;
+        }
+        const float *da = P.a, *db = P.b;
+        if (!dev_in) {
+            float *ia = reinterpret_cast<float *>(base + off_in), *ib = reinterpret_cast<float *>(base + off_in + in_bytes);
+            e = cudaMemcpyAsync(ia, P.a, sizeof(float) * 3 * P.n, cudaMemcpyDefault, stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(ib, P.b, sizeof(float) * 3 * P.n, cudaMemcpyDefault, stream);
+            if (e != cudaSuccess) return cuda_fail(e, "copying alg1 inputs");
+            da = ia;
+            db = ib;
+        }
+        // keep_trace >= 2: an event pair around each stage (kinds 5, 6, 7), for rot_vote_stage_times
+        const bool profile = cfg.keep_trace >= 2;
+        if (profile) {
+            prof.clear();
+            while (prof_ev.size() < 6) {
+                cudaEvent_t ev;
+                if (cudaEventCreate(&ev) != cudaSuccess) return fail(ROT_VOTE_ECUDA, "creating events");
+                prof_ev.push_back(ev);
+            }
+        }
+        auto mark = [&](int stage, bool begin) {
+            if (!profile || e != cudaSuccess) return;
+            if (begin) prof.push_back(rot_vote_stage{5 + stage, -1, 0.f});
+            e = cudaEventRecord(prof_ev[2 * stage + (begin ? 0 : 1)], stream);
+        };
+        float4 *q1f = reinterpret_cast<float4 *>(base + off_q1f), *q2f = reinterpret_cast<float4 *>(base + off_q2f);
+        double2 *qd = reinterpret_cast<double2 *>(base + off_qd);
+        if (e == cudaSuccess) e = cudaEventRecord(a1_ev[0], stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(hdr, 0, sizeof(A1Hdr), stream);
+        mark(0, true);
+        if (e == cudaSuccess) {
+            const int64_t want = (std::max<int64_t>(P.n, cells / 4) + kA1Threads - 1) / kA1Threads;
+            const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * 8));
+            alg1_prep_kernel<<<blocks, kA1Threads, 0, stream>>>(da, db, P.n, q1f, q2f, qd, acc, cells, 1, J, hdr);
+            e = cudaGetLastError();
+        }
+        mark(0, false);
+        mark(1, true);
+        if (e == cudaSuccess) {
+            // persistent grid: resident blocks, or fewer when there are fewer samples
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, alg1_vote_kernel, kA1Threads, 0);
+            const int64_t total = P.n * (int64_t)J;
+            const int64_t want = (total + kA1Threads * kA1U - 1) / (kA1Threads * kA1U);
+            const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * std::max(per_sm, 1)));
+            const int64_t stride = (int64_t)blocks * kA1Threads * kA1U;
+            if (e == cudaSuccess) {
+                alg1_vote_kernel<<<blocks, kA1Threads, 0, stream>>>(q1f, q2f, qd, t32, t64, J, side, acc, hdr, total,
+                                                                   stride / J, (int)(stride % J));
+                e = cudaGetLastError();
+            }
+        }
+        mark(1, false);
+        mark(2, true);
+        if (e == cudaSuccess) {
+            const int64_t want = (cells / 4 + kArgThreads - 1) / kArgThreads;
+            const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * 8));
+            alg1_argmax_kernel<<<blocks, kArgThreads, 0, stream>>>(acc, side, hdr);
+            e = cudaGetLastError();
+        }
+        mark(2, false);
+        if (e == cudaSuccess) e = cudaEventRecord(a1_ev[1], stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(a1_hdr_h, hdr, sizeof(A1Hdr), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess && P.accumulator)
+            e = cudaMemcpyAsync(P.accumulator, acc, sizeof(int32_t) * (size_t)cells, cudaMemcpyDefault, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e, "running alg1");
+        const A1Hdr *hh = static_cast<const A1Hdr *>(a1_hdr_h);
+        r = hh->res;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a1_ev[0], a1_ev[1]);
+        r.ms_gpu = ms;
+        for (size_t q = 0; profile && q < prof.size(); ++q)
+            cudaEventElapsedTime(&prof[q].ms, prof_ev[2 * q], prof_ev[2 * q + 1]);
+    }
+    return ROT_VOTE_OK;
+}
+
+}  // namespace rv
+
+extern "C" int rot_vote_alg1(rot_vote_ctx *ctx, const rot_vote_alg1_problem *p, int n_problems,
+                             rot_vote_alg1_result *out) {
+    if (!ctx || !p || !out || n_problems < 1) return ROT_VOTE_EINVAL;
+    return reinterpret_cast<rv::Context *>(ctx)->alg1(p, n_problems, out);
+}

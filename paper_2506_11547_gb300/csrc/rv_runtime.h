@@ -122,6 +122,13 @@ class Context {
     Wave main_wave;
     bool trace_valid = false;
     std::vector<int> trace_sel;
+    // Alg. 1 (rv_alg1.cu): header, angle tables, staged inputs and the accumulator
+    void *a1_mem = nullptr;
+    size_t a1_cap = 0;
+    int a1_J = 0;            // J of the angle tables in a1_mem (0 = none)
+    size_t a1_toff = 0;      // their offset
+    void *a1_hdr_h = nullptr;
+    cudaEvent_t a1_ev[2] = {nullptr, nullptr};
 
     // serving
     std::mutex mu;          // guards everything below and every launch
@@ -156,6 +163,8 @@ class Context {
     int level_trace(int problem, int level, int64_t *idx, int32_t *count, int64_t cap, int64_t *ncells,
                     int64_t *kept_idx, int32_t *nkept);
     int stage_times(rot_vote_stage *out, int cap, int *count);
+    int alg1(const rot_vote_alg1_problem *p, int n, rot_vote_alg1_result *out);
+    void alg1_release();
     int submit(const rot_vote_problem &p, uint64_t *ticket);
     int poll(uint64_t ticket, rot_vote_result *out, int timeout_us);
     void sched_loop();

@@ -65,6 +65,7 @@ void Context::shutdown() {
     for (auto &w : waves) w.release(*this);
     waves.clear();
     main_wave.release(*this);
+    alg1_release();
     for (auto ev : prof_ev) cudaEventDestroy(ev);
     prof_ev.clear();
     for (auto &g : grids)

@@ -43,16 +43,29 @@ class rot_vote_result(C.Structure):
                 ("latency_ms", C.c_float)]
 
 
+class rot_vote_alg1_problem(C.Structure):
+    _fields_ = [("a", C.c_void_p), ("b", C.c_void_p), ("n", C.c_int64), ("samples", C.c_int),
+                ("accum_side", C.c_int), ("accumulator", C.c_void_p)]
+
+
+class rot_vote_alg1_result(C.Structure):
+    _fields_ = [("q", C.c_double * 4), ("R", C.c_double * 9), ("best_count", C.c_int32), ("status", C.c_int32),
+                ("best_cell", C.c_int64), ("samples_cast", C.c_int64), ("rechecked", C.c_int64),
+                ("ms_gpu", C.c_float), ("pad", C.c_float)]
+
+
 class rot_vote_stage(C.Structure):
     _fields_ = [("kind", C.c_int32), ("level", C.c_int32), ("ms", C.c_float)]
 
 
-STAGE_KIND = {0: "pair_prep", 1: "vote", 2: "topk", 3: "children", 4: "fit"}
+STAGE_KIND = {0: "pair_prep", 1: "vote", 2: "topk", 3: "children", 4: "fit", 5: "alg1_zero", 6: "alg1_vote",
+              7: "alg1_argmax"}
 
 _lib = None
 
 EXPORTS = ("rot_vote_create", "rot_vote_solve", "rot_vote_submit", "rot_vote_poll", "rot_vote_level_trace",
-           "rot_vote_stage_times", "rot_vote_destroy", "rot_vote_last_error", "rot_vote_count_cells_static")
+           "rot_vote_stage_times", "rot_vote_destroy", "rot_vote_last_error", "rot_vote_count_cells_static",
+           "rot_vote_alg1")
 
 
 def load(path: str = LIB_PATH):
@@ -83,6 +96,9 @@ def load(path: str = LIB_PATH):
     L.rot_vote_count_cells_static.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, C.c_void_p,
                                               C.c_int32, C.c_void_p, C.c_void_p]
     L.rot_vote_count_cells_static.restype = C.c_int
+    L.rot_vote_alg1.argtypes = [C.c_void_p, C.POINTER(rot_vote_alg1_problem), C.c_int,
+                                C.POINTER(rot_vote_alg1_result)]
+    L.rot_vote_alg1.restype = C.c_int
     _lib = L
     return L
 
@@ -109,6 +125,24 @@ class Result:
                       inliers=r.inliers, best_cell=r.best_cell, best_level=r.best_level, refits=r.refits,
                       tests=r.tests, rechecked=r.rechecked, ambiguous=r.ambiguous, status=r.status,
                       ms_gpu=r.ms_gpu, latency_ms=r.latency_ms)
+
+
+@dataclasses.dataclass
+class Alg1Result:
+    q: np.ndarray
+    R: np.ndarray
+    best_count: int
+    status: int
+    best_cell: int
+    samples_cast: int
+    rechecked: int
+    ms_gpu: float
+
+    @staticmethod
+    def of(r: rot_vote_alg1_result) -> "Alg1Result":
+        return Alg1Result(q=np.array(r.q[:]), R=np.array(r.R[:]).reshape(3, 3), best_count=r.best_count,
+                          status=r.status, best_cell=r.best_cell, samples_cast=r.samples_cast,
+                          rechecked=r.rechecked, ms_gpu=r.ms_gpu)
 
 
 class RotVoteError(RuntimeError):
@@ -207,6 +241,44 @@ class Context:
         self._check(rc)
         self._keep.pop(ticket, None)
         return Result.of(out)
+
+    def alg1(self, problems):
+        """rot_vote_alg1.  problems: list of (a, b[, samples[, accum_side[, accumulator]]]); accumulator: an
+        int32 array or device tensor of accum_side^3 elements that receives the counts.  Returns Alg1Result list."""
+        n = len(problems)
+        arr = (rot_vote_alg1_problem * n)()
+        keep = []
+        for k, pr in enumerate(problems):
+            a, b = pr[0], pr[1]
+            J = int(pr[2]) if len(pr) > 2 else 0
+            side = int(pr[3]) if len(pr) > 3 else 0
+            acc = pr[4] if len(pr) > 4 else None
+            pa, ka = _ptr(a)
+            pb, kb = _ptr(b)
+            if _nrows(b) != _nrows(a):
+                raise ValueError("a and b differ in length")
+            pacc = 0
+            if acc is not None:
+                if hasattr(acc, "data_ptr"):
+                    if str(acc.dtype) != "torch.int32" or not acc.is_contiguous():
+                        raise TypeError("accumulator must be a contiguous int32 tensor")
+                    pacc = acc.data_ptr()
+                else:
+                    if acc.dtype != np.int32 or not acc.flags["C_CONTIGUOUS"]:
+                        raise TypeError("accumulator must be a contiguous int32 array")
+                    pacc = acc.ctypes.data
+                need = (side or 360) ** 3
+                if int(np.prod(acc.shape)) != need:
+                    raise ValueError(f"accumulator must hold {need} elements")
+            arr[k] = rot_vote_alg1_problem(pa, pb, _nrows(a), J, side, pacc or None)
+            keep.append((ka, kb, acc))
+        out = (rot_vote_alg1_result * n)()
+        self._check(self._L.rot_vote_alg1(self._h, arr, n, out))
+        return [Alg1Result.of(out[k]) for k in range(n)]
+
+    def alg1_raw(self, arr, n, out):
+        """Calls rot_vote_alg1 on prepared ctypes arrays (for timing loops)."""
+        return self._check(self._L.rot_vote_alg1(self._h, arr, n, out))
 
     def level_trace(self, problem: int, level: int, cap: int = 1 << 22):
         """(idx[n], count[n], kept_idx[k]) of one level of the last solve (keep_trace=1)."""

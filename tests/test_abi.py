@@ -15,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "rot_vote.h")
 def _declared():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(rot_vote_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(rot_vote_[a-z0-9_]+)\s*\(", txt)))
 
 
 @pytest.fixture(scope="module")
@@ -50,6 +50,9 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(rot_vote_config), sizeof(rot_vote_problem), sizeof(rot_vote_result));
   printf("%zu %zu %zu %zu\n", offsetof(rot_vote_result, status), offsetof(rot_vote_result, ms_gpu),
          offsetof(rot_vote_config, cuda_stream), offsetof(rot_vote_problem, delta));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(rot_vote_alg1_problem), sizeof(rot_vote_alg1_result),
+         offsetof(rot_vote_alg1_problem, accumulator), offsetof(rot_vote_alg1_result, samples_cast),
+         offsetof(rot_vote_alg1_result, ms_gpu));
   return 0;
 }
 '''
@@ -67,6 +70,11 @@ int main(void) {
     assert sizes[4] == rv.rot_vote_result.ms_gpu.offset
     assert sizes[5] == rv.rot_vote_config.cuda_stream.offset
     assert sizes[6] == rv.rot_vote_problem.delta.offset
+    assert sizes[7] == ctypes.sizeof(rv.rot_vote_alg1_problem)
+    assert sizes[8] == ctypes.sizeof(rv.rot_vote_alg1_result)
+    assert sizes[9] == rv.rot_vote_alg1_problem.accumulator.offset
+    assert sizes[10] == rv.rot_vote_alg1_result.samples_cast.offset
+    assert sizes[11] == rv.rot_vote_alg1_result.ms_gpu.offset
 
 
 def test_missing_library_fails_loudly(tmp_path):

@@ -1,0 +1,143 @@
+"""GPU parity of Alg. 1 (Sec. 4.3.2) through the C ABI against the FP64 oracle.
+
+The bar is bit-exact: the library decides every sample's cell as the IEEE
+double evaluation of the formulas does (FP32 first, FP64 again near a cell
+boundary or near q3 = 0), so the whole n^3 accumulator, the winner, its count
+and the number of samples cast equal the oracle's, and so does the rotation
+(the same IEEE operations on the same cell centre).
+"""
+import numpy as np
+import pytest
+
+from paper_2506_11547_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+from paper_2506_11547_gb300 import rot_vote as rv  # noqa: E402
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def edge_pairs():
+    """Pairs that exercise the special cases: axis-aligned a = b (samples on
+    cell boundaries: p_1 = p_2 = 0 exactly), a = -b (w = 0: no circle), and
+    near-antipodal pairs with |a| slightly above 1, whose basis norms are far
+    from 1 (every sample on the FP64 path)."""
+    a, b = [], []
+    for k in range(3):
+        e = np.zeros(3, np.float32)
+        e[k] = 1.0
+        a += [e, e, e]
+        b += [e, -e, np.roll(e, 1)]
+    s = np.float32(1.0 + 4e-6)  # | |a|^2 - 1 | = 8e-6: valid
+    for th in (3e-3, 4e-3, 6e-3):
+        a.append(np.array([s, 0.0, 0.0], np.float32))
+        b.append(np.array([-np.cos(th), np.sin(th), 0.0], np.float32))
+    return np.array(a, np.float32), np.array(b, np.float32)
+
+
+def with_edges(p):
+    ea, eb = edge_pairs()
+    return np.concatenate([p.a, ea]), np.concatenate([p.b, eb])
+
+
+def run_both(a, b, J, side, device=True, acc_on_device=False):
+    import oracle
+    cells = side ** 3
+    acc = torch.zeros(cells, dtype=torch.int32, device="cuda") if acc_on_device else np.zeros(cells, np.int32)
+    with rv.Context() as ctx:
+        r = ctx.alg1([((dev(a), dev(b)) if device else (a, b)) + (J, side, acc)])[0]
+    acc = acc.cpu().numpy() if acc_on_device else acc
+    o = oracle.alg1(a, b, J, side)
+    return r, acc, o
+
+
+def check(r, acc, o):
+    o_acc, o_bi, o_bc, o_q, o_cast = o
+    assert r.status == rv.OK
+    d = np.nonzero(acc != o_acc)[0]
+    assert len(d) == 0, f"{len(d)} accumulator cells differ, e.g. {d[:5]}: {acc[d[:5]]} vs {o_acc[d[:5]]}"
+    assert (r.best_cell, r.best_count, r.samples_cast) == (o_bi, o_bc, o_cast)
+    assert np.array_equal(r.q, o_q), (r.q, o_q)
+    import oracle
+    assert np.allclose(r.R, oracle.quat_to_R(o_q), rtol=0, atol=1e-15)
+
+
+def test_alg1_small_with_edge_cases():
+    p = synth.make_problem(1000, 0.9, 0.01, 0.03, seed=2101)
+    a, b = with_edges(p)
+    r, acc, o = run_both(a, b, 180, 64)
+    check(r, acc, o)
+    # the axis-aligned samples sit on cell boundaries and the near-antipodal
+    # pairs take the FP64 path for every sample
+    assert r.rechecked >= 3 * 180
+    # the a = -b pairs cast nothing
+    assert r.samples_cast == 180 * (len(a) - 3)
+
+
+@pytest.mark.parametrize("J,side,device", [(1, 8, True), (7, 37, False), (256, 90, True), (257, 360, False),
+                                           (540, 128, True), (180, 2, True)])
+def test_alg1_samples_and_sides(J, side, device):
+    p = synth.make_problem(3000, 0.8, 0.01, 0.03, seed=2200 + J + side)
+    a, b = with_edges(p)
+    r, acc, o = run_both(a, b, J, side, device=device, acc_on_device=(J % 2 == 0))
+    check(r, acc, o)
+
+
+def test_alg1_paper_default_n1e5():
+    """The paper's default resolution (1/180 -> a 360^3 accumulator) and J = 180
+    on 1e5 pairs with 99% outliers."""
+    p = synth.make_problem(100000, 0.99, 0.01, 0.03, seed=2301)
+    r, acc, o = run_both(p.a, p.b, 180, 360)
+    check(r, acc, o)
+    # FP64 re-evaluations are the rare boundary cases
+    assert r.rechecked < 0.05 * r.samples_cast
+
+
+def test_alg1_n1e6():
+    """1e6 pairs, 99% outliers (the paper's large-scale claim), full accumulator."""
+    p = synth.make_problem(1000000, 0.99, 0.005, 0.03, seed=2302)
+    r, acc, o = run_both(p.a, p.b, 180, 360)
+    check(r, acc, o)
+
+
+def test_alg1_batch_equals_single_calls():
+    ps = [synth.make_problem(n, 0.9, 0.01, 0.03, seed=2400 + n) for n in (50, 777, 4096)]
+    with rv.Context() as ctx:
+        many = ctx.alg1([(dev(p.a), dev(p.b), 90, 48) for p in ps])
+        one = [ctx.alg1([(dev(p.a), dev(p.b), 90, 48)])[0] for p in ps]
+    for x, y in zip(many, one):
+        assert (x.best_cell, x.best_count, x.samples_cast) == (y.best_cell, y.best_count, y.samples_cast)
+        assert np.array_equal(x.q, y.q)
+
+
+def test_alg1_invalid_inputs_and_arguments():
+    p = synth.make_problem(500, 0.5, 0.01, 0.03, seed=2500)
+    bad = p.a.copy()
+    bad[7] *= 1.01  # not unit
+    nan = p.a.copy()
+    nan[3, 1] = np.nan
+    with rv.Context() as ctx:
+        r = ctx.alg1([(dev(bad), dev(p.b)), (dev(nan), dev(p.b)), (dev(p.a), dev(p.b), 0, 1),
+                      (dev(p.a), dev(p.b), 70000, 16), (dev(p.a[:1]), dev(p.b[:1])), (dev(p.a), dev(p.b), 0, 24)])
+    assert [x.status for x in r[:5]] == [rv.EINVAL] * 5
+    assert r[5].status == rv.OK and r[5].samples_cast == 180 * 500  # J = 0 selects 180
+
+
+def test_alg1_noise_free_winner_is_the_true_rotation_cell():
+    """Noise-free inliers: every circle passes through the true rotation, so
+    the winner's centre is within one cell of it (chart distortion <= 2)."""
+    from tests._util import quat_angle
+    p = synth.make_problem(2000, 0.5, 0.0, 0.03, seed=2600)
+    side = 180
+    with rv.Context() as ctx:
+        r = ctx.alg1([(dev(p.a), dev(p.b), 720, side)])[0]
+    assert r.status == rv.OK
+    # a cell of side 2/n in the chart spans at most 2 * sqrt(3) * (2/n) on S^3 (conformal factor <= 2)
+    assert quat_angle(r.q, p.q_true) <= 2 * (2 * np.sqrt(3) * 2 / side)

@@ -33,6 +33,27 @@ WORKLOAD_DESC = ("N=1e5 float32 unit pairs, 99% uniform outliers, inlier noise s
                  "64^3 coarse grid over the vector-part ball (146,864 cells) + 3 levels of 2x2x2 "
                  "subdivision of the top-16 cells; exact counts, EXCESS ranking, FP64 fit with 8 refits")
 FLOPS_PER_TEST = 20.0  # algorithmic: 10 multiply-adds of the (cell monomials . pair S entries) contraction
+# DRAM bytes (read + write) of one coarse-vote launch of the default workload, from one ncu capture
+# (profiles/vote_simt2_fp32_n1e5_64L3.md, profiles/vote_tc_fp16x2_n1e5_64L3.md).  A figure stands
+# only while the kernel's source file hashes to the value it was captured with.
+NCU_TRAFFIC = {
+    "fp32": (17163776, "k_vote_simt.cu", "d52c7728ebbc0e1fbfd454867409765a97ca859fbf31c2dea502e38392acd269"),
+    "fp16x2": (26736128, "k_vote_tc.cu", "052eb2a7a37a24cb8693af1f163ddbbf00cad21ef292a824f5c62bc2f74d8b3a"),
+}
+
+
+def ncu_traffic(precision: str, workload: str):
+    """Captured DRAM bytes per coarse-vote launch, or None (other workload, or kernel changed)."""
+    import hashlib
+    if workload != WORKLOAD or precision not in NCU_TRAFFIC:
+        return None
+    nbytes, src, digest = NCU_TRAFFIC[precision]
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2506_11547_gb300", "csrc", src)
+    try:
+        ok = hashlib.sha256(open(path, "rb").read()).hexdigest() == digest
+    except OSError:
+        ok = False
+    return nbytes if ok else None
 
 
 def parse():
@@ -514,7 +535,8 @@ def main():
             peak = peaks["bf16_tflops"]
             bound, note = "tensor", f"dense bf16 tensor peak ({peak_src})"
         roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": f"{dom[0]} level {dom[1]}", "kernel_ms": stage_avg[dom],
+                    "traffic": ncu_traffic(args.precision, args.workload), "traffic_unit": "B per launch",
+                    "kernel": f"{dom[0]} level {dom[1]}", "kernel_ms": stage_avg[dom],
                     "flops_per_test": FLOPS_PER_TEST, "tests_per_launch": tests_dom, "peak_source": note,
                     "executed_fma_per_test": 9 if args.precision == "fp32" else None,
                     "share_of_step": stage_avg[dom] / sum(stage_avg.values())}

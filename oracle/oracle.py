@@ -56,11 +56,13 @@ def lib():
         L.rvo_cell_exists.argtypes = [C.c_int, C.c_int64, C.c_int64, C.c_int64]
         L.rvo_cell_exists.restype = C.c_int
         L.rvo_cell_geom.argtypes = [C.c_int, C.c_int64, C.c_int64, C.c_int64, _f64p, C.POINTER(C.c_double)]
+        L.rvo_cell_geom_chart.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, _f64p,
+                                          C.POINTER(C.c_double)]
         L.rvo_tau.argtypes = [C.c_double, C.c_double, C.c_double]
         L.rvo_tau.restype = C.c_double
         L.rvo_level_cells.argtypes = [C.c_int, C.c_void_p]
         L.rvo_level_cells.restype = C.c_int64
-        L.rvo_vote_cells.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, _i64p, C.c_int64,
+        L.rvo_vote_cells.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int, _i64p, C.c_int64,
                                      _i32p, _i32p, _f64p, C.c_int]
         L.rvo_vote_cells.restype = C.c_int
         L.rvo_rank.argtypes = [_i32p, _f64p, _i64p, C.c_int64, C.c_int64, C.c_int, C.c_int64, _i64p, _f64p]
@@ -68,9 +70,9 @@ def lib():
         L.rvo_jacobi4.argtypes = [_f64p, _f64p, _f64p]
         L.rvo_canonical.argtypes = [_f64p]
         L.rvo_solve.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
-                                C.c_int, C.c_int, C.POINTER(_Result), C.POINTER(_Trace)]
+                                C.c_int, C.c_int, C.c_int, C.POINTER(_Result), C.POINTER(_Trace)]
         L.rvo_solve.restype = C.c_int
-        L.rvo_fit_cell.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int64, C.c_int,
+        L.rvo_fit_cell.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int, C.c_int64, C.c_int,
                                    C.POINTER(_Result)]
         L.rvo_fit_cell.restype = C.c_int
         L.rvo_alg1_basis.argtypes = [_f32p, _f32p, _f64p, _f64p]
@@ -119,11 +121,11 @@ def cell_exists(n, ix, iy, iz) -> bool:
     return bool(lib().rvo_cell_exists(int(n), int(ix), int(iy), int(iz)))
 
 
-def cell_geom(n, ix, iy, iz):
-    """(q_cell[4], chord) of cell (ix, iy, iz) of the n^3 grid."""
+def cell_geom(n, ix, iy, iz, chart: int = 0):
+    """(q_cell[4], chord) of cell (ix, iy, iz) of the n^3 grid; chart 0 orthographic, 1 stereographic."""
     q = np.zeros(4)
     ch = C.c_double()
-    lib().rvo_cell_geom(int(n), int(ix), int(iy), int(iz), q, C.byref(ch))
+    lib().rvo_cell_geom_chart(int(chart), int(n), int(ix), int(iy), int(iz), q, C.byref(ch))
     return q, ch.value
 
 
@@ -152,15 +154,15 @@ def _f32_pairs(a, b):
     return a, b
 
 
-def vote_cells(a, b, delta: float, n_side: int, cells, nthreads: int = 1):
+def vote_cells(a, b, delta: float, n_side: int, cells, nthreads: int = 1, chart: int = 0):
     """(count, ambiguous, tau) for each linear cell index in `cells`."""
     a, b = _f32_pairs(a, b)
     cells = np.ascontiguousarray(cells, dtype=np.int64)
     cnt = np.zeros(len(cells), dtype=np.int32)
     amb = np.zeros(len(cells), dtype=np.int32)
     tau_ = np.zeros(len(cells), dtype=np.float64)
-    rc = lib().rvo_vote_cells(a.reshape(-1), b.reshape(-1), a.shape[0], float(delta), int(n_side), cells,
-                              len(cells), cnt, amb, tau_, int(nthreads))
+    rc = lib().rvo_vote_cells(a.reshape(-1), b.reshape(-1), a.shape[0], float(delta), int(n_side), int(chart),
+                              cells, len(cells), cnt, amb, tau_, int(nthreads))
     assert rc == 0
     return cnt, amb, tau_
 
@@ -205,8 +207,8 @@ class OracleResult:
 
 
 def solve(a, b, delta: float, grid_n: int, levels: int = 0, top_k: int = 16, rank_mode: int = 0,
-          refit_iters: int = 8, nthreads: int = 1, trace: bool = True) -> OracleResult:
-    """The full path: vote on each level, rank, subdivide, fit."""
+          refit_iters: int = 8, nthreads: int = 1, trace: bool = True, chart: int = 0) -> OracleResult:
+    """The full path: vote on each level, rank, subdivide, fit (chart 0 orthographic, 1 stereographic)."""
     a, b = _f32_pairs(a, b)
     L = lib()
     res = _Result()
@@ -225,7 +227,7 @@ def solve(a, b, delta: float, grid_n: int, levels: int = 0, top_k: int = 16, ran
         tr_p = C.byref(tr)
         keep = [tr, arrs]
     L.rvo_solve(a.reshape(-1), b.reshape(-1), a.shape[0], float(delta), int(grid_n), int(levels), int(top_k),
-                int(rank_mode), int(refit_iters), int(nthreads), C.byref(res), tr_p)
+                int(rank_mode), int(refit_iters), int(chart), int(nthreads), C.byref(res), tr_p)
     per_level = []
     if trace:
         arrs = keep[1]
@@ -244,11 +246,11 @@ def solve(a, b, delta: float, grid_n: int, levels: int = 0, top_k: int = 16, ran
                         ambiguous=res.ambiguous, status=res.status, refits=res.refits, levels=per_level)
 
 
-def fit_cell(a, b, delta: float, n_side: int, idx: int, refit_iters: int = 8) -> OracleResult:
+def fit_cell(a, b, delta: float, n_side: int, idx: int, refit_iters: int = 8, chart: int = 0) -> OracleResult:
     """The fit alone (step 8), from winning cell `idx` of the n_side grid."""
     a, b = _f32_pairs(a, b)
     res = _Result()
-    lib().rvo_fit_cell(a.reshape(-1), b.reshape(-1), a.shape[0], float(delta), int(n_side), int(idx),
+    lib().rvo_fit_cell(a.reshape(-1), b.reshape(-1), a.shape[0], float(delta), int(n_side), int(chart), int(idx),
                        int(refit_iters), C.byref(res))
     return OracleResult(q=np.array(res.q[:]), R=np.array(res.R[:]).reshape(3, 3), best_count=res.best_count,
                         inliers=res.inliers, best_cell=res.best_cell, tests=res.tests, ambiguous=res.ambiguous,

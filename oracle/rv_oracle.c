@@ -200,6 +200,42 @@ void rvo_cell_geom(int n, int64_t ix, int64_t iy, int64_t iz, double q[4], doubl
     *chord = sqrt(dv * dv + dw * dw);
 }
 
+/* The stereographic chart of Sec. 4.3.1: the cell's box in p-space maps onto
+ * S^3 by the inverse projection P'(p) = (2 p, |p|^2 - 1) / (1 + |p|^2), read
+ * as (q0, q1, q2, q3); the closed unit ball is the half q3 <= 0.  Centre
+ * q = P'(c).  Covering chord: for p in the box,
+ *   |P'(p) - P'(c)| = 2 |p - c| / sqrt((1 + |p|^2)(1 + |c|^2))
+ * (the chordal distance of the inverse stereographic projection), and
+ * |p - c| <= (sqrt 3 / 2) h, |p|^2 >= min over the box, so
+ *   chord = sqrt(3) h / sqrt((1 + min |p|^2)(1 + |c|^2)). */
+void rvo_cell_geom_stereo(int n, int64_t ix, int64_t iy, int64_t iz, double q[4], double *chord) {
+    const double h = 2.0 / (double)n;
+    const int64_t id[3] = {ix, iy, iz};
+    double c[3], c2 = 0.0, minv2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double lo = -1.0 + (double)id[k] * h, hi = lo + h;
+        c[k] = -1.0 + ((double)id[k] + 0.5) * h;
+        c2 += c[k] * c[k];
+        const double d = dist0(lo, hi);
+        minv2 += d * d;
+    }
+    const double den = 1.0 + c2;
+    q[0] = 2.0 * c[0] / den;
+    q[1] = 2.0 * c[1] / den;
+    q[2] = 2.0 * c[2] / den;
+    q[3] = (c2 - 1.0) / den;
+    *chord = sqrt(3.0) * h / sqrt((1.0 + minv2) * den);
+}
+
+/* Cell geometry in the chosen chart: 0 orthographic (the vector part of q,
+ * w >= 0), 1 stereographic (Sec. 4.3.1). */
+void rvo_cell_geom_chart(int chart, int n, int64_t ix, int64_t iy, int64_t iz, double q[4], double *chord) {
+    if (chart == 1)
+        rvo_cell_geom_stereo(n, ix, iy, iz, q, chord);
+    else
+        rvo_cell_geom(n, ix, iy, iz, q, chord);
+}
+
 /* tau = sin^2(delta + r), r = 2 asin(x), x = min(1, chord / 2); tau = 1 once
  * delta + r >= pi/2.  Written with cos r = 1 - 2x^2, sin r = 2x sqrt(1-x^2)
  * (an identity), so that it needs only sqrt. */
@@ -241,6 +277,7 @@ typedef struct {
     const double *S;  /* [n_pairs][16] */
     int64_t n_pairs;
     int n_side;
+    int chart;
     const int64_t *cells;
     int64_t c0, c1;
     double sin_d, cos_d;
@@ -254,7 +291,7 @@ static void *vote_worker(void *arg) {
         int64_t ix, iy, iz;
         unpack_idx(j->n_side, j->cells[c], &ix, &iy, &iz);
         double q[4], chord;
-        rvo_cell_geom(j->n_side, ix, iy, iz, q, &chord);
+        rvo_cell_geom_chart(j->chart, j->n_side, ix, iy, iz, q, &chord);
         const double tau = rvo_tau(j->sin_d, j->cos_d, chord);
         int32_t cnt = 0, amb = 0;
         for (int64_t i = 0; i < j->n_pairs; ++i) {
@@ -269,16 +306,16 @@ static void *vote_worker(void *arg) {
     return NULL;
 }
 
-static void vote_cells_S(const double *S, int64_t n, int n_side, const int64_t *cells, int64_t ncells,
-                         double sin_d, double cos_d, int32_t *count, int32_t *amb, double *tau_out,
-                         int nthreads) {
+static void vote_cells_S(const double *S, int64_t n, int n_side, int chart, const int64_t *cells,
+                         int64_t ncells, double sin_d, double cos_d, int32_t *count, int32_t *amb,
+                         double *tau_out, int nthreads) {
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     if ((int64_t)nthreads > ncells) nthreads = ncells > 0 ? (int)ncells : 1;
     vote_job jobs[256];
     pthread_t th[256];
     for (int t = 0; t < nthreads; ++t) {
-        jobs[t] = (vote_job){S, n, n_side, cells, ncells * t / nthreads, ncells * (t + 1) / nthreads,
+        jobs[t] = (vote_job){S, n, n_side, chart, cells, ncells * t / nthreads, ncells * (t + 1) / nthreads,
                              sin_d, cos_d, count, amb, tau_out};
     }
     if (nthreads == 1) {
@@ -297,13 +334,13 @@ static double *all_pair_S(const float *a, const float *b, int64_t n) {
 }
 
 /* Counts (and ambiguous counts, and tau) for an arbitrary list of cells of
- * the n_side grid. */
-int rvo_vote_cells(const float *a, const float *b, int64_t n, double delta, int n_side,
+ * the n_side grid in the given chart. */
+int rvo_vote_cells(const float *a, const float *b, int64_t n, double delta, int n_side, int chart,
                    const int64_t *cells, int64_t ncells, int32_t *count, int32_t *amb, double *tau_out,
                    int nthreads) {
     double *S = all_pair_S(a, b, n);
     if (!S) return RVO_EINVAL;
-    vote_cells_S(S, n, n_side, cells, ncells, sin(delta), cos(delta), count, amb, tau_out, nthreads);
+    vote_cells_S(S, n, n_side, chart, cells, ncells, sin(delta), cos(delta), count, amb, tau_out, nthreads);
     free(S);
     return RVO_OK;
 }
@@ -460,11 +497,11 @@ typedef struct {
     int64_t *nkept;    /* [levels+1] */
 } rvo_trace;
 
-static int fit_from_cell(const double *S, int64_t n, double sd, double cd, int n_side, int64_t idx,
+static int fit_from_cell(const double *S, int64_t n, double sd, double cd, int n_side, int chart, int64_t idx,
                          int refit_iters, rvo_result *res);
 
 int rvo_solve(const float *a, const float *b, int64_t n, double delta, int grid_n, int levels, int top_k,
-              int rank_mode, int refit_iters, int nthreads, rvo_result *res, rvo_trace *tr) {
+              int rank_mode, int refit_iters, int chart, int nthreads, rvo_result *res, rvo_trace *tr) {
     memset(res, 0, sizeof *res);
     if (n < 2 || grid_n < 1 || levels < 0 || top_k < 1 || !(delta > 0.0)) {
         res->status = RVO_EINVAL;
@@ -486,7 +523,7 @@ int rvo_solve(const float *a, const float *b, int64_t n, double delta, int grid_
         int32_t *count = (int32_t *)malloc(sizeof(int32_t) * (size_t)nc);
         int32_t *amb = (int32_t *)malloc(sizeof(int32_t) * (size_t)nc);
         double *tau = (double *)malloc(sizeof(double) * (size_t)nc);
-        vote_cells_S(S, n, n_side, cells, nc, sd, cd, count, amb, tau, nthreads);
+        vote_cells_S(S, n, n_side, chart, cells, nc, sd, cd, count, amb, tau, nthreads);
         res->tests += nc * n;
         for (int64_t c = 0; c < nc; ++c) res->ambiguous += amb[c];
 
@@ -542,7 +579,7 @@ int rvo_solve(const float *a, const float *b, int64_t n, double delta, int grid_
     (void)win_tau;
     res->best_cell = win_idx;
     res->best_count = win_count;
-    const int status = fit_from_cell(S, n, sd, cd, (int)win_n, win_idx, refit_iters, res);
+    const int status = fit_from_cell(S, n, sd, cd, (int)win_n, chart, win_idx, refit_iters, res);
     free(S);
     return status;
 }
@@ -551,12 +588,12 @@ int rvo_solve(const float *a, const float *b, int64_t n, double delta, int grid_
  * I_0 = voters of the cell, q_0 = smallest eigenvector of sum_{I_0} S_i; then
  * I_t = {i : q_{t-1}^T S_i q_{t-1} <= sin^2(delta)}, stopping when |I_t| < 2 or
  * I_t = I_{t-1}; the cell centre is returned if the first fit is degenerate. */
-static int fit_from_cell(const double *S, int64_t n, double sd, double cd, int n_side, int64_t idx,
+static int fit_from_cell(const double *S, int64_t n, double sd, double cd, int n_side, int chart, int64_t idx,
                          int refit_iters, rvo_result *res) {
     int64_t ix, iy, iz;
     unpack_idx(n_side, idx, &ix, &iy, &iz);
     double qc[4], chord;
-    rvo_cell_geom(n_side, ix, iy, iz, qc, &chord);
+    rvo_cell_geom_chart(chart, n_side, ix, iy, iz, qc, &chord);
     const double win_tau = rvo_tau(sd, cd, chord);
 
     unsigned char *in0 = (unsigned char *)calloc((size_t)n, 1);
@@ -603,13 +640,13 @@ static int fit_from_cell(const double *S, int64_t n, double sd, double cd, int n
 }
 
 /* The fit alone, from a given winning cell. */
-int rvo_fit_cell(const float *a, const float *b, int64_t n, double delta, int n_side, int64_t idx, int refit_iters,
-                 rvo_result *res) {
+int rvo_fit_cell(const float *a, const float *b, int64_t n, double delta, int n_side, int chart, int64_t idx,
+                 int refit_iters, rvo_result *res) {
     memset(res, 0, sizeof *res);
     double *S = all_pair_S(a, b, n);
     if (!S) return RVO_EINVAL;
     res->best_cell = idx;
-    const int status = fit_from_cell(S, n, sin(delta), cos(delta), n_side, idx, refit_iters, res);
+    const int status = fit_from_cell(S, n, sin(delta), cos(delta), n_side, chart, idx, refit_iters, res);
     free(S);
     return status;
 }

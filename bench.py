@@ -573,6 +573,25 @@ def main():
                            "same_result_as_fp32": bool(rr.best_cell == res0.best_cell and
                                                        list(rr.q) == list(res0.q))}
             cx.close()
+        # the same workload in the stereographic chart (Sec. 4.3.1), FP32 form
+        cx = rv.Context(grid_n=grid_n, levels=levels, precision="fp32", chart="stereographic",
+                        cuda_stream=stream.cuda_stream)
+        for _ in range(3):
+            cx.solve_raw(arr, 1, out)
+        ts = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            cx.solve_raw(arr, 1, out)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(s0.elapsed_time(s1))
+        rr = rv.Result.of(out[0])
+        extra["stereographic_fp32"] = {"value": rr.tests / (sum(ts) / len(ts) / 1e3), "unit": UNIT,
+                                       "ms_per_step": sum(ts) / len(ts), "tests_per_step": rr.tests,
+                                       "angle_to_truth_rad": _angle(rr.q, p.q_true)}
+        cx.close()
 
     batched = serving = alg1 = None
     if not args.no_extra and ws == 1:

@@ -116,6 +116,12 @@ typedef struct {
                                  (epilogue warpgroups) + 10 (16-column TMEM chunks) + 100 (128-pair
                                  MMA units), i.e. 2, 4, 12, 14, 102, 104, 112, 114.  A code that
                                  does not exist for the precision fails the solve with EINVAL. */
+    int chart;                /* chart of the cell grid over [-1,1]^3: 0 = orthographic (default), the
+                                 quaternion's vector part with w >= 0; 1 = stereographic (Sec. 4.3.1),
+                                 q = P'(p) = (2p, |p|^2 - 1) / (1 + |p|^2) read as (q0, q1, q2, q3), so
+                                 the unit ball is the half q3 <= 0.  In the stereographic chart every
+                                 cell's covering radius is within a factor ~2 of every other's on a
+                                 level; rot_vote_level_trace indices refer to the chosen chart */
 } rot_vote_config;
 
 /* One problem.  a, b: [n, 3] row-major float32 unit vectors (host or device).

@@ -120,7 +120,7 @@ __device__ void block_children(const LevelRef &L, const LevelRef &C, const Cand 
             if (k < w) base += warp_tot[k];
             tot += warp_tot[k];
         }
-        if (ex) write_cell(C.cells, base + __popc(ball & ((1u << lane) - 1u)), 2 * L.n_side, cx, cy, cz);
+        if (ex) write_cell(C.cells, base + __popc(ball & ((1u << lane) - 1u)), 2 * L.n_side, C.chart, cx, cy, cz);
         __syncthreads();
         if (threadIdx.x == 0) s_base += tot;
         __syncthreads();

@@ -14,7 +14,8 @@ namespace rv {
 // linear index.  rows[] lists the non-empty (iy, iz) rows: {first position,
 // ix_lo, ix_hi, iz*n + iy}; within a row the member ix form one interval.
 // ---------------------------------------------------------------------------
-__global__ void build_level0_kernel(const int4 *__restrict__ rows, int nrows, int n, int64_t ncells, CellSoA out) {
+__global__ void build_level0_kernel(const int4 *__restrict__ rows, int nrows, int n, int chart, int64_t ncells,
+                                    CellSoA out) {
     const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= ncells) return;
     int lo = 0, hi = nrows - 1;  // last row with first <= pos
@@ -26,15 +27,15 @@ __global__ void build_level0_kernel(const int4 *__restrict__ rows, int nrows, in
     const int4 r = rows[lo];
     const int64_t ix = r.y + (pos - r.x);
     const int64_t iy = r.w % n, iz = r.w / n;
-    write_cell(out, pos, n, ix, iy, iz);
+    write_cell(out, pos, n, chart, ix, iy, iz);
 }
 
-cudaError_t launch_build_level0(const int4 *rows, int nrows, int n, int64_t ncells, CellSoA out,
-                                     cudaStream_t s) {
+cudaError_t launch_build_level0(const int4 *rows, int nrows, int n, int chart, int64_t ncells, CellSoA out,
+                                cudaStream_t s) {
     if (ncells <= 0) return cudaSuccess;
     const int bs = 256;
     const int64_t nb = (ncells + bs - 1) / bs;
-    build_level0_kernel<<<(unsigned)nb, bs, 0, s>>>(rows, nrows, n, ncells, out);
+    build_level0_kernel<<<(unsigned)nb, bs, 0, s>>>(rows, nrows, n, chart, ncells, out);
     return cudaGetLastError();
 }
 

@@ -95,7 +95,7 @@ int Context::grid_table(int n, const GridTable **out) {
     cudaError_t e = cudaMemcpyAsync(rows_d, rows.data(), sizeof(int4) * rows.size(), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g.ncells_dev, &nc32, sizeof(int32_t), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = launch_build_level0(rows_d, (int)rows.size(), n, total, g.cells, stream);
+    if (e == cudaSuccess) e = launch_build_level0(rows_d, (int)rows.size(), n, cfg.chart, total, g.cells, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
         cudaFree(g.mem);
@@ -384,6 +384,8 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     for (int k = 0; k < P; ++k) {
         for (int lev = 0; lev <= levs[k]; ++lev) {
             LevelRef &L = pl.lref_h[(size_t)k * S + lev];
+            L.chart = cfg.chart;
+            L.pad = 0;
             if (lev == 0) {
                 L.cells = gt[k]->cells;
                 L.ncells = gt[k]->ncells_dev;
@@ -960,7 +962,7 @@ int rot_vote_create(const rot_vote_config *cfg_in, rot_vote_ctx **out) {
     if (c.autotune == 0) c.autotune = 1;
     if (c.grid_n < 2 || c.grid_n > 256 || (c.grid_n & (c.grid_n - 1)) || c.levels < 0 || c.levels > kMaxLevels ||
         c.top_k < 1 || c.top_k > kMaxTopK || c.precision < 0 || c.precision > ROT_PREC_BF16X2 || c.rank_mode < 0 ||
-        c.rank_mode > 1 || c.max_inflight < 1 || !(c.recheck_band >= 0.f))
+        c.rank_mode > 1 || c.max_inflight < 1 || !(c.recheck_band >= 0.f) || c.chart < 0 || c.chart > 1)
         return ROT_VOTE_EINVAL;
     Context *ctx = new (std::nothrow) Context();
     if (!ctx) return ROT_VOTE_ENOMEM;

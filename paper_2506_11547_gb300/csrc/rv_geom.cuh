@@ -80,7 +80,8 @@ __device__ __forceinline__ bool cell_exists(int n, int64_t ix, int64_t iy, int64
 //   |sqrt(1-|p|^2) - sqrt(1-|c'|^2)| <= min(sqrt(D), D / w),
 //   D = max_p | |p|^2 - |c'|^2 |   (|p|^2 clamped to 1)                      = dw
 // and chord = sqrt(dv^2 + dw^2).
-__device__ __forceinline__ void cell_geom(int n, int64_t ix, int64_t iy, int64_t iz, double q[4], double *chord) {
+__device__ __forceinline__ void cell_geom_ortho(int n, int64_t ix, int64_t iy, int64_t iz, double q[4],
+                                                double *chord) {
     const double h = ddiv(2.0, (double)n);
     const int64_t id[3] = {ix, iy, iz};
     double c[3];
@@ -127,6 +128,44 @@ __device__ __forceinline__ void cell_geom(int n, int64_t ix, int64_t iy, int64_t
     *chord = dsqrt(dadd(dmul(dv, dv), dmul(dw, dw)));
 }
 
+// Stereographic chart (Sec. 4.3.1): the box maps onto S^3 by the inverse
+// projection P'(p) = (2 p, |p|^2 - 1) / (1 + |p|^2), read as (q0, q1, q2, q3)
+// (the unit ball is the half q3 <= 0).  Centre q = P'(c).  For p in the box
+//   |P'(p) - P'(c)| = 2 |p - c| / sqrt((1 + |p|^2)(1 + |c|^2))
+//                  <= sqrt(3) h / sqrt((1 + min_box |p|^2)(1 + |c|^2)) = chord.
+__device__ __forceinline__ void cell_geom_stereo(int n, int64_t ix, int64_t iy, int64_t iz, double q[4],
+                                                 double *chord) {
+    const double h = ddiv(2.0, (double)n);
+    const int64_t id[3] = {ix, iy, iz};
+    double c[3];
+    double c2 = 0.0, minv2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double lo = dadd(-1.0, dmul((double)id[k], h));
+        const double hi = dadd(lo, h);
+        c[k] = dadd(-1.0, dmul(dadd((double)id[k], 0.5), h));
+        c2 = dadd(c2, dmul(c[k], c[k]));
+        const double d = dist0(lo, hi);
+        minv2 = dadd(minv2, dmul(d, d));
+    }
+    const double den = dadd(1.0, c2);
+    q[0] = ddiv(dmul(2.0, c[0]), den);
+    q[1] = ddiv(dmul(2.0, c[1]), den);
+    q[2] = ddiv(dmul(2.0, c[2]), den);
+    q[3] = ddiv(dsub(c2, 1.0), den);
+    *chord = ddiv(dmul(dsqrt(3.0), h), dsqrt(dmul(dadd(1.0, minv2), den)));
+}
+
+// Cell geometry in the context's chart (rot_vote_config.chart): 0 orthographic
+// (vector part of q, w >= 0), 1 stereographic.
+__device__ __forceinline__ void cell_geom(int chart, int n, int64_t ix, int64_t iy, int64_t iz, double q[4],
+                                          double *chord) {
+    if (chart == 1)
+        cell_geom_stereo(n, ix, iy, iz, q, chord);
+    else
+        cell_geom_ortho(n, ix, iy, iz, q, chord);
+}
+
 // Rotation matrix of a unit quaternion (App. A), row-major.
 __device__ __forceinline__ void quat_to_R(const double q[4], double R[9]) {
     const double q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
@@ -158,10 +197,10 @@ __device__ __forceinline__ void monomials(const double q[4], double m[10]) {
 
 // Writes one cell record (FP64 geometry, f32 monomials and rotation).
 template <class CellSoAT>
-__device__ __forceinline__ void write_cell(const CellSoAT &t, int64_t pos, int n, int64_t ix, int64_t iy,
+__device__ __forceinline__ void write_cell(const CellSoAT &t, int64_t pos, int n, int chart, int64_t ix, int64_t iy,
                                            int64_t iz) {
     double q[4], chord;
-    cell_geom(n, ix, iy, iz, q, &chord);
+    cell_geom(chart, n, ix, iy, iz, q, &chord);
     t.q[pos] = make_double4_32a(q[0], q[1], q[2], q[3]);
     t.chord[pos] = chord;
     t.trig[pos] = cell_trig(chord);

@@ -41,6 +41,8 @@ struct LevelRef {
     int32_t *counts;        // [cap] vote counts (zeroed before the vote)
     int32_t cap;            // capacity of the table
     int32_t n_side;         // grid side at this level
+    int32_t chart;          // 0 orthographic, 1 stereographic (Sec. 4.3.1)
+    int32_t pad;
 };
 
 // One problem of a solve.
@@ -100,7 +102,7 @@ struct PairPool {
 // ---- launchers (each returns cudaGetLastError() of its launch) ----
 
 // Coarse table of an n^3 grid from its non-empty rows {first table position, ix_lo, ix_hi, iz*n + iy}.
-cudaError_t launch_build_level0(const int4 *rows, int nrows, int n, int64_t ncells, CellSoA out, cudaStream_t s);
+cudaError_t launch_build_level0(const int4 *rows, int nrows, int n, int chart, int64_t ncells, CellSoA out, cudaStream_t s);
 
 // Pair step over a list of {problem, pair tile}: validates inputs and fills the pair pool.
 cudaError_t launch_pair_prep(const ProbRef *probs, const int2 *tiles, int ntiles, PairPool pool, int tc_prec,

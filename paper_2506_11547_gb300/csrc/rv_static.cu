@@ -99,6 +99,7 @@ __global__ void static_setup_kernel(StaticArgs A) {
             L.counts = A.counts;
             L.cap = A.ncells;
             L.n_side = A.grid_n;
+            L.chart = 0;
             *reinterpret_cast<LevelRef *>(base + kOffLevel) = L;
             ProbStats S;
             S.tests = 0;
@@ -127,7 +128,7 @@ __global__ void static_setup_kernel(StaticArgs A) {
     const int64_t n = A.grid_n, idx = A.cells[pos];
     const int64_t ix = idx % n, iy = (idx / n) % n, iz = idx / (n * n);
     if (idx >= 0 && idx < n * n * n && cell_exists(A.grid_n, ix, iy, iz)) {
-        write_cell(cells, pos, A.grid_n, ix, iy, iz);
+        write_cell(cells, pos, A.grid_n, 0, ix, iy, iz);
     } else {  // reported as EINVAL (counts then unspecified); the slot gets a placeholder record
         atomicOr(&flags[1], 1);
         cells.q[pos] = make_double4_32a(1.0, 0.0, 0.0, 0.0);

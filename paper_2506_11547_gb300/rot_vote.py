@@ -22,13 +22,14 @@ OK, PENDING, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEDOUT, EDEGENERATE, ENOTFOUND, E
 STATIC_SCRATCH_BYTES, STATIC_MAX_PAIRS, STATIC_MAX_CELLS = 4 << 20, 32768, 8192
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2, "fp16x2": 3, "bf16x2": 4}
 RANK = {"excess": 0, "raw": 1}
+CHART = {"orthographic": 0, "stereographic": 1}
 
 
 class rot_vote_config(C.Structure):
     _fields_ = [("grid_n", C.c_int), ("levels", C.c_int), ("top_k", C.c_int), ("precision", C.c_int),
                 ("recheck_band", C.c_float), ("rank_mode", C.c_int), ("refit_iters", C.c_int),
                 ("device_mem_budget", C.c_size_t), ("max_inflight", C.c_int), ("cuda_stream", C.c_void_p),
-                ("use_graphs", C.c_int), ("keep_trace", C.c_int), ("autotune", C.c_int)]
+                ("use_graphs", C.c_int), ("keep_trace", C.c_int), ("autotune", C.c_int), ("chart", C.c_int)]
 
 
 class rot_vote_problem(C.Structure):
@@ -182,7 +183,7 @@ class Context:
 
     def __init__(self, grid_n=0, levels=0, top_k=0, precision="fp32", recheck_band=0.0, rank_mode="excess",
                  refit_iters=0, device_mem_budget=0, max_inflight=0, cuda_stream=None, use_graphs=0,
-                 keep_trace=0, autotune=0):
+                 keep_trace=0, autotune=0, chart="orthographic"):
         L = load()
         self._L = L
         cfg = rot_vote_config(int(grid_n), int(levels), int(top_k),
@@ -190,7 +191,7 @@ class Context:
                               float(recheck_band), RANK[rank_mode] if isinstance(rank_mode, str) else int(rank_mode),
                               int(refit_iters), int(device_mem_budget), int(max_inflight),
                               C.c_void_p(cuda_stream) if cuda_stream else None, int(use_graphs), int(keep_trace),
-                              int(autotune))
+                              int(autotune), CHART[chart] if isinstance(chart, str) else int(chart))
         h = C.c_void_p()
         rc = L.rot_vote_create(C.byref(cfg), C.byref(h))
         if rc != OK:

@@ -50,6 +50,7 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(rot_vote_config), sizeof(rot_vote_problem), sizeof(rot_vote_result));
   printf("%zu %zu %zu %zu\n", offsetof(rot_vote_result, status), offsetof(rot_vote_result, ms_gpu),
          offsetof(rot_vote_config, cuda_stream), offsetof(rot_vote_problem, delta));
+  printf("%zu\n", offsetof(rot_vote_config, chart));
   printf("%zu %zu %zu %zu %zu\n", sizeof(rot_vote_alg1_problem), sizeof(rot_vote_alg1_result),
          offsetof(rot_vote_alg1_problem, accumulator), offsetof(rot_vote_alg1_result, samples_cast),
          offsetof(rot_vote_alg1_result, ms_gpu));
@@ -70,11 +71,12 @@ int main(void) {
     assert sizes[4] == rv.rot_vote_result.ms_gpu.offset
     assert sizes[5] == rv.rot_vote_config.cuda_stream.offset
     assert sizes[6] == rv.rot_vote_problem.delta.offset
-    assert sizes[7] == ctypes.sizeof(rv.rot_vote_alg1_problem)
-    assert sizes[8] == ctypes.sizeof(rv.rot_vote_alg1_result)
-    assert sizes[9] == rv.rot_vote_alg1_problem.accumulator.offset
-    assert sizes[10] == rv.rot_vote_alg1_result.samples_cast.offset
-    assert sizes[11] == rv.rot_vote_alg1_result.ms_gpu.offset
+    assert sizes[7] == rv.rot_vote_config.chart.offset
+    assert sizes[8] == ctypes.sizeof(rv.rot_vote_alg1_problem)
+    assert sizes[9] == ctypes.sizeof(rv.rot_vote_alg1_result)
+    assert sizes[10] == rv.rot_vote_alg1_problem.accumulator.offset
+    assert sizes[11] == rv.rot_vote_alg1_result.samples_cast.offset
+    assert sizes[12] == rv.rot_vote_alg1_result.ms_gpu.offset
 
 
 def test_missing_library_fails_loudly(tmp_path):

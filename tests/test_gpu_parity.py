@@ -48,15 +48,16 @@ def check_kept(gpu_kept, lev, n_pairs):
     assert np.allclose(np.sort(ws), np.sort(gs), atol=1e-9) and np.max(np.abs(ws - gs)) < 1e-9 + 2 * lev["amb"].max()
 
 
-def run_both(p, grid_n, levels, precision="fp32", top_k=16, rank_mode="excess", refit=8, device=True, shape=0):
+def run_both(p, grid_n, levels, precision="fp32", top_k=16, rank_mode="excess", refit=8, device=True, shape=0,
+             chart=0):
     import oracle
     a, b = (dev(p.a), dev(p.b)) if device else (p.a, p.b)
     with rv.Context(grid_n=grid_n, levels=levels, top_k=top_k, precision=precision, rank_mode=rank_mode,
-                    refit_iters=refit if refit else -1, keep_trace=1, autotune=shape) as ctx:
+                    refit_iters=refit if refit else -1, keep_trace=1, autotune=shape, chart=chart) as ctx:
         r = ctx.solve([(a, b, p.delta)])[0]
         tr = [ctx.level_trace(0, lev) for lev in range(levels + 1)]
     o = oracle.solve(p.a, p.b, f32(p.delta), grid_n=grid_n, levels=levels, top_k=top_k,
-                     rank_mode=rv.RANK[rank_mode], refit_iters=refit, nthreads=NTHREADS)
+                     rank_mode=rv.RANK[rank_mode], refit_iters=refit, nthreads=NTHREADS, chart=chart)
     return r, tr, o
 
 
@@ -195,3 +196,41 @@ def test_full_size_fp32_workload():
     r, tr, o = run_both(p, g, L)
     assert_parity(p, r, tr, o, L)
     assert quat_angle(r.q, p.q_true) < 0.01
+
+
+# ---- the stereographic chart of Sec. 4.3.1 (rot_vote_config.chart = 1) ----
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16x2", "bf16"])
+def test_stereographic_chart_every_level(precision):
+    p, g, L = synth.config_problem("small_n1e3_32")
+    r, tr, o = run_both(p, g, L, precision=precision, chart=1)
+    assert_parity(p, r, tr, o, L)
+    q = synth.make_problem(3000, rho=0.9, sigma=0.01, delta=0.03, seed=81)
+    r, tr, o = run_both(q, 16, 3, precision=precision, chart=1)
+    assert_parity(q, r, tr, o, 3)
+
+
+@pytest.mark.parametrize("n", [2, 129, 257])
+def test_stereographic_chart_ragged(n):
+    p = synth.make_problem(n, rho=0.5, sigma=0.01, delta=0.05, seed=300 + n)
+    r, tr, o = run_both(p, 8, 2, chart=1)
+    assert_parity(p, r, tr, o, 2)
+
+
+def test_stereographic_chart_full_size_fp32_workload():
+    """The 1e5-pair, 64^3 + 3-level workload in the stereographic chart, every level."""
+    p, g, L = synth.config_problem("fp32_n1e5_64L3")
+    r, tr, o = run_both(p, g, L, chart=1)
+    assert_parity(p, r, tr, o, L)
+    assert quat_angle(r.q, p.q_true) < 0.01
+
+
+def test_stereographic_chart_batched_equals_alone():
+    probs = [synth.make_problem(n, rho=0.8, sigma=0.01, delta=0.03, seed=s)
+             for n, s in ((50, 21), (700, 22), (4096, 23))]
+    args = [(dev(p.a), dev(p.b), p.delta) for p in probs]
+    with rv.Context(grid_n=32, levels=2, chart="stereographic") as ctx:
+        batch = ctx.solve(args)
+        alone = [ctx.solve([x])[0] for x in args]
+    for rb, ra in zip(batch, alone):
+        assert np.array_equal(rb.q, ra.q) and (rb.best_cell, rb.best_count) == (ra.best_cell, ra.best_count)

@@ -18,7 +18,8 @@ from . import build as _build
 __all__ = [
     "lib", "pair_M", "pair_S", "quad", "quat_to_R", "cell_exists", "cell_geom", "tau",
     "level_cells", "vote_cells", "rank", "jacobi4", "canonical", "solve", "OracleResult",
-    "AMBIG", "cell_of_point", "fit_cell", "alg1_basis", "alg1_cell", "alg1_table", "alg1",
+    "AMBIG", "cell_of_point", "fit_cell", "alg1_basis", "alg1_cell", "alg1_table", "alg1", "alg1_centre",
+    "alg1_peaks",
 ]
 
 AMBIG = 1e-6
@@ -84,6 +85,11 @@ def lib():
         L.rvo_alg1.argtypes = [_f32p, _f32p, C.c_int64, _f64p, C.c_int, C.c_int, _i32p, C.POINTER(C.c_int64),
                                C.POINTER(C.c_int32), _f64p]
         L.rvo_alg1.restype = C.c_int64
+        L.rvo_alg1_centre.argtypes = [C.c_int, C.c_int64, _f64p]
+        L.rvo_alg1_centre.restype = None
+        L.rvo_alg1_peaks.argtypes = [_i32p, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_double, _i64p, _i32p, _f64p,
+                                     C.POINTER(C.c_int32)]
+        L.rvo_alg1_peaks.restype = C.c_int
         _lib = L
     return _lib
 
@@ -293,3 +299,22 @@ def alg1(a, b, J: int, n: int):
     q = np.zeros(4)
     cast = lib().rvo_alg1(a.reshape(-1), b.reshape(-1), a.shape[0], cs, int(J), int(n), acc, C.byref(bi), C.byref(bc), q)
     return acc, int(bi.value), int(bc.value), q, int(cast)
+
+
+def alg1_centre(n: int, idx: int) -> np.ndarray:
+    """Rotation (canonical quaternion) of the centre of accumulator cell idx."""
+    q = np.zeros(4)
+    lib().rvo_alg1_centre(int(n), int(idx), q)
+    return q
+
+
+def alg1_peaks(acc, n: int, M: int, theta: float, min_count: int = 1, kmax: int = 16384):
+    """Multiple rotations (Sec. 4.4): (idx[k], count[k], q[k, 4], T) of up to M peaks by greedy NMS."""
+    acc = np.ascontiguousarray(acc, dtype=np.int32)
+    pidx = np.zeros(max(1, M), np.int64)
+    pcnt = np.zeros(max(1, M), np.int32)
+    pq = np.zeros((max(1, M), 4))
+    T = C.c_int32()
+    k = lib().rvo_alg1_peaks(acc, int(n), int(M), int(min_count), int(kmax), float(theta), pidx, pcnt,
+                             pq.reshape(-1), C.byref(T))
+    return pidx[:k], pcnt[:k], pq[:k], int(T.value)

@@ -713,6 +713,8 @@ int64_t rvo_alg1_cell(const double q1[4], const double q2[4], double cj, double 
  * p* = -1 + (i + 1/2) 2/n: q = [2 p*, |p*|^2 - 1] / (1 + |p*|^2), canonical
  * sign.  cs holds (cos(alpha_j/2), sin(alpha_j/2)) for j < J.  Returns the
  * number of samples cast. */
+void rvo_alg1_centre(int n, int64_t idx, double q[4]);
+
 int64_t rvo_alg1(const float *a, const float *b, int64_t n_pairs, const double *cs, int J, int n, int32_t *acc,
                  int64_t *best_idx, int32_t *best_count, double q[4]) {
     const int64_t cells = (int64_t)n * n * n;
@@ -731,7 +733,15 @@ int64_t rvo_alg1(const float *a, const float *b, int64_t n_pairs, const double *
         if (acc[c] > acc[bi]) bi = c;
     *best_idx = bi;
     *best_count = acc[bi];
-    const int64_t ix = bi % n, iy = (bi / n) % n, iz = bi / ((int64_t)n * n);
+    rvo_alg1_centre(n, bi, q);
+    return cast;
+}
+
+/* Rotation of the centre of accumulator cell idx (n^3 grid): the inverse
+ * projection (Sec. 4.3.1) of p* = -1 + (i + 1/2) 2/n,
+ * q = [2 p*, |p*|^2 - 1] / (1 + |p*|^2), canonical sign. */
+void rvo_alg1_centre(int n, int64_t idx, double q[4]) {
+    const int64_t ix = idx % n, iy = (idx / n) % n, iz = idx / ((int64_t)n * n);
     const double h = 2.0 / (double)n;
     const double p[3] = {-1.0 + ((double)ix + 0.5) * h, -1.0 + ((double)iy + 0.5) * h, -1.0 + ((double)iz + 0.5) * h};
     const double pp = (p[0] * p[0] + p[1] * p[1]) + p[2] * p[2];
@@ -741,7 +751,67 @@ int64_t rvo_alg1(const float *a, const float *b, int64_t n_pairs, const double *
     q[2] = (2.0 * p[2]) / den;
     q[3] = (pp - 1.0) / den;
     rvo_canonical(q);
-    return cast;
+}
+
+typedef struct {
+    int32_t count;
+    int64_t idx;
+} peak_cand;
+
+static int peak_cmp(const void *x, const void *y) { /* count desc, index asc */
+    const peak_cand *a = (const peak_cand *)x, *b = (const peak_cand *)y;
+    if (a->count != b->count) return a->count > b->count ? -1 : 1;
+    return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+/* Multiple rotations (Sec. 4.4): up to M peaks of the accumulator, by greedy
+ * non-maximum suppression.  The candidates are the cells with count >= T,
+ * T = max(min_count, the smallest t >= 1 with #{cells: count >= t} <= kmax),
+ * taken in (count desc, index asc) order.  A candidate becomes a peak unless
+ * its centre rotation lies within theta of an earlier peak's:
+ * |q . q_peak| >= cos(theta / 2), the dot product summed as
+ * ((q0 q0' + q1 q1') + q2 q2') + q3 q3'.  Writes the peaks' index, count and
+ * centre rotation; returns how many were found and sets *T_out. */
+int rvo_alg1_peaks(const int32_t *acc, int n, int M, int min_count, int64_t kmax, double theta, int64_t *pidx,
+                   int32_t *pcount, double *pq, int32_t *T_out) {
+    const int64_t cells = (int64_t)n * n * n;
+    int32_t maxc = 0;
+    for (int64_t c = 0; c < cells; ++c)
+        if (acc[c] > maxc) maxc = acc[c];
+    /* ge[t] = number of cells with count >= t */
+    int64_t *ge = (int64_t *)calloc((size_t)maxc + 2, sizeof(int64_t));
+    for (int64_t c = 0; c < cells; ++c) ge[acc[c]] += 1;
+    for (int64_t t = (int64_t)maxc - 1; t >= 0; --t) ge[t] += ge[t + 1];
+    int64_t T = 1;
+    while (T <= maxc && ge[T] > kmax) ++T;
+    if (T < min_count) T = min_count;
+    *T_out = (int32_t)T;
+    const int64_t ncand = T <= maxc ? ge[T] : 0;
+    free(ge);
+    peak_cand *cand = (peak_cand *)malloc(sizeof(peak_cand) * (size_t)(ncand > 0 ? ncand : 1));
+    int64_t k = 0;
+    for (int64_t c = 0; c < cells; ++c)
+        if (acc[c] >= T) cand[k++] = (peak_cand){acc[c], c};
+    qsort(cand, (size_t)ncand, sizeof(peak_cand), peak_cmp);
+    const double cth = cos(theta / 2.0);
+    int np = 0;
+    for (int64_t i = 0; i < ncand && np < M; ++i) {
+        double q[4];
+        rvo_alg1_centre(n, cand[i].idx, q);
+        int near = 0;
+        for (int m = 0; m < np && !near; ++m) {
+            const double *o = pq + 4 * m;
+            const double d = ((q[0] * o[0] + q[1] * o[1]) + q[2] * o[2]) + q[3] * o[3];
+            near = fabs(d) >= cth;
+        }
+        if (near) continue;
+        pidx[np] = cand[i].idx;
+        pcount[np] = cand[i].count;
+        for (int j = 0; j < 4; ++j) pq[4 * np + j] = q[j];
+        ++np;
+    }
+    free(cand);
+    return np;
 }
 
 /* (cos(alpha_j/2), sin(alpha_j/2)) for alpha_j = -pi + 2 pi j / J, j < J: the

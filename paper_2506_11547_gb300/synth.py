@@ -29,6 +29,8 @@ __all__ = [
     "config_problem",
     "batched_problems",
     "serving_stream",
+    "MultiProblem",
+    "make_multi_problem",
     "SEED_BASE",
 ]
 
@@ -164,3 +166,46 @@ def serving_stream(count: int, rate_hz: float = 2000.0, seed: int = SEED_BASE + 
     probs = [make_problem(int(ns[k]), float(rhos[k]), 0.01, delta, seed=int(seeds[k]))
              for k in range(count)]
     return t, probs
+
+
+@dataclasses.dataclass
+class MultiProblem:
+    """Correspondences from several rotation motions in one scene (Sec. 4.4)."""
+
+    a: np.ndarray          # float32 [n, 3]
+    b: np.ndarray          # float32 [n, 3]
+    q_true: np.ndarray     # float64 [models, 4], w >= 0
+    label: np.ndarray      # int [n]: the motion of each pair, -1 for outliers
+
+    @property
+    def n(self) -> int:
+        return int(self.a.shape[0])
+
+
+def make_multi_problem(models: int, per_model: int, sigma: float = 0.01, outlier_frac: float = 0.0,
+                       seed: int = SEED_BASE + 5) -> MultiProblem:
+    """`models` uniform random rotations with `per_model` pairs each (a uniform on
+    S^2, b = normalize(R_m a + sigma N(0, I3))), plus round(outlier_frac * total)
+    pairs with b uniform, shuffled by a seeded permutation: the multiple-rotation
+    protocol of the paper's Sec. 5.5.1."""
+    rng = np.random.default_rng(seed)
+    qs, aa, bb, lab = [], [], [], []
+    for m in range(models):
+        q, R = _random_rotation(rng)
+        a = _normalize_rows(rng.standard_normal((per_model, 3)))
+        b = a @ R.T
+        if sigma > 0:
+            b = b + sigma * rng.standard_normal((per_model, 3))
+        qs.append(q)
+        aa.append(a)
+        bb.append(_normalize_rows(b))
+        lab.append(np.full(per_model, m))
+    n_out = int(round(outlier_frac * models * per_model))
+    if n_out:
+        aa.append(_normalize_rows(rng.standard_normal((n_out, 3))))
+        bb.append(_normalize_rows(rng.standard_normal((n_out, 3))))
+        lab.append(np.full(n_out, -1))
+    a, b, label = np.concatenate(aa), np.concatenate(bb), np.concatenate(lab)
+    perm = rng.permutation(len(label))
+    return MultiProblem(a=a[perm].astype(np.float32), b=b[perm].astype(np.float32), q_true=np.array(qs),
+                        label=label[perm])

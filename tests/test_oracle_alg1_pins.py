@@ -119,3 +119,65 @@ def test_outliers_do_not_move_the_noise_free_winner():
     ins = ~p.outlier
     _, bi2, _, _, _ = o.alg1(p.a[ins], p.b[ins], 120, 40)
     assert bi == bi2
+
+
+# ---- multiple rotations (Sec. 4.4): peaks by greedy non-maximum suppression ----
+
+def _angle(q1, q2):
+    from tests._util import quat_angle
+    return quat_angle(q1, q2)
+
+
+def test_one_peak_is_the_argmax():
+    o = _oracle()
+    p = synth.make_problem(1500, rho=0.7, sigma=0.01, delta=0.03, seed=31)
+    acc, bi, bc, q, _ = o.alg1(p.a, p.b, 180, 64)
+    idx, cnt, qs, T = o.alg1_peaks(acc, 64, 1, 0.1)
+    assert list(idx) == [bi] and list(cnt) == [bc] and np.array_equal(qs[0], q)
+
+
+def test_peaks_obey_the_greedy_suppression_invariants():
+    """Independently of how the oracle orders its work: (i) T is the rule's value;
+    (ii) peaks come in (count desc, index asc) order, pairwise farther apart than
+    theta; (iii) every candidate ranked before the last peak that is not a peak lies
+    within theta of an earlier-ranked peak; (iv) with fewer than M peaks, every
+    candidate is a peak or suppressed."""
+    o = _oracle()
+    mp = synth.make_multi_problem(4, 800, sigma=0.01, outlier_frac=0.5, seed=32)
+    n, theta = 60, 0.15
+    acc, *_ = o.alg1(mp.a, mp.b, 180, n)
+    for M, kmax, min_count in ((6, 16384, 1), (40, 300, 1), (6, 16384, 25)):
+        idx, cnt, qs, T = o.alg1_peaks(acc, n, M, theta, min_count=min_count, kmax=kmax)
+        ge = lambda t: int(np.sum(acc >= t))
+        t0 = 1
+        while ge(t0) > kmax:
+            t0 += 1
+        assert T == max(t0, min_count)
+        cand = np.nonzero(acc >= T)[0]
+        order = sorted(cand, key=lambda c: (-acc[c], c))
+        rank = {c: r for r, c in enumerate(order)}
+        assert [rank[c] for c in idx] == sorted(rank[c] for c in idx)
+        centre = {c: o.alg1_centre(n, c) for c in order}
+        for i in range(len(idx)):
+            assert np.allclose(qs[i], centre[idx[i]])
+            for j in range(i):
+                assert _angle(qs[i], qs[j]) > theta - 1e-9
+        last = rank[idx[-1]] if len(idx) == M else len(order) - 1
+        picked = set(idx.tolist())
+        for c in order[: last + 1]:
+            if c in picked:
+                continue
+            assert any(rank[pk] < rank[c] and _angle(centre[c], centre[pk]) <= theta + 1e-9 for pk in idx)
+
+
+def test_peaks_recover_every_rotation_of_a_multi_motion_scene():
+    """Noise-free scene of three motions with 1000 pairs each and 50% extra outliers:
+    the three highest peaks are the three rotations, each within its cell's reach."""
+    o = _oracle()
+    mp = synth.make_multi_problem(3, 1000, sigma=0.0, outlier_frac=0.5, seed=33)
+    n = 120
+    acc, *_ = o.alg1(mp.a, mp.b, 540, n)
+    idx, cnt, qs, T = o.alg1_peaks(acc, n, 3, 0.2)
+    assert len(idx) == 3
+    for qt in mp.q_true:
+        assert min(_angle(q, qt) for q in qs) < 2 * 4.0 / n

@@ -278,6 +278,30 @@ int rot_vote_count_cells_static(const float *a, const float *b, int64_t n, doubl
  * (times a safety factor) of a cell boundary or of q3 = 0; the accumulator is
  * therefore exact.  A pair with a = -b (w = 0, no circle) casts no sample.
  */
+/* Multiple rotations (Sec. 4.4: several motions in one scene vote several
+ * peaks).  With rot_vote_alg1_problem.peaks = M >= 1 the call also returns up
+ * to M peaks of the accumulator by greedy non-maximum suppression:
+ *   - T = max(min_count, the smallest t >= 1 with at most
+ *     ROT_VOTE_ALG1_PEAK_CANDIDATES cells of count >= t);
+ *   - the candidates, the cells with count >= T, are taken in (count desc,
+ *     index asc) order;
+ *   - a candidate becomes a peak unless its centre rotation lies within
+ *     nms_angle of an earlier peak's, i.e. |q . q_peak| >= cos(nms_angle / 2)
+ *     with the dot product summed as ((q0 q0' + q1 q1') + q2 q2') + q3 q3' in
+ *     IEEE double arithmetic; q of a cell is the inverse projection of its
+ *     centre, as for the winner.
+ * The decisions equal that FP64 definition exactly.  When more than
+ * ROT_VOTE_ALG1_PEAK_CANDIDATES cells reach 65535 counts, T is not computed:
+ * peak_threshold = -1 and no peak is returned. */
+#define ROT_VOTE_ALG1_MAX_PEAKS 64
+#define ROT_VOTE_ALG1_PEAK_CANDIDATES 16384
+typedef struct {
+    double q[4];            /* centre rotation of the peak's cell, canonical sign */
+    int64_t cell;           /* its linear index */
+    int32_t count;          /* its count */
+    int32_t pad;
+} rot_vote_peak;
+
 typedef struct {
     const float *a;         /* [n,3] row-major float32 unit vectors, host or device memory; */
     const float *b;         /*   validity as in rot_vote_problem */
@@ -286,6 +310,10 @@ typedef struct {
     int accum_side;         /* n of the n^3 accumulator, 2 <= n <= 1024; 0 = 360 */
     int32_t *accumulator;   /* optional (NULL: not returned): host or device int32 [n^3], receives the
                                counts in linear-index order; owned by the caller */
+    int peaks;              /* M, 0 <= M <= ROT_VOTE_ALG1_MAX_PEAKS: 0 = no peak list */
+    int min_count;          /* peaks: the smallest count a peak may have; 0 = 1 */
+    float nms_angle;        /* peaks: suppression radius theta, a rotation angle in radians, >= 0 */
+    rot_vote_peak *peak_out; /* peaks: host array of M entries, written in peak order; owned by the caller */
 } rot_vote_alg1_problem;
 
 typedef struct {
@@ -297,7 +325,9 @@ typedef struct {
     int64_t samples_cast;   /* J x (pairs with a circle) */
     int64_t rechecked;      /* samples whose cell the device decided in FP64 */
     float ms_gpu;           /* device time of this problem (accumulator zeroing to result) */
-    float pad;
+    int32_t npeaks;         /* peaks written to peak_out */
+    int32_t peak_threshold; /* T of the peak search (-1: not computed), 0 without peaks */
+    int32_t pad;
 } rot_vote_alg1_result;
 
 /* Run Alg. 1 on n_problems problems, one after another on the context's

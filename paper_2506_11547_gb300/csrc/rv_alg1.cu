@@ -22,6 +22,7 @@
 // kEdgeRel (n/2) of an integer, or whose FP32 q3 lies within kQ3Guard of 0
 // (the sign choice), is evaluated again in FP64, operation for operation as
 // the formulas are written, so every count equals the FP64 count.
+#include <limits.h>
 #include <math.h>
 #include <string.h>
 
@@ -59,6 +60,8 @@ struct A1Hdr {
     unsigned long long rechecked;  // samples evaluated in FP64
     int32_t invalid;               // an input vector failed validation
     uint32_t blocks_done;          // argmax blocks finished (the last one writes the result)
+    int32_t peak_T;                // peak threshold (-1: not computed)
+    uint32_t ncand;                // peak candidates collected
     rot_vote_alg1_result res;
 };
 static_assert(sizeof(A1Hdr) <= 256, "header slot");
@@ -266,9 +269,65 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long x, unsig
 }
 
 constexpr int kArgThreads = 256;
+constexpr int kHistBins = 65536;   // count histogram for the peak threshold; counts >= 65535 share the top bin
+constexpr int kHistSmem = 2048;    // bins counted in shared memory per block
+constexpr int kPeakCand = ROT_VOTE_ALG1_PEAK_CANDIDATES;
+constexpr int kPeakThreads = 1024;
 
+// Rotation of the centre of accumulator cell idx: the inverse projection
+// (Sec. 4.3.1) of p* = -1 + (i + 1/2) 2/n, q = (2 p*, |p*|^2 - 1) / (1 + |p*|^2),
+// with the sign w > 0 (w = 0: the first nonzero component > 0).
+__device__ __forceinline__ void alg1_centre64(int side, uint32_t idx, double q[4]) {
+    const int64_t n = side;
+    const int64_t ix = idx % n, iy = (idx / n) % n, iz = idx / (n * n);
+    const double h = ddiv(2.0, (double)side);
+    const double p[3] = {dadd(-1.0, dmul(dadd((double)ix, 0.5), h)), dadd(-1.0, dmul(dadd((double)iy, 0.5), h)),
+                         dadd(-1.0, dmul(dadd((double)iz, 0.5), h))};
+    const double pp = dadd(dadd(dmul(p[0], p[0]), dmul(p[1], p[1])), dmul(p[2], p[2]));
+    const double den = dadd(1.0, pp);
+    q[0] = ddiv(dmul(2.0, p[0]), den);
+    q[1] = ddiv(dmul(2.0, p[1]), den);
+    q[2] = ddiv(dmul(2.0, p[2]), den);
+    q[3] = ddiv(dsub(pp, 1.0), den);
+    for (int c = 0; c < 4; ++c) {
+        if (q[c] > 0.0) break;
+        if (q[c] < 0.0) {
+            for (int m = 0; m < 4; ++m) q[m] = -q[m];
+            break;
+        }
+    }
+}
+
+// One cell's count into the histogram: counts 1..15 in sixteen 4-bit fields of
+// a register (flushed to shared memory when a field reaches 15), 16..2047 in
+// shared memory, larger counts in global memory (65535 and above in one bin).
+__device__ __forceinline__ void hist_add(int c, unsigned long long &nib, unsigned *sh, unsigned *hist) {
+    if (c <= 0) return;
+    if (c < 16) {
+        const int s = 4 * c;
+        nib += 1ull << s;
+        if (((nib >> s) & 15ull) == 15ull) {
+            atomicAdd(&sh[c], 15u);
+            nib -= 15ull << s;
+        }
+    } else if (c < kHistSmem) {
+        atomicAdd(&sh[c], 1u);
+    } else {
+        atomicAdd(&hist[min(c, kHistBins - 1)], 1u);
+    }
+}
+
+// (count, -index) maximum over the accumulator; with HIST also the count
+// histogram.  The last block to finish writes the result.
+template <bool HIST>
 __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(const int32_t *__restrict__ acc, int side,
-                                                                  A1Hdr *hdr) {
+                                                                  A1Hdr *hdr, unsigned *__restrict__ hist) {
+    __shared__ unsigned sh[HIST ? kHistSmem : 1];
+    if (HIST) {
+        for (int b = threadIdx.x; b < kHistSmem; b += kArgThreads) sh[b] = 0;
+        __syncthreads();
+    }
+    unsigned long long nib = 0;
     const int64_t cells = (int64_t)side * side * side;
     const int64_t nvec = cells >> 2;
     const int4 *v = reinterpret_cast<const int4 *>(acc);
@@ -286,6 +345,12 @@ __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(const int32_t 
             best = umax64(best, a1_key(c[u].y, i + 1));
             best = umax64(best, a1_key(c[u].z, i + 2));
             best = umax64(best, a1_key(c[u].w, i + 3));
+            if (HIST) {
+                hist_add(c[u].x, nib, sh, hist);
+                hist_add(c[u].y, nib, sh, hist);
+                hist_add(c[u].z, nib, sh, hist);
+                hist_add(c[u].w, nib, sh, hist);
+            }
         }
     }
     for (; k < nvec; k += stride) {
@@ -295,9 +360,28 @@ __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(const int32_t 
         best = umax64(best, a1_key(c.y, i + 1));
         best = umax64(best, a1_key(c.z, i + 2));
         best = umax64(best, a1_key(c.w, i + 3));
+        if (HIST) {
+            hist_add(c.x, nib, sh, hist);
+            hist_add(c.y, nib, sh, hist);
+            hist_add(c.z, nib, sh, hist);
+            hist_add(c.w, nib, sh, hist);
+        }
     }
-    for (int64_t r = (nvec << 2) + (int64_t)blockIdx.x * kArgThreads + threadIdx.x; r < cells; r += stride)
+    for (int64_t r = (nvec << 2) + (int64_t)blockIdx.x * kArgThreads + threadIdx.x; r < cells; r += stride) {
         best = umax64(best, a1_key(acc[r], (uint32_t)r));
+        if (HIST) hist_add(acc[r], nib, sh, hist);
+    }
+    if (HIST) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int c = 1; c < 16; ++c) {
+            const unsigned f = __reduce_add_sync(0xffffffffu, (unsigned)((nib >> (4 * c)) & 15ull));
+            if (lane == 0 && f) atomicAdd(&sh[c], f);
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < kHistSmem; b += kArgThreads)
+            if (sh[b]) atomicAdd(&hist[b], sh[b]);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, o));
     __shared__ unsigned long long wbest[kArgThreads / 32];
@@ -312,28 +396,12 @@ __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(const int32_t 
     }
     __syncthreads();
     if (!last || threadIdx.x != 0) return;
-    // The last block: every block's maximum is in best_key.  Inverse projection
-    // of the winner's centre p* = -1 + (i + 1/2) 2/n (Sec. 4.3.1):
-    // q = (2 p*, |p*|^2 - 1) / (1 + |p*|^2).
+    // The last block: every block's maximum is in best_key.
     __threadfence();
     const unsigned long long key = atomicAdd(&hdr->best_key, 0ull);
     const uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffull);
-    const int64_t n = side;
-    const int64_t ix = idx % n, iy = (idx / n) % n, iz = idx / (n * n);
-    const double h = ddiv(2.0, (double)side);
-    const double p[3] = {dadd(-1.0, dmul(dadd((double)ix, 0.5), h)), dadd(-1.0, dmul(dadd((double)iy, 0.5), h)),
-                         dadd(-1.0, dmul(dadd((double)iz, 0.5), h))};
-    const double pp = dadd(dadd(dmul(p[0], p[0]), dmul(p[1], p[1])), dmul(p[2], p[2]));
-    const double den = dadd(1.0, pp);
-    double q[4] = {ddiv(dmul(2.0, p[0]), den), ddiv(dmul(2.0, p[1]), den), ddiv(dmul(2.0, p[2]), den),
-                   ddiv(dsub(pp, 1.0), den)};
-    for (int c = 0; c < 4; ++c) {  // sign: w > 0, else the first nonzero component > 0
-        if (q[c] > 0.0) break;
-        if (q[c] < 0.0) {
-            for (int m = 0; m < 4; ++m) q[m] = -q[m];
-            break;
-        }
-    }
+    double q[4];
+    alg1_centre64(side, idx, q);
     double R[9];
     quat_to_R(q, R);
     rot_vote_alg1_result &res = hdr->res;
@@ -345,7 +413,185 @@ __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(const int32_t 
     res.samples_cast = (int64_t)hdr->cast;
     res.rechecked = (int64_t)hdr->rechecked;
     res.ms_gpu = 0.f;
-    res.pad = 0.f;
+    res.npeaks = 0;
+    res.peak_threshold = 0;
+    res.pad = 0;
+}
+
+// Peak threshold T = max(min_count, the smallest t >= 1 with
+// #{cells: count >= t} <= kPeakCand), from the histogram; -1 when even the top
+// bin holds more than kPeakCand cells.  One block.
+__global__ void __launch_bounds__(kPeakThreads) alg1_threshold_kernel(const unsigned *__restrict__ hist,
+                                                                      int min_count, A1Hdr *hdr) {
+    constexpr int per = kHistBins / kPeakThreads;
+    __shared__ unsigned long long part[kPeakThreads];
+    __shared__ int tmin[kPeakThreads / 32];
+    const int t = threadIdx.x;
+    unsigned long long s = 0;
+    for (int k = 0; k < per; ++k) s += hist[t * per + k];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < kPeakThreads; off <<= 1) {  // suffix sums over the threads' ranges
+        const unsigned long long v = t + off < kPeakThreads ? part[t + off] : 0ull;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned long long ge = t + 1 < kPeakThreads ? part[t + 1] : 0ull;  // cells with count >= (t + 1) per
+    int best = INT_MAX;
+    for (int k = per - 1; k >= 0; --k) {  // ge(u) is non-increasing in u: keep the smallest u that fits
+        const int u = t * per + k;
+        ge += hist[u];
+        if (u >= 1 && ge <= (unsigned long long)kPeakCand) best = u;
+    }
+    best = __reduce_min_sync(0xffffffffu, best);
+    if ((t & 31) == 0) tmin[t >> 5] = best;
+    __syncthreads();
+    if (t == 0) {
+        int m = INT_MAX;
+        for (int w = 0; w < kPeakThreads / 32; ++w) m = min(m, tmin[w]);
+        hdr->peak_T = m == INT_MAX ? -1 : max(m, max(min_count, 1));
+        hdr->ncand = 0;
+    }
+}
+
+// Candidates: every cell with count >= T, as (count, -index) keys.
+__global__ void __launch_bounds__(kArgThreads) alg1_collect_kernel(const int32_t *__restrict__ acc, int side,
+                                                                   A1Hdr *hdr, unsigned long long *cand) {
+    const int T = hdr->peak_T;
+    if (T < 1) return;
+    const int64_t cells = (int64_t)side * side * side;
+    const int64_t nvec = cells >> 2;
+    const int4 *v = reinterpret_cast<const int4 *>(acc);
+    const int64_t stride = (int64_t)gridDim.x * kArgThreads;
+    auto put = [&](int c, uint32_t i) {
+        if (c >= T) {
+            const unsigned pos = atomicAdd(&hdr->ncand, 1u);
+            if (pos < (unsigned)kPeakCand) cand[pos] = a1_key(c, i);
+        }
+    };
+    for (int64_t k = (int64_t)blockIdx.x * kArgThreads + threadIdx.x; k < nvec; k += stride) {
+        const int4 c = __ldcs(v + k);
+        const uint32_t i = (uint32_t)(k << 2);
+        put(c.x, i);
+        put(c.y, i + 1);
+        put(c.z, i + 2);
+        put(c.w, i + 3);
+    }
+    for (int64_t r = (nvec << 2) + (int64_t)blockIdx.x * kArgThreads + threadIdx.x; r < cells; r += stride)
+        put(acc[r], (uint32_t)r);
+}
+
+// FP32 centre rotation of cell idx (no sign normalisation; |dot| ignores it).
+// Error per component <= 90 u against alg1_centre64 (p: 3u, |p|^2: 40u,
+// 1 + |p|^2: 41u, quotient: u), so |dot32 - dot64| <= 190 u = 1.2e-5.
+__device__ __forceinline__ float4 alg1_centre32(int side, float h, uint32_t idx) {
+    const uint32_t n = (uint32_t)side;
+    const float p0 = fmaf((float)(idx % n) + 0.5f, h, -1.f);
+    const float p1 = fmaf((float)((idx / n) % n) + 0.5f, h, -1.f);
+    const float p2 = fmaf((float)(idx / (n * n)) + 0.5f, h, -1.f);
+    const float pp = fmaf(p0, p0, fmaf(p1, p1, p2 * p2));
+    const float den = 1.f + pp;
+    return make_float4(__fdiv_rn(2.f * p0, den), __fdiv_rn(2.f * p1, den), __fdiv_rn(2.f * p2, den),
+                       __fdiv_rn(pp - 1.f, den));
+}
+
+constexpr float kPeakBand = 3e-5f;  // FP32 |dot| within this of cos(theta/2): decided in FP64
+
+// Sorts the candidates (count desc, index asc) and picks up to M peaks by
+// greedy suppression.  One block; keys and flags in shared memory.
+__global__ void __launch_bounds__(kPeakThreads) alg1_peaks_kernel(const unsigned long long *__restrict__ cand,
+                                                                  int side, int M, double cth, A1Hdr *hdr,
+                                                                  rot_vote_peak *out) {
+    extern __shared__ unsigned long long keys[];
+    unsigned char *supp = reinterpret_cast<unsigned char *>(keys + kPeakCand);
+    __shared__ double pq[ROT_VOTE_ALG1_MAX_PEAKS][4];
+    __shared__ float4 pq32[ROT_VOTE_ALG1_MAX_PEAKS];
+    __shared__ int wmin[kPeakThreads / 32];
+    __shared__ int s_first;
+    const int t = threadIdx.x;
+    const int T = hdr->peak_T;
+    const int nc = T < 1 ? 0 : (int)min(hdr->ncand, (unsigned)kPeakCand);
+    int P = 1;
+    while (P < nc) P <<= 1;
+    for (int i = t; i < P; i += kPeakThreads) {
+        keys[i] = i < nc ? cand[i] : 0ull;
+        supp[i] = 0;
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {  // bitonic sort, descending keys
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = t; i < P; i += kPeakThreads) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = keys[i], b = keys[l];
+                    if (((i & k) == 0) ? (a < b) : (a > b)) {
+                        keys[i] = b;
+                        keys[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const float h = __fdiv_rn(2.f, (float)side);
+    const float lo = (float)cth - kPeakBand, hi = (float)cth + kPeakBand;
+    int np = 0, pos = 0;
+    while (np < M) {
+        int first = INT_MAX;
+        for (int i = pos + t; i < nc; i += kPeakThreads)
+            if (!supp[i]) {
+                first = i;
+                break;
+            }
+        first = __reduce_min_sync(0xffffffffu, first);
+        if ((t & 31) == 0) wmin[t >> 5] = first;
+        __syncthreads();
+        if (t == 0) {
+            int m = INT_MAX;
+            for (int w = 0; w < kPeakThreads / 32; ++w) m = min(m, wmin[w]);
+            s_first = m;
+            if (m != INT_MAX) {
+                const uint32_t idx = 0xffffffffu - (uint32_t)(keys[m] & 0xffffffffull);
+                double q[4];
+                alg1_centre64(side, idx, q);
+                for (int c = 0; c < 4; ++c) pq[np][c] = q[c];
+                pq32[np] = alg1_centre32(side, h, idx);
+                rot_vote_peak pk;
+                for (int c = 0; c < 4; ++c) pk.q[c] = q[c];
+                pk.cell = idx;
+                pk.count = (int32_t)(keys[m] >> 32);
+                pk.pad = 0;
+                out[np] = pk;
+            }
+        }
+        __syncthreads();
+        const int f = s_first;
+        if (f == INT_MAX) break;
+        const float4 a = pq32[np];
+        for (int i = f + 1 + t; i < nc; i += kPeakThreads) {
+            if (supp[i]) continue;
+            const uint32_t idx = 0xffffffffu - (uint32_t)(keys[i] & 0xffffffffull);
+            const float4 b = alg1_centre32(side, h, idx);
+            const float d = fabsf(fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x))));
+            if (d >= hi) {
+                supp[i] = 1;
+            } else if (d > lo) {  // near cos(theta/2): the FP64 definition decides
+                double q[4];
+                alg1_centre64(side, idx, q);
+                const double d64 = dadd(dadd(dadd(dmul(q[0], pq[np][0]), dmul(q[1], pq[np][1])), dmul(q[2], pq[np][2])),
+                                        dmul(q[3], pq[np][3]));
+                if (fabs(d64) >= cth) supp[i] = 1;
+            }
+        }
+        ++np;
+        pos = f + 1;
+        __syncthreads();
+    }
+    if (t == 0) {
+        hdr->res.npeaks = np;
+        hdr->res.peak_threshold = T;
+    }
 }
 
 constexpr int64_t kA1MaxPairs = (int64_t)1 << 30;
@@ -396,8 +642,10 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         const rot_vote_alg1_problem &P = p[k];
         const int J = P.samples == 0 ? 180 : P.samples;
         const int side = P.accum_side == 0 ? 360 : P.accum_side;
+        const int M = P.peaks;
         if (!P.a || !P.b || P.n < 2 || P.n > kA1MaxPairs || J < 1 || J > kA1MaxSamples || side < 2 ||
-            side > kA1MaxSide) {
+            side > kA1MaxSide || M < 0 || M > ROT_VOTE_ALG1_MAX_PEAKS ||
+            (M > 0 && (!P.peak_out || !(P.nms_angle >= 0.f) || !isfinite(P.nms_angle) || P.min_count < 0))) {
             r.status = ROT_VOTE_EINVAL;
             last_error = "alg1 problem " + std::to_string(k) + ": bad argument";
             continue;
@@ -412,7 +660,10 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         const size_t off_q1f = align_up(off_t64 + sizeof(double2) * J, 256);
         const size_t off_q2f = align_up(off_q1f + sizeof(float4) * (size_t)P.n, 256);
         const size_t off_qd = align_up(off_q2f + sizeof(float4) * (size_t)P.n, 256);
-        const size_t off_in = align_up(off_qd + 4 * sizeof(double2) * (size_t)P.n, 256);
+        const size_t off_hist = align_up(off_qd + 4 * sizeof(double2) * (size_t)P.n, 256);
+        const size_t off_cand = align_up(off_hist + (M > 0 ? sizeof(unsigned) * kHistBins : 0), 256);
+        const size_t off_pk = align_up(off_cand + (M > 0 ? sizeof(unsigned long long) * kPeakCand : 0), 256);
+        const size_t off_in = align_up(off_pk + (M > 0 ? sizeof(rot_vote_peak) * ROT_VOTE_ALG1_MAX_PEAKS : 0), 256);
         const size_t in_bytes = dev_in ? 0 : align_up(sizeof(float) * 3 * (size_t)P.n, 256);
         const size_t need = off_in + 2 * in_bytes;
         if (need > a1_cap) {
@@ -508,17 +759,46 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         }
         mark(1, false);
         mark(2, true);
+        unsigned *hist = reinterpret_cast<unsigned *>(base + off_hist);
+        unsigned long long *cand = reinterpret_cast<unsigned long long *>(base + off_cand);
+        rot_vote_peak *pk = reinterpret_cast<rot_vote_peak *>(base + off_pk);
+        const int64_t want_arg = (cells / 4 + kArgThreads - 1) / kArgThreads;
+        const int arg_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_arg, (int64_t)sm_count * 8));
+        if (e == cudaSuccess && M > 0) e = cudaMemsetAsync(hist, 0, sizeof(unsigned) * kHistBins, stream);
         if (e == cudaSuccess) {
-            const int64_t want = (cells / 4 + kArgThreads - 1) / kArgThreads;
-            const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * 8));
-            alg1_argmax_kernel<<<blocks, kArgThreads, 0, stream>>>(acc, side, hdr);
+            if (M > 0)
+                alg1_argmax_kernel<true><<<arg_blocks, kArgThreads, 0, stream>>>(acc, side, hdr, hist);
+            else
+                alg1_argmax_kernel<false><<<arg_blocks, kArgThreads, 0, stream>>>(acc, side, hdr, nullptr);
             e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && M > 0) {
+            // peaks (Sec. 4.4): threshold, candidates, sort and greedy suppression
+            alg1_threshold_kernel<<<1, kPeakThreads, 0, stream>>>(hist, P.min_count, hdr);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) {
+                alg1_collect_kernel<<<arg_blocks, kArgThreads, 0, stream>>>(acc, side, hdr, cand);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess && !a1_peaks_attr) {
+                e = cudaFuncSetAttribute(alg1_peaks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kPeakCand * (sizeof(unsigned long long) + 1)));
+                a1_peaks_attr = e == cudaSuccess;
+            }
+            if (e == cudaSuccess) {
+                const double cth = cos((double)P.nms_angle / 2.0);
+                alg1_peaks_kernel<<<1, kPeakThreads, kPeakCand * (sizeof(unsigned long long) + 1), stream>>>(
+                    cand, side, M, cth, hdr, pk);
+                e = cudaGetLastError();
+            }
         }
         mark(2, false);
         if (e == cudaSuccess) e = cudaEventRecord(a1_ev[1], stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(a1_hdr_h, hdr, sizeof(A1Hdr), cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess && P.accumulator)
             e = cudaMemcpyAsync(P.accumulator, acc, sizeof(int32_t) * (size_t)cells, cudaMemcpyDefault, stream);
+        if (e == cudaSuccess && M > 0)
+            e = cudaMemcpyAsync(P.peak_out, pk, sizeof(rot_vote_peak) * M, cudaMemcpyDefault, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) return cuda_fail(e, "running alg1");
         const A1Hdr *hh = static_cast<const A1Hdr *>(a1_hdr_h);

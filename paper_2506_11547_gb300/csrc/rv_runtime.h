@@ -127,6 +127,7 @@ class Context {
     size_t a1_cap = 0;
     int a1_J = 0;            // J of the angle tables in a1_mem (0 = none)
     size_t a1_toff = 0;      // their offset
+    bool a1_peaks_attr = false;  // dynamic shared memory of the peak kernel raised
     void *a1_hdr_h = nullptr;
     cudaEvent_t a1_ev[2] = {nullptr, nullptr};
 

@@ -44,15 +44,23 @@ class rot_vote_result(C.Structure):
                 ("latency_ms", C.c_float)]
 
 
+ALG1_MAX_PEAKS, ALG1_PEAK_CANDIDATES = 64, 16384
+
+
+class rot_vote_peak(C.Structure):
+    _fields_ = [("q", C.c_double * 4), ("cell", C.c_int64), ("count", C.c_int32), ("pad", C.c_int32)]
+
+
 class rot_vote_alg1_problem(C.Structure):
     _fields_ = [("a", C.c_void_p), ("b", C.c_void_p), ("n", C.c_int64), ("samples", C.c_int),
-                ("accum_side", C.c_int), ("accumulator", C.c_void_p)]
+                ("accum_side", C.c_int), ("accumulator", C.c_void_p), ("peaks", C.c_int), ("min_count", C.c_int),
+                ("nms_angle", C.c_float), ("peak_out", C.c_void_p)]
 
 
 class rot_vote_alg1_result(C.Structure):
     _fields_ = [("q", C.c_double * 4), ("R", C.c_double * 9), ("best_count", C.c_int32), ("status", C.c_int32),
                 ("best_cell", C.c_int64), ("samples_cast", C.c_int64), ("rechecked", C.c_int64),
-                ("ms_gpu", C.c_float), ("pad", C.c_float)]
+                ("ms_gpu", C.c_float), ("npeaks", C.c_int32), ("peak_threshold", C.c_int32), ("pad", C.c_int32)]
 
 
 class rot_vote_stage(C.Structure):
@@ -138,12 +146,16 @@ class Alg1Result:
     samples_cast: int
     rechecked: int
     ms_gpu: float
+    peak_threshold: int = 0
+    peaks: list = dataclasses.field(default_factory=list)  # [(cell, count, q[4])] in peak order
 
     @staticmethod
-    def of(r: rot_vote_alg1_result) -> "Alg1Result":
+    def of(r: rot_vote_alg1_result, peaks=None) -> "Alg1Result":
+        pk = [] if peaks is None else [(int(peaks[k].cell), int(peaks[k].count), np.array(peaks[k].q[:]))
+                                       for k in range(r.npeaks)]
         return Alg1Result(q=np.array(r.q[:]), R=np.array(r.R[:]).reshape(3, 3), best_count=r.best_count,
                           status=r.status, best_cell=r.best_cell, samples_cast=r.samples_cast,
-                          rechecked=r.rechecked, ms_gpu=r.ms_gpu)
+                          rechecked=r.rechecked, ms_gpu=r.ms_gpu, peak_threshold=r.peak_threshold, peaks=pk)
 
 
 class RotVoteError(RuntimeError):
@@ -243,12 +255,15 @@ class Context:
         self._keep.pop(ticket, None)
         return Result.of(out)
 
-    def alg1(self, problems):
+    def alg1(self, problems, peaks: int = 0, nms_angle: float = 0.0, min_count: int = 0):
         """rot_vote_alg1.  problems: list of (a, b[, samples[, accum_side[, accumulator]]]); accumulator: an
-        int32 array or device tensor of accum_side^3 elements that receives the counts.  Returns Alg1Result list."""
+        int32 array or device tensor of accum_side^3 elements that receives the counts.  peaks = M > 0 also
+        returns up to M peaks (greedy suppression within nms_angle) in each result's `peaks`.
+        Returns Alg1Result list."""
         n = len(problems)
         arr = (rot_vote_alg1_problem * n)()
         keep = []
+        pk_bufs = []
         for k, pr in enumerate(problems):
             a, b = pr[0], pr[1]
             J = int(pr[2]) if len(pr) > 2 else 0
@@ -271,11 +286,14 @@ class Context:
                 need = (side or 360) ** 3
                 if int(np.prod(acc.shape)) != need:
                     raise ValueError(f"accumulator must hold {need} elements")
-            arr[k] = rot_vote_alg1_problem(pa, pb, _nrows(a), J, side, pacc or None)
+            pbuf = (rot_vote_peak * max(1, int(peaks)))()
+            pk_bufs.append(pbuf)
+            arr[k] = rot_vote_alg1_problem(pa, pb, _nrows(a), J, side, pacc or None, int(peaks), int(min_count),
+                                           float(nms_angle), C.cast(pbuf, C.c_void_p) if peaks else None)
             keep.append((ka, kb, acc))
         out = (rot_vote_alg1_result * n)()
         self._check(self._L.rot_vote_alg1(self._h, arr, n, out))
-        return [Alg1Result.of(out[k]) for k in range(n)]
+        return [Alg1Result.of(out[k], pk_bufs[k] if peaks else None) for k in range(n)]
 
     def alg1_raw(self, arr, n, out):
         """Calls rot_vote_alg1 on prepared ctypes arrays (for timing loops)."""

@@ -51,6 +51,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(rot_vote_result, status), offsetof(rot_vote_result, ms_gpu),
          offsetof(rot_vote_config, cuda_stream), offsetof(rot_vote_problem, delta));
   printf("%zu\n", offsetof(rot_vote_config, chart));
+  printf("%zu %zu %zu %zu\n", sizeof(rot_vote_peak), offsetof(rot_vote_alg1_problem, peak_out),
+         offsetof(rot_vote_alg1_result, npeaks), offsetof(rot_vote_alg1_result, peak_threshold));
   printf("%zu %zu %zu %zu %zu\n", sizeof(rot_vote_alg1_problem), sizeof(rot_vote_alg1_result),
          offsetof(rot_vote_alg1_problem, accumulator), offsetof(rot_vote_alg1_result, samples_cast),
          offsetof(rot_vote_alg1_result, ms_gpu));
@@ -72,11 +74,15 @@ int main(void) {
     assert sizes[5] == rv.rot_vote_config.cuda_stream.offset
     assert sizes[6] == rv.rot_vote_problem.delta.offset
     assert sizes[7] == rv.rot_vote_config.chart.offset
-    assert sizes[8] == ctypes.sizeof(rv.rot_vote_alg1_problem)
-    assert sizes[9] == ctypes.sizeof(rv.rot_vote_alg1_result)
-    assert sizes[10] == rv.rot_vote_alg1_problem.accumulator.offset
-    assert sizes[11] == rv.rot_vote_alg1_result.samples_cast.offset
-    assert sizes[12] == rv.rot_vote_alg1_result.ms_gpu.offset
+    assert sizes[8] == ctypes.sizeof(rv.rot_vote_peak)
+    assert sizes[9] == rv.rot_vote_alg1_problem.peak_out.offset
+    assert sizes[10] == rv.rot_vote_alg1_result.npeaks.offset
+    assert sizes[11] == rv.rot_vote_alg1_result.peak_threshold.offset
+    assert sizes[12] == ctypes.sizeof(rv.rot_vote_alg1_problem)
+    assert sizes[13] == ctypes.sizeof(rv.rot_vote_alg1_result)
+    assert sizes[14] == rv.rot_vote_alg1_problem.accumulator.offset
+    assert sizes[15] == rv.rot_vote_alg1_result.samples_cast.offset
+    assert sizes[16] == rv.rot_vote_alg1_result.ms_gpu.offset
 
 
 def test_missing_library_fails_loudly(tmp_path):

@@ -141,3 +141,65 @@ def test_alg1_noise_free_winner_is_the_true_rotation_cell():
     assert r.status == rv.OK
     # a cell of side 2/n in the chart spans at most 2 * sqrt(3) * (2/n) on S^3 (conformal factor <= 2)
     assert quat_angle(r.q, p.q_true) <= 2 * (2 * np.sqrt(3) * 2 / side)
+
+
+# ---- multiple rotations (Sec. 4.4): peaks by greedy suppression ----
+
+def run_peaks(a, b, J, side, M, theta, min_count=0):
+    import oracle
+    acc = np.zeros(side ** 3, np.int32)
+    with rv.Context() as ctx:
+        r = ctx.alg1([(dev(a), dev(b), J, side, acc)], peaks=M, nms_angle=theta, min_count=min_count)[0]
+    theta32 = float(np.float32(theta))  # the ABI carries the angle as float32
+    o_idx, o_cnt, o_q, o_T = oracle.alg1_peaks(acc, side, M, theta32, min_count=min_count,
+                                               kmax=rv.ALG1_PEAK_CANDIDATES)
+    return r, acc, (o_idx, o_cnt, o_q, o_T)
+
+
+def check_peaks(r, o):
+    o_idx, o_cnt, o_q, o_T = o
+    assert r.status == rv.OK
+    assert r.peak_threshold == o_T
+    assert [p[0] for p in r.peaks] == list(o_idx)
+    assert [p[1] for p in r.peaks] == list(o_cnt)
+    for (_, _, q), oq in zip(r.peaks, o_q):
+        assert np.array_equal(q, oq)
+
+
+@pytest.mark.parametrize("M,theta,min_count", [(1, 0.1, 0), (6, 0.15, 0), (64, 0.05, 0), (9, 0.3, 40), (12, 0.0, 0)])
+def test_alg1_peaks_multi_motion_scene(M, theta, min_count):
+    mp = synth.make_multi_problem(4, 800, sigma=0.01, outlier_frac=0.5, seed=2700 + M)
+    r, acc, o = run_peaks(mp.a, mp.b, 540, 120, M, theta, min_count)
+    check_peaks(r, o)
+    if M == 1:
+        assert r.peaks[0][0] == r.best_cell and r.peaks[0][1] == r.best_count
+
+
+def test_alg1_peaks_threshold_above_one():
+    """1e5 pairs at the paper's resolution: more than 16384 cells are voted, so the
+    candidate threshold T rises above 1, exactly as the oracle computes it."""
+    p = synth.make_problem(100000, 0.99, 0.01, 0.03, seed=2801)
+    r, acc, o = run_peaks(p.a, p.b, 180, 360, 9, 0.1)
+    assert o[3] > 1
+    check_peaks(r, o)
+
+
+def test_alg1_peaks_recover_nine_motions():
+    """The paper's multiple-rotation experiment shape: 9 motions x 3000 pairs, noise
+    0.01, J = 540: the 9 highest peaks are the 9 rotations."""
+    from tests._util import quat_angle
+    mp = synth.make_multi_problem(9, 3000, sigma=0.01, seed=2802)
+    r, acc, o = run_peaks(mp.a, mp.b, 540, 360, 9, 0.1)
+    check_peaks(r, o)
+    assert len(r.peaks) == 9
+    for qt in mp.q_true:
+        assert min(quat_angle(q, qt) for _, _, q in r.peaks) < 0.05
+
+
+def test_alg1_peaks_argument_errors():
+    p = synth.make_problem(300, 0.5, 0.01, 0.03, seed=2803)
+    with rv.Context() as ctx:
+        for kw in (dict(peaks=65, nms_angle=0.1), dict(peaks=3, nms_angle=-1.0), dict(peaks=3, nms_angle=float("nan")),
+                   dict(peaks=3, nms_angle=0.1, min_count=-2)):
+            r = ctx.alg1([(dev(p.a), dev(p.b), 90, 32)], **kw)[0]
+            assert r.status == rv.EINVAL

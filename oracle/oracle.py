@@ -19,7 +19,7 @@ __all__ = [
     "lib", "pair_M", "pair_S", "quad", "quat_to_R", "cell_exists", "cell_geom", "tau",
     "level_cells", "vote_cells", "rank", "jacobi4", "canonical", "solve", "OracleResult",
     "AMBIG", "cell_of_point", "fit_cell", "alg1_basis", "alg1_cell", "alg1_table", "alg1", "alg1_centre",
-    "alg1_peaks",
+    "alg1_peaks", "pose_pairs", "pose_translation", "pose",
 ]
 
 AMBIG = 1e-6
@@ -90,6 +90,12 @@ def lib():
         L.rvo_alg1_peaks.argtypes = [_i32p, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_double, _i64p, _i32p, _f64p,
                                      C.POINTER(C.c_int32)]
         L.rvo_alg1_peaks.restype = C.c_int
+        L.rvo_pose_pairs.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                     C.c_int64]
+        L.rvo_pose_pairs.restype = C.c_int64
+        L.rvo_pose_translation.argtypes = [_f32p, _f32p, C.c_int64, _f64p, C.c_double, C.c_int, _f64p,
+                                           C.POINTER(C.c_int64)]
+        L.rvo_pose_translation.restype = C.c_int32
         _lib = L
     return _lib
 
@@ -318,3 +324,40 @@ def alg1_peaks(acc, n: int, M: int, theta: float, min_count: int = 1, kmax: int 
     k = lib().rvo_alg1_peaks(acc, int(n), int(M), int(min_count), int(kmax), float(theta), pidx, pcnt,
                              pq.reshape(-1), C.byref(T))
     return pidx[:k], pcnt[:k], pq[:k], int(T.value)
+
+
+# ---- rigid pose (Sec. 4.5): pairwise length check, rotation vote, translation vote ----
+
+def pose_pairs(x, y, mu: float, lmin: float = 0.0, want_pairs: bool = True):
+    """(a[K, 3], b[K, 3]) float32 unit pairs (m/|m|, n/|n|) of the kept i < j pairs, lexicographic order."""
+    x, y = _f32_pairs(x, y)
+    n = x.shape[0]
+    L = lib()
+    k = int(L.rvo_pose_pairs(x.reshape(-1), y.reshape(-1), n, float(mu), float(lmin), None, None, 0))
+    if not want_pairs:
+        return k
+    a = np.zeros((max(k, 1), 3), np.float32)
+    b = np.zeros((max(k, 1), 3), np.float32)
+    L.rvo_pose_pairs(x.reshape(-1), y.reshape(-1), n, float(mu), float(lmin), a.ctypes.data, b.ctypes.data, k)
+    return a[:k], b[:k]
+
+
+def pose_translation(x, y, R, L_half: float = 5.0, G: int = 400):
+    """(t[3] cell centre, cell index, count) of the translation vote with rotation R."""
+    x, y = _f32_pairs(x, y)
+    t = np.zeros(3)
+    cell = C.c_int64()
+    cnt = lib().rvo_pose_translation(x.reshape(-1), y.reshape(-1), x.shape[0],
+                                     np.ascontiguousarray(R, dtype=np.float64).reshape(9), float(L_half), int(G), t,
+                                     C.byref(cell))
+    return t, int(cell.value), int(cnt)
+
+
+def pose(x, y, mu: float, delta: float, grid_n: int, levels: int, lmin: float = 0.0, L_half: float = 5.0,
+         G: int = 400, chart: int = 0, nthreads: int = 1):
+    """The whole pose pipeline: kept pairs, the rotation solve over them, the translation vote.
+    Returns (OracleResult of the rotation, t, cell, count, kept pairs)."""
+    a, b = pose_pairs(x, y, mu, lmin)
+    r = solve(a, b, delta, grid_n=grid_n, levels=levels, chart=chart, nthreads=nthreads, trace=False)
+    t, cell, cnt = pose_translation(x, y, r.R, L_half, G)
+    return r, t, cell, cnt, len(a)

@@ -823,3 +823,92 @@ void rvo_alg1_table(int J, double *cs) {
         cs[2 * j + 1] = sin(alpha / 2.0);
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Rigid pose (Sec. 4.5): pairwise differences with the length check,  */
+/* rotation from the kept pairs, translation by voting.                */
+/* ------------------------------------------------------------------ */
+
+/* For every i < j (in lexicographic order): m = x_i - x_j, n = y_i - y_j
+ * (from the float32 points, in double), |m| = sqrt(m.m), |n| = sqrt(n.n).
+ * The pair is kept iff |m| > lmin, |n| > lmin and | |m| - |n| | <= mu (the
+ * rotation-invariant length check of Sec. 4.5.1), and then becomes the unit
+ * correspondence (m / |m|, n / |n|), rounded to float32, written to a_out,
+ * b_out when they are not NULL (up to cap pairs).  Returns the number kept. */
+int64_t rvo_pose_pairs(const float *x, const float *y, int64_t n, double mu, double lmin, float *a_out, float *b_out,
+                       int64_t cap) {
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j) {
+            double m[3], v[3];
+            for (int c = 0; c < 3; ++c) {
+                m[c] = (double)x[3 * i + c] - (double)x[3 * j + c];
+                v[c] = (double)y[3 * i + c] - (double)y[3 * j + c];
+            }
+            const double lm = sqrt((m[0] * m[0] + m[1] * m[1]) + m[2] * m[2]);
+            const double ln = sqrt((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
+            if (!(lm > lmin && ln > lmin && fabs(lm - ln) <= mu)) continue;
+            if (a_out && b_out && k < cap)
+                for (int c = 0; c < 3; ++c) {
+                    a_out[3 * k + c] = (float)(m[c] / lm);
+                    b_out[3 * k + c] = (float)(v[c] / ln);
+                }
+            ++k;
+        }
+    return k;
+}
+
+static int cmp_i64(const void *p, const void *q) {
+    const int64_t a = *(const int64_t *)p, b = *(const int64_t *)q;
+    return (a > b) - (a < b);
+}
+
+/* Translation by voting (Sec. 4.5.2): each correspondence gives the
+ * candidate t_i = y_i - R x_i (row k: y_k - ((R_k0 x_0 + R_k1 x_1) + R_k2 x_2)),
+ * counted in the cell c = floor((t + L) / s), s = 2L / G, of a G^3 grid over
+ * [-L, L]^3 (candidates outside are not counted).  The winner is the largest
+ * count, ties to the smallest linear index (c_z G + c_y) G + c_x; t is its
+ * centre -L + (c + 1/2) s.  Returns the winner's count (0: no candidate). */
+int32_t rvo_pose_translation(const float *x, const float *y, int64_t n, const double R[9], double L, int G, double t[3],
+                             int64_t *cell) {
+    const double s = (2.0 * L) / (double)G;
+    int64_t *key = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t nk = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c3[3];
+        int ok = 1;
+        for (int r = 0; r < 3; ++r) {
+            const double rx = (R[3 * r] * (double)x[3 * i] + R[3 * r + 1] * (double)x[3 * i + 1]) +
+                              R[3 * r + 2] * (double)x[3 * i + 2];
+            const double tk = (double)y[3 * i + r] - rx;
+            const double f = floor((tk + L) / s);
+            if (!(f >= 0.0 && f < (double)G)) ok = 0;
+            c3[r] = ok ? (int64_t)f : 0;
+        }
+        if (ok) key[nk++] = (c3[2] * G + c3[1]) * G + c3[0];
+    }
+    /* counts by sorting the keys */
+    qsort(key, (size_t)nk, sizeof(int64_t), cmp_i64);
+    int64_t best = -1;
+    int32_t bc = 0;
+    for (int64_t a = 0; a < nk;) {
+        int64_t b = a;
+        while (b < nk && key[b] == key[a]) ++b;
+        if (b - a > bc) { /* strictly larger: the first (smallest) key keeps ties */
+            bc = (int32_t)(b - a);
+            best = key[a];
+        }
+        a = b;
+    }
+    free(key);
+    *cell = best;
+    if (best < 0) {
+        t[0] = t[1] = t[2] = 0.0;
+        return 0;
+    }
+    const int64_t cx = best % G, cy = (best / G) % G, cz = best / ((int64_t)G * G);
+    t[0] = -L + ((double)cx + 0.5) * s;
+    t[1] = -L + ((double)cy + 0.5) * s;
+    t[2] = -L + ((double)cz + 0.5) * s;
+    return bc;
+}

@@ -31,6 +31,8 @@ __all__ = [
     "serving_stream",
     "MultiProblem",
     "make_multi_problem",
+    "PoseProblem",
+    "make_pose_problem",
     "SEED_BASE",
 ]
 
@@ -209,3 +211,40 @@ def make_multi_problem(models: int, per_model: int, sigma: float = 0.01, outlier
     perm = rng.permutation(len(label))
     return MultiProblem(a=a[perm].astype(np.float32), b=b[perm].astype(np.float32), q_true=np.array(qs),
                         label=label[perm])
+
+
+@dataclasses.dataclass
+class PoseProblem:
+    """Point correspondences under a rigid motion y = R x + t (Sec. 4.5)."""
+
+    x: np.ndarray          # float32 [n, 3]
+    y: np.ndarray          # float32 [n, 3]
+    q_true: np.ndarray     # float64 [4], w >= 0
+    R_true: np.ndarray     # float64 [3, 3]
+    t_true: np.ndarray     # float64 [3]
+    outlier: np.ndarray    # bool [n]
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+
+def make_pose_problem(n: int, rho: float, sigma: float, seed: int = SEED_BASE + 6) -> PoseProblem:
+    """The paper's rigid-pose protocol (Sec. 5.4.1): x_i uniform in [-1, 1]^3,
+    y_i = R x_i + t + sigma N(0, I3) with t uniform in [-1, 1]^3; an exact
+    round(rho n) subset (seeded permutation) has x_i and y_i both uniform in
+    [-1, 1]^3."""
+    rng = np.random.default_rng(seed)
+    q, R = _random_rotation(rng)
+    t = rng.uniform(-1.0, 1.0, 3)
+    x = rng.uniform(-1.0, 1.0, (n, 3))
+    y = x @ R.T + t
+    if sigma > 0:
+        y = y + sigma * rng.standard_normal((n, 3))
+    n_out = int(round(rho * n))
+    perm = rng.permutation(n)
+    out = np.zeros(n, dtype=bool)
+    out[perm[:n_out]] = True
+    x[out] = rng.uniform(-1.0, 1.0, (n_out, 3))
+    y[out] = rng.uniform(-1.0, 1.0, (n_out, 3))
+    return PoseProblem(x=x.astype(np.float32), y=y.astype(np.float32), q_true=q, R_true=R, t_true=t, outlier=out)

@@ -337,6 +337,40 @@ def bench_alg1(rv, synth, torch, stream, flush, peaks, reps: int = 5):
     return res
 
 
+def bench_pose(rv, synth, torch, stream, flush, reps: int = 5):
+    """Rigid pose (Sec. 4.5) on the paper's default synthetic setting (Sec. 5.4.1): N = 5000,
+    90% outliers, noise 0.01; mu_t = 0.04; rotation vote 32^3 + 2 levels, delta = 0.03; the
+    paper's 400^3 translation grid over [-5, 5]^3.  Times the whole call on the device."""
+    import numpy as np
+    p = synth.make_pose_problem(5000, 0.9, 0.01, seed=3003)
+    x, y = torch.from_numpy(p.x).cuda(), torch.from_numpy(p.y).cuda()
+    res = {}
+    for prec in ("fp32", "fp16x2"):
+        ctx = rv.Context(grid_n=32, levels=2, precision=prec, cuda_stream=stream.cuda_stream)
+        for _ in range(2):
+            ctx.pose(x, y, 0.04, 0.03)
+        ts, front = [], []
+        for _ in range(reps):
+            flush.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            r = ctx.pose(x, y, 0.04, 0.03)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(s0.elapsed_time(s1))
+            front.append(r.ms_gpu)
+        ctx.close()
+        res[prec] = {"ms_per_pose": sum(ts) / len(ts), "ms_pairs_and_translation": sum(front) / len(front),
+                     "ms_rotation_solve": r.rot.ms_gpu, "pairs_tested": r.pairs_tested, "pairs_kept": r.pairs_kept,
+                     "pairs_rechecked": r.pairs_rechecked, "rotation_tests": r.rot.tests,
+                     "angle_to_truth_rad": _angle(r.rot.q, p.q_true),
+                     "translation_error": float(np.linalg.norm(r.t - p.t_true)), "status": r.status}
+    res["workload"] = ("rigid pose: N = 5000 correspondences, 90% outliers, noise 0.01, mu_t = 0.04, "
+                       "32^3 + 2 levels, delta 0.03, 400^3 translation grid over [-5, 5]^3")
+    res["paper_note"] = "the paper plots its rigid-pose running time (Fig. 9) without a table; context only"
+    return res
+
+
 def bench_serving(rv, synth, torch, seconds: float, rate_hz: float = 2000.0, distinct: int = 512):
     """Poisson arrivals at rate_hz (N log-uniform [100, 1e5], outliers U[0.8, 0.99],
     sigma 0.01, delta 0.03; 32^3 + 2 levels, FP16 hi/lo form) through
@@ -619,11 +653,12 @@ def main():
                                        "angle_to_truth_rad": _angle(rr.q, p.q_true)}
         cx.close()
 
-    batched = serving = alg1 = None
+    batched = serving = alg1 = pose = None
     if not args.no_extra and ws == 1:
         batched = bench_batched(rv, synth, torch, stream, flush)
         serving = bench_serving(rv, synth, torch, args.serve_seconds)
         alg1 = bench_alg1(rv, synth, torch, stream, flush, peaks)
+        pose = bench_pose(rv, synth, torch, stream, flush)
 
     lat = per
     line = {
@@ -644,6 +679,7 @@ def main():
         "batched": batched,
         "serving": serving,
         "alg1": alg1,
+        "pose": pose,
         "clocks": clocks,
         "cpu_baseline": cpu,
         "result": {"status": res0.status, "angle_to_truth_rad": None, "rechecked": res0.rechecked,

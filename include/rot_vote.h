@@ -339,6 +339,59 @@ typedef struct {
  * ECUDA / EINVAL when it could not run at all. */
 int rot_vote_alg1(rot_vote_ctx *ctx, const rot_vote_alg1_problem *p, int n_problems, rot_vote_alg1_result *out);
 
+/* ---- Rigid pose (Sec. 4.5): rotation and translation from point correspondences ----
+ *
+ * y_i = R x_i + t for the inliers.  Every pair i < j gives the translation-free
+ * correspondence R m = n with m = x_i - x_j, n = y_i - y_j; the rotation-invariant
+ * length check of Sec. 4.5.1 keeps the pair iff
+ *   |m| > min_length,  |n| > min_length  and  | |m| - |n| | <= mu
+ * (lengths sqrt((v0^2 + v1^2) + v2^2) in IEEE double from the float32 points).
+ * The kept pairs, as the float32 unit vectors (m / |m|, n / |n|) in (i, j)
+ * lexicographic order, are solved by the context's rotation vote
+ * (rot_vote_solve with delta, grid_n, levels).  Translation (Sec. 4.5.2): every
+ * correspondence gives t_i = y_i - R x_i with the solved R (row r:
+ * y_r - ((R_r0 x_0 + R_r1 x_1) + R_r2 x_2), double), counted in the cell
+ * floor((t + L) / s), s = 2L / G, of a G^3 grid over [-L, L]^3; the winner is
+ * the largest count (ties: the smallest index (c_z G + c_y) G + c_x) and t is its
+ * centre -L + (c + 1/2) s.  The kept pairs equal the IEEE double definition
+ * exactly: each length check is made in FP32 and, within its rigorous error
+ * band of a threshold, in FP64. */
+typedef struct {
+    const float *x;         /* [n][3] float32 points, host or device; finite, |coordinate| <= 1e15 */
+    const float *y;
+    int64_t n;              /* 2 <= n <= 65536 */
+    float mu;               /* length tolerance mu_t > 0 */
+    float min_length;       /* >= 0: shorter differences are dropped (no direction) */
+    float delta;            /* rotation vote tolerance, as rot_vote_problem.delta */
+    int grid_n;             /* rotation grid, as rot_vote_problem (0 = context defaults) */
+    int levels;
+    float t_half;           /* L, the translation domain [-L, L]^3; 0 = 5 */
+    int t_cells;            /* G, cells per axis, 1..1024; 0 = 400 (step 0.025 for L = 5) */
+    float *pairs_a;         /* optional (pairs_cap > 0): host or device float32 [pairs_cap][3] receiving */
+    float *pairs_b;         /*   the first pairs_cap kept unit pairs; owned by the caller */
+    int64_t pairs_cap;
+} rot_vote_pose_problem;
+
+typedef struct {
+    rot_vote_result rot;    /* the rotation solve over the kept pairs (its own status and ms_gpu) */
+    double t[3];            /* translation: the centre of the winning cell */
+    int64_t t_cell;         /* its linear index; -1 when no candidate fell inside [-L, L]^3 */
+    int64_t pairs_tested;   /* n (n - 1) / 2 */
+    int64_t pairs_kept;
+    int64_t pairs_rechecked; /* length checks decided in FP64 */
+    int32_t t_count;        /* candidates in the winning cell */
+    int32_t status;         /* OK; EINVAL (bad argument or point); EDEGENERATE (fewer than 2 pairs kept, or
+                               the rotation fit degenerate); otherwise the rotation solve's status */
+    float ms_gpu;           /* device time of the pair stage and the translation vote */
+    float pad;
+} rot_vote_pose_result;
+
+/* Solve n_problems pose problems one after another on the context's stream and
+ * block until out[] is written.  Device memory for the kept pairs (24 bytes per
+ * pair) counts against config.device_mem_budget.  Returns OK when the call ran
+ * (per-problem status in out[k].status), or ENOMEM / ECUDA / EINVAL. */
+int rot_vote_pose(rot_vote_ctx *ctx, const rot_vote_pose_problem *p, int n_problems, rot_vote_pose_result *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -128,6 +128,11 @@ class Context {
     int a1_J = 0;            // J of the angle tables in a1_mem (0 = none)
     size_t a1_toff = 0;      // their offset
     bool a1_peaks_attr = false;  // dynamic shared memory of the peak kernel raised
+    // rigid pose (rv_pose.cu): row counts and offsets, translation table, staged points, kept pairs
+    void *ps_mem = nullptr;
+    size_t ps_cap = 0;
+    void *ps_hdr_h = nullptr;
+    cudaEvent_t ps_ev[2] = {nullptr, nullptr};
     void *a1_hdr_h = nullptr;
     cudaEvent_t a1_ev[2] = {nullptr, nullptr};
 
@@ -166,6 +171,9 @@ class Context {
     int stage_times(rot_vote_stage *out, int cap, int *count);
     int alg1(const rot_vote_alg1_problem *p, int n, rot_vote_alg1_result *out);
     void alg1_release();
+    int pose(const rot_vote_pose_problem *p, int n, rot_vote_pose_result *out);
+    int pose_ensure(size_t need);
+    void pose_release();
     int submit(const rot_vote_problem &p, uint64_t *ticket);
     int poll(uint64_t ticket, rot_vote_result *out, int timeout_us);
     void sched_loop();

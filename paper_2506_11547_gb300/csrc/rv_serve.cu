@@ -66,6 +66,7 @@ void Context::shutdown() {
     waves.clear();
     main_wave.release(*this);
     alg1_release();
+    pose_release();
     for (auto ev : prof_ev) cudaEventDestroy(ev);
     prof_ev.clear();
     for (auto &g : grids)

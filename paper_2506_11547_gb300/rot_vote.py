@@ -63,6 +63,18 @@ class rot_vote_alg1_result(C.Structure):
                 ("ms_gpu", C.c_float), ("npeaks", C.c_int32), ("peak_threshold", C.c_int32), ("pad", C.c_int32)]
 
 
+class rot_vote_pose_problem(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("n", C.c_int64), ("mu", C.c_float), ("min_length", C.c_float),
+                ("delta", C.c_float), ("grid_n", C.c_int), ("levels", C.c_int), ("t_half", C.c_float),
+                ("t_cells", C.c_int), ("pairs_a", C.c_void_p), ("pairs_b", C.c_void_p), ("pairs_cap", C.c_int64)]
+
+
+class rot_vote_pose_result(C.Structure):
+    _fields_ = [("rot", rot_vote_result), ("t", C.c_double * 3), ("t_cell", C.c_int64), ("pairs_tested", C.c_int64),
+                ("pairs_kept", C.c_int64), ("pairs_rechecked", C.c_int64), ("t_count", C.c_int32),
+                ("status", C.c_int32), ("ms_gpu", C.c_float), ("pad", C.c_float)]
+
+
 class rot_vote_stage(C.Structure):
     _fields_ = [("kind", C.c_int32), ("level", C.c_int32), ("ms", C.c_float)]
 
@@ -74,7 +86,7 @@ _lib = None
 
 EXPORTS = ("rot_vote_create", "rot_vote_solve", "rot_vote_submit", "rot_vote_poll", "rot_vote_level_trace",
            "rot_vote_stage_times", "rot_vote_destroy", "rot_vote_last_error", "rot_vote_count_cells_static",
-           "rot_vote_alg1")
+           "rot_vote_alg1", "rot_vote_pose")
 
 
 def load(path: str = LIB_PATH):
@@ -108,6 +120,9 @@ def load(path: str = LIB_PATH):
     L.rot_vote_alg1.argtypes = [C.c_void_p, C.POINTER(rot_vote_alg1_problem), C.c_int,
                                 C.POINTER(rot_vote_alg1_result)]
     L.rot_vote_alg1.restype = C.c_int
+    L.rot_vote_pose.argtypes = [C.c_void_p, C.POINTER(rot_vote_pose_problem), C.c_int,
+                                C.POINTER(rot_vote_pose_result)]
+    L.rot_vote_pose.restype = C.c_int
     _lib = L
     return L
 
@@ -156,6 +171,25 @@ class Alg1Result:
         return Alg1Result(q=np.array(r.q[:]), R=np.array(r.R[:]).reshape(3, 3), best_count=r.best_count,
                           status=r.status, best_cell=r.best_cell, samples_cast=r.samples_cast,
                           rechecked=r.rechecked, ms_gpu=r.ms_gpu, peak_threshold=r.peak_threshold, peaks=pk)
+
+
+@dataclasses.dataclass
+class PoseResult:
+    rot: Result
+    t: np.ndarray
+    t_cell: int
+    t_count: int
+    pairs_tested: int
+    pairs_kept: int
+    pairs_rechecked: int
+    status: int
+    ms_gpu: float
+
+    @staticmethod
+    def of(r: rot_vote_pose_result) -> "PoseResult":
+        return PoseResult(rot=Result.of(r.rot), t=np.array(r.t[:]), t_cell=r.t_cell, t_count=r.t_count,
+                          pairs_tested=r.pairs_tested, pairs_kept=r.pairs_kept, pairs_rechecked=r.pairs_rechecked,
+                          status=r.status, ms_gpu=r.ms_gpu)
 
 
 class RotVoteError(RuntimeError):
@@ -298,6 +332,28 @@ class Context:
     def alg1_raw(self, arr, n, out):
         """Calls rot_vote_alg1 on prepared ctypes arrays (for timing loops)."""
         return self._check(self._L.rot_vote_alg1(self._h, arr, n, out))
+
+    def pose(self, x, y, mu: float, delta: float, grid_n: int = 0, levels: int = 0, min_length: float = 0.0,
+             t_half: float = 0.0, t_cells: int = 0, pairs_out=None):
+        """rot_vote_pose on one problem.  pairs_out: optional (a, b) float32 arrays or device tensors of
+        shape [cap, 3] that receive the first cap kept unit pairs.  Returns PoseResult."""
+        px, kx = _ptr(x)
+        py, ky = _ptr(y)
+        if _nrows(x) != _nrows(y):
+            raise ValueError("x and y differ in length")
+        pa = pb = None
+        cap = 0
+        if pairs_out is not None:
+            oa, ob = pairs_out
+            pa = oa.data_ptr() if hasattr(oa, "data_ptr") else oa.ctypes.data
+            pb = ob.data_ptr() if hasattr(ob, "data_ptr") else ob.ctypes.data
+            cap = int(oa.shape[0])
+        pr = rot_vote_pose_problem(px, py, _nrows(x), float(mu), float(min_length), float(delta), int(grid_n),
+                                   int(levels), float(t_half), int(t_cells), pa, pb, cap)
+        out = rot_vote_pose_result()
+        self._check(self._L.rot_vote_pose(self._h, C.byref(pr), 1, C.byref(out)))
+        del kx, ky
+        return PoseResult.of(out)
 
     def level_trace(self, problem: int, level: int, cap: int = 1 << 22):
         """(idx[n], count[n], kept_idx[k]) of one level of the last solve (keep_trace=1)."""

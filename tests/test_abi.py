@@ -51,6 +51,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(rot_vote_result, status), offsetof(rot_vote_result, ms_gpu),
          offsetof(rot_vote_config, cuda_stream), offsetof(rot_vote_problem, delta));
   printf("%zu\n", offsetof(rot_vote_config, chart));
+  printf("%zu %zu %zu %zu\n", sizeof(rot_vote_pose_problem), sizeof(rot_vote_pose_result),
+         offsetof(rot_vote_pose_problem, pairs_cap), offsetof(rot_vote_pose_result, status));
   printf("%zu %zu %zu %zu\n", sizeof(rot_vote_peak), offsetof(rot_vote_alg1_problem, peak_out),
          offsetof(rot_vote_alg1_result, npeaks), offsetof(rot_vote_alg1_result, peak_threshold));
   printf("%zu %zu %zu %zu %zu\n", sizeof(rot_vote_alg1_problem), sizeof(rot_vote_alg1_result),
@@ -74,6 +76,9 @@ int main(void) {
     assert sizes[5] == rv.rot_vote_config.cuda_stream.offset
     assert sizes[6] == rv.rot_vote_problem.delta.offset
     assert sizes[7] == rv.rot_vote_config.chart.offset
+    assert sizes[8:12] == [ctypes.sizeof(rv.rot_vote_pose_problem), ctypes.sizeof(rv.rot_vote_pose_result),
+                           rv.rot_vote_pose_problem.pairs_cap.offset, rv.rot_vote_pose_result.status.offset]
+    sizes = sizes[:8] + sizes[12:]
     assert sizes[8] == ctypes.sizeof(rv.rot_vote_peak)
     assert sizes[9] == rv.rot_vote_alg1_problem.peak_out.offset
     assert sizes[10] == rv.rot_vote_alg1_result.npeaks.offset

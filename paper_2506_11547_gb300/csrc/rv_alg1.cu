@@ -420,37 +420,55 @@ __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(const int32_t 
 
 // Peak threshold T = max(min_count, the smallest t >= 1 with
 // #{cells: count >= t} <= kPeakCand), from the histogram; -1 when even the top
-// bin holds more than kPeakCand cells.  One block.
+// bin holds more than kPeakCand cells.  One block: thread t sums bins
+// [64 t, 64 t + 64) (16-byte loads), a shuffle scan gives the suffix sums
+// S_t = #{count >= 64 t}, and the one thread whose range holds T walks its
+// 64 bins.
 __global__ void __launch_bounds__(kPeakThreads) alg1_threshold_kernel(const unsigned *__restrict__ hist,
                                                                       int min_count, A1Hdr *hdr) {
-    constexpr int per = kHistBins / kPeakThreads;
-    __shared__ unsigned long long part[kPeakThreads];
-    __shared__ int tmin[kPeakThreads / 32];
-    const int t = threadIdx.x;
+    constexpr int per = kHistBins / kPeakThreads;  // 64
+    __shared__ unsigned long long wsum[kPeakThreads / 32];
+    __shared__ int first;  // smallest thread index t with S_t <= kPeakCand
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) first = kPeakThreads;
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(hist + t * per);
     unsigned long long s = 0;
-    for (int k = 0; k < per; ++k) s += hist[t * per + k];
-    part[t] = s;
-    __syncthreads();
-    for (int off = 1; off < kPeakThreads; off <<= 1) {  // suffix sums over the threads' ranges
-        const unsigned long long v = t + off < kPeakThreads ? part[t + off] : 0ull;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+#pragma unroll
+    for (int k = 0; k < per / 4; ++k) {
+        const uint4 v = h4[k];
+        s += (unsigned long long)v.x + v.y + v.z + v.w;
     }
-    unsigned long long ge = t + 1 < kPeakThreads ? part[t + 1] : 0ull;  // cells with count >= (t + 1) per
-    int best = INT_MAX;
-    for (int k = per - 1; k >= 0; --k) {  // ge(u) is non-increasing in u: keep the smallest u that fits
-        const int u = t * per + k;
-        ge += hist[u];
-        if (u >= 1 && ge <= (unsigned long long)kPeakCand) best = u;
+    // inclusive suffix scan within the warp (lanes above)
+    unsigned long long suf = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_down_sync(0xffffffffu, suf, o);
+        if (lane + o < 32) suf += v;
     }
-    best = __reduce_min_sync(0xffffffffu, best);
-    if ((t & 31) == 0) tmin[t >> 5] = best;
+    if (lane == 0) wsum[w] = suf;  // the warp's total
     __syncthreads();
-    if (t == 0) {
-        int m = INT_MAX;
-        for (int w = 0; w < kPeakThreads / 32; ++w) m = min(m, tmin[w]);
-        hdr->peak_T = m == INT_MAX ? -1 : max(m, max(min_count, 1));
+    unsigned long long above = 0;  // totals of the warps after this one
+    for (int k = w + 1; k < kPeakThreads / 32; ++k) above += wsum[k];
+    const unsigned long long S = suf + above;  // #{count >= 64 t}
+    if (S <= (unsigned long long)kPeakCand) atomicMin(&first, t);
+    __syncthreads();
+    const int f = first;
+    // T lies in (64 (f - 1), 64 f]: thread f - 1 walks down its bins (f = 0: T = 1)
+    const int walker = f == 0 ? -1 : f - 1;
+    if (t == 0 && f == 0) {
+        hdr->peak_T = max(1, max(min_count, 1));
+        hdr->ncand = 0;
+    }
+    if (t == walker) {
+        unsigned long long ge = S - s;  // #{count >= 64 (t + 1)}
+        // T = 64 (t + 1) itself fits when t + 1 = f (S_f <= kPeakCand); above the last bin nothing is known
+        int best = t + 1 < kPeakThreads ? (t + 1) * per : INT_MAX;
+        for (int k = per - 1; k >= 0; --k) {
+            const int u = t * per + k;
+            ge += hist[u];
+            if (u >= 1 && ge <= (unsigned long long)kPeakCand) best = u;
+        }
+        hdr->peak_T = best == INT_MAX ? -1 : max(best, max(min_count, 1));
         hdr->ncand = 0;
     }
 }
@@ -482,110 +500,115 @@ __global__ void __launch_bounds__(kArgThreads) alg1_collect_kernel(const int32_t
         put(acc[r], (uint32_t)r);
 }
 
-// FP32 centre rotation of cell idx (no sign normalisation; |dot| ignores it).
-// Error per component <= 90 u against alg1_centre64 (p: 3u, |p|^2: 40u,
-// 1 + |p|^2: 41u, quotient: u), so |dot32 - dot64| <= 190 u = 1.2e-5.
-__device__ __forceinline__ float4 alg1_centre32(int side, float h, uint32_t idx) {
+// A cell's grid coordinates and 1 + |p|^2 of its centre p = -1 + (i + 1/2) h, in FP32.
+struct CellF {
+    int ix, iy, iz;
+    float s;
+};
+
+__device__ __forceinline__ CellF alg1_cellf(int side, float h, uint32_t idx) {
     const uint32_t n = (uint32_t)side;
-    const float p0 = fmaf((float)(idx % n) + 0.5f, h, -1.f);
-    const float p1 = fmaf((float)((idx / n) % n) + 0.5f, h, -1.f);
-    const float p2 = fmaf((float)(idx / (n * n)) + 0.5f, h, -1.f);
-    const float pp = fmaf(p0, p0, fmaf(p1, p1, p2 * p2));
-    const float den = 1.f + pp;
-    return make_float4(__fdiv_rn(2.f * p0, den), __fdiv_rn(2.f * p1, den), __fdiv_rn(2.f * p2, den),
-                       __fdiv_rn(pp - 1.f, den));
+    CellF c;
+    c.ix = (int)(idx % n);
+    c.iy = (int)((idx / n) % n);
+    c.iz = (int)(idx / (n * n));
+    const float p0 = fmaf((float)c.ix + 0.5f, h, -1.f);
+    const float p1 = fmaf((float)c.iy + 0.5f, h, -1.f);
+    const float p2 = fmaf((float)c.iz + 0.5f, h, -1.f);
+    c.s = 1.f + fmaf(p0, p0, fmaf(p1, p1, p2 * p2));
+    return c;
 }
 
-constexpr float kPeakBand = 3e-5f;  // FP32 |dot| within this of cos(theta/2): decided in FP64
+// e = 1 - q.q' for the centre rotations q = P'(p), q' = P'(p') of two cells, by
+// the chordal identity of the inverse projection,
+//   |P'(p) - P'(p')|^2 = 4 |p - p'|^2 / ((1 + |p|^2)(1 + |p'|^2)) = 2 - 2 q.q',
+// with p - p' = (i - i') h exact up to h, so e = 2 h^2 m / (s s'), m the integer
+// sum of squared index differences.  Relative error (FP32): h^2 3u, each s 5u
+// (p to 2u, |p|^2 and the sum 3u), product and quotient 2u: <= 16u.
+__device__ __forceinline__ float alg1_one_minus_dot(const CellF &a, const CellF &b, float h2) {
+    const int dx = a.ix - b.ix, dy = a.iy - b.iy, dz = a.iz - b.iz;
+    const float m = (float)(dx * dx + dy * dy + dz * dz);  // <= 3 * 1023^2 < 2^24: exact
+    return __fdiv_rn(2.f * h2 * m, a.s * b.s);
+}
 
-// Sorts the candidates (count desc, index asc) and picks up to M peaks by
-// greedy suppression.  One block; keys and flags in shared memory.
+// Picks up to M peaks by greedy suppression.  Each round takes the largest
+// (count, -index) key among the candidates not yet suppressed -- the first
+// unsuppressed candidate in (count desc, index asc) order -- and suppresses
+// every candidate within the angle of it (setting its key to 0).  One block,
+// the keys in shared memory.
+// |q.q'| >= cos(theta/2) <=> e <= 1 - cos(theta/2) or e >= 1 + cos(theta/2), e = 1 - q.q'.
+// The FP32 e is within 16u e of the exact value and the FP64 dot product of the
+// definition within 1e-15 of it; an e within 32u e + 1e-12 of either bound is
+// decided by the FP64 definition.
 __global__ void __launch_bounds__(kPeakThreads) alg1_peaks_kernel(const unsigned long long *__restrict__ cand,
                                                                   int side, int M, double cth, A1Hdr *hdr,
                                                                   rot_vote_peak *out) {
     extern __shared__ unsigned long long keys[];
-    unsigned char *supp = reinterpret_cast<unsigned char *>(keys + kPeakCand);
-    __shared__ double pq[ROT_VOTE_ALG1_MAX_PEAKS][4];
-    __shared__ float4 pq32[ROT_VOTE_ALG1_MAX_PEAKS];
-    __shared__ int wmin[kPeakThreads / 32];
-    __shared__ int s_first;
+    __shared__ double pq[4];
+    __shared__ CellF pcell;
+    __shared__ unsigned long long wmax[kPeakThreads / 32];
+    __shared__ unsigned long long s_pick;
     const int t = threadIdx.x;
     const int T = hdr->peak_T;
     const int nc = T < 1 ? 0 : (int)min(hdr->ncand, (unsigned)kPeakCand);
-    int P = 1;
-    while (P < nc) P <<= 1;
-    for (int i = t; i < P; i += kPeakThreads) {
-        keys[i] = i < nc ? cand[i] : 0ull;
-        supp[i] = 0;
-    }
+    for (int i = t; i < nc; i += kPeakThreads) keys[i] = cand[i];
     __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {  // bitonic sort, descending keys
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = t; i < P; i += kPeakThreads) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const unsigned long long a = keys[i], b = keys[l];
-                    if (((i & k) == 0) ? (a < b) : (a > b)) {
-                        keys[i] = b;
-                        keys[l] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    const float h = __fdiv_rn(2.f, (float)side);
-    const float lo = (float)cth - kPeakBand, hi = (float)cth + kPeakBand;
-    int np = 0, pos = 0;
+    const float h = __fdiv_rn(2.f, (float)side), h2 = h * h;
+    const float em = (float)(1.0 - cth), ep = (float)(1.0 + cth);
+    int np = 0;
     while (np < M) {
-        int first = INT_MAX;
-        for (int i = pos + t; i < nc; i += kPeakThreads)
-            if (!supp[i]) {
-                first = i;
-                break;
-            }
-        first = __reduce_min_sync(0xffffffffu, first);
-        if ((t & 31) == 0) wmin[t >> 5] = first;
+        unsigned long long best = 0;
+        for (int i = t; i < nc; i += kPeakThreads) best = keys[i] > best ? keys[i] : best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+            best = v > best ? v : best;
+        }
+        if ((t & 31) == 0) wmax[t >> 5] = best;
         __syncthreads();
         if (t == 0) {
-            int m = INT_MAX;
-            for (int w = 0; w < kPeakThreads / 32; ++w) m = min(m, wmin[w]);
-            s_first = m;
-            if (m != INT_MAX) {
-                const uint32_t idx = 0xffffffffu - (uint32_t)(keys[m] & 0xffffffffull);
+            unsigned long long m = 0;
+            for (int w = 0; w < kPeakThreads / 32; ++w) m = wmax[w] > m ? wmax[w] : m;
+            s_pick = m;
+            if (m) {
+                const uint32_t idx = 0xffffffffu - (uint32_t)(m & 0xffffffffull);
                 double q[4];
                 alg1_centre64(side, idx, q);
-                for (int c = 0; c < 4; ++c) pq[np][c] = q[c];
-                pq32[np] = alg1_centre32(side, h, idx);
+                for (int c = 0; c < 4; ++c) pq[c] = q[c];
+                pcell = alg1_cellf(side, h, idx);
                 rot_vote_peak pk;
                 for (int c = 0; c < 4; ++c) pk.q[c] = q[c];
                 pk.cell = idx;
-                pk.count = (int32_t)(keys[m] >> 32);
+                pk.count = (int32_t)(m >> 32);
                 pk.pad = 0;
                 out[np] = pk;
             }
         }
         __syncthreads();
-        const int f = s_first;
-        if (f == INT_MAX) break;
-        const float4 a = pq32[np];
-        for (int i = f + 1 + t; i < nc; i += kPeakThreads) {
-            if (supp[i]) continue;
-            const uint32_t idx = 0xffffffffu - (uint32_t)(keys[i] & 0xffffffffull);
-            const float4 b = alg1_centre32(side, h, idx);
-            const float d = fabsf(fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x))));
-            if (d >= hi) {
-                supp[i] = 1;
-            } else if (d > lo) {  // near cos(theta/2): the FP64 definition decides
+        const unsigned long long pick = s_pick;
+        if (!pick) break;
+        const CellF a = pcell;
+        for (int i = t; i < nc; i += kPeakThreads) {
+            const unsigned long long k = keys[i];
+            if (!k) continue;
+            if (k == pick) {
+                keys[i] = 0;
+                continue;
+            }
+            const uint32_t idx = 0xffffffffu - (uint32_t)(k & 0xffffffffull);
+            const float e = alg1_one_minus_dot(a, alg1_cellf(side, h, idx), h2);
+            const float b = 32.f * 5.9604645e-8f * e + 1e-12f;
+            bool sup = e <= em || e >= ep;
+            if (fabsf(e - em) <= b || fabsf(e - ep) <= b) {  // near a bound: the FP64 definition decides
                 double q[4];
                 alg1_centre64(side, idx, q);
-                const double d64 = dadd(dadd(dadd(dmul(q[0], pq[np][0]), dmul(q[1], pq[np][1])), dmul(q[2], pq[np][2])),
-                                        dmul(q[3], pq[np][3]));
-                if (fabs(d64) >= cth) supp[i] = 1;
+                const double d64 = dadd(dadd(dadd(dmul(q[0], pq[0]), dmul(q[1], pq[1])), dmul(q[2], pq[2])),
+                                        dmul(q[3], pq[3]));
+                sup = fabs(d64) >= cth;
             }
+            if (sup) keys[i] = 0;
         }
         ++np;
-        pos = f + 1;
         __syncthreads();
     }
     if (t == 0) {
@@ -782,12 +805,12 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
             }
             if (e == cudaSuccess && !a1_peaks_attr) {
                 e = cudaFuncSetAttribute(alg1_peaks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kPeakCand * (sizeof(unsigned long long) + 1)));
+                                         (int)(kPeakCand * sizeof(unsigned long long)));
                 a1_peaks_attr = e == cudaSuccess;
             }
             if (e == cudaSuccess) {
                 const double cth = cos((double)P.nms_angle / 2.0);
-                alg1_peaks_kernel<<<1, kPeakThreads, kPeakCand * (sizeof(unsigned long long) + 1), stream>>>(
+                alg1_peaks_kernel<<<1, kPeakThreads, kPeakCand * sizeof(unsigned long long), stream>>>(
                     cand, side, M, cth, hdr, pk);
                 e = cudaGetLastError();
             }

@@ -66,6 +66,72 @@ struct A1Hdr {
 };
 static_assert(sizeof(A1Hdr) <= 256, "header slot");
 
+// The accumulator in 16-bit counters, two cells per 32-bit word (cell c in word
+// c >> 1, bits 16 (c & 1) .. +15), so that an n = 360 grid (93 MB) fits in L2.
+// Counts stay exact through a record of the rare counter wraps: with E_L the
+// wraps of a word's low half and E_H the wraps of the whole word, the low cell
+// counts low + 65536 E_L and the high cell high + 65536 E_H - E_L (the low
+// half's carries land in the high half).  Words with wraps are flagged in a
+// bitmap and their counts kept in an open-addressing table.
+struct Acc16 {
+    uint32_t *w;     // [nw] counter words
+    uint32_t *bits;  // [(nw + 31) / 32] words with wraps
+    uint32_t *ekey;  // [emask + 1] word + 1 (0: empty slot)
+    uint32_t *elo;   // [emask + 1] E_L
+    uint32_t *ehi;   // [emask + 1] E_H
+    uint32_t emask;
+    int64_t nw;
+};
+
+__device__ __forceinline__ uint32_t a1_hash(uint32_t k) {
+    k ^= k >> 16;
+    k *= 0x7feb352du;
+    k ^= k >> 15;
+    k *= 0x846ca68bu;
+    k ^= k >> 16;
+    return k;
+}
+
+// Records wraps of word `word`.  The table holds twice the largest possible
+// number of wrapping words (each wrap takes 65536 increments), so the probe ends.
+__device__ __noinline__ void acc16_event(const Acc16 &A, uint32_t word, bool low_wrap, bool word_wrap) {
+    atomicOr(&A.bits[word >> 5], 1u << (word & 31));
+    uint32_t h = a1_hash(word) & A.emask;
+    for (uint32_t probe = 0; probe <= A.emask; ++probe) {
+        const uint32_t k = atomicCAS(&A.ekey[h], 0u, word + 1u);
+        if (k == 0u || k == word + 1u) {
+            if (low_wrap) atomicAdd(&A.elo[h], 1u);
+            if (word_wrap) atomicAdd(&A.ehi[h], 1u);
+            return;
+        }
+        h = (h + 1u) & A.emask;
+    }
+}
+
+__device__ __forceinline__ void acc16_add(const Acc16 &A, uint32_t cell) {
+    const uint32_t word = cell >> 1, inc = (cell & 1u) ? 0x10000u : 1u;
+    const uint32_t old = atomicAdd(&A.w[word], inc);
+    const bool lw = inc == 1u && (old & 0xffffu) == 0xffffu;
+    const bool ww = old > 0xffffffffu - inc;  // old + inc passes 2^32
+    if (lw || ww) acc16_event(A, word, lw, ww);
+}
+
+// E_L, E_H of a flagged word (0, 0 if absent).
+__device__ __forceinline__ void acc16_lookup(const Acc16 &A, uint32_t word, uint32_t &el, uint32_t &eh) {
+    el = eh = 0;
+    uint32_t h = a1_hash(word) & A.emask;
+    for (uint32_t probe = 0; probe <= A.emask; ++probe) {
+        const uint32_t k = A.ekey[h];
+        if (k == word + 1u) {
+            el = A.elo[h];
+            eh = A.ehi[h];
+            return;
+        }
+        if (k == 0u) return;
+        h = (h + 1u) & A.emask;
+    }
+}
+
 // q_b1, q_b2 of pair (a, b) (Sec. 4.1), each value the written sequence of
 // IEEE double operations.  False when w = 0 (a = -b: no circle).
 __device__ __forceinline__ bool alg1_basis(double a0, double a1, double a2, double b0, double b1, double b2,
@@ -111,21 +177,26 @@ __device__ __forceinline__ int alg1_cell64(const double q1[4], const double q2[4
     return (i[2] * n + i[1]) * n + i[0];
 }
 
-// Zeroes acc[0, cells) (if zero) and writes every pair's basis: q1f, q2f the
+// Zeroes the accumulator and its wrap record and writes every pair's basis: q1f, q2f the
 // FP32 roundings of q_b1, q_b2 (q1f.x = kNoCircle / kFp64Only flags the
 // pair), qd[4 i .. 4 i + 3] = q_b1, q_b2 in FP64.
 __global__ void __launch_bounds__(kA1Threads) alg1_prep_kernel(const float *__restrict__ a,
                                                                const float *__restrict__ b, int64_t n,
                                                                float4 *__restrict__ q1f, float4 *__restrict__ q2f,
-                                                               double2 *__restrict__ qd, int32_t *__restrict__ acc,
-                                                               int64_t cells, int zero, int J, A1Hdr *hdr) {
+                                                               double2 *__restrict__ qd, Acc16 A, int J, A1Hdr *hdr) {
     const int64_t T = (int64_t)gridDim.x * kA1Threads;
     const int64_t g = (int64_t)blockIdx.x * kA1Threads + threadIdx.x;
-    if (zero) {
-        int4 *v = reinterpret_cast<int4 *>(acc);
-        const int64_t nvec = cells >> 2;
-        for (int64_t k = g; k < nvec; k += T) v[k] = make_int4(0, 0, 0, 0);
-        for (int64_t r = (nvec << 2) + g; r < cells; r += T) acc[r] = 0;
+    {
+        uint4 *v = reinterpret_cast<uint4 *>(A.w);
+        const int64_t nvec = A.nw >> 2;
+        for (int64_t k = g; k < nvec; k += T) v[k] = make_uint4(0u, 0u, 0u, 0u);
+        for (int64_t r = (nvec << 2) + g; r < A.nw; r += T) A.w[r] = 0u;
+        for (int64_t r = g; r < (A.nw + 31) / 32; r += T) A.bits[r] = 0u;
+        for (int64_t r = g; r <= (int64_t)A.emask; r += T) {
+            A.ekey[r] = 0u;
+            A.elo[r] = 0u;
+            A.ehi[r] = 0u;
+        }
     }
     unsigned circles = 0;
     for (int64_t i = g; i < n; i += T) {
@@ -147,12 +218,14 @@ __global__ void __launch_bounds__(kA1Threads) alg1_prep_kernel(const float *__re
             if (!(fabs(n1 - 1.0) <= kNormGuard && fabs(n2 - 1.0) <= kNormGuard)) A.x = kFp64Only;
             ++circles;
         }
-        q1f[i] = A;
-        q2f[i] = B;
-        qd[4 * i + 0] = make_double2(q1[0], q1[1]);
-        qd[4 * i + 1] = make_double2(q1[2], q1[3]);
-        qd[4 * i + 2] = make_double2(q2[0], q2[1]);
-        qd[4 * i + 3] = make_double2(q2[2], q2[3]);
+        // streaming (evict-first) stores: the basis is read once per warp round and must
+        // not displace the accumulator from L2
+        __stcs(&q1f[i], A);
+        __stcs(&q2f[i], B);
+        __stcs(&qd[4 * i + 0], make_double2(q1[0], q1[1]));
+        __stcs(&qd[4 * i + 1], make_double2(q1[2], q1[3]));
+        __stcs(&qd[4 * i + 2], make_double2(q2[0], q2[1]));
+        __stcs(&qd[4 * i + 3], make_double2(q2[2], q2[3]));
     }
     const unsigned cw = __reduce_add_sync(0xffffffffu, circles);
     if ((threadIdx.x & 31) == 0 && cw) atomicAdd(&hdr->cast, (unsigned long long)cw * (unsigned long long)J);
@@ -160,8 +233,8 @@ __global__ void __launch_bounds__(kA1Threads) alg1_prep_kernel(const float *__re
 
 // A warp's queued samples (pair << 16 | angle), 32 per pass, in FP64.
 __device__ __forceinline__ void alg1_drain(const unsigned long long *wq, int qn, const double2 *__restrict__ qd,
-                                           const double2 *__restrict__ t64, int side, double hd,
-                                           int32_t *__restrict__ acc, int lane) {
+                                           const double2 *__restrict__ t64, int side, double hd, const Acc16 &A,
+                                           int lane) {
     for (int k = lane; k < qn; k += 32) {
         const unsigned long long e = wq[k];
         const int64_t i = (int64_t)(e >> 16);
@@ -169,7 +242,7 @@ __device__ __forceinline__ void alg1_drain(const unsigned long long *wq, int qn,
         const double2 u0 = qd[4 * i], u1 = qd[4 * i + 1], u2 = qd[4 * i + 2], u3 = qd[4 * i + 3];
         const double q1[4] = {u0.x, u0.y, u1.x, u1.y}, q2[4] = {u2.x, u2.y, u3.x, u3.y};
         const double2 cs = t64[jj];
-        atomicAdd(&acc[alg1_cell64(q1, q2, cs.x, cs.y, side, hd)], 1);
+        acc16_add(A, (uint32_t)alg1_cell64(q1, q2, cs.x, cs.y, side, hd));
     }
 }
 
@@ -181,8 +254,8 @@ __global__ void __launch_bounds__(kA1Threads) alg1_vote_kernel(const float4 *__r
                                                                const double2 *__restrict__ qd,
                                                                const float2 *__restrict__ t32,
                                                                const double2 *__restrict__ t64, int J, int side,
-                                                               int32_t *__restrict__ acc, A1Hdr *hdr, int64_t total,
-                                                               int64_t adv_p, int adv_j) {
+                                                               Acc16 acc, A1Hdr *hdr, int64_t total, int64_t adv_p,
+                                                               int adv_j) {
     __shared__ unsigned long long queue[kA1Warps][kWarpQ];
     const int lane = threadIdx.x & 31;
     unsigned long long *wq = queue[threadIdx.x >> 5];
@@ -204,9 +277,9 @@ __global__ void __launch_bounds__(kA1Threads) alg1_vote_kernel(const float4 *__r
         for (int k = 0; k < kA1U; ++k) {
             bool slow = false;
             if (base + 32 * k + lane < total) {
-                const float4 A = __ldg(&q1f[pp]);
+                const float4 A = __ldcs(&q1f[pp]);
                 if (A.x > 0.f) {
-                    const float4 B = __ldg(&q2f[pp]);
+                    const float4 B = __ldcs(&q2f[pp]);
                     const float2 cs = __ldg(&t32[jj]);
                     const float q0 = fmaf(A.x, cs.x, B.x * cs.y);
                     const float q1 = fmaf(A.y, cs.x, B.y * cs.y);
@@ -224,7 +297,7 @@ __global__ void __launch_bounds__(kA1Threads) alg1_vote_kernel(const float4 *__r
                         const int i0 = min(max((int)f0, 0), side - 1);
                         const int i1 = min(max((int)f1, 0), side - 1);
                         const int i2 = min(max((int)f2, 0), side - 1);
-                        atomicAdd(&acc[(i2 * side + i1) * side + i0], 1);
+                        acc16_add(acc, (uint32_t)((i2 * side + i1) * side + i0));
                     }
                 } else {
                     slow = A.x == kFp64Only;
@@ -317,60 +390,84 @@ __device__ __forceinline__ void hist_add(int c, unsigned long long &nib, unsigne
     }
 }
 
+// The counts of one word's two cells (cells 2 wi, 2 wi + 1) from its stored
+// halves and, for a word with wraps, its record.
+__device__ __forceinline__ void acc16_pair(const Acc16 &A, uint32_t x, uint32_t wi, bool ev, int64_t &lo,
+                                           int64_t &hi) {
+    lo = x & 0xffffu;
+    hi = x >> 16;
+    if (ev) {
+        uint32_t el, eh;
+        acc16_lookup(A, wi, el, eh);
+        lo += 65536ll * el;
+        hi += 65536ll * eh - el;
+    }
+}
+
+// Visits every word of the accumulator: f(x, word index, has wraps), with
+// four 16-byte loads in flight per thread and the wrap bitmap read once per
+// four words.
+template <class F>
+__device__ __forceinline__ void acc16_scan(const Acc16 &A, F &&f) {
+    const int64_t nvec = A.nw >> 2;
+    const uint4 *v = reinterpret_cast<const uint4 *>(A.w);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; k + 3 * stride < nvec; k += 4 * stride) {
+        uint4 c[4];
+        uint32_t bm[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = __ldcs(v + k + u * stride);
+            bm[u] = A.bits[(k + u * stride) >> 3] >> (((k + u * stride) & 7) * 4);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t wi = (uint32_t)((k + u * stride) << 2);
+            f(c[u].x, wi, (bm[u] & 1u) != 0);
+            f(c[u].y, wi + 1, (bm[u] & 2u) != 0);
+            f(c[u].z, wi + 2, (bm[u] & 4u) != 0);
+            f(c[u].w, wi + 3, (bm[u] & 8u) != 0);
+        }
+    }
+    for (; k < nvec; k += stride) {
+        const uint4 c = __ldcs(v + k);
+        const uint32_t bm = A.bits[k >> 3] >> ((k & 7) * 4);
+        const uint32_t wi = (uint32_t)(k << 2);
+        f(c.x, wi, (bm & 1u) != 0);
+        f(c.y, wi + 1, (bm & 2u) != 0);
+        f(c.z, wi + 2, (bm & 4u) != 0);
+        f(c.w, wi + 3, (bm & 8u) != 0);
+    }
+    for (int64_t r = (nvec << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < A.nw; r += stride)
+        f(A.w[r], (uint32_t)r, ((A.bits[r >> 5] >> (r & 31)) & 1u) != 0);
+}
+
 // (count, -index) maximum over the accumulator; with HIST also the count
-// histogram.  The last block to finish writes the result.
+// histogram.  Words with wraps are left to the last block, which counts them
+// from the wrap record and writes the result.  A cell past the grid (the high
+// half of the last word when n^3 is odd) is never incremented: its count 0 and
+// index cannot win and add nothing to the histogram.
 template <bool HIST>
-__global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(const int32_t *__restrict__ acc, int side,
-                                                                  A1Hdr *hdr, unsigned *__restrict__ hist) {
+__global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(Acc16 A, int side, A1Hdr *hdr,
+                                                                  unsigned *__restrict__ hist) {
     __shared__ unsigned sh[HIST ? kHistSmem : 1];
     if (HIST) {
         for (int b = threadIdx.x; b < kHistSmem; b += kArgThreads) sh[b] = 0;
         __syncthreads();
     }
     unsigned long long nib = 0;
-    const int64_t cells = (int64_t)side * side * side;
-    const int64_t nvec = cells >> 2;
-    const int4 *v = reinterpret_cast<const int4 *>(acc);
     unsigned long long best = 0;
-    const int64_t stride = (int64_t)gridDim.x * kArgThreads;
-    int64_t k = (int64_t)blockIdx.x * kArgThreads + threadIdx.x;
-    for (; k + 3 * stride < nvec; k += 4 * stride) {  // four independent 16-byte loads in flight
-        int4 c[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) c[u] = __ldcs(v + k + u * stride);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint32_t i = (uint32_t)((k + u * stride) << 2);
-            best = umax64(best, a1_key(c[u].x, i));
-            best = umax64(best, a1_key(c[u].y, i + 1));
-            best = umax64(best, a1_key(c[u].z, i + 2));
-            best = umax64(best, a1_key(c[u].w, i + 3));
-            if (HIST) {
-                hist_add(c[u].x, nib, sh, hist);
-                hist_add(c[u].y, nib, sh, hist);
-                hist_add(c[u].z, nib, sh, hist);
-                hist_add(c[u].w, nib, sh, hist);
-            }
-        }
-    }
-    for (; k < nvec; k += stride) {
-        const int4 c = __ldcs(v + k);
-        const uint32_t i = (uint32_t)(k << 2);
-        best = umax64(best, a1_key(c.x, i));
-        best = umax64(best, a1_key(c.y, i + 1));
-        best = umax64(best, a1_key(c.z, i + 2));
-        best = umax64(best, a1_key(c.w, i + 3));
+    acc16_scan(A, [&](uint32_t x, uint32_t wi, bool ev) {
+        if (ev) return;
+        const int lo = (int)(x & 0xffffu), hi = (int)(x >> 16);
+        best = umax64(best, a1_key(lo, 2u * wi));
+        best = umax64(best, a1_key(hi, 2u * wi + 1u));
         if (HIST) {
-            hist_add(c.x, nib, sh, hist);
-            hist_add(c.y, nib, sh, hist);
-            hist_add(c.z, nib, sh, hist);
-            hist_add(c.w, nib, sh, hist);
+            hist_add(lo, nib, sh, hist);
+            hist_add(hi, nib, sh, hist);
         }
-    }
-    for (int64_t r = (nvec << 2) + (int64_t)blockIdx.x * kArgThreads + threadIdx.x; r < cells; r += stride) {
-        best = umax64(best, a1_key(acc[r], (uint32_t)r));
-        if (HIST) hist_add(acc[r], nib, sh, hist);
-    }
+    });
     if (HIST) {
         const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -382,10 +479,10 @@ __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(const int32_t 
         for (int b = threadIdx.x; b < kHistSmem; b += kArgThreads)
             if (sh[b]) atomicAdd(&hist[b], sh[b]);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, o));
     __shared__ unsigned long long wbest[kArgThreads / 32];
     __shared__ bool last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, o));
     if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -395,10 +492,34 @@ __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(const int32_t 
         last = atomicAdd(&hdr->blocks_done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
-    // The last block: every block's maximum is in best_key.
+    if (!last) return;
+    // The last block: every other block's maximum is in best_key.  The words
+    // with wraps, from the record.
     __threadfence();
-    const unsigned long long key = atomicAdd(&hdr->best_key, 0ull);
+    const int64_t cells = (int64_t)side * side * side;
+    best = 0;
+    for (uint32_t h = threadIdx.x; h <= A.emask; h += kArgThreads) {
+        const uint32_t key = A.ekey[h];
+        if (!key) continue;
+        const uint32_t wi = key - 1u;
+        const uint32_t x = A.w[wi];
+        const int64_t lo = (int64_t)(x & 0xffffu) + 65536ll * A.elo[h];
+        const int64_t hi = (int64_t)(x >> 16) + 65536ll * A.ehi[h] - A.elo[h];
+        best = umax64(best, a1_key((int)lo, 2u * wi));
+        if (2ll * wi + 1 < cells) best = umax64(best, a1_key((int)hi, 2u * wi + 1u));
+        if (HIST) {
+            if (lo >= 1) atomicAdd(&hist[min(lo, (int64_t)kHistBins - 1)], 1u);
+            if (hi >= 1) atomicAdd(&hist[min(hi, (int64_t)kHistBins - 1)], 1u);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int w = 0; w < kArgThreads / 32; ++w) best = umax64(best, wbest[w]);
+    const unsigned long long key = umax64(best, atomicAdd(&hdr->best_key, 0ull));
+    hdr->best_key = key;
     const uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffull);
     double q[4];
     alg1_centre64(side, idx, q);
@@ -416,6 +537,17 @@ __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(const int32_t 
     res.npeaks = 0;
     res.peak_threshold = 0;
     res.pad = 0;
+}
+
+// The accumulator as int32 counts (the caller's copy).
+__global__ void __launch_bounds__(kArgThreads) alg1_expand_kernel(Acc16 A, int64_t cells, int32_t *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * kArgThreads;
+    for (int64_t r = (int64_t)blockIdx.x * kArgThreads + threadIdx.x; r < A.nw; r += stride) {
+        int64_t lo, hi;
+        acc16_pair(A, A.w[r], (uint32_t)r, ((A.bits[r >> 5] >> (r & 31)) & 1u) != 0, lo, hi);
+        out[2 * r] = (int32_t)lo;
+        if (2 * r + 1 < cells) out[2 * r + 1] = (int32_t)hi;
+    }
 }
 
 // Peak threshold T = max(min_count, the smallest t >= 1 with
@@ -473,31 +605,32 @@ __global__ void __launch_bounds__(kPeakThreads) alg1_threshold_kernel(const unsi
     }
 }
 
-// Candidates: every cell with count >= T, as (count, -index) keys.
-__global__ void __launch_bounds__(kArgThreads) alg1_collect_kernel(const int32_t *__restrict__ acc, int side,
-                                                                   A1Hdr *hdr, unsigned long long *cand) {
+// Candidates: every cell with count >= T, as (count, -index) keys (words with
+// wraps from their record).
+__global__ void __launch_bounds__(kArgThreads) alg1_collect_kernel(Acc16 A, int side, A1Hdr *hdr,
+                                                                   unsigned long long *cand) {
     const int T = hdr->peak_T;
     if (T < 1) return;
     const int64_t cells = (int64_t)side * side * side;
-    const int64_t nvec = cells >> 2;
-    const int4 *v = reinterpret_cast<const int4 *>(acc);
-    const int64_t stride = (int64_t)gridDim.x * kArgThreads;
-    auto put = [&](int c, uint32_t i) {
+    auto put = [&](int64_t c, uint32_t i) {
         if (c >= T) {
             const unsigned pos = atomicAdd(&hdr->ncand, 1u);
-            if (pos < (unsigned)kPeakCand) cand[pos] = a1_key(c, i);
+            if (pos < (unsigned)kPeakCand) cand[pos] = a1_key((int)c, i);
         }
     };
-    for (int64_t k = (int64_t)blockIdx.x * kArgThreads + threadIdx.x; k < nvec; k += stride) {
-        const int4 c = __ldcs(v + k);
-        const uint32_t i = (uint32_t)(k << 2);
-        put(c.x, i);
-        put(c.y, i + 1);
-        put(c.z, i + 2);
-        put(c.w, i + 3);
+    acc16_scan(A, [&](uint32_t x, uint32_t wi, bool ev) {
+        if (ev) return;
+        put(x & 0xffffu, 2u * wi);
+        put(x >> 16, 2u * wi + 1u);
+    });
+    const int64_t stride = (int64_t)gridDim.x * kArgThreads;
+    for (int64_t h = (int64_t)blockIdx.x * kArgThreads + threadIdx.x; h <= (int64_t)A.emask; h += stride) {
+        const uint32_t key = A.ekey[h];
+        if (!key) continue;
+        const uint32_t wi = key - 1u, x = A.w[wi];
+        put((int64_t)(x & 0xffffu) + 65536ll * A.elo[h], 2u * wi);
+        if (2ll * wi + 1 < cells) put((int64_t)(x >> 16) + 65536ll * A.ehi[h] - A.elo[h], 2u * wi + 1u);
     }
-    for (int64_t r = (nvec << 2) + (int64_t)blockIdx.x * kArgThreads + threadIdx.x; r < cells; r += stride)
-        put(acc[r], (uint32_t)r);
 }
 
 // A cell's grid coordinates and 1 + |p|^2 of its centre p = -1 + (i + 1/2) h, in FP32.
@@ -667,7 +800,7 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         const int side = P.accum_side == 0 ? 360 : P.accum_side;
         const int M = P.peaks;
         if (!P.a || !P.b || P.n < 2 || P.n > kA1MaxPairs || J < 1 || J > kA1MaxSamples || side < 2 ||
-            side > kA1MaxSide || M < 0 || M > ROT_VOTE_ALG1_MAX_PEAKS ||
+            side > kA1MaxSide || P.n * (int64_t)J > (int64_t)INT_MAX || M < 0 || M > ROT_VOTE_ALG1_MAX_PEAKS ||
             (M > 0 && (!P.peak_out || !(P.nms_angle >= 0.f) || !isfinite(P.nms_angle) || P.min_count < 0))) {
             r.status = ROT_VOTE_EINVAL;
             last_error = "alg1 problem " + std::to_string(k) + ": bad argument";
@@ -675,10 +808,20 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         }
         const bool dev_in = a1_on_device(P.a) && a1_on_device(P.b);
         const int64_t cells = (int64_t)side * side * side;
-        // layout: header | accumulator | FP32 angle table | FP64 angle table | FP32 basis (2 x 16 B per pair) |
-        //         FP64 basis (64 B per pair) | staged inputs
-        const size_t off_acc = 256;
-        const size_t off_t32 = align_up(off_acc + sizeof(int32_t) * (size_t)cells, 256);
+        // layout: header | 16-bit counter words | wrap bitmap | wrap table (3 arrays) | FP32 angle table |
+        //         FP64 angle table | FP32 basis (2 x 16 B per pair) | FP64 basis (64 B per pair) | peak buffers |
+        //         int32 copy of the counts (host output only) | staged inputs
+        const int64_t nw = (cells + 1) / 2;
+        const int64_t total = P.n * (int64_t)J;
+        uint32_t esize = 1024;  // >= twice the most words that can wrap (each wrap takes 65536 increments)
+        while ((int64_t)esize < 2 * (2 * (total >> 16) + 2)) esize <<= 1;
+        const bool acc_dev = P.accumulator && a1_on_device(P.accumulator);
+        const size_t off_w = 256;
+        const size_t off_bits = align_up(off_w + sizeof(uint32_t) * (size_t)nw, 256);
+        const size_t off_ek = align_up(off_bits + sizeof(uint32_t) * (size_t)((nw + 31) / 32), 256);
+        const size_t off_el = align_up(off_ek + sizeof(uint32_t) * esize, 256);
+        const size_t off_eh = align_up(off_el + sizeof(uint32_t) * esize, 256);
+        const size_t off_t32 = align_up(off_eh + sizeof(uint32_t) * esize, 256);
         const size_t off_t64 = align_up(off_t32 + sizeof(float2) * J, 256);
         const size_t off_q1f = align_up(off_t64 + sizeof(double2) * J, 256);
         const size_t off_q2f = align_up(off_q1f + sizeof(float4) * (size_t)P.n, 256);
@@ -686,7 +829,9 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         const size_t off_hist = align_up(off_qd + 4 * sizeof(double2) * (size_t)P.n, 256);
         const size_t off_cand = align_up(off_hist + (M > 0 ? sizeof(unsigned) * kHistBins : 0), 256);
         const size_t off_pk = align_up(off_cand + (M > 0 ? sizeof(unsigned long long) * kPeakCand : 0), 256);
-        const size_t off_in = align_up(off_pk + (M > 0 ? sizeof(rot_vote_peak) * ROT_VOTE_ALG1_MAX_PEAKS : 0), 256);
+        const size_t off_o32 = align_up(off_pk + (M > 0 ? sizeof(rot_vote_peak) * ROT_VOTE_ALG1_MAX_PEAKS : 0), 256);
+        const size_t off_in =
+            align_up(off_o32 + (P.accumulator && !acc_dev ? sizeof(int32_t) * (size_t)cells : 0), 256);
         const size_t in_bytes = dev_in ? 0 : align_up(sizeof(float) * 3 * (size_t)P.n, 256);
         const size_t need = off_in + 2 * in_bytes;
         if (need > a1_cap) {
@@ -711,7 +856,14 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         A1Hdr *hdr = reinterpret_cast<A1Hdr *>(base);
         float2 *t32 = reinterpret_cast<float2 *>(base + off_t32);
         double2 *t64 = reinterpret_cast<double2 *>(base + off_t64);
-        int32_t *acc = reinterpret_cast<int32_t *>(base + off_acc);
+        Acc16 acc;
+        acc.w = reinterpret_cast<uint32_t *>(base + off_w);
+        acc.bits = reinterpret_cast<uint32_t *>(base + off_bits);
+        acc.ekey = reinterpret_cast<uint32_t *>(base + off_ek);
+        acc.elo = reinterpret_cast<uint32_t *>(base + off_el);
+        acc.ehi = reinterpret_cast<uint32_t *>(base + off_eh);
+        acc.emask = esize - 1;
+        acc.nw = nw;
         cudaError_t e = cudaSuccess;
         if (a1_J != J || a1_toff != off_t32) {
             // (cos, sin)(alpha_j / 2), alpha_j = -pi + 2 pi j / J: the uniform samples of [-pi, pi) of Alg. 1
@@ -759,9 +911,9 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         if (e == cudaSuccess) e = cudaMemsetAsync(hdr, 0, sizeof(A1Hdr), stream);
         mark(0, true);
         if (e == cudaSuccess) {
-            const int64_t want = (std::max<int64_t>(P.n, cells / 4) + kA1Threads - 1) / kA1Threads;
+            const int64_t want = (std::max<int64_t>(P.n, nw / 4) + kA1Threads - 1) / kA1Threads;
             const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * 8));
-            alg1_prep_kernel<<<blocks, kA1Threads, 0, stream>>>(da, db, P.n, q1f, q2f, qd, acc, cells, 1, J, hdr);
+            alg1_prep_kernel<<<blocks, kA1Threads, 0, stream>>>(da, db, P.n, q1f, q2f, qd, acc, J, hdr);
             e = cudaGetLastError();
         }
         mark(0, false);
@@ -785,7 +937,7 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         unsigned *hist = reinterpret_cast<unsigned *>(base + off_hist);
         unsigned long long *cand = reinterpret_cast<unsigned long long *>(base + off_cand);
         rot_vote_peak *pk = reinterpret_cast<rot_vote_peak *>(base + off_pk);
-        const int64_t want_arg = (cells / 4 + kArgThreads - 1) / kArgThreads;
+        const int64_t want_arg = (nw / 4 + kArgThreads - 1) / kArgThreads;
         const int arg_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_arg, (int64_t)sm_count * 8));
         if (e == cudaSuccess && M > 0) e = cudaMemsetAsync(hist, 0, sizeof(unsigned) * kHistBins, stream);
         if (e == cudaSuccess) {
@@ -818,8 +970,13 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         mark(2, false);
         if (e == cudaSuccess) e = cudaEventRecord(a1_ev[1], stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(a1_hdr_h, hdr, sizeof(A1Hdr), cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess && P.accumulator)
-            e = cudaMemcpyAsync(P.accumulator, acc, sizeof(int32_t) * (size_t)cells, cudaMemcpyDefault, stream);
+        if (e == cudaSuccess && P.accumulator) {  // the counts as int32, into the caller's buffer
+            int32_t *o32 = acc_dev ? P.accumulator : reinterpret_cast<int32_t *>(base + off_o32);
+            alg1_expand_kernel<<<arg_blocks, kArgThreads, 0, stream>>>(acc, cells, o32);
+            e = cudaGetLastError();
+            if (e == cudaSuccess && !acc_dev)
+                e = cudaMemcpyAsync(P.accumulator, o32, sizeof(int32_t) * (size_t)cells, cudaMemcpyDeviceToHost, stream);
+        }
         if (e == cudaSuccess && M > 0)
             e = cudaMemcpyAsync(P.peak_out, pk, sizeof(rot_vote_peak) * M, cudaMemcpyDefault, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);

@@ -203,3 +203,46 @@ def test_alg1_peaks_argument_errors():
                    dict(peaks=3, nms_angle=0.1, min_count=-2)):
             r = ctx.alg1([(dev(p.a), dev(p.b), 90, 32)], **kw)[0]
             assert r.status == rv.EINVAL
+
+
+# ---- the 16-bit counters: wraps of a word's low half, carries, wraps of the word ----
+
+def _pairs_by_cell(side, J, n_try=4000, seed=2900):
+    """Random pairs and the cell of their last sample (the oracle's cell function)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((n_try, 3))
+    b = rng.standard_normal((n_try, 3))
+    a = (a / np.linalg.norm(a, axis=1, keepdims=True)).astype(np.float32)
+    b = (b / np.linalg.norm(b, axis=1, keepdims=True)).astype(np.float32)
+    cs = oracle.alg1_table(J)
+    cells = []
+    for i in range(n_try):
+        ok, q1, q2 = oracle.alg1_basis(a[i], b[i])
+        cells.append(oracle.alg1_cell(q1, q2, cs[-1, 0], cs[-1, 1], side) if ok else -1)
+    return a, b, np.array(cells)
+
+
+@pytest.mark.parametrize("n_lo,n_hi", [(140000, 70000), (65535, 0), (65536, 1), (0, 65536), (131072, 65535)])
+def test_alg1_counter_wraps(n_lo, n_hi):
+    """n_lo copies of a pair whose second sample (alpha = 0: q_b1) lands in an even
+    cell 2w and n_hi of one landing in 2w + 1, plus random pairs: counts of 65536
+    and more wrap the 16-bit halves; the int32 accumulator, the winner and the peaks
+    equal the oracle's."""
+    side, J = 8, 2
+    a, b, cells = _pairs_by_cell(side, J)
+    pick = None
+    for i in np.nonzero((cells >= 0) & (cells % 2 == 0))[0]:
+        j = np.nonzero(cells == cells[i] + 1)[0]
+        if len(j):
+            pick = (i, j[0])
+            break
+    assert pick is not None
+    i, j = pick
+    A = np.concatenate([np.repeat(a[i:i + 1], n_lo, 0), np.repeat(a[j:j + 1], n_hi, 0), a[:1000]])
+    B = np.concatenate([np.repeat(b[i:i + 1], n_lo, 0), np.repeat(b[j:j + 1], n_hi, 0), b[:1000]])
+    r, acc, o = run_both(A, B, J, side)
+    check(r, acc, o)
+    assert acc[cells[i]] >= n_lo and acc[cells[i] + 1] >= n_hi
+    rp, accp, op = run_peaks(A, B, J, side, 4, 0.3)
+    check_peaks(rp, op)

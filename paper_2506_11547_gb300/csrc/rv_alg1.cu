@@ -605,8 +605,15 @@ __global__ void __launch_bounds__(kPeakThreads) alg1_threshold_kernel(const unsi
     }
 }
 
-// Candidates: every cell with count >= T, as (count, -index) keys (words with
-// wraps from their record).
+// (count, -(iz << 20 | iy << 10 | ix)) key of cell idx: the packed coordinates
+// order as the linear index (iz n + iy) n + ix does, and decode with shifts.
+__device__ __forceinline__ unsigned long long a1_pkey(int count, uint32_t idx, uint32_t n) {
+    const uint32_t ix = idx % n, iy = (idx / n) % n, iz = idx / (n * n);
+    return a1_key(count, (iz << 20) | (iy << 10) | ix);
+}
+
+// Candidates: every cell with count >= T, as packed keys (words with wraps
+// from their record).
 __global__ void __launch_bounds__(kArgThreads) alg1_collect_kernel(Acc16 A, int side, A1Hdr *hdr,
                                                                    unsigned long long *cand) {
     const int T = hdr->peak_T;
@@ -615,7 +622,7 @@ __global__ void __launch_bounds__(kArgThreads) alg1_collect_kernel(Acc16 A, int 
     auto put = [&](int64_t c, uint32_t i) {
         if (c >= T) {
             const unsigned pos = atomicAdd(&hdr->ncand, 1u);
-            if (pos < (unsigned)kPeakCand) cand[pos] = a1_key((int)c, i);
+            if (pos < (unsigned)kPeakCand) cand[pos] = a1_pkey((int)c, i, (uint32_t)side);
         }
     };
     acc16_scan(A, [&](uint32_t x, uint32_t wi, bool ev) {
@@ -639,12 +646,11 @@ struct CellF {
     float s;
 };
 
-__device__ __forceinline__ CellF alg1_cellf(int side, float h, uint32_t idx) {
-    const uint32_t n = (uint32_t)side;
+__device__ __forceinline__ CellF alg1_cellf(float h, uint32_t packed) {
     CellF c;
-    c.ix = (int)(idx % n);
-    c.iy = (int)((idx / n) % n);
-    c.iz = (int)(idx / (n * n));
+    c.ix = (int)(packed & 1023u);
+    c.iy = (int)((packed >> 10) & 1023u);
+    c.iz = (int)(packed >> 20);
     const float p0 = fmaf((float)c.ix + 0.5f, h, -1.f);
     const float p1 = fmaf((float)c.iy + 0.5f, h, -1.f);
     const float p2 = fmaf((float)c.iz + 0.5f, h, -1.f);
@@ -665,7 +671,7 @@ __device__ __forceinline__ float alg1_one_minus_dot(const CellF &a, const CellF 
 }
 
 // Picks up to M peaks by greedy suppression.  Each round takes the largest
-// (count, -index) key among the candidates not yet suppressed -- the first
+// (count, -packed index) key among the candidates not yet suppressed -- the first
 // unsuppressed candidate in (count desc, index asc) order -- and suppresses
 // every candidate within the angle of it (setting its key to 0).  One block,
 // the keys in shared memory.
@@ -704,11 +710,13 @@ __global__ void __launch_bounds__(kPeakThreads) alg1_peaks_kernel(const unsigned
             for (int w = 0; w < kPeakThreads / 32; ++w) m = wmax[w] > m ? wmax[w] : m;
             s_pick = m;
             if (m) {
-                const uint32_t idx = 0xffffffffu - (uint32_t)(m & 0xffffffffull);
+                const uint32_t pk3 = 0xffffffffu - (uint32_t)(m & 0xffffffffull);
+                const uint32_t idx = ((pk3 >> 20) * (uint32_t)side + ((pk3 >> 10) & 1023u)) * (uint32_t)side +
+                                     (pk3 & 1023u);
                 double q[4];
                 alg1_centre64(side, idx, q);
                 for (int c = 0; c < 4; ++c) pq[c] = q[c];
-                pcell = alg1_cellf(side, h, idx);
+                pcell = alg1_cellf(h, pk3);
                 rot_vote_peak pk;
                 for (int c = 0; c < 4; ++c) pk.q[c] = q[c];
                 pk.cell = idx;
@@ -728,13 +736,14 @@ __global__ void __launch_bounds__(kPeakThreads) alg1_peaks_kernel(const unsigned
                 keys[i] = 0;
                 continue;
             }
-            const uint32_t idx = 0xffffffffu - (uint32_t)(k & 0xffffffffull);
-            const float e = alg1_one_minus_dot(a, alg1_cellf(side, h, idx), h2);
+            const uint32_t pk3 = 0xffffffffu - (uint32_t)(k & 0xffffffffull);
+            const CellF cb = alg1_cellf(h, pk3);
+            const float e = alg1_one_minus_dot(a, cb, h2);
             const float b = 32.f * 5.9604645e-8f * e + 1e-12f;
             bool sup = e <= em || e >= ep;
             if (fabsf(e - em) <= b || fabsf(e - ep) <= b) {  // near a bound: the FP64 definition decides
                 double q[4];
-                alg1_centre64(side, idx, q);
+                alg1_centre64(side, ((uint32_t)cb.iz * (uint32_t)side + (uint32_t)cb.iy) * (uint32_t)side + (uint32_t)cb.ix, q);
                 const double d64 = dadd(dadd(dadd(dmul(q[0], pq[0]), dmul(q[1], pq[1])), dmul(q[2], pq[2])),
                                         dmul(q[3], pq[3]));
                 sup = fabs(d64) >= cth;

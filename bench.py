@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--only-solve", action="store_true",
                     help="warm-up + timed solves only (a short, fixed launch sequence for profiler captures)")
+    ap.add_argument("--profile-case", choices=["alg1_n1e5", "alg1_multi9", "pose_n5000"], default=None,
+                    help="three calls of one Alg. 1 / peak / pose case and nothing else (for profiler captures)")
     return ap.parse_args()
 
 
@@ -481,10 +483,38 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def profile_case(case: str):
+    """Three calls of one case, each after a 256 MiB L2 flush, for profiler captures."""
+    import torch
+    from paper_2506_11547_gb300 import rot_vote as rv
+    from paper_2506_11547_gb300 import synth
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    if case == "alg1_n1e5":  # 1e5 pairs, 99% outliers, J = 180, 360^3
+        p = synth.make_problem(100000, 0.99, 0.01, 0.03, seed=2301)
+        args = [(torch.from_numpy(p.a).cuda(), torch.from_numpy(p.b).cuda(), 180, 360)]
+        kw = {}
+    elif case == "alg1_multi9":  # 9 motions x 3000 pairs, J = 540, 360^3, 9 peaks within 0.1 rad
+        mp = synth.make_multi_problem(9, 3000, sigma=0.01, seed=2802)
+        args = [(torch.from_numpy(mp.a).cuda(), torch.from_numpy(mp.b).cuda(), 540, 360)]
+        kw = dict(peaks=9, nms_angle=0.1)
+    else:  # rigid pose, N = 5000, 90% outliers, FP16X2 rotation vote 32^3 + 2 levels
+        p = synth.make_pose_problem(5000, 0.9, 0.01, seed=3003)
+        x, y = torch.from_numpy(p.x).cuda(), torch.from_numpy(p.y).cuda()
+    with rv.Context(grid_n=32, levels=2, precision="fp16x2") as ctx:
+        for _ in range(3):
+            flush.zero_()
+            r = ctx.pose(x, y, 0.04, 0.03) if case == "pose_n5000" else ctx.alg1(args, **kw)[0]
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": case, "status": r.status}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_case:
+        profile_case(args.profile_case)
         return
     import numpy as np
     import torch

@@ -518,6 +518,81 @@ struct FitShared {
     int done, status, nin, refits;
 };
 
+// One fit iteration's decision, by warp 0, from the member sums Btot (9 sums
+// of b a^T, member count, changed count): iteration 0 fits the winner's
+// voters (degenerate below 2 members or without an eigenvalue gap);
+// iteration t >= 1 refits unless the set is small or unchanged.  Publishes q,
+// the member count and the iteration in sh, and sh.done when the loop ends.
+__device__ void fit_step_warp0(int t, int refit_iters, const double *Btot, double (*As)[4], float (*Vf)[4],
+                               const double qc[4], FitShared &sh) {
+    const int m = (int)Btot[9], chg = (int)Btot[10];
+    double u[10];
+    sumS_from_B(Btot, (double)m, u);
+    bool stop = false, degenerate = false;
+    if (t == 0) {
+        degenerate = m < 2;
+    } else {
+        stop = m < 2 || chg == 0;
+    }
+    if (!stop && !degenerate) {
+        const double Ain[4][4] = {{u[0], u[4], u[5], u[6]}, {u[4], u[1], u[7], u[8]},
+                                  {u[5], u[7], u[2], u[9]}, {u[6], u[8], u[9], u[3]}};
+        if (threadIdx.x < 16) As[threadIdx.x >> 2][threadIdx.x & 3] = Ain[threadIdx.x >> 2][threadIdx.x & 3];
+        __syncwarp();
+        double qn[4];
+        const bool gap_ok = eig4_smallest(As, Vf, qn);
+        if (threadIdx.x == 0) {
+            if (!gap_ok) {
+                if (t == 0) degenerate = true;
+                else stop = true;
+            }
+            if (!degenerate && !stop) {
+                for (int r = 0; r < 4; ++r) sh.q[r] = qn[r];
+                sh.nin = m;
+                sh.refits = t;
+            }
+        }
+        __syncwarp();
+    }
+    if (threadIdx.x == 0) {
+        if (t == 0) {
+            sh.status = degenerate ? ROT_VOTE_EDEGENERATE : ROT_VOTE_OK;
+            if (degenerate) {
+                for (int r = 0; r < 4; ++r) sh.q[r] = qc[r];
+                sh.nin = m;
+                sh.refits = 0;
+            }
+            sh.done = degenerate || refit_iters == 0;
+        } else {
+            sh.done = stop || t == refit_iters;
+        }
+    }
+}
+
+// Writes problem p's result from the fit state.
+__device__ void fit_result(int p, const LevelRef &L, int wpos, int last, const FitShared &sh,
+                           const ProbStats *__restrict__ stats, rot_vote_result *results) {
+    double q[4] = {sh.q[0], sh.q[1], sh.q[2], sh.q[3]};
+    canonical(q);
+    double R[9];
+    quat_to_R(q, R);
+    rot_vote_result r;
+    for (int k = 0; k < 4; ++k) r.q[k] = q[k];
+    for (int k = 0; k < 9; ++k) r.R[k] = R[k];
+    r.best_count = L.counts[wpos];
+    r.inliers = sh.nin;
+    r.best_cell = L.cells.idx[wpos];
+    r.best_level = last;
+    r.refits = sh.refits;
+    r.tests = (int64_t)stats[p].tests;
+    r.rechecked = (int64_t)stats[p].rechecked;
+    r.ambiguous = (int64_t)stats[p].ambiguous;
+    r.status = stats[p].invalid ? ROT_VOTE_EINVAL : sh.status;
+    r.ms_gpu = 0.f;
+    r.latency_ms = 0.f;
+    results[p] = r;
+}
+
 // Fit of one problem per thread-block cluster (gridDim.x = problems x C):
 // the C CTAs split the problem's slices round-robin and write per-slice
 // partial sums to global memory; after a cluster barrier, rank 0 sums the
@@ -529,13 +604,14 @@ __global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restr
                                                           const int32_t *__restrict__ kept_pos, int top_k,
                                                           int refit_iters, PairPool pool, uint8_t *member,
                                                           double *slice_part, const int64_t *slice_off,
+                                                          const int32_t *__restrict__ plist,
                                                           const ProbStats *__restrict__ stats,
                                                           rot_vote_result *results) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
-    const int p = blockIdx.x / C;
+    const int p = plist[blockIdx.x / C];
     const ProbRef P = probs[p];
     const int last = P.levels;
     const LevelRef L = lref[p * level_stride + last];
@@ -581,50 +657,7 @@ __global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restr
                 Btot[threadIdx.x] = acc;
             }
             __syncthreads();
-            if (threadIdx.x < 32) {
-                const int m = (int)Btot[9], chg = (int)Btot[10];
-                double u[10];
-                sumS_from_B(Btot, (double)m, u);
-                bool stop = false, degenerate = false;
-                if (t == 0) {
-                    degenerate = m < 2;
-                } else {
-                    stop = m < 2 || chg == 0;
-                }
-                if (!stop && !degenerate) {
-                    const double Ain[4][4] = {{u[0], u[4], u[5], u[6]}, {u[4], u[1], u[7], u[8]},
-                                              {u[5], u[7], u[2], u[9]}, {u[6], u[8], u[9], u[3]}};
-                    if (threadIdx.x < 16) As[threadIdx.x >> 2][threadIdx.x & 3] = Ain[threadIdx.x >> 2][threadIdx.x & 3];
-                    __syncwarp();
-                    double qn[4];
-                    const bool gap_ok = eig4_smallest(As, Vf, qn);
-                    if (threadIdx.x == 0) {
-                        if (!gap_ok) {
-                            if (t == 0) degenerate = true;
-                            else stop = true;
-                        }
-                        if (!degenerate && !stop) {
-                            for (int r = 0; r < 4; ++r) sh.q[r] = qn[r];
-                            sh.nin = m;
-                            sh.refits = t;
-                        }
-                    }
-                    __syncwarp();
-                }
-                if (threadIdx.x == 0) {
-                    if (t == 0) {
-                        sh.status = degenerate ? ROT_VOTE_EDEGENERATE : ROT_VOTE_OK;
-                        if (degenerate) {
-                            for (int r = 0; r < 4; ++r) sh.q[r] = qc[r];
-                            sh.nin = m;
-                            sh.refits = 0;
-                        }
-                        sh.done = degenerate || refit_iters == 0;
-                    } else {
-                        sh.done = stop || t == refit_iters;
-                    }
-                }
-            }
+            if (threadIdx.x < 32) fit_step_warp0(t, refit_iters, Btot, As, Vf, qc, sh);
         }
         cluster.sync();  // rank 0 has published q / done
         if (root->done) break;  // uniform: every CTA reads rank 0's flag
@@ -633,30 +666,105 @@ __global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restr
         thr = thr_refit;
         cluster.sync();  // rank 0's state is not rewritten before everyone has read it
     }
-    if (rank == 0 && threadIdx.x == 0) {
-        double q[4] = {sh.q[0], sh.q[1], sh.q[2], sh.q[3]};
-        canonical(q);
-        double R[9];
-        quat_to_R(q, R);
-        rot_vote_result r;
-        for (int k = 0; k < 4; ++k) r.q[k] = q[k];
-        for (int k = 0; k < 9; ++k) r.R[k] = R[k];
-        r.best_count = L.counts[wpos];
-        r.inliers = sh.nin;
-        r.best_cell = L.cells.idx[wpos];
-        r.best_level = last;
-        r.refits = sh.refits;
-        r.tests = (int64_t)stats[p].tests;
-        r.rechecked = (int64_t)stats[p].rechecked;
-        r.ambiguous = (int64_t)stats[p].ambiguous;
-        r.status = stats[p].invalid ? ROT_VOTE_EINVAL : sh.status;
-        r.ms_gpu = 0.f;
-        r.latency_ms = 0.f;
-        results[p] = r;
-    }
+    if (rank == 0 && threadIdx.x == 0) fit_result(p, L, wpos, last, sh, stats, results);
     cluster.sync();  // rank 0's shared memory stays alive until every CTA is done reading it
 }
 
+
+// Fit of one small problem (n <= kFitSmallMax) per CTA, no cluster: the same
+// membership rule, stop rule and eigen-solve as fit_kernel.  Thread t takes the
+// pairs t, t + kFitSmallThreads, ... and sums its members' b a^T in FP64 in
+// that order; the sums are then reduced in a fixed tree, so the result depends
+// only on the problem (not on the batch).
+constexpr int kFitSmallThreads = 128;
+
+__global__ void __launch_bounds__(kFitSmallThreads) fit_small_kernel(
+    const ProbRef *__restrict__ probs, const LevelRef *__restrict__ lref, int level_stride,
+    const int32_t *__restrict__ kept_pos, int top_k, int refit_iters, PairPool pool, uint8_t *member,
+    const int32_t *__restrict__ plist, const ProbStats *__restrict__ stats, rot_vote_result *results) {
+    const int p = plist[blockIdx.x];
+    const ProbRef P = probs[p];
+    const int last = P.levels;
+    const LevelRef L = lref[p * level_stride + last];
+    const int wpos = kept_pos[(p * level_stride + last) * top_k];
+    __shared__ FitShared sh;
+    __shared__ double As[4][4];
+    __shared__ float Vf[4][4];
+    __shared__ double Btot[11];
+    __shared__ double red[kFitSmallThreads / 32][11];
+    if (wpos < 0) {  // no cell at the last level (cannot happen for valid inputs)
+        if (threadIdx.x == 0) {
+            rot_vote_result r = {};
+            r.status = ROT_VOTE_EDEGENERATE;
+            results[p] = r;
+        }
+        return;
+    }
+    const int64_t n = P.n;
+    const float4 *pr = pool.pr + 2 * P.pool_off;
+    uint8_t *mem = member + P.pool_off;
+    double qc[4];
+    {
+        const double4_32a q4 = L.cells.q[wpos];
+        qc[0] = q4.x; qc[1] = q4.y; qc[2] = q4.z; qc[3] = q4.w;
+    }
+    const float thr_refit = (float)(P.sin_d * P.sin_d);
+    float4 R0 = L.cells.R32[3 * wpos], R1 = L.cells.R32[3 * wpos + 1], R2 = L.cells.R32[3 * wpos + 2];
+    float thr = (float)tau_cs(P.sin_d, P.cos_d, L.cells.trig[wpos]);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = 0; t <= refit_iters; ++t) {
+        double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        int cnt = 0, chg = 0;
+        for (int64_t i = threadIdx.x; i < n; i += kFitSmallThreads) {
+            const float4 p0 = pr[2 * i], p1 = pr[2 * i + 1];
+            const bool in = recheck_v(R0, R1, R2, p0, p1) <= thr;
+            if (t > 0) chg += in != (mem[i] != 0);
+            mem[i] = in;
+            if (in) {
+                ++cnt;
+                const double a0 = p0.x, a1 = p0.y, a2 = p0.z, b0 = p0.w, b1 = p1.x, b2 = p1.y;
+                acc[0] = fma(b0, a0, acc[0]);
+                acc[1] = fma(b0, a1, acc[1]);
+                acc[2] = fma(b0, a2, acc[2]);
+                acc[3] = fma(b1, a0, acc[3]);
+                acc[4] = fma(b1, a1, acc[4]);
+                acc[5] = fma(b1, a2, acc[5]);
+                acc[6] = fma(b2, a0, acc[6]);
+                acc[7] = fma(b2, a1, acc[7]);
+                acc[8] = fma(b2, a2, acc[8]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+            chg += __shfl_down_sync(0xffffffffu, chg, o);
+        }
+        if (lane == 0) {
+            for (int k = 0; k < 9; ++k) red[w][k] = acc[k];
+            red[w][9] = (double)cnt;
+            red[w][10] = (double)chg;
+        }
+        __syncthreads();
+        if (w == 0) {
+            if (lane < 11) {  // warps summed in order
+                double s = 0.0;
+                for (int k = 0; k < kFitSmallThreads / 32; ++k) s += red[k][lane];
+                Btot[lane] = s;
+            }
+            __syncwarp();
+            fit_step_warp0(t, refit_iters, Btot, As, Vf, qc, sh);
+        }
+        __syncthreads();  // sh is published
+        if (sh.done) break;
+        const double q[4] = {sh.q[0], sh.q[1], sh.q[2], sh.q[3]};
+        R32_of(q, R0, R1, R2);
+        thr = thr_refit;
+        __syncthreads();  // sh is read before warp 0 rewrites it
+    }
+    if (threadIdx.x == 0) fit_result(p, L, wpos, last, sh, stats, results);
+}
 }  // namespace
 
 cudaError_t launch_topk(const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride, int level,
@@ -687,14 +795,20 @@ cudaError_t launch_select_small(const ProbRef *probs, int nprob, const LevelRef 
 
 int fit_slices(int64_t n) { return (int)((n + kFitSlice - 1) / kFitSlice); }
 
-cudaError_t launch_fit(const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride,
-                       const int32_t *kept_pos, int top_k, int refit_iters, PairPool pool, uint8_t *member,
-                       double *slice_part, const int64_t *slice_off, int cluster, const ProbStats *stats,
-                       rot_vote_result *results, cudaStream_t s) {
-    if (nprob <= 0) return cudaSuccess;
+cudaError_t launch_fit(const ProbRef *probs, const LevelRef *lref, int level_stride, const int32_t *kept_pos,
+                       int top_k, int refit_iters, PairPool pool, uint8_t *member, double *slice_part,
+                       const int64_t *slice_off, const int32_t *small_list, int nsmall, const int32_t *big_list,
+                       int nbig, int cluster, const ProbStats *stats, rot_vote_result *results, cudaStream_t s) {
+    if (nsmall > 0) {
+        fit_small_kernel<<<nsmall, kFitSmallThreads, 0, s>>>(probs, lref, level_stride, kept_pos, top_k, refit_iters,
+                                                             pool, member, small_list, stats, results);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (nbig <= 0) return cudaSuccess;
     if (cluster < 1 || cluster > kFitMaxCluster) return cudaErrorInvalidValue;
     cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3((unsigned)(nprob * cluster));
+    lc.gridDim = dim3((unsigned)(nbig * cluster));
     lc.blockDim = dim3(kFitThreads);
     lc.dynamicSmemBytes = 0;
     lc.stream = s;
@@ -706,7 +820,7 @@ cudaError_t launch_fit(const ProbRef *probs, int nprob, const LevelRef *lref, in
     lc.attrs = at;
     lc.numAttrs = 1;
     return cudaLaunchKernelEx(&lc, fit_kernel, probs, lref, level_stride, kept_pos, top_k, refit_iters, pool, member,
-                              slice_part, slice_off, stats, results);
+                              slice_part, slice_off, big_list, stats, results);
 }
 
 }  // namespace rv

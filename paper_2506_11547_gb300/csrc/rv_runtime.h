@@ -45,6 +45,8 @@ struct Plan {
     std::vector<int64_t> in_off;
     std::vector<int64_t> slice_off_h;
     int fit_cluster = 1;
+    std::vector<int32_t> fit_list_h;  // fit order: small problems (one CTA each), then large (one cluster each)
+    int fit_nsmall = 0;
     // device pointers (inside the wave's workspace)
     ProbRef *d_probs = nullptr;
     LevelRef *d_lref = nullptr;
@@ -60,6 +62,7 @@ struct Plan {
     rot_vote_result *d_res = nullptr;
     double *d_slice = nullptr;
     int64_t *d_sloff = nullptr;
+    int32_t *d_flist = nullptr;
     int *d_err = nullptr;
     int *d_ictr = nullptr;  // per-level work-item counters of the CUDA-core vote (zeroed per solve)
 };

@@ -306,7 +306,8 @@ typedef struct {
     const float *a;         /* [n,3] row-major float32 unit vectors, host or device memory; */
     const float *b;         /*   validity as in rot_vote_problem */
     int64_t n;              /* pairs, 2 <= n <= 2^30 */
-    int samples;            /* J, samples per circle, 1 <= J <= 65536; 0 = 180 */
+    int samples;            /* J, samples per circle, 1 <= J <= 65536, n J <= 2^31 - 1 (counts are
+                               int32); 0 = 180 */
     int accum_side;         /* n of the n^3 accumulator, 2 <= n <= 1024; 0 = 360 */
     int32_t *accumulator;   /* optional (NULL: not returned): host or device int32 [n^3], receives the
                                counts in linear-index order; owned by the caller */
@@ -332,7 +333,8 @@ typedef struct {
 
 /* Run Alg. 1 on n_problems problems, one after another on the context's
  * stream (each needs its own n^3 accumulator; the context keeps one, of
- * 4 n^3 bytes, inside config.device_mem_budget), and block until out[] is
+ * 16-bit counters with an exact record of their wraps, about 2 n^3 bytes,
+ * inside config.device_mem_budget), and block until out[] is
  * written.  Returns OK when the call ran (per-problem status in
  * out[k].status: OK, or EINVAL for bad arguments or inputs -- non-finite
  * or non-unit vectors -- with the rest of out[k] unspecified), or ENOMEM /

@@ -3,18 +3,25 @@
 // stereographically (Sec. 4.3.1) and counted in an n^3 accumulator over
 // [-1, 1]^3, then the argmax and the inverse projection of its centre.
 //
+// The accumulator holds 16-bit counters, two cells per 32-bit word (see
+// Acc16), with an exact record of the rare counter wraps.
+//
 // Launches per problem, on the context's stream:
-//   alg1_prep_kernel    zeroes the accumulator (4 n^3 bytes) and writes each
-//             pair's circle basis: FP64 (the IEEE operation sequence of the
-//             formulas) and its FP32 rounding
+//   alg1_prep_kernel    zeroes the counters (2 n^3 bytes) and the wrap record
+//             and writes each pair's circle basis: FP64 (the IEEE operation
+//             sequence of the formulas) and its FP32 rounding
 //   alg1_vote_kernel    persistent; the N J samples in FP32, 32 consecutive
 //             samples per warp instruction (coalesced angle-table reads), four
 //             independent samples per thread, one atomic add each.  Samples
 //             that need FP64 go to a per-warp shared-memory queue that the
 //             warp empties 32 at a time, so FP64 work runs in full warps
-//   alg1_argmax_kernel  (count, -index) maximum over the accumulator; the
-//             last block to finish writes the result (inverse projection,
-//             canonical sign, rotation matrix)
+//   alg1_argmax_kernel  (count, -index) maximum over the accumulator (with
+//             peaks: also the count histogram); the last block adds the words
+//             with wraps and writes the result (inverse projection, canonical
+//             sign, rotation matrix)
+//   with peaks (Sec. 4.4): alg1_threshold_kernel, alg1_collect_kernel,
+//             alg1_peaks_kernel (greedy suppression)
+//   with the caller's int32 copy: alg1_expand_kernel
 //
 // Exactness.  A sample's cell is floor of x_k = (p_k + 1) n/2.  The FP32
 // evaluation below differs from the FP64 one by at most 1.1e-6 (n/2) cells

@@ -457,3 +457,44 @@ def test_incompatible_pairs_have_no_common_point(oracle_mod):
     S2 = oracle_mod.pair_S(a2.astype(np.float32), b2.astype(np.float32))
     ev = np.linalg.eigvalsh(S1 + S2)
     assert ev[0] > 1e-3   # min over unit q of q^T (S1+S2) q is bounded away from 0
+
+
+def _appD_A(a32, b32):
+    """App. D's A for one pair (written out here): A q = 0 on the pair's circle."""
+    a64, b64 = a32.astype(np.float64), b32.astype(np.float64)
+    d, p = a64 - b64, a64 + b64
+    A = np.zeros((4, 4))
+    A[0, 1:] = d
+    A[1:, 0] = -d
+    A[1:, 1:] = [[0, -p[2], p[1]], [p[2], 0, -p[0]], [-p[1], p[0], 0]]
+    return A, (a64 @ a64 + b64 @ b64 - 2) / 4
+
+
+def test_refit_converges_to_a_fixed_point(oracle_mod):
+    """The refit rule (reading C9): when the refit stops because the inlier set
+    repeats, the returned q is a fixed point -- the smallest eigenvector of
+    sum_{i in I(q)} S_i with I(q) = {i : q^T S_i q <= sin^2(delta)} -- and the
+    reported inlier count is |I(q)|.  S_i = A_i^T A_i / 4 - c_i I from App. D,
+    evaluated here in numpy (eigh), independently of the oracle."""
+    checked = 0
+    for seed in range(6):
+        p = synth.make_problem(800, rho=0.7, sigma=0.01, delta=0.03, seed=700 + seed)
+        delta = float(np.float32(p.delta))
+        r = oracle_mod.solve(p.a, p.b, delta, grid_n=16, levels=2, refit_iters=8, trace=False)
+        if r.status != 0 or r.refits >= 8:
+            continue  # stopped by the iteration cap, not by a repeated set
+        As = [_appD_A(p.a[i], p.b[i]) for i in range(p.n)]
+        v = np.array([np.sum((A @ r.q) ** 2) / 4 - c for A, c in As])
+        thr = np.sin(delta) ** 2
+        near = np.abs(v - thr) < 1e-12
+        inl = v <= thr
+        assert abs(inl.sum() - r.inliers) <= near.sum()
+        if near.any():
+            continue
+        Ssum = sum(A.T @ A / 4 - c * np.eye(4) for (A, c), k in zip(As, inl) if k)
+        w, V = np.linalg.eigh(Ssum)
+        e = V[:, 0]
+        assert w[1] - w[0] > 1e-9 * abs(w).max()
+        assert min(np.linalg.norm(e - r.q), np.linalg.norm(e + r.q)) < 1e-9
+        checked += 1
+    assert checked >= 3

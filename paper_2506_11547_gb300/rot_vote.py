@@ -355,8 +355,14 @@ class Context:
         del kx, ky
         return PoseResult.of(out)
 
-    def level_trace(self, problem: int, level: int, cap: int = 1 << 22):
-        """(idx[n], count[n], kept_idx[k]) of one level of the last solve (keep_trace=1)."""
+    def level_trace(self, problem: int, level: int, cap: int = 0):
+        """(idx[n], count[n], kept_idx[k]) of one level of the last solve (keep_trace=1).
+        cap = 0: the level's whole table (its size is queried first)."""
+        if cap <= 0:
+            nc0 = C.c_int64()
+            self._check(self._L.rot_vote_level_trace(self._h, int(problem), int(level), None, None, 0,
+                                                     C.byref(nc0), None, None))
+            cap = max(1, nc0.value)
         idx = np.zeros(cap, np.int64)
         cnt = np.zeros(cap, np.int32)
         kept = np.zeros(64, np.int64)

@@ -234,3 +234,31 @@ def test_stereographic_chart_batched_equals_alone():
         alone = [ctx.solve([x])[0] for x in args]
     for rb, ra in zip(batch, alone):
         assert np.array_equal(rb.q, ra.q) and (rb.best_cell, rb.best_count) == (ra.best_cell, ra.best_count)
+
+
+# ---- extremes of the configuration space ----
+
+def test_largest_coarse_grid_256():
+    """256^3 coarse grid (about 8.8M cells meeting the ball) + 1 level, FP32 and FP16X2."""
+    p = synth.make_problem(300, rho=0.8, sigma=0.01, delta=0.03, seed=401)
+    for prec in ("fp32", "fp16x2"):
+        r, tr, o = run_both(p, 256, 1, precision=prec)
+        assert_parity(p, r, tr, o, 1)
+
+
+def test_deep_refinement_side_512():
+    """8^3 + 6 levels: the last level is a 512-per-axis grid."""
+    p = synth.make_problem(2000, rho=0.7, sigma=0.005, delta=0.01, seed=402)
+    r, tr, o = run_both(p, 8, 6)
+    assert_parity(p, r, tr, o, 6)
+
+
+@pytest.mark.parametrize("delta", [1e-4, 1.5])
+def test_delta_extremes(delta):
+    """delta = 1e-4 (few voters; the fit may be degenerate) and delta = 1.5 rad
+    (every threshold saturates at 1: every cell votes for every pair)."""
+    p = synth.make_problem(500, rho=0.5, sigma=0.0, delta=delta, seed=403)
+    r, tr, o = run_both(p, 16, 1)
+    assert_parity(p, r, tr, o, 1)
+    if delta == 1.5:
+        assert all(int(c.min()) == p.n for _, c, _ in tr[:1])

@@ -339,6 +339,40 @@ def bench_alg1(rv, synth, torch, stream, flush, peaks, reps: int = 5):
     return res
 
 
+def bench_paper_scale(rv, synth, torch, stream, flush, reps: int = 3):
+    """The precision forms at the paper's scale: 1e6 pairs, 99% outliers, sigma 0.005, delta 0.03,
+    128^3 + 3 levels (1.14e12 cell tests per solve).  Device time per solve (L2 flushed before
+    each), the angle to the true rotation, and how many tests the FP32 re-check decided."""
+    p, g, L = synth.config_problem("lowp_n1e6_128L3")
+    a_d, b_d = torch.from_numpy(p.a).cuda(), torch.from_numpy(p.b).cuda()
+    arr = (rv.rot_vote_problem * 1)()
+    arr[0], keep = rv.problem(a_d, b_d, p.delta)
+    out = (rv.rot_vote_result * 1)()
+    res = {}
+    for prec in ("fp16x2", "bf16x2", "fp16", "bf16", "fp32"):
+        ctx = rv.Context(grid_n=g, levels=L, precision=prec, cuda_stream=stream.cuda_stream)
+        for _ in range(2):
+            ctx.solve_raw(arr, 1, out)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            ctx.solve_raw(arr, 1, out)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(s0.elapsed_time(s1))
+        ctx.close()
+        r = rv.Result.of(out[0])
+        ms = sum(ts) / len(ts)
+        res[prec] = {"value": r.tests / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms, "tests": r.tests,
+                     "rechecked": r.rechecked, "ambiguous": r.ambiguous, "status": r.status,
+                     "angle_to_truth_rad": _angle(r.q, p.q_true)}
+    res["workload"] = ("1e6 pairs, 99% outliers, sigma 0.005, delta 0.03; 128^3 coarse grid (1,136,840 cells) "
+                       "+ 3 levels; one solve per call")
+    return res
+
+
 def bench_pose(rv, synth, torch, stream, flush, reps: int = 5):
     """Rigid pose (Sec. 4.5) on the paper's default synthetic setting (Sec. 5.4.1): N = 5000,
     90% outliers, noise 0.01; mu_t = 0.04; rotation vote 32^3 + 2 levels, delta = 0.03; the
@@ -683,12 +717,13 @@ def main():
                                        "angle_to_truth_rad": _angle(rr.q, p.q_true)}
         cx.close()
 
-    batched = serving = alg1 = pose = None
+    batched = serving = alg1 = pose = paper_scale = None
     if not args.no_extra and ws == 1:
         batched = bench_batched(rv, synth, torch, stream, flush)
         serving = bench_serving(rv, synth, torch, args.serve_seconds)
         alg1 = bench_alg1(rv, synth, torch, stream, flush, peaks)
         pose = bench_pose(rv, synth, torch, stream, flush)
+        paper_scale = bench_paper_scale(rv, synth, torch, stream, flush)
 
     lat = per
     line = {
@@ -710,6 +745,7 @@ def main():
         "serving": serving,
         "alg1": alg1,
         "pose": pose,
+        "paper_scale": paper_scale,
         "clocks": clocks,
         "cpu_baseline": cpu,
         "result": {"status": res0.status, "angle_to_truth_rad": None, "rechecked": res0.rechecked,

@@ -247,12 +247,18 @@ def bench_batched(rv, synth, torch, stream, flush, launches: int = 3):
 
 def bench_alg1(rv, synth, torch, stream, flush, peaks, reps: int = 5):
     """Alg. 1 (Sec. 4.3.2) at the paper's default resolution (1/180: a 360^3
-    accumulator) and J = 180, on 1e5 and 1e6 pairs with 99% outliers.  Device
-    time per solve (inputs resident, L2 flushed before each), the end-to-end
-    call with pinned host inputs, and each stage's time from a profiled run."""
+    accumulator) and J = 180, on 1e5 and 1e6 pairs with 99% outliers, and on 1e6
+    pairs with 50% outliers, where the winning cell's count passes the 16-bit
+    counters' 65536.  Device time per solve (inputs resident, L2 flushed before
+    each), the end-to-end call with pinned host inputs, and each stage's time
+    from a profiled run.  A context solving the wrapping problem after one
+    without wraps votes twice (vote path 1, timed apart); solving it again, it
+    votes once with the wrap record (path 2)."""
     res = {}
-    for n, sigma, seed in ((100000, 0.01, 2301), (1000000, 0.005, 2302)):
-        p = synth.make_problem(n, 0.99, sigma, 0.03, seed=seed)
+    prev = None
+    for key, n, rho, sigma, seed in (("n100000", 100000, 0.99, 0.01, 2301), ("n1000000", 1000000, 0.99, 0.005, 2302),
+                                     ("n1000000_outliers50", 1000000, 0.5, 0.005, 2303)):
+        p = synth.make_problem(n, rho, sigma, 0.03, seed=seed)
         a_d, b_d = torch.from_numpy(p.a).cuda(), torch.from_numpy(p.b).cuda()
         a_h, b_h = torch.from_numpy(p.a).pin_memory(), torch.from_numpy(p.b).pin_memory()
         arr = (rv.rot_vote_alg1_problem * 1)(rv.rot_vote_alg1_problem(a_d.data_ptr(), b_d.data_ptr(), n, 180, 360,
@@ -261,6 +267,20 @@ def bench_alg1(rv, synth, torch, stream, flush, peaks, reps: int = 5):
                                                                           None))
         out = (rv.rot_vote_alg1_result * 1)()
         ctx = rv.Context(cuda_stream=stream.cuda_stream)
+        path1 = []
+        if prev is not None:
+            # vote path 1: the wrapping problem right after one without wraps (the previous
+            # case, of the same size, so the workspace is already allocated)
+            for _ in range(reps):
+                ctx.alg1_raw(prev[0], 1, out)
+                flush.zero_()
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                ctx.alg1_raw(arr, 1, out)
+                s1.record(stream)
+                torch.cuda.synchronize()
+                assert out[0].vote_path == 1
+                path1.append(s0.elapsed_time(s1))
         for _ in range(3):
             ctx.alg1_raw(arr, 1, out)
         ts = []
@@ -293,13 +313,14 @@ def bench_alg1(rv, synth, torch, stream, flush, peaks, reps: int = 5):
         st = {k: sum(v) / len(v) for k, v in st.items()}
         ms = sum(ts) / len(ts)
         cells = 360 ** 3
-        acc_bytes = 4 * cells
-        res[f"n{n}"] = {
+        acc_bytes = 4 * ((cells + 1) // 2)  # 16-bit counters, two per 32-bit word
+        res[key] = {
             "ms_per_solve": ms, "samples_per_s": r.samples_cast / (ms / 1e3), "rotations_per_s": 1e3 / ms,
             "e2e_ms": 1e3 * sum(e2e) / len(e2e), "samples_cast": r.samples_cast, "rechecked": r.rechecked,
             "best_count": r.best_count, "angle_to_truth_rad": _angle(r.q, p.q_true), "status": r.status,
-            "stage_ms": st,
-            # the accumulator pass: 4 n^3 bytes read per argmax launch, 4 n^3 written per zeroing
+            "vote_path": r.vote_path, "wrapped_words": r.wrapped_words,
+            "ms_per_solve_vote_path1": sum(path1) / len(path1) if path1 else None, "stage_ms": st,
+            # the accumulator pass: its 2 n^3 bytes read per argmax launch, written per zeroing
             "argmax_gbs": acc_bytes / (st["alg1_argmax"] / 1e3) / 1e9 if st.get("alg1_argmax") else None,
             "zero_gbs": acc_bytes / (st["alg1_zero"] / 1e3) / 1e9 if st.get("alg1_zero") else None,
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
@@ -307,7 +328,9 @@ def bench_alg1(rv, synth, torch, stream, flush, peaks, reps: int = 5):
             "paper_s": 0.04 if n == 100000 else 0.5,
             "paper_note": ("RTX 4080, Python + CuPy, 1e5 pairs (Table I); context only" if n == 100000 else
                            "the paper's bound for 1e6 pairs (Sec. 1, abstract); context only"),
+            "outlier_ratio": rho,
         }
+        prev = (arr, a_d, b_d) if key == "n1000000" else None  # the problem before the wrapping one
     # multiple rotations (Sec. 4.4): the paper's largest multiple-rotation setting (9 motions x 3000 pairs,
     # noise 0.01, J = 540), 9 peaks by greedy suppression within 0.1 rad
     mp = synth.make_multi_problem(9, 3000, sigma=0.01, seed=2802)
@@ -335,7 +358,7 @@ def bench_alg1(rv, synth, torch, stream, flush, peaks, reps: int = 5):
                      "max_angle_to_truth_rad": max(errs) if errs else None, "samples_cast": r.samples_cast,
                      "workload": "9 motions x 3000 pairs, noise 0.01, J = 540, 360^3, 9 peaks within 0.1 rad"}
     res["workload"] = ("Alg. 1: J = 180 samples per circle, 360^3 accumulator over [-1,1]^3 (resolution 1/180), "
-                       "99% outliers; one problem per call")
+                       "99% outliers (and 50% at 1e6 pairs); one problem per call")
     return res
 
 

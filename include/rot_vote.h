@@ -328,7 +328,11 @@ typedef struct {
     float ms_gpu;           /* device time of this problem (accumulator zeroing to result) */
     int32_t npeaks;         /* peaks written to peak_out */
     int32_t peak_threshold; /* T of the peak search (-1: not computed), 0 without peaks */
-    int32_t pad;
+    int32_t vote_path;      /* how the counts were taken (exact on every path): 0 one vote with
+                               return-less atomics; 1 that vote, whose 16-bit counters wrapped, then
+                               the vote again with atomics that record the wraps; 2 the recording
+                               vote alone, chosen when the context's previous problem had wraps */
+    int32_t wrapped_words;  /* counter words (two cells each) holding a cell with 65536 or more votes */
 } rot_vote_alg1_result;
 
 /* Run Alg. 1 on n_problems problems, one after another on the context's

@@ -298,11 +298,10 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     const size_t o_res = reserve(sizeof(rot_vote_result) * P);
     // fit: per-slice partial sums (11 doubles per 4096-pair slice) and slice offsets
     pl.slice_off_h.assign(P, 0);
-    int64_t nsl = 0, maxn = 0;
+    int64_t nsl = 0;
     for (int k = 0; k < P; ++k) {
         pl.slice_off_h[k] = nsl;
         nsl += fit_slices(pl.probs_h[k].n);
-        maxn = std::max<int64_t>(maxn, pl.probs_h[k].n);
     }
     const size_t o_slice = reserve(sizeof(double) * 11 * (size_t)std::max<int64_t>(1, nsl));
     const size_t o_sloff = reserve(sizeof(int64_t) * P);
@@ -321,7 +320,6 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     const size_t o_flist = reserve(sizeof(int32_t) * P);
     pl.fit_cluster = 1;
     while (pl.fit_cluster < 8 && (int64_t)pl.fit_cluster * 2 * 4096 < maxbig) pl.fit_cluster *= 2;
-    (void)maxn;
     // child tables: P x max_levels x child_cap cells
     const size_t nchild = (size_t)P * std::max(1, max_levels) * child_cap;
     const size_t o_cq = reserve(sizeof(double4_32a) * nchild);

@@ -4,21 +4,32 @@
 // [-1, 1]^3, then the argmax and the inverse projection of its centre.
 //
 // The accumulator holds 16-bit counters, two cells per 32-bit word (see
-// Acc16), with an exact record of the rare counter wraps.
+// Acc16).  The vote adds with return-less atomics; the argmax pass checks the
+// sum of the counts against the samples cast, and only when a counter wrapped
+// (a cell with 65536 or more votes) is the vote run again with atomics that
+// return, which keep an exact record of the wraps.
 //
 // Launches per problem, on the context's stream:
 //   alg1_prep_kernel    zeroes the counters (2 n^3 bytes) and the wrap record
 //             and writes each pair's circle basis: FP64 (the IEEE operation
 //             sequence of the formulas) and its FP32 rounding
-//   alg1_vote_kernel    persistent; the N J samples in FP32, 32 consecutive
-//             samples per warp instruction (coalesced angle-table reads), four
-//             independent samples per thread, one atomic add each.  Samples
-//             that need FP64 go to a per-warp shared-memory queue that the
-//             warp empties 32 at a time, so FP64 work runs in full warps
-//   alg1_argmax_kernel  (count, -index) maximum over the accumulator (with
-//             peaks: also the count histogram); the last block adds the words
-//             with wraps and writes the result (inverse projection, canonical
-//             sign, rotation matrix)
+//   alg1_vote_kernel<false>  persistent; the N J samples in FP32, 32
+//             consecutive samples per warp instruction (coalesced angle-table
+//             reads), four independent samples per thread, one return-less
+//             atomic add each.  Samples that need FP64 go to a per-warp
+//             shared-memory queue that the warp empties 32 at a time, so FP64
+//             work runs in full warps
+//   alg1_argmax_kernel<., false>  (count, -index) maximum over the accumulator
+//             (with peaks: also the count histogram) and the sum of the
+//             counts; the last block writes the result (inverse projection,
+//             canonical sign, rotation matrix) and sets path 1 when that sum
+//             misses the samples cast
+//   gated on path 1 (launched when N J >= 65536, returning at once
+//             otherwise): alg1_rezero_kernel, alg1_vote_kernel<true> (atomics
+//             with return and the wrap record), alg1_argmax_kernel<., true>
+//             (the last block adds the words with wraps from the record)
+//   path 2, after a problem with wraps: alg1_vote_kernel<true> and
+//             alg1_argmax_kernel<., true> in place of the return-less pair
 //   with peaks (Sec. 4.4): alg1_threshold_kernel, alg1_collect_kernel,
 //             alg1_peaks_kernel (greedy suppression)
 //   with the caller's int32 copy: alg1_expand_kernel
@@ -69,6 +80,9 @@ struct A1Hdr {
     uint32_t blocks_done;          // argmax blocks finished (the last one writes the result)
     int32_t peak_T;                // peak threshold (-1: not computed)
     uint32_t ncand;                // peak candidates collected
+    unsigned long long decoded;    // sum of the counts as read after the return-less vote
+    uint32_t path;                 // vote path (result field vote_path); nonzero: the recording vote runs
+    uint32_t pad;
     rot_vote_alg1_result res;
 };
 static_assert(sizeof(A1Hdr) <= 256, "header slot");
@@ -115,8 +129,16 @@ __device__ __noinline__ void acc16_event(const Acc16 &A, uint32_t word, bool low
     }
 }
 
+// One count into cell `cell`.  REC: an atomic with return that records the
+// wraps it causes; otherwise a return-less atomic (a reduction in L2, about
+// 1.6x the rate), exact as long as no counter wraps.
+template <bool REC>
 __device__ __forceinline__ void acc16_add(const Acc16 &A, uint32_t cell) {
     const uint32_t word = cell >> 1, inc = (cell & 1u) ? 0x10000u : 1u;
+    if (!REC) {
+        atomicAdd(&A.w[word], inc);
+        return;
+    }
     const uint32_t old = atomicAdd(&A.w[word], inc);
     const bool lw = inc == 1u && (old & 0xffffu) == 0xffffu;
     const bool ww = old > 0xffffffffu - inc;  // old + inc passes 2^32
@@ -136,6 +158,86 @@ __device__ __forceinline__ void acc16_lookup(const Acc16 &A, uint32_t word, uint
         }
         if (k == 0u) return;
         h = (h + 1u) & A.emask;
+    }
+}
+
+// ---- The ball region ----
+// A pair whose basis norms lie within kNormGuard of 1 has samples with
+// |q|^2 = c^2 |q_b1|^2 + s^2 |q_b2|^2 within 1e-3 of 1 (q_b1 . q_b2 = 0, since
+// q_b2 is q_b1 times a pure quaternion), so |p| <= sqrt(1.001) < 1.0005 and its
+// cell meets the ball |p| <= kRegionR.  When n is a multiple of 8 (rows of
+// whole 16-byte vectors), the return-less path zeroes and scans only the
+// vectors of those cells, about pi/6 of the accumulator.  A sample outside the
+// region (only FP64-only pairs can stray there) is missing from the scanned
+// sum of counts, so the count check sends the problem to the recording path,
+// which zeroes and scans every word.
+constexpr float kRegionR = 1.01f;
+
+// The vectors [v0, v0 + len) of row `row` = iz n + iy holding its cells that
+// meet the ball, with one cell of margin on each side (len = 0: none).  FP32
+// with explicit rounding, so every kernel finds the same vectors.  Vector
+// indices fit int32: n <= 1024 gives at most 2^27 vectors.
+__device__ __forceinline__ void region_row(int side, int64_t row, int &v0, int &len) {
+    v0 = 0;
+    len = 0;
+    if (row >= (int64_t)side * side) return;
+    const int iy = (int)(row % side), iz = (int)(row / side);
+    const float h = __fdiv_rn(2.f, (float)side);
+    auto dist = [&](int i) {  // distance from 0 to the cell interval [-1 + i h, -1 + (i + 1) h]
+        const float lo = __fmaf_rn((float)i, h, -1.f), hi = __fmaf_rn((float)(i + 1), h, -1.f);
+        return lo > 0.f ? lo : (hi < 0.f ? -hi : 0.f);
+    };
+    const float dy = dist(iy), dz = dist(iz);
+    const float r2 = __fsub_rn(__fsub_rn(kRegionR * kRegionR, __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    if (!(r2 >= 0.f)) return;
+    const float rx = __fsqrt_rn(r2);
+    const int lo = max((int)floorf(__fdiv_rn(__fsub_rn(1.f, rx), h)) - 1, 0);
+    const int hi = min((int)floorf(__fdiv_rn(__fadd_rn(1.f, rx), h)) + 1, side - 1);
+    const int64_t base = row * side;
+    v0 = (int)((base + lo) >> 3);
+    len = (int)((base + hi) >> 3) - v0 + 1;
+}
+
+// Visits the region's vectors: one warp per group of eight rows (lane r < 8
+// finds row 8 g + r), f(k[4], m) on up to four vectors per lane at a time
+// (k[u] valid for u < m), so that their loads can be in flight together.
+template <class F>
+__device__ __forceinline__ void region_scan(int side, F &&f) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ngroups = ((int64_t)side * side + 7) >> 3;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroups; g += nwarps) {
+        int v0, len;
+        region_row(side, 8 * g + (lane & 7), v0, len);
+        int off = len;  // inclusive prefix over lanes 0..7, then exclusive
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, off, d);
+            if ((lane & 7) >= d) off += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, off, 7);
+        off -= len;
+        int roff[8], rbase[8];  // vector k = rbase[r] + j for flat index j in row r
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            roff[r] = __shfl_sync(0xffffffffu, off, r);
+            rbase[r] = __shfl_sync(0xffffffffu, v0, r) - roff[r];
+        }
+        for (int j0 = lane; j0 < total; j0 += 128) {
+            int k[4];
+            int m = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + 32 * u;
+                int b = rbase[0];
+#pragma unroll
+                for (int r = 1; r < 8; ++r)
+                    if (j >= roff[r]) b = rbase[r];  // roff is nondecreasing; empty rows are skipped
+                k[u] = b + j;
+                m += j < total;
+            }
+            f(k, m);
+        }
     }
 }
 
@@ -184,20 +286,32 @@ __device__ __forceinline__ int alg1_cell64(const double q1[4], const double q2[4
     return (i[2] * n + i[1]) * n + i[0];
 }
 
-// Zeroes the accumulator and its wrap record and writes every pair's basis: q1f, q2f the
-// FP32 roundings of q_b1, q_b2 (q1f.x = kNoCircle / kFp64Only flags the
-// pair), qd[4 i .. 4 i + 3] = q_b1, q_b2 in FP64.
+// Zeroes the accumulator (every word, or with !full only the region's, the
+// others being zero already) and its wrap record, sets the vote path (0, or 2
+// for the recording vote alone) and writes every pair's basis: q1f, q2f the
+// FP32 roundings of q_b1, q_b2 (q1f.x = kNoCircle / kFp64Only flags the pair),
+// qd[4 i .. 4 i + 3] = q_b1, q_b2 in FP64.
 __global__ void __launch_bounds__(kA1Threads) alg1_prep_kernel(const float *__restrict__ a,
                                                                const float *__restrict__ b, int64_t n,
                                                                float4 *__restrict__ q1f, float4 *__restrict__ q2f,
-                                                               double2 *__restrict__ qd, Acc16 A, int J, A1Hdr *hdr) {
+                                                               double2 *__restrict__ qd, Acc16 A, int J, A1Hdr *hdr,
+                                                               uint32_t path, int side, bool full) {
     const int64_t T = (int64_t)gridDim.x * kA1Threads;
     const int64_t g = (int64_t)blockIdx.x * kA1Threads + threadIdx.x;
+    if (g == 0) hdr->path = path;
     {
         uint4 *v = reinterpret_cast<uint4 *>(A.w);
-        const int64_t nvec = A.nw >> 2;
-        for (int64_t k = g; k < nvec; k += T) v[k] = make_uint4(0u, 0u, 0u, 0u);
-        for (int64_t r = (nvec << 2) + g; r < A.nw; r += T) A.w[r] = 0u;
+        if (full) {
+            const int64_t nvec = A.nw >> 2;
+            for (int64_t k = g; k < nvec; k += T) v[k] = make_uint4(0u, 0u, 0u, 0u);
+            for (int64_t r = (nvec << 2) + g; r < A.nw; r += T) A.w[r] = 0u;
+        } else {  // the words outside the region are already zero
+            region_scan(side, [&](const int *k, int m) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (u < m) v[k[u]] = make_uint4(0u, 0u, 0u, 0u);
+            });
+        }
         for (int64_t r = g; r < (A.nw + 31) / 32; r += T) A.bits[r] = 0u;
         for (int64_t r = g; r <= (int64_t)A.emask; r += T) {
             A.ekey[r] = 0u;
@@ -239,6 +353,7 @@ __global__ void __launch_bounds__(kA1Threads) alg1_prep_kernel(const float *__re
 }
 
 // A warp's queued samples (pair << 16 | angle), 32 per pass, in FP64.
+template <bool REC>
 __device__ __forceinline__ void alg1_drain(const unsigned long long *wq, int qn, const double2 *__restrict__ qd,
                                            const double2 *__restrict__ t64, int side, double hd, const Acc16 &A,
                                            int lane) {
@@ -249,20 +364,27 @@ __device__ __forceinline__ void alg1_drain(const unsigned long long *wq, int qn,
         const double2 u0 = qd[4 * i], u1 = qd[4 * i + 1], u2 = qd[4 * i + 2], u3 = qd[4 * i + 3];
         const double q1[4] = {u0.x, u0.y, u1.x, u1.y}, q2[4] = {u2.x, u2.y, u3.x, u3.y};
         const double2 cs = t64[jj];
-        acc16_add(A, (uint32_t)alg1_cell64(q1, q2, cs.x, cs.y, side, hd));
+        acc16_add<REC>(A, (uint32_t)alg1_cell64(q1, q2, cs.x, cs.y, side, hd));
     }
 }
 
 // Sample s in [0, N J) is (pair s / J, angle s % J).  Warp w takes the 32 kA1U
 // samples from w 32 kA1U on, lane l the samples w 32 kA1U + 32 k + l, then
 // moves on by the whole grid's share (adv_p pairs, adv_j angles).
-__global__ void __launch_bounds__(kA1Threads) alg1_vote_kernel(const float4 *__restrict__ q1f,
+// REC = false: the return-less vote.  REC = true: the vote with the wrap
+// record, which runs only when hdr->path is nonzero.
+// The recording vote waits on each atomic's return: five resident blocks per
+// SM hide more of that latency (measured: 1.71 -> 1.52 ms at 1e6 pairs, 50% outliers); the
+// return-less vote runs best at four.
+template <bool REC>
+__global__ void __launch_bounds__(kA1Threads, REC ? 5 : 4) alg1_vote_kernel(const float4 *__restrict__ q1f,
                                                                const float4 *__restrict__ q2f,
                                                                const double2 *__restrict__ qd,
                                                                const float2 *__restrict__ t32,
                                                                const double2 *__restrict__ t64, int J, int side,
                                                                Acc16 acc, A1Hdr *hdr, int64_t total, int64_t adv_p,
                                                                int adv_j) {
+    if (REC && !hdr->path) return;
     __shared__ unsigned long long queue[kA1Warps][kWarpQ];
     const int lane = threadIdx.x & 31;
     unsigned long long *wq = queue[threadIdx.x >> 5];
@@ -304,7 +426,7 @@ __global__ void __launch_bounds__(kA1Threads) alg1_vote_kernel(const float4 *__r
                         const int i0 = min(max((int)f0, 0), side - 1);
                         const int i1 = min(max((int)f1, 0), side - 1);
                         const int i2 = min(max((int)f2, 0), side - 1);
-                        acc16_add(acc, (uint32_t)((i2 * side + i1) * side + i0));
+                        acc16_add<REC>(acc, (uint32_t)((i2 * side + i1) * side + i0));
                     }
                 } else {
                     slow = A.x == kFp64Only;
@@ -322,7 +444,7 @@ __global__ void __launch_bounds__(kA1Threads) alg1_vote_kernel(const float4 *__r
         }
         if (qn > kWarpQ - 32 * kA1U) {
             __syncwarp();
-            alg1_drain(wq, qn, qd, t64, side, hd, acc, lane);
+            alg1_drain<REC>(wq, qn, qd, t64, side, hd, acc, lane);
             queued += qn;
             qn = 0;
             __syncwarp();
@@ -335,7 +457,7 @@ __global__ void __launch_bounds__(kA1Threads) alg1_vote_kernel(const float4 *__r
         }
     }
     __syncwarp();
-    alg1_drain(wq, qn, qd, t64, side, hd, acc, lane);
+    alg1_drain<REC>(wq, qn, qd, t64, side, hd, acc, lane);
     queued += qn;
     if (lane == 0 && queued) atomicAdd(&hdr->rechecked, (unsigned long long)queued);
 }
@@ -455,26 +577,58 @@ __device__ __forceinline__ void acc16_scan(const Acc16 &A, F &&f) {
 // from the wrap record and writes the result.  A cell past the grid (the high
 // half of the last word when n^3 is odd) is never incremented: its count 0 and
 // index cannot win and add nothing to the histogram.
-template <bool HIST>
+//
+// REDO = false follows the return-less vote and checks it: every cast sample
+// added one count, and each counter wrap lowers the sum of the counts as read
+// by 65535 (a low half passing 0xffff carries into the high half) or 65536 (a
+// word passing 2^32), so that sum equals hdr->cast exactly when nothing
+// wrapped.  With n a multiple of 8 it reads only the ball region's words; a
+// sample outside the region is then missing from the sum as well.  Otherwise the last block sets hdr->path = 1, and the gated
+// kernels that follow (alg1_rezero_kernel, alg1_vote_kernel<true>, this kernel
+// with REDO = true) count again with the wrap record.  REDO = true (on path 1
+// or 2) also counts the words with wraps.
+template <bool HIST, bool REDO>
 __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(Acc16 A, int side, A1Hdr *hdr,
                                                                   unsigned *__restrict__ hist) {
+    if (REDO && !hdr->path) return;
     __shared__ unsigned sh[HIST ? kHistSmem : 1];
     if (HIST) {
         for (int b = threadIdx.x; b < kHistSmem; b += kArgThreads) sh[b] = 0;
         __syncthreads();
     }
     unsigned long long nib = 0;
-    unsigned long long best = 0;
-    acc16_scan(A, [&](uint32_t x, uint32_t wi, bool ev) {
+    // cell 0 with count 0: the winner when nothing was counted (a region scan does not visit it)
+    unsigned long long best = a1_key(0, 0u), sum = 0;
+    auto visit = [&](uint32_t x, uint32_t wi, bool ev) {
         if (ev) return;
         const int lo = (int)(x & 0xffffu), hi = (int)(x >> 16);
+        sum += (unsigned)(lo + hi);
         best = umax64(best, a1_key(lo, 2u * wi));
         best = umax64(best, a1_key(hi, 2u * wi + 1u));
         if (HIST) {
             hist_add(lo, nib, sh, hist);
             hist_add(hi, nib, sh, hist);
         }
-    });
+    };
+    if (!REDO && side % 8 == 0) {  // after the return-less vote: the region's words (the wrap record is empty)
+        const uint4 *v = reinterpret_cast<const uint4 *>(A.w);
+        region_scan(side, [&](const int *k, int m) {
+            uint4 c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) c[u] = u < m ? __ldcs(v + k[u]) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (u < m) {
+                    const uint32_t wi = (uint32_t)k[u] << 2;
+                    visit(c[u].x, wi, false);
+                    visit(c[u].y, wi + 1, false);
+                    visit(c[u].z, wi + 2, false);
+                    visit(c[u].w, wi + 3, false);
+                }
+        });
+    } else {
+        acc16_scan(A, visit);
+    }
     if (HIST) {
         const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -486,15 +640,26 @@ __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(Acc16 A, int s
         for (int b = threadIdx.x; b < kHistSmem; b += kArgThreads)
             if (sh[b]) atomicAdd(&hist[b], sh[b]);
     }
-    __shared__ unsigned long long wbest[kArgThreads / 32];
+    __shared__ unsigned long long wbest[kArgThreads / 32], wsum[kArgThreads / 32];
     __shared__ bool last;
+    __shared__ int wrapped;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
+    for (int o = 16; o > 0; o >>= 1) {
+        best = umax64(best, __shfl_xor_sync(0xffffffffu, best, o));
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        wbest[threadIdx.x >> 5] = best;
+        wsum[threadIdx.x >> 5] = sum;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < kArgThreads / 32; ++w) best = umax64(best, wbest[w]);
+        for (int w = 1; w < kArgThreads / 32; ++w) {
+            best = umax64(best, wbest[w]);
+            sum += wsum[w];
+        }
         atomicMax(&hdr->best_key, best);
+        if (!REDO) atomicAdd(&hdr->decoded, sum);
         __threadfence();
         last = atomicAdd(&hdr->blocks_done, 1u) == gridDim.x - 1;
     }
@@ -505,9 +670,14 @@ __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(Acc16 A, int s
     __threadfence();
     const int64_t cells = (int64_t)side * side * side;
     best = 0;
+    if (threadIdx.x == 0) wrapped = 0;
+    __syncthreads();
+    // The return-less vote leaves the wrap record empty: with REDO = false this
+    // loop finds no words.
     for (uint32_t h = threadIdx.x; h <= A.emask; h += kArgThreads) {
         const uint32_t key = A.ekey[h];
         if (!key) continue;
+        atomicAdd(&wrapped, 1);
         const uint32_t wi = key - 1u;
         const uint32_t x = A.w[wi];
         const int64_t lo = (int64_t)(x & 0xffffu) + 65536ll * A.elo[h];
@@ -525,6 +695,7 @@ __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(Acc16 A, int s
     __syncthreads();
     if (threadIdx.x != 0) return;
     for (int w = 0; w < kArgThreads / 32; ++w) best = umax64(best, wbest[w]);
+    if (!REDO && atomicAdd(&hdr->decoded, 0ull) != hdr->cast) hdr->path = 1u;
     const unsigned long long key = umax64(best, atomicAdd(&hdr->best_key, 0ull));
     hdr->best_key = key;
     const uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffull);
@@ -543,7 +714,27 @@ __global__ void __launch_bounds__(kArgThreads) alg1_argmax_kernel(Acc16 A, int s
     res.ms_gpu = 0.f;
     res.npeaks = 0;
     res.peak_threshold = 0;
-    res.pad = 0;
+    res.vote_path = (int32_t)hdr->path;
+    res.wrapped_words = wrapped;
+}
+
+// Path 1, before the vote with the wrap record: clears the counters, the
+// histogram and the return-less vote's sums (the wrap record is still empty).
+__global__ void __launch_bounds__(kArgThreads) alg1_rezero_kernel(Acc16 A, A1Hdr *hdr, unsigned *__restrict__ hist) {
+    if (hdr->path != 1u) return;
+    const int64_t T = (int64_t)gridDim.x * kArgThreads;
+    const int64_t g = (int64_t)blockIdx.x * kArgThreads + threadIdx.x;
+    uint4 *v = reinterpret_cast<uint4 *>(A.w);
+    const int64_t nvec = A.nw >> 2;
+    for (int64_t k = g; k < nvec; k += T) v[k] = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t r = (nvec << 2) + g; r < A.nw; r += T) A.w[r] = 0u;
+    if (hist)
+        for (int64_t b = g; b < kHistBins; b += T) hist[b] = 0u;
+    if (g == 0) {
+        hdr->best_key = 0ull;
+        hdr->blocks_done = 0u;
+        hdr->rechecked = 0ull;
+    }
 }
 
 // The accumulator as int32 counts (the caller's copy).
@@ -790,6 +981,8 @@ void Context::alg1_release() {
     a1_mem = nullptr;
     a1_cap = 0;
     a1_J = 0;
+    a1_wrapped = false;
+    a1_clean_side = -1;
     if (a1_hdr_h) cudaFreeHost(a1_hdr_h);
     a1_hdr_h = nullptr;
     for (auto &e : a1_ev)
@@ -866,6 +1059,7 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
                 return fail(ROT_VOTE_ENOMEM, "cudaMalloc of the alg1 workspace failed");
             }
             a1_cap = need;
+            a1_clean_side = -1;
             bytes_held += need;
         }
         unsigned char *base = static_cast<unsigned char *>(a1_mem);
@@ -925,29 +1119,46 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         double2 *qd = reinterpret_cast<double2 *>(base + off_qd);
         if (e == cudaSuccess) e = cudaEventRecord(a1_ev[0], stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(hdr, 0, sizeof(A1Hdr), stream);
+        // Vote path.  Fewer than 65536 counts cannot wrap a counter: the
+        // return-less vote alone.  After a problem with wraps the recording
+        // vote runs alone (path 2).  Otherwise the return-less vote runs and
+        // the gated recording vote follows, returning at once unless the
+        // counters wrapped (path 1).
+        const bool may_wrap = total >= 65536;
+        const uint32_t path0 = may_wrap && a1_wrapped ? 2u : 0u;
+        // Zeroing: the ball region's words alone when the words outside it are
+        // known to be zero (the last problem had this n, took path 0 and so
+        // counted nothing outside the region); otherwise every word.
+        const bool full_zero = side % 8 != 0 || a1_clean_side != side;
+        a1_clean_side = -1;  // until this problem is known to have taken path 0
         mark(0, true);
         if (e == cudaSuccess) {
             const int64_t want = (std::max<int64_t>(P.n, nw / 4) + kA1Threads - 1) / kA1Threads;
             const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * 8));
-            alg1_prep_kernel<<<blocks, kA1Threads, 0, stream>>>(da, db, P.n, q1f, q2f, qd, acc, J, hdr);
+            alg1_prep_kernel<<<blocks, kA1Threads, 0, stream>>>(da, db, P.n, q1f, q2f, qd, acc, J, hdr, path0, side,
+                                                                full_zero);
             e = cudaGetLastError();
         }
         mark(0, false);
-        mark(1, true);
-        if (e == cudaSuccess) {
-            // persistent grid: resident blocks, or fewer when there are fewer samples
+        // persistent vote grid: resident blocks, or fewer when there are fewer samples
+        auto vote = [&](auto kernel) {
+            if (e != cudaSuccess) return;
             int per_sm = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, alg1_vote_kernel, kA1Threads, 0);
-            const int64_t total = P.n * (int64_t)J;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kA1Threads, 0);
             const int64_t want = (total + kA1Threads * kA1U - 1) / (kA1Threads * kA1U);
             const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * std::max(per_sm, 1)));
             const int64_t stride = (int64_t)blocks * kA1Threads * kA1U;
             if (e == cudaSuccess) {
-                alg1_vote_kernel<<<blocks, kA1Threads, 0, stream>>>(q1f, q2f, qd, t32, t64, J, side, acc, hdr, total,
-                                                                   stride / J, (int)(stride % J));
+                kernel<<<blocks, kA1Threads, 0, stream>>>(q1f, q2f, qd, t32, t64, J, side, acc, hdr, total, stride / J,
+                                                          (int)(stride % J));
                 e = cudaGetLastError();
             }
-        }
+        };
+        mark(1, true);
+        if (path0 == 2u)
+            vote(alg1_vote_kernel<true>);
+        else
+            vote(alg1_vote_kernel<false>);
         mark(1, false);
         mark(2, true);
         unsigned *hist = reinterpret_cast<unsigned *>(base + off_hist);
@@ -955,13 +1166,27 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         rot_vote_peak *pk = reinterpret_cast<rot_vote_peak *>(base + off_pk);
         const int64_t want_arg = (nw / 4 + kArgThreads - 1) / kArgThreads;
         const int arg_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_arg, (int64_t)sm_count * 8));
-        if (e == cudaSuccess && M > 0) e = cudaMemsetAsync(hist, 0, sizeof(unsigned) * kHistBins, stream);
-        if (e == cudaSuccess) {
+        auto argmax = [&](auto k_hist, auto k_plain) {
+            if (e != cudaSuccess) return;
             if (M > 0)
-                alg1_argmax_kernel<true><<<arg_blocks, kArgThreads, 0, stream>>>(acc, side, hdr, hist);
+                k_hist<<<arg_blocks, kArgThreads, 0, stream>>>(acc, side, hdr, hist);
             else
-                alg1_argmax_kernel<false><<<arg_blocks, kArgThreads, 0, stream>>>(acc, side, hdr, nullptr);
+                k_plain<<<arg_blocks, kArgThreads, 0, stream>>>(acc, side, hdr, nullptr);
             e = cudaGetLastError();
+        };
+        if (e == cudaSuccess && M > 0) e = cudaMemsetAsync(hist, 0, sizeof(unsigned) * kHistBins, stream);
+        if (path0 == 2u) {
+            argmax(alg1_argmax_kernel<true, true>, alg1_argmax_kernel<false, true>);
+        } else {
+            argmax(alg1_argmax_kernel<true, false>, alg1_argmax_kernel<false, false>);
+            if (may_wrap) {
+                if (e == cudaSuccess) {
+                    alg1_rezero_kernel<<<arg_blocks, kArgThreads, 0, stream>>>(acc, hdr, M > 0 ? hist : nullptr);
+                    e = cudaGetLastError();
+                }
+                vote(alg1_vote_kernel<true>);
+                argmax(alg1_argmax_kernel<true, true>, alg1_argmax_kernel<false, true>);
+            }
         }
         if (e == cudaSuccess && M > 0) {
             // peaks (Sec. 4.4): threshold, candidates, sort and greedy suppression
@@ -999,6 +1224,8 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         if (e != cudaSuccess) return cuda_fail(e, "running alg1");
         const A1Hdr *hh = static_cast<const A1Hdr *>(a1_hdr_h);
         r = hh->res;
+        a1_wrapped = r.wrapped_words > 0;
+        if (side % 8 == 0 && r.vote_path == 0) a1_clean_side = side;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, a1_ev[0], a1_ev[1]);
         r.ms_gpu = ms;

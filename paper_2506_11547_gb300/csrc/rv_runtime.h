@@ -131,6 +131,8 @@ class Context {
     int a1_J = 0;            // J of the angle tables in a1_mem (0 = none)
     size_t a1_toff = 0;      // their offset
     bool a1_peaks_attr = false;  // dynamic shared memory of the peak kernel raised
+    bool a1_wrapped = false;     // the last Alg. 1 problem had counter wraps: vote with the wrap record first
+    int a1_clean_side = -1;      // n whose counter words outside the ball region are all zero (-1: not known)
     // rigid pose (rv_pose.cu): row counts and offsets, translation table, staged points, kept pairs
     void *ps_mem = nullptr;
     size_t ps_cap = 0;

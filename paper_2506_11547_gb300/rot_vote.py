@@ -60,7 +60,8 @@ class rot_vote_alg1_problem(C.Structure):
 class rot_vote_alg1_result(C.Structure):
     _fields_ = [("q", C.c_double * 4), ("R", C.c_double * 9), ("best_count", C.c_int32), ("status", C.c_int32),
                 ("best_cell", C.c_int64), ("samples_cast", C.c_int64), ("rechecked", C.c_int64),
-                ("ms_gpu", C.c_float), ("npeaks", C.c_int32), ("peak_threshold", C.c_int32), ("pad", C.c_int32)]
+                ("ms_gpu", C.c_float), ("npeaks", C.c_int32), ("peak_threshold", C.c_int32), ("vote_path", C.c_int32),
+                ("wrapped_words", C.c_int32)]
 
 
 class rot_vote_pose_problem(C.Structure):
@@ -163,6 +164,8 @@ class Alg1Result:
     ms_gpu: float
     peak_threshold: int = 0
     peaks: list = dataclasses.field(default_factory=list)  # [(cell, count, q[4])] in peak order
+    vote_path: int = 0  # 0 return-less vote; 1 that vote, wrapped, then the recording vote; 2 recording vote only
+    wrapped_words: int = 0  # counter words holding a cell with 65536 or more votes
 
     @staticmethod
     def of(r: rot_vote_alg1_result, peaks=None) -> "Alg1Result":
@@ -170,7 +173,8 @@ class Alg1Result:
                                        for k in range(r.npeaks)]
         return Alg1Result(q=np.array(r.q[:]), R=np.array(r.R[:]).reshape(3, 3), best_count=r.best_count,
                           status=r.status, best_cell=r.best_cell, samples_cast=r.samples_cast,
-                          rechecked=r.rechecked, ms_gpu=r.ms_gpu, peak_threshold=r.peak_threshold, peaks=pk)
+                          rechecked=r.rechecked, ms_gpu=r.ms_gpu, peak_threshold=r.peak_threshold, peaks=pk,
+                          vote_path=r.vote_path, wrapped_words=r.wrapped_words)
 
 
 @dataclasses.dataclass

@@ -58,6 +58,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(rot_vote_alg1_problem), sizeof(rot_vote_alg1_result),
          offsetof(rot_vote_alg1_problem, accumulator), offsetof(rot_vote_alg1_result, samples_cast),
          offsetof(rot_vote_alg1_result, ms_gpu));
+  printf("%zu %zu\n", offsetof(rot_vote_alg1_result, vote_path), offsetof(rot_vote_alg1_result, wrapped_words));
   return 0;
 }
 '''
@@ -88,6 +89,7 @@ int main(void) {
     assert sizes[14] == rv.rot_vote_alg1_problem.accumulator.offset
     assert sizes[15] == rv.rot_vote_alg1_result.samples_cast.offset
     assert sizes[16] == rv.rot_vote_alg1_result.ms_gpu.offset
+    assert sizes[17:19] == [rv.rot_vote_alg1_result.vote_path.offset, rv.rot_vote_alg1_result.wrapped_words.offset]
 
 
 def test_missing_library_fails_loudly(tmp_path):

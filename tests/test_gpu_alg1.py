@@ -4,7 +4,10 @@ The bar is bit-exact: the library decides every sample's cell as the IEEE
 double evaluation of the formulas does (FP32 first, FP64 again near a cell
 boundary or near q3 = 0), so the whole n^3 accumulator, the winner, its count
 and the number of samples cast equal the oracle's, and so does the rotation
-(the same IEEE operations on the same cell centre).
+(the same IEEE operations on the same cell centre).  The counter-wrap cases
+also check the vote path: the return-less vote, then the vote with the wrap
+record exactly when a cell reached 65536 votes, or the recording vote alone
+after a problem with wraps.
 """
 import numpy as np
 import pytest
@@ -28,7 +31,9 @@ def edge_pairs():
     """Pairs that exercise the special cases: axis-aligned a = b (samples on
     cell boundaries: p_1 = p_2 = 0 exactly), a = -b (w = 0: no circle), and
     near-antipodal pairs with |a| slightly above 1, whose basis norms are far
-    from 1 (every sample on the FP64 path)."""
+    from 1 (every sample on the FP64 path).  Along a diagonal, such a pair's
+    samples reach |p| of about 3 and clamp onto the cube's edges, far outside
+    the unit ball."""
     a, b = [], []
     for k in range(3):
         e = np.zeros(3, np.float32)
@@ -39,6 +44,11 @@ def edge_pairs():
     for th in (3e-3, 4e-3, 6e-3):
         a.append(np.array([s, 0.0, 0.0], np.float32))
         b.append(np.array([-np.cos(th), np.sin(th), 0.0], np.float32))
+        for ux, uy in ((1, 1), (1, -1)):
+            u = np.array([ux, uy, 0.0]) / np.sqrt(2)
+            a.append((s * u).astype(np.float32))
+            c, sn = np.cos(th), np.sin(th)
+            b.append(np.array([-(u[0] * c - u[1] * sn), -(u[0] * sn + u[1] * c), 0.0], np.float32))
     return np.array(a, np.float32), np.array(b, np.float32)
 
 
@@ -58,6 +68,38 @@ def run_both(a, b, J, side, device=True, acc_on_device=False):
     return r, acc, o
 
 
+def wrapped_words(acc):
+    """Counter words (cells 2w, 2w + 1) holding a count of 65536 or more."""
+    hot = np.nonzero(acc >= 65536)[0]
+    return len(np.unique(hot // 2))
+
+
+def box_distance(side):
+    """Distance from the origin to each cell's box, in linear-index order."""
+    h = 2.0 / side
+    lo = -1 + np.arange(side) * h
+    d = np.where(lo > 0, lo, np.where(lo + h < 0, -(lo + h), 0.0))
+    return np.sqrt(d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2).reshape(-1)
+
+
+def expected_vote_paths(acc, side):
+    """Vote paths a fresh context may take.  Path 1 (the recording re-vote) is
+    certain when a counter wrapped.  With n a multiple of 8 the return-less pass
+    scans the cells within 1.01 of the origin (plus a margin of up to eight
+    cells along x), so counts in cells beyond 1.0005 may also send a problem to
+    path 1, and counts beyond that margin must."""
+    if wrapped_words(acc):
+        return {1}
+    if side % 8:
+        return {0}
+    D, voted = box_distance(side), acc > 0
+    if not (voted & (D > 1.0005)).any():
+        return {0}
+    if (voted & (D > 1.01 + 9 * 2.0 / side)).any():
+        return {1}
+    return {0, 1}
+
+
 def check(r, acc, o):
     o_acc, o_bi, o_bc, o_q, o_cast = o
     assert r.status == rv.OK
@@ -65,6 +107,12 @@ def check(r, acc, o):
     assert len(d) == 0, f"{len(d)} accumulator cells differ, e.g. {d[:5]}: {acc[d[:5]]} vs {o_acc[d[:5]]}"
     assert (r.best_cell, r.best_count, r.samples_cast) == (o_bi, o_bc, o_cast)
     assert np.array_equal(r.q, o_q), (r.q, o_q)
+    # a word wraps exactly when one of its two cells holds 65536 or more votes;
+    # a fresh context takes the return-less vote first and re-votes with the
+    # wrap record when a counter wrapped or a count fell outside the scanned region
+    assert r.wrapped_words == wrapped_words(o_acc)
+    side = round(len(o_acc) ** (1 / 3))
+    assert r.vote_path in expected_vote_paths(o_acc, side), (r.vote_path, expected_vote_paths(o_acc, side))
     import oracle
     assert np.allclose(r.R, oracle.quat_to_R(o_q), rtol=0, atol=1e-15)
 
@@ -246,3 +294,55 @@ def test_alg1_counter_wraps(n_lo, n_hi):
     assert acc[cells[i]] >= n_lo and acc[cells[i] + 1] >= n_hi
     rp, accp, op = run_peaks(A, B, J, side, 4, 0.3)
     check_peaks(rp, op)
+    assert np.array_equal(accp, acc) and rp.wrapped_words == r.wrapped_words and rp.vote_path == r.vote_path
+
+
+def test_alg1_vote_path_follows_the_previous_problem():
+    """One context, problems with and without counter wraps in turn: the
+    return-less vote first (re-voting when it wrapped), the recording vote
+    alone after a problem with wraps; every accumulator equals the oracle's."""
+    import oracle
+    side, J = 8, 2
+    a, b, cells = _pairs_by_cell(side, J)
+    i = int(np.nonzero(cells >= 0)[0][0])
+    hot_a = np.concatenate([np.repeat(a[i:i + 1], 70000, 0), a[:500]])
+    hot_b = np.concatenate([np.repeat(b[i:i + 1], 70000, 0), b[:500]])
+    # 40000 random pairs: 80000 samples (enough to wrap a counter) over 512 cells, none near 65536
+    rng = np.random.default_rng(2910)
+    cold_a, cold_b = (rng.standard_normal((40000, 3)) for _ in range(2))
+    cold_a = (cold_a / np.linalg.norm(cold_a, axis=1, keepdims=True)).astype(np.float32)
+    cold_b = (cold_b / np.linalg.norm(cold_b, axis=1, keepdims=True)).astype(np.float32)
+    seq = [(cold_a, cold_b, 0), (hot_a, hot_b, 1), (hot_a, hot_b, 2), (cold_a, cold_b, 2), (cold_a, cold_b, 0)]
+    with rv.Context() as ctx:
+        for A, B, path in seq:
+            acc = np.zeros(side ** 3, np.int32)
+            r = ctx.alg1([(dev(A), dev(B), J, side, acc)])[0]
+            o = oracle.alg1(A, B, J, side)
+            assert r.vote_path == path
+            assert r.wrapped_words == wrapped_words(o[0])
+            assert np.array_equal(acc, o[0])
+            assert (r.best_cell, r.best_count, r.samples_cast) == (o[1], o[2], o[4])
+            assert np.array_equal(r.q, o[3])
+
+
+def test_alg1_zeroing_after_stray_counts_and_side_changes():
+    """One context: a problem whose FP64-only pairs count far outside the ball
+    (re-voted on path 1, leaving counts outside the region), then problems of
+    the same and of other sides, which must start from a fully zeroed
+    accumulator whenever the words outside the region are not known to be zero."""
+    import oracle
+    p = synth.make_problem(4000, 0.9, 0.01, 0.03, seed=2920)
+    ea, eb = with_edges(p)
+    seq = [(ea, eb, 64), (p.a, p.b, 64), (p.a, p.b, 64), (p.a, p.b, 48), (p.a, p.b, 64), (ea, eb, 48),
+           (p.a, p.b, 48)]
+    with rv.Context() as ctx:
+        for k, (A, B, side) in enumerate(seq):
+            acc = np.zeros(side ** 3, np.int32)
+            r = ctx.alg1([(dev(A), dev(B), 180, side, acc)])[0]
+            o = oracle.alg1(A, B, 180, side)
+            assert np.array_equal(acc, o[0]), k
+            assert (r.best_cell, r.best_count, r.samples_cast) == (o[1], o[2], o[4]), k
+            assert np.array_equal(r.q, o[3]), k
+            if k == 0:
+                # the near-antipodal non-unit pairs count outside the region
+                assert (o[0][box_distance(side) > 1.2] > 0).any() and r.vote_path == 1

@@ -214,10 +214,13 @@ def check_peaks(r, o):
         assert np.array_equal(q, oq)
 
 
-@pytest.mark.parametrize("M,theta,min_count", [(1, 0.1, 0), (6, 0.15, 0), (64, 0.05, 0), (9, 0.3, 40), (12, 0.0, 0)])
-def test_alg1_peaks_multi_motion_scene(M, theta, min_count):
+@pytest.mark.parametrize("M,theta,min_count,side", [(1, 0.1, 0, 120), (6, 0.15, 0, 120), (64, 0.05, 0, 120),
+                                                    (9, 0.3, 40, 120), (12, 0.0, 0, 120), (6, 0.15, 0, 90)])
+def test_alg1_peaks_multi_motion_scene(M, theta, min_count, side):
+    """At side 120 the argmax after the return-less vote reads only the ball
+    region's words; at side 90 (not a multiple of 8) it reads every word."""
     mp = synth.make_multi_problem(4, 800, sigma=0.01, outlier_frac=0.5, seed=2700 + M)
-    r, acc, o = run_peaks(mp.a, mp.b, 540, 120, M, theta, min_count)
+    r, acc, o = run_peaks(mp.a, mp.b, 540, side, M, theta, min_count)
     check_peaks(r, o)
     if M == 1:
         assert r.peaks[0][0] == r.best_cell and r.peaks[0][1] == r.best_count

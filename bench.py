@@ -362,6 +362,29 @@ def bench_alg1(rv, synth, torch, stream, flush, peaks, reps: int = 5):
     return res
 
 
+def tensor_pipe_fraction(rv, prec, grid_n, levels, a_d, b_d, delta, stream, flush, tests0, peaks, peak_src):
+    """The tcgen05 coarse-vote launch of a precision form against the dense bf16/fp16 tensor peak:
+    its duration from stage events on the launching stream (mean of 3 solves after one, L2 flushed
+    before each), the algorithmic rate (20 flops per test, the 10 multiply-adds of the contraction)
+    and the executed MMA rate (2 K flops per test: K = 32 for the hi/lo forms, 16 otherwise)."""
+    ctx = rv.Context(grid_n=grid_n, levels=levels, precision=prec, cuda_stream=stream.cuda_stream, keep_trace=2)
+    ms = []
+    for k in range(4):
+        flush.zero_()
+        ctx.solve([(a_d, b_d, delta)])
+        if k:
+            ms += [t for kind, lev, t in ctx.stage_times() if kind == "vote" and lev == 0]
+    ctx.close()
+    t = sum(ms) / len(ms) / 1e3
+    k = 32 if prec.endswith("x2") else 16
+    peak = peaks["bf16_tflops"]
+    return {"kernel": "vote level 0", "kernel_ms": t * 1e3, "tests_per_launch": tests0,
+            "algorithmic_tflops": FLOPS_PER_TEST * tests0 / t / 1e12, "mma_flops_per_test": 2 * k,
+            "mma_tflops": 2 * k * tests0 / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac_algorithmic": FLOPS_PER_TEST * tests0 / t / 1e12 / peak, "frac_mma": 2 * k * tests0 / t / 1e12 / peak,
+            "peak_source": f"dense bf16 tensor burst ({peak_src}); fp16 dense has the same nominal rate"}
+
+
 def bench_paper_scale(rv, synth, torch, stream, flush, reps: int = 3):
     """The precision forms at the paper's scale: 1e6 pairs, 99% outliers, sigma 0.005, delta 0.03,
     128^3 + 3 levels (1.14e12 cell tests per solve).  Device time per solve (L2 flushed before
@@ -718,7 +741,9 @@ def main():
             extra[prec] = {"value": tests_per_step / (sum(ts) / len(ts) / 1e3), "unit": UNIT,
                            "ms_per_step": sum(ts) / len(ts), "rechecked": rr.rechecked,
                            "same_result_as_fp32": bool(rr.best_cell == res0.best_cell and
-                                                       list(rr.q) == list(res0.q))}
+                                                       list(rr.q) == list(res0.q)),
+                           "tensor_pipe": tensor_pipe_fraction(rv, prec, grid_n, levels, a_d, b_d, p.delta, stream,
+                                                               flush, n_cells0 * p.n, peaks, peak_src)}
             cx.close()
         # the same workload in the stereographic chart (Sec. 4.3.1), FP32 form
         cx = rv.Context(grid_n=grid_n, levels=levels, precision="fp32", chart="stereographic",

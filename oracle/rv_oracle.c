@@ -38,10 +38,10 @@
  * Pins (tests/test_oracle_pins.py): steps 1-7 and the fit of a given inlier
  * set are each checked against the paper's closed forms, brute force, an
  * independent lattice count or numpy/SVD.  The refit iteration of step 8 is
- * pinned by its fixed point: when it stops on a repeated inlier set, q is the
- * smallest eigenvector of the sum of App. D's S_i over {i : q^T S_i q <=
- * sin^2(delta)} (numpy eigh).  A refit stopped by the iteration cap has no
- * further pin.
+ * pinned step by step: the fit with cap T returns the T-th iterate, which is
+ * the smallest eigenvector of the sum of App. D's S_i over {i : q^T S_i q <=
+ * sin^2(delta)} for the previous iterate q (numpy eigh), and at a repeated
+ * inlier set q is a fixed point of that rule.
  */
 #include <math.h>
 #include <pthread.h>

@@ -498,3 +498,38 @@ def test_refit_converges_to_a_fixed_point(oracle_mod):
         assert min(np.linalg.norm(e - r.q), np.linalg.norm(e + r.q)) < 1e-9
         checked += 1
     assert checked >= 3
+
+
+def test_refit_each_step_follows_the_rule(oracle_mod):
+    """Every refit step (reading C9), including a refit stopped by the iteration
+    cap: the fit from a cell with cap T returns the T-th iterate, so for each T
+    up to the step where the inlier set repeats, q_T is the smallest eigenvector
+    of sum S_i over I(q_{T-1}) = {i : q_{T-1}^T S_i q_{T-1} <= sin^2(delta)} and
+    the reported inlier count is |I(q_{T-1})|, with S_i from App. D and the
+    eigenvector from numpy eigh.  Past that step the iterate no longer moves."""
+    steps = 0
+    for seed in (900, 902, 910):
+        p = synth.make_problem(1500, rho=0.8, sigma=0.03, delta=0.04, seed=seed)
+        delta = float(np.float32(p.delta))
+        cell = oracle_mod.solve(p.a, p.b, delta, grid_n=24, levels=0, refit_iters=0, trace=False).best_cell
+        rs = [oracle_mod.fit_cell(p.a, p.b, delta, 24, cell, refit_iters=T) for T in range(8)]
+        As = [_appD_A(p.a[i], p.b[i]) for i in range(p.n)]
+        Ss = np.array([A.T @ A / 4 - c * np.eye(4) for A, c in As])
+        thr = np.sin(delta) ** 2
+        for T in range(1, 8):
+            prev, cur = rs[T - 1], rs[T]
+            assert cur.status == 0
+            if cur.refits < T:  # the set repeated: the iterate stays
+                assert cur.refits == prev.refits and np.array_equal(cur.q, prev.q)
+                continue
+            assert cur.refits == T
+            v = np.einsum("j,ijk,k->i", prev.q, Ss, prev.q)
+            assert not (np.abs(v - thr) < 1e-12).any()
+            inl = v <= thr
+            assert inl.sum() == cur.inliers
+            w, V = np.linalg.eigh(Ss[inl].sum(0))
+            assert w[1] - w[0] > 1e-9 * abs(w).max()
+            e = V[:, 0]
+            assert min(np.linalg.norm(e - cur.q), np.linalg.norm(e + cur.q)) < 1e-9
+            steps += 1
+    assert steps >= 9

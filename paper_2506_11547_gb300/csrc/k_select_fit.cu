@@ -1,7 +1,8 @@
 // k_select_fit.cu -- ranking of the voted cells, top-K selection, and the
 // final fit (Eq. stack, Sec. 4.2) with its refit loop.
-#include <cooperative_groups.h>
 #include <float.h>
+
+#include <algorithm>
 
 #include "rv_geom.cuh"
 #include "rv_internal.h"
@@ -308,7 +309,6 @@ __device__ __forceinline__ void sumS_from_B(const double B[9], double m, double 
 
 constexpr int kFitPer = 8;                     // pairs per thread per slice
 constexpr int kFitSlice = kFitThreads * kFitPer;  // 4096 pairs: the unit of the fixed reduction order
-constexpr int kFitMaxCluster = 8;
 
 // Deterministic block-wide exclusive scan of a small per-thread count.
 __device__ __forceinline__ int block_excl_scan(int v, int *total) {
@@ -334,11 +334,16 @@ __device__ __forceinline__ int block_excl_scan(int v, int *total) {
 
 // One slice of a fit pass: membership by the FP32 re-check
 // (|b - R a|^2/4 - c <= thr) for pairs [base, base + kFitSlice), stored in
-// mem[]; members compacted in index order and their b a^T summed in FP64 by
-// warp 0 in a fixed order.  Writes the slice's 9 sums, member count and
-// changed count to part[0..10] (thread 0).  Depends only on the slice.
+// mem[]; members compacted in index order, thread t summing the b a^T of
+// members t, t + kFitThreads, ... in FP64, and the thread sums reduced by a
+// fixed pairwise tree in shared memory.  The tree skips a partner whose whole
+// subtree lies at or beyond the member count: such a subtree holds only
+// zeros, and adding 0.0 changes nothing, so the result is that of the full
+// tree.  Writes the slice's 9 sums, member count and changed count to
+// part[0..10] (thread 0).  Depends only on the slice.
 __device__ void fit_slice(const float4 *__restrict__ pr, uint8_t *mem, int64_t n, int64_t base, const float4 &R0,
-                          const float4 &R1, const float4 &R2, float thr, bool first, int *list, double *part) {
+                          const float4 &R1, const float4 &R2, float thr, bool first, int *list,
+                          double (*red)[kFitThreads / 2], double *part) {
     int mine[kFitPer];
     int cnt = 0, chg = 0;
 #pragma unroll
@@ -361,34 +366,50 @@ __device__ void fit_slice(const float4 *__restrict__ pr, uint8_t *mem, int64_t n
     for (int e = 0; e < kFitPer; ++e)
         if (e < cnt) list[off + e] = mine[e];
     __syncthreads();
-    if (threadIdx.x < 32) {
-        double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int k = threadIdx.x; k < tot; k += 32) {
-            const int64_t i = base + list[k];
-            const float4 p0 = pr[2 * i], p1 = pr[2 * i + 1];
-            const double a0 = p0.x, a1 = p0.y, a2 = p0.z, b0 = p0.w, b1 = p1.x, b2 = p1.y;
-            acc[0] = fma(b0, a0, acc[0]);
-            acc[1] = fma(b0, a1, acc[1]);
-            acc[2] = fma(b0, a2, acc[2]);
-            acc[3] = fma(b1, a0, acc[3]);
-            acc[4] = fma(b1, a1, acc[4]);
-            acc[5] = fma(b1, a2, acc[5]);
-            acc[6] = fma(b2, a0, acc[6]);
-            acc[7] = fma(b2, a1, acc[7]);
-            acc[8] = fma(b2, a2, acc[8]);
-        }
-        if (tot > 0) {
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < tot; k += kFitThreads) {
+        const int64_t i = base + list[k];
+        const float4 p0 = pr[2 * i], p1 = pr[2 * i + 1];
+        const double a0 = p0.x, a1 = p0.y, a2 = p0.z, b0 = p0.w, b1 = p1.x, b2 = p1.y;
+        acc[0] = fma(b0, a0, acc[0]);
+        acc[1] = fma(b0, a1, acc[1]);
+        acc[2] = fma(b0, a2, acc[2]);
+        acc[3] = fma(b1, a0, acc[3]);
+        acc[4] = fma(b1, a1, acc[4]);
+        acc[5] = fma(b1, a2, acc[5]);
+        acc[6] = fma(b2, a0, acc[6]);
+        acc[7] = fma(b2, a1, acc[7]);
+        acc[8] = fma(b2, a2, acc[8]);
+    }
+    const int active = tot < kFitThreads ? tot : kFitThreads;  // threads holding a member
+    constexpr int kHalf = kFitThreads / 2;
+    const int t = threadIdx.x;
+    // first level (stride kHalf) through shared memory into the lower half's registers
+    if (t >= kHalf && t < active)
 #pragma unroll
-            for (int k = 0; k < 9; ++k)
-                for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-        }
-        if (threadIdx.x == 0) {
-            for (int k = 0; k < 9; ++k) part[k] = tot > 0 ? acc[k] : 0.0;
-            part[9] = (double)tot;
-            int c = 0;
-            for (int j = 0; j < kFitThreads / 32; ++j) c += wchg[j];
-            part[10] = (double)c;
-        }
+        for (int v = 0; v < 9; ++v) red[v][t - kHalf] = acc[v];
+    __syncthreads();
+    if (t < kHalf && t + kHalf < active)
+#pragma unroll
+        for (int v = 0; v < 9; ++v) acc[v] += red[v][t];
+    __syncthreads();
+    if (t < kHalf && t < active)
+#pragma unroll
+        for (int v = 0; v < 9; ++v) red[v][t] = acc[v];
+    __syncthreads();
+#pragma unroll 1
+    for (int st = kHalf / 2; st > 0; st >>= 1) {
+        if (t < st && t + st < active)
+#pragma unroll
+            for (int v = 0; v < 9; ++v) red[v][t] += red[v][t + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int v = 0; v < 9; ++v) part[v] = active > 0 ? red[v][0] : 0.0;
+        part[9] = (double)tot;
+        int c = 0;
+        for (int j = 0; j < kFitThreads / 32; ++j) c += wchg[j];
+        part[10] = (double)c;
     }
     __syncthreads();
 }
@@ -512,7 +533,7 @@ __device__ __forceinline__ void R32_of(const double q[4], float4 &R0, float4 &R1
     R2 = make_float4((float)R[8], 0.f, 0.f, 0.f);
 }
 
-// Shared state of the fit, owned by the cluster's rank-0 CTA.
+// The fit state of one problem in shared memory.
 struct FitShared {
     double q[4];
     int done, status, nin, refits;
@@ -593,86 +614,128 @@ __device__ void fit_result(int p, const LevelRef &L, int wpos, int last, const F
     results[p] = r;
 }
 
-// Fit of one problem per thread-block cluster (gridDim.x = problems x C):
-// the C CTAs split the problem's slices round-robin and write per-slice
-// partial sums to global memory; after a cluster barrier, rank 0 sums the
-// slices in index order, solves the 4x4 eigenproblem and publishes q in its
-// shared memory, which the other CTAs read through distributed shared memory.
-// The result is independent of C and of the other problems in the batch.
-__global__ void __launch_bounds__(kFitThreads) fit_kernel(const ProbRef *__restrict__ probs,
-                                                          const LevelRef *__restrict__ lref, int level_stride,
-                                                          const int32_t *__restrict__ kept_pos, int top_k,
-                                                          int refit_iters, PairPool pool, uint8_t *member,
-                                                          double *slice_part, const int64_t *slice_off,
-                                                          const int32_t *__restrict__ plist,
-                                                          const ProbStats *__restrict__ stats,
-                                                          rot_vote_result *results) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int C = (int)cluster.num_blocks();
-    const int rank = (int)cluster.block_rank();
-    const int p = plist[blockIdx.x / C];
-    const ProbRef P = probs[p];
-    const int last = P.levels;
-    const LevelRef L = lref[p * level_stride + last];
-    const int wpos = kept_pos[(p * level_stride + last) * top_k];
-    __shared__ FitShared sh;
-    __shared__ double As[4][4];
-    __shared__ float Vf[4][4];
-    __shared__ double Btot[11];
-    __shared__ int list[kFitSlice];
-    FitShared *root = cluster.map_shared_rank(&sh, 0);
-    if (wpos < 0) {  // no cell at the last level (cannot happen for valid inputs)
-        if (rank == 0 && threadIdx.x == 0) {
-            rot_vote_result r = {};
-            r.status = ROT_VOTE_EDEGENERATE;
-            results[p] = r;
-        }
-        return;  // uniform across the cluster
+// One fit step of large problem k (big_list[k] = p) by one warp, once all its
+// slices of iteration t are written: the slices summed in index order (read
+// past L1: other SMs wrote them), the 4x4 eigen-solve, and q and the stop
+// state kept in state[k]; the result is written when the fit stops.
+__device__ void fit_solve_warp(int k, int p, int t, int refit_iters, const ProbRef &P, const LevelRef &L, int wpos,
+                               int last, const double *slice_part, const int64_t *__restrict__ slice_off,
+                               FitState *state, const ProbStats *__restrict__ stats, rot_vote_result *results,
+                               FitShared &sh, double (*As)[4], float (*Vf)[4], double *Btot) {
+    const int lane = threadIdx.x;
+    if (lane == 0 && t > 0) {
+        for (int r = 0; r < 4; ++r) sh.q[r] = state[k].q[r];
+        sh.done = 0;
+        sh.status = state[k].status;
+        sh.nin = state[k].nin;
+        sh.refits = state[k].refits;
     }
-    const int64_t n = P.n;
-    const float4 *pr = pool.pr + 2 * P.pool_off;
-    uint8_t *mem = member + P.pool_off;
-    double *part = slice_part + 11 * slice_off[p];
-    const int64_t nslices = (n + kFitSlice - 1) / kFitSlice;
+    const double *part = slice_part + 11 * slice_off[p];
+    const int64_t nslices = (P.n + kFitSlice - 1) / kFitSlice;
+    if (lane < 11) {  // slices summed in index order
+        double acc = 0.0;
+        for (int64_t sl = 0; sl < nslices; ++sl) acc += __ldcg(part + 11 * sl + lane);
+        Btot[lane] = acc;
+    }
+    __syncwarp();
     double qc[4];
     {
         const double4_32a q4 = L.cells.q[wpos];
         qc[0] = q4.x; qc[1] = q4.y; qc[2] = q4.z; qc[3] = q4.w;
     }
-
-    // iteration 0: the voters of the winning cell (FP32 re-check decisions);
-    // iterations t >= 1: q_{t-1}^T S_i q_{t-1} <= sin^2(delta)
-    const float thr_refit = (float)(P.sin_d * P.sin_d);
-    float4 R0 = L.cells.R32[3 * wpos], R1 = L.cells.R32[3 * wpos + 1], R2 = L.cells.R32[3 * wpos + 2];
-    float thr = (float)tau_cs(P.sin_d, P.cos_d, L.cells.trig[wpos]);
-    for (int t = 0; t <= refit_iters; ++t) {
-        for (int64_t sl = rank; sl < nslices; sl += C)
-            fit_slice(pr, mem, n, sl * kFitSlice, R0, R1, R2, thr, t == 0, list, part + 11 * sl);
-        cluster.sync();  // every slice partial is written
-        if (rank == 0) {
-            if (threadIdx.x < 11) {  // slices summed in index order
-                double acc = 0.0;
-                for (int64_t sl = 0; sl < nslices; ++sl) acc += part[11 * sl + threadIdx.x];
-                Btot[threadIdx.x] = acc;
-            }
-            __syncthreads();
-            if (threadIdx.x < 32) fit_step_warp0(t, refit_iters, Btot, As, Vf, qc, sh);
-        }
-        cluster.sync();  // rank 0 has published q / done
-        if (root->done) break;  // uniform: every CTA reads rank 0's flag
-        double q[4] = {root->q[0], root->q[1], root->q[2], root->q[3]};
-        R32_of(q, R0, R1, R2);
-        thr = thr_refit;
-        cluster.sync();  // rank 0's state is not rewritten before everyone has read it
+    fit_step_warp0(t, refit_iters, Btot, As, Vf, qc, sh);
+    __syncwarp();
+    if (lane == 0) {
+        FitState &st = state[k];
+        for (int r = 0; r < 4; ++r) st.q[r] = sh.q[r];
+        st.status = sh.status;
+        st.nin = sh.nin;
+        st.refits = sh.refits;
+        st.done = sh.done;
+        if (sh.done) fit_result(p, L, wpos, last, sh, stats, results);
     }
-    if (rank == 0 && threadIdx.x == 0) fit_result(p, L, wpos, last, sh, stats, results);
-    cluster.sync();  // rank 0's shared memory stays alive until every CTA is done reading it
+}
+
+// Iteration t of the fit of the large problems (n > kFitSmallMax), all of
+// them on the whole GPU, one launch per iteration: a grid-stride pass over the
+// flat list of their slices (big_soff[k] is the first slice of the k-th large
+// problem), skipping problems whose fit has stopped.  The block that writes a
+// problem's last slice (counted in done_cnt[k], reset for the next iteration)
+// then runs that problem's fit step with its first warp.  Iteration 0 takes
+// the winning cell's voters (its rotation and threshold), iteration t >= 1 the
+// pairs with q_{t-1}^T S_i q_{t-1} <= sin^2(delta).  The result depends only
+// on the problem.
+__global__ void __launch_bounds__(kFitThreads, 2) fit_iter_kernel(
+    const ProbRef *__restrict__ probs, const LevelRef *__restrict__ lref, int level_stride,
+    const int32_t *__restrict__ kept_pos, int top_k, int t, int refit_iters, PairPool pool, uint8_t *member,
+    double *slice_part, const int64_t *__restrict__ slice_off, const int32_t *__restrict__ big_list,
+    const int64_t *__restrict__ big_soff, int nbig, FitState *state, int *done_cnt,
+    const ProbStats *__restrict__ stats, rot_vote_result *results) {
+    __shared__ int list[kFitSlice];
+    __shared__ double red[9][kFitThreads / 2];
+    __shared__ FitShared sh;
+    __shared__ double As[4][4];
+    __shared__ float Vf[4][4];
+    __shared__ double Btot[11];
+    __shared__ bool last_block;
+    const int64_t total = big_soff[nbig];
+    for (int64_t f = blockIdx.x; f < total; f += gridDim.x) {
+        int k = 0, hi = nbig - 1;  // the large problem holding slice f: largest k with big_soff[k] <= f
+        while (k < hi) {
+            const int mid = (k + hi + 1) >> 1;
+            if (big_soff[mid] <= f) k = mid;
+            else hi = mid - 1;
+        }
+        if (t > 0 && state[k].done) continue;  // uniform across the block
+        const int p = big_list[k];
+        const ProbRef P = probs[p];
+        const int last = P.levels;
+        const LevelRef L = lref[p * level_stride + last];
+        const int wpos = kept_pos[(p * level_stride + last) * top_k];
+        if (wpos < 0) {  // no cell at the last level (cannot happen for valid inputs)
+            if (f == big_soff[k] && threadIdx.x == 0) {
+                rot_vote_result r = {};
+                r.status = ROT_VOTE_EDEGENERATE;
+                results[p] = r;
+                state[k].done = 1;
+            }
+            continue;
+        }
+        float4 R0, R1, R2;
+        float thr;
+        if (t == 0) {
+            R0 = L.cells.R32[3 * wpos];
+            R1 = L.cells.R32[3 * wpos + 1];
+            R2 = L.cells.R32[3 * wpos + 2];
+            thr = (float)tau_cs(P.sin_d, P.cos_d, L.cells.trig[wpos]);
+        } else {
+            const double q[4] = {state[k].q[0], state[k].q[1], state[k].q[2], state[k].q[3]};
+            R32_of(q, R0, R1, R2);
+            thr = (float)(P.sin_d * P.sin_d);
+        }
+        const int64_t sl = f - big_soff[k];
+        fit_slice(pool.pr + 2 * P.pool_off, member + P.pool_off, P.n, sl * kFitSlice, R0, R1, R2, thr, t == 0, list,
+                  red, slice_part + 11 * (slice_off[p] + sl));
+        if (threadIdx.x == 0) {
+            __threadfence();  // this slice's sums are visible before it is counted
+            last_block = atomicAdd(&done_cnt[k], 1) == (int)(big_soff[k + 1] - big_soff[k]) - 1;
+        }
+        __syncthreads();
+        if (last_block) {
+            if (threadIdx.x < 32) {
+                __threadfence();
+                fit_solve_warp(k, p, t, refit_iters, P, L, wpos, last, slice_part, slice_off, state, stats, results,
+                               sh, As, Vf, Btot);
+            }
+            if (threadIdx.x == 0) done_cnt[k] = 0;  // every slice of iteration t is counted
+        }
+        __syncthreads();
+    }
 }
 
 
-// Fit of one small problem (n <= kFitSmallMax) per CTA, no cluster: the same
-// membership rule, stop rule and eigen-solve as fit_kernel.  Thread t takes the
+// Fit of one small problem (n <= kFitSmallMax) per CTA: the same membership
+// rule, stop rule and eigen-solve as the large problems' passes.  Thread t takes the
 // pairs t, t + kFitSmallThreads, ... and sums its members' b a^T in FP64 in
 // that order; the sums are then reduced in a fixed tree, so the result depends
 // only on the problem (not on the batch).
@@ -798,7 +861,8 @@ int fit_slices(int64_t n) { return (int)((n + kFitSlice - 1) / kFitSlice); }
 cudaError_t launch_fit(const ProbRef *probs, const LevelRef *lref, int level_stride, const int32_t *kept_pos,
                        int top_k, int refit_iters, PairPool pool, uint8_t *member, double *slice_part,
                        const int64_t *slice_off, const int32_t *small_list, int nsmall, const int32_t *big_list,
-                       int nbig, int cluster, const ProbStats *stats, rot_vote_result *results, cudaStream_t s) {
+                       int nbig, const int64_t *big_soff, int64_t big_slices, FitState *state, int *done_cnt,
+                       int sms, const ProbStats *stats, rot_vote_result *results, cudaStream_t s) {
     if (nsmall > 0) {
         fit_small_kernel<<<nsmall, kFitSmallThreads, 0, s>>>(probs, lref, level_stride, kept_pos, top_k, refit_iters,
                                                              pool, member, small_list, stats, results);
@@ -806,21 +870,17 @@ cudaError_t launch_fit(const ProbRef *probs, const LevelRef *lref, int level_str
         if (e != cudaSuccess) return e;
     }
     if (nbig <= 0) return cudaSuccess;
-    if (cluster < 1 || cluster > kFitMaxCluster) return cudaErrorInvalidValue;
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3((unsigned)(nbig * cluster));
-    lc.blockDim = dim3(kFitThreads);
-    lc.dynamicSmemBytes = 0;
-    lc.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    lc.attrs = at;
-    lc.numAttrs = 1;
-    return cudaLaunchKernelEx(&lc, fit_kernel, probs, lref, level_stride, kept_pos, top_k, refit_iters, pool, member,
-                              slice_part, slice_off, big_list, stats, results);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_iter_kernel, kFitThreads, 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(done_cnt, 0, sizeof(int) * nbig, s);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(big_slices, (int64_t)sms * std::max(per_sm, 1)));
+    for (int t = 0; t <= refit_iters && e == cudaSuccess; ++t) {
+        fit_iter_kernel<<<grid, kFitThreads, 0, s>>>(probs, lref, level_stride, kept_pos, top_k, t, refit_iters, pool,
+                                                     member, slice_part, slice_off, big_list, big_soff, nbig, state,
+                                                     done_cnt, stats, results);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace rv

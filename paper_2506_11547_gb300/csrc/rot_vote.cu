@@ -305,21 +305,22 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     }
     const size_t o_slice = reserve(sizeof(double) * 11 * (size_t)std::max<int64_t>(1, nsl));
     const size_t o_sloff = reserve(sizeof(int64_t) * P);
-    // fit paths: one CTA per small problem, a cluster per large one; the cluster
-    // size gives the largest one enough CTAs for its slices (power of two <= 8)
+    // fit paths: one CTA per small problem; the large ones in whole-GPU passes
+    // over the flat list of their slices
     pl.fit_list_h.clear();
-    int64_t maxbig = 0;
+    pl.fit_bsoff_h.assign(1, 0);
     for (int k = 0; k < P; ++k)
         if (pl.probs_h[k].n <= kFitSmallMax) pl.fit_list_h.push_back(k);
     pl.fit_nsmall = (int)pl.fit_list_h.size();
     for (int k = 0; k < P; ++k)
         if (pl.probs_h[k].n > kFitSmallMax) {
             pl.fit_list_h.push_back(k);
-            maxbig = std::max<int64_t>(maxbig, pl.probs_h[k].n);
+            pl.fit_bsoff_h.push_back(pl.fit_bsoff_h.back() + fit_slices(pl.probs_h[k].n));
         }
     const size_t o_flist = reserve(sizeof(int32_t) * P);
-    pl.fit_cluster = 1;
-    while (pl.fit_cluster < 8 && (int64_t)pl.fit_cluster * 2 * 4096 < maxbig) pl.fit_cluster *= 2;
+    const size_t o_bsoff = reserve(sizeof(int64_t) * (P + 1));
+    const size_t o_fstate = reserve(sizeof(FitState) * P);
+    const size_t o_fcnt = reserve(sizeof(int) * P);
     // child tables: P x max_levels x child_cap cells
     const size_t nchild = (size_t)P * std::max(1, max_levels) * child_cap;
     const size_t o_cq = reserve(sizeof(double4_32a) * nchild);
@@ -357,6 +358,9 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     pl.d_slice = (double *)(B + o_slice);
     pl.d_sloff = (int64_t *)(B + o_sloff);
     pl.d_flist = (int32_t *)(B + o_flist);
+    pl.d_bsoff = (int64_t *)(B + o_bsoff);
+    pl.d_fstate = (FitState *)(B + o_fstate);
+    pl.d_fcnt = (int *)(B + o_fcnt);
     pl.d_err = (int *)(B + o_err);
     pl.d_ictr = (int *)(B + o_ictr);
 
@@ -440,7 +444,7 @@ int Context::upload(Wave &w, const rot_vote_problem *p, const std::vector<int> &
     // descriptor block: probs, lref, items, tiles -> contiguous in the workspace?  They are
     // separate ranges; pack them into one pinned staging block and copy each range.
     size_t hb = sizeof(ProbRef) * P + sizeof(LevelRef) * (size_t)P * S + sizeof(int2) * pl.tiles_h.size() +
-                sizeof(int64_t) * P + sizeof(int32_t) * P + 16 * 8;
+                sizeof(int64_t) * P + sizeof(int32_t) * P + sizeof(int64_t) * (P + 1) + 16 * 9;
     for (int lev = 0; lev < S; ++lev) hb += sizeof(VoteItem) * pl.items_h[lev].size();
     int rc = w.ensure_pinned(hb + 4096);
     if (rc != ROT_VOTE_OK) return fail(rc, "pinned staging allocation failed");
@@ -461,6 +465,7 @@ int Context::upload(Wave &w, const rot_vote_problem *p, const std::vector<int> &
     if (e == cudaSuccess) e = put(pl.d_tiles, pl.tiles_h.data(), sizeof(int2) * pl.tiles_h.size());
     if (e == cudaSuccess) e = put(pl.d_sloff, pl.slice_off_h.data(), sizeof(int64_t) * pl.slice_off_h.size());
     if (e == cudaSuccess) e = put(pl.d_flist, pl.fit_list_h.data(), sizeof(int32_t) * pl.fit_list_h.size());
+    if (e == cudaSuccess) e = put(pl.d_bsoff, pl.fit_bsoff_h.data(), sizeof(int64_t) * pl.fit_bsoff_h.size());
     if (e != cudaSuccess) return cuda_fail(e, "uploading descriptors");
     if (!pl.inputs_on_device) {
         // host inputs: direct copies from pinned caller memory when few problems, else pack
@@ -543,7 +548,8 @@ int Context::enqueue_pipeline(Wave &w) {
     if (e == cudaSuccess)
         e = launch_fit(pl.d_probs, pl.d_lref, S, pl.d_kept, K, cfg.refit_iters, pl.pool, pl.d_member, pl.d_slice,
                        pl.d_sloff, pl.d_flist, pl.fit_nsmall, pl.d_flist + pl.fit_nsmall, P - pl.fit_nsmall,
-                       pl.fit_cluster, pl.d_stats, pl.d_res, w.stream);
+                       pl.d_bsoff, pl.fit_bsoff_h.back(), pl.d_fstate, pl.d_fcnt, sm_count, pl.d_stats, pl.d_res,
+                       w.stream);
     done();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(w.results_h, pl.d_res, sizeof(rot_vote_result) * P, cudaMemcpyDeviceToHost, w.stream);

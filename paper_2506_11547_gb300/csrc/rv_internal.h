@@ -150,16 +150,27 @@ cudaError_t launch_select_small(const ProbRef *probs, int nprob, const LevelRef 
 cudaError_t launch_vote_small(const ProbRef *probs, const int2 *tiles, int ntiles, const LevelRef *lref,
                               int level_stride, int level, PairPool pool, ProbStats *stats, cudaStream_t s);
 
+// Fit state of a large problem between its passes.
+struct FitState {
+    double q[4];
+    int32_t done, status, nin, refits;
+};
+
 // Fit: winner voters, FP64 sum of S_i, eigen-solve, refit loop; writes results.
-// Problems with n <= kFitSmallMax (small_list) get one CTA each; the others
-// (big_list) one thread-block cluster of `cluster` CTAs each, slice_part
-// holding 11 doubles per 4096-pair slice, problem p's slices starting at
-// slice_off[p].  The path depends only on the problem's own size.
+// Problems with n <= kFitSmallMax (small_list) get one CTA each.  The others
+// (big_list) are fitted together on the whole GPU, one launch per iteration
+// over every slice of every large problem (slice_part holds 11 doubles per
+// 4096-pair slice, problem p's slices from slice_off[p]; big_soff[k] is the
+// first of the k-th large problem's slices in a flat list of big_slices); the
+// block finishing a problem's slices (done_cnt[k], nbig counters) does its
+// reduction and eigen-solve, keeping q in state[k].  The path depends only on
+// the problem's own size.
 constexpr int64_t kFitSmallMax = 32768;
 int fit_slices(int64_t n);
 cudaError_t launch_fit(const ProbRef *probs, const LevelRef *lref, int level_stride, const int32_t *kept_pos,
                        int top_k, int refit_iters, PairPool pool, uint8_t *member, double *slice_part,
                        const int64_t *slice_off, const int32_t *small_list, int nsmall, const int32_t *big_list,
-                       int nbig, int cluster, const ProbStats *stats, rot_vote_result *results, cudaStream_t s);
+                       int nbig, const int64_t *big_soff, int64_t big_slices, FitState *state, int *done_cnt,
+                       int sms, const ProbStats *stats, rot_vote_result *results, cudaStream_t s);
 
 }  // namespace rv

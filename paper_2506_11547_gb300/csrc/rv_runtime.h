@@ -44,9 +44,9 @@ struct Plan {
     std::vector<int2> tiles_h;
     std::vector<int64_t> in_off;
     std::vector<int64_t> slice_off_h;
-    int fit_cluster = 1;
-    std::vector<int32_t> fit_list_h;  // fit order: small problems (one CTA each), then large (one cluster each)
+    std::vector<int32_t> fit_list_h;  // fit order: small problems (one CTA each), then large (whole-GPU passes)
     int fit_nsmall = 0;
+    std::vector<int64_t> fit_bsoff_h;  // first slice of each large problem in the flat slice list, + total
     // device pointers (inside the wave's workspace)
     ProbRef *d_probs = nullptr;
     LevelRef *d_lref = nullptr;
@@ -63,6 +63,9 @@ struct Plan {
     double *d_slice = nullptr;
     int64_t *d_sloff = nullptr;
     int32_t *d_flist = nullptr;
+    int64_t *d_bsoff = nullptr;
+    FitState *d_fstate = nullptr;
+    int *d_fcnt = nullptr;  // per large problem: slices of the current fit iteration written
     int *d_err = nullptr;
     int *d_ictr = nullptr;  // per-level work-item counters of the CUDA-core vote (zeroed per solve)
 };

@@ -307,7 +307,7 @@ def bench_alg1(rv, synth, torch, stream, flush, peaks, reps: int = 5):
             flush.zero_()
             prof.alg1_raw(arr, 1, out)
             if k:
-                for kind, _, ms in prof.stage_times():
+                for kind, _, ms, _ in prof.stage_times():
                     st.setdefault(kind, []).append(ms)
         prof.close()
         st = {k: sum(v) / len(v) for k, v in st.items()}
@@ -373,7 +373,7 @@ def tensor_pipe_fraction(rv, prec, grid_n, levels, a_d, b_d, delta, stream, flus
         flush.zero_()
         ctx.solve([(a_d, b_d, delta)])
         if k:
-            ms += [t for kind, lev, t in ctx.stage_times() if kind == "vote" and lev == 0]
+            ms += [t for kind, lev, t, _ in ctx.stage_times() if kind == "vote" and lev == 0]
     ctx.close()
     t = sum(ms) / len(ms) / 1e3
     k = 32 if prec.endswith("x2") else 16
@@ -685,8 +685,8 @@ def main():
         flush.zero_()
         prof.solve([(a_d, b_d, p.delta)])
         st = prof.stage_times()
-        launches = len(st)
-        for kind, lev, ms in st:
+        launches = sum(k for _, _, _, k in st)  # kernels one solve launches
+        for kind, lev, ms, _ in st:
             stage_ms.setdefault((kind, lev), []).append(ms)
     n_cells0 = len(prof.level_trace(0, 0)[0])
     prof.close()

@@ -182,19 +182,23 @@ int rot_vote_poll(rot_vote_ctx *ctx, uint64_t ticket, rot_vote_result *out, int 
 int rot_vote_level_trace(rot_vote_ctx *ctx, int problem, int level, int64_t *idx, int32_t *count,
                          int64_t cap, int64_t *ncells, int64_t *kept_idx, int32_t *nkept);
 
-/* Diagnostic: device time of each kernel launch of the last rot_vote_solve (or rot_vote_alg1) on
+/* Diagnostic: device time of each stage of the last rot_vote_solve (or rot_vote_alg1) on
  * a context created with keep_trace = 2.  Such a context launches the
  * pipeline stage by stage (no CUDA graph) with a pair of CUDA events on its
- * stream around every kernel (a stage may be two kernels).  kind: 0 pair step,
- * 1 vote, 2 top-K with the next level's children, 4 fit (3 is unused); level:
- * the level (-1 for pair step and fit).  After rot_vote_alg1 the entries are
- * the stages of its last problem: kind 5 accumulator zeroing and circle
- * bases, 6 sampling vote, 7 argmax and result (level -1).
+ * stream around every stage; `kernels` is the number of kernel launches the
+ * stage made (the coarse top-K is two kernels, the fit one per refit
+ * iteration for problems above 32768 pairs).  kind: 0 pair step, 1 vote,
+ * 2 top-K with the next level's children, 4 fit (3 is unused); level: the
+ * level (-1 for pair step and fit).  After rot_vote_alg1 the entries are the
+ * stages of its last problem: kind 5 accumulator zeroing and circle bases,
+ * 6 sampling vote, 7 argmax, the kernels gated on a counter wrap, the peak
+ * search and the result (level -1).
  * Writes up to cap entries and their total count.  Returns OK or EINVAL. */
 typedef struct {
     int32_t kind;
     int32_t level;
     float ms;
+    int32_t kernels;
 } rot_vote_stage;
 
 int rot_vote_stage_times(rot_vote_ctx *ctx, rot_vote_stage *out, int cap, int *count);

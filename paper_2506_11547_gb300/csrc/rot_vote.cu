@@ -503,7 +503,7 @@ int Context::enqueue_pipeline(Wave &w) {
     const bool profile = cfg.keep_trace >= 2 && &w == &main_wave;
     size_t nev = 0;
     if (profile) prof.clear();
-    auto mark = [&](int kind, int level) {  // event pair around the next launch
+    auto mark = [&](int kind, int level, int kernels) {  // event pair around the next stage's launches
         if (!profile) return;
         while (prof_ev.size() < nev + 2) {
             cudaEvent_t ev;
@@ -511,14 +511,14 @@ int Context::enqueue_pipeline(Wave &w) {
             prof_ev.push_back(ev);
         }
         cudaEventRecord(prof_ev[nev], w.stream);
-        prof.push_back(rot_vote_stage{kind, level, 0.f});
+        prof.push_back(rot_vote_stage{kind, level, 0.f, kernels});
         nev += 2;
     };
     auto done = [&]() {
         if (profile) cudaEventRecord(prof_ev[nev - 1], w.stream);
     };
     cudaError_t e = cudaMemsetAsync(B + pl.zero_off, 0, pl.zero_bytes, w.stream);
-    mark(0, -1);
+    mark(0, -1, 1);
     if (e == cudaSuccess)
         e = launch_pair_prep(pl.d_probs, pl.d_tiles, (int)pl.tiles_h.size(), pl.pool, pl.prec, pl.d_stats, w.stream);
     done();
@@ -526,14 +526,14 @@ int Context::enqueue_pipeline(Wave &w) {
     // levels (<= 8 top_k cells per problem): the pair-major vote and a one-block
     // top-K.  Each ranking step also writes the next level's children.
     for (int lev = 0; lev < S && e == cudaSuccess; ++lev) {
-        mark(1, lev);
+        mark(1, lev, 1);
         if (lev == 0)
             e = launch_vote(w, lev, pl.variant);
         else
             e = launch_vote_small(pl.d_probs, pl.d_tiles, (int)pl.tiles_h.size(), pl.d_lref, S, lev, pl.pool,
                                   pl.d_stats, w.stream);
         done();
-        mark(2, lev);
+        mark(2, lev, lev == 0 ? 2 : 1);
         if (e == cudaSuccess) {
             if (lev == 0)
                 e = launch_topk(pl.d_probs, P, pl.d_lref, S, lev, K, cfg.rank_mode, 0, pl.d_cand,
@@ -544,7 +544,7 @@ int Context::enqueue_pipeline(Wave &w) {
         }
         done();
     }
-    mark(4, -1);
+    mark(4, -1, (pl.fit_nsmall > 0 ? 1 : 0) + (P > pl.fit_nsmall ? cfg.refit_iters + 1 : 0));
     if (e == cudaSuccess)
         e = launch_fit(pl.d_probs, pl.d_lref, S, pl.d_kept, K, cfg.refit_iters, pl.pool, pl.d_member, pl.d_slice,
                        pl.d_sloff, pl.d_flist, pl.fit_nsmall, pl.d_flist + pl.fit_nsmall, P - pl.fit_nsmall,

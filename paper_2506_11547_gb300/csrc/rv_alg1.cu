@@ -1110,9 +1110,9 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
                 prof_ev.push_back(ev);
             }
         }
-        auto mark = [&](int stage, bool begin) {
+        auto mark = [&](int stage, bool begin, int kernels = 0) {
             if (!profile || e != cudaSuccess) return;
-            if (begin) prof.push_back(rot_vote_stage{5 + stage, -1, 0.f});
+            if (begin) prof.push_back(rot_vote_stage{5 + stage, -1, 0.f, kernels});
             e = cudaEventRecord(prof_ev[2 * stage + (begin ? 0 : 1)], stream);
         };
         float4 *q1f = reinterpret_cast<float4 *>(base + off_q1f), *q2f = reinterpret_cast<float4 *>(base + off_q2f);
@@ -1131,7 +1131,7 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
         // counted nothing outside the region); otherwise every word.
         const bool full_zero = side % 8 != 0 || a1_clean_side != side;
         a1_clean_side = -1;  // until this problem is known to have taken path 0
-        mark(0, true);
+        mark(0, true, 1);
         if (e == cudaSuccess) {
             const int64_t want = (std::max<int64_t>(P.n, nw / 4) + kA1Threads - 1) / kA1Threads;
             const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * 8));
@@ -1154,13 +1154,14 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
                 e = cudaGetLastError();
             }
         };
-        mark(1, true);
+        mark(1, true, 1);
         if (path0 == 2u)
             vote(alg1_vote_kernel<true>);
         else
             vote(alg1_vote_kernel<false>);
         mark(1, false);
-        mark(2, true);
+        // argmax, the three gated kernels after a return-less vote that could wrap, the peak search
+        mark(2, true, 1 + (path0 != 2u && may_wrap ? 3 : 0) + (M > 0 ? 3 : 0));
         unsigned *hist = reinterpret_cast<unsigned *>(base + off_hist);
         unsigned long long *cand = reinterpret_cast<unsigned long long *>(base + off_cand);
         rot_vote_peak *pk = reinterpret_cast<rot_vote_peak *>(base + off_pk);

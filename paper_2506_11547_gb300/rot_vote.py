@@ -77,7 +77,7 @@ class rot_vote_pose_result(C.Structure):
 
 
 class rot_vote_stage(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("level", C.c_int32), ("ms", C.c_float)]
+    _fields_ = [("kind", C.c_int32), ("level", C.c_int32), ("ms", C.c_float), ("kernels", C.c_int32)]
 
 
 STAGE_KIND = {0: "pair_prep", 1: "vote", 2: "topk", 3: "children", 4: "fit", 5: "alg1_zero", 6: "alg1_vote",
@@ -378,11 +378,12 @@ class Context:
         return idx[:m], cnt[:m], kept[:nk.value]
 
     def stage_times(self):
-        """[(kind, level, ms)] of the last solve (context created with keep_trace=2)."""
+        """[(kind, level, ms, kernels)] of the last solve (context created with keep_trace=2):
+        each stage's device time and the number of kernels it launched."""
         buf = (rot_vote_stage * 256)()
         n = C.c_int()
         self._check(self._L.rot_vote_stage_times(self._h, buf, 256, C.byref(n)))
-        return [(STAGE_KIND[buf[k].kind], buf[k].level, buf[k].ms) for k in range(min(n.value, 256))]
+        return [(STAGE_KIND[buf[k].kind], buf[k].level, buf[k].ms, buf[k].kernels) for k in range(min(n.value, 256))]
 
     def close(self):
         if getattr(self, "_h", None):

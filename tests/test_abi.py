@@ -59,6 +59,7 @@ int main(void) {
          offsetof(rot_vote_alg1_problem, accumulator), offsetof(rot_vote_alg1_result, samples_cast),
          offsetof(rot_vote_alg1_result, ms_gpu));
   printf("%zu %zu\n", offsetof(rot_vote_alg1_result, vote_path), offsetof(rot_vote_alg1_result, wrapped_words));
+  printf("%zu %zu\n", sizeof(rot_vote_stage), offsetof(rot_vote_stage, kernels));
   return 0;
 }
 '''
@@ -90,6 +91,7 @@ int main(void) {
     assert sizes[15] == rv.rot_vote_alg1_result.samples_cast.offset
     assert sizes[16] == rv.rot_vote_alg1_result.ms_gpu.offset
     assert sizes[17:19] == [rv.rot_vote_alg1_result.vote_path.offset, rv.rot_vote_alg1_result.wrapped_words.offset]
+    assert sizes[19:21] == [ctypes.sizeof(rv.rot_vote_stage), rv.rot_vote_stage.kernels.offset]
 
 
 def test_missing_library_fails_loudly(tmp_path):

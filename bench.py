@@ -422,7 +422,8 @@ def bench_paper_scale(rv, synth, torch, stream, flush, reps: int = 3):
 def bench_pose(rv, synth, torch, stream, flush, reps: int = 5):
     """Rigid pose (Sec. 4.5) on the paper's default synthetic setting (Sec. 5.4.1): N = 5000,
     90% outliers, noise 0.01; mu_t = 0.04; rotation vote 32^3 + 2 levels, delta = 0.03; the
-    paper's 400^3 translation grid over [-5, 5]^3.  Times the whole call on the device."""
+    paper's 400^3 translation grid over [-5, 5]^3.  Times the whole call on the device, and the
+    rotation solve's stages with event pairs on a profiling context."""
     import numpy as np
     p = synth.make_pose_problem(5000, 0.9, 0.01, seed=3003)
     x, y = torch.from_numpy(p.x).cuda(), torch.from_numpy(p.y).cuda()
@@ -442,8 +443,20 @@ def bench_pose(rv, synth, torch, stream, flush, reps: int = 5):
             ts.append(s0.elapsed_time(s1))
             front.append(r.ms_gpu)
         ctx.close()
+        # the rotation solve's stages (event pairs around each stage; mean of 3 poses after one)
+        prof = rv.Context(grid_n=32, levels=2, precision=prec, cuda_stream=stream.cuda_stream, keep_trace=2)
+        st = {}
+        for k in range(4):
+            flush.zero_()
+            prof.pose(x, y, 0.04, 0.03)
+            if k:
+                for kind, lev, ms, _ in prof.stage_times():
+                    key = f"{kind}:{lev}"
+                    st[key] = st.get(key, 0.0) + ms / 3
+        prof.close()
         res[prec] = {"ms_per_pose": sum(ts) / len(ts), "ms_pairs_and_translation": sum(front) / len(front),
-                     "ms_rotation_solve": r.rot.ms_gpu, "pairs_tested": r.pairs_tested, "pairs_kept": r.pairs_kept,
+                     "ms_rotation_solve": r.rot.ms_gpu, "rotation_stage_ms": st,
+                     "pairs_tested": r.pairs_tested, "pairs_kept": r.pairs_kept,
                      "pairs_rechecked": r.pairs_rechecked, "rotation_tests": r.rot.tests,
                      "angle_to_truth_rad": _angle(r.rot.q, p.q_true),
                      "translation_error": float(np.linalg.norm(r.t - p.t_true)), "status": r.status}

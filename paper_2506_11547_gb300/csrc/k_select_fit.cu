@@ -90,6 +90,46 @@ __device__ void block_select(const Key (&mine)[kPerThread], int k, Cand *out) {
     }
 }
 
+// The same selection as block_select, by ranks: the valid keys go to shared
+// memory (in any order), and each key's rank is the number of keys better than
+// it -- `better` is a strict total order, the indices being distinct -- so the
+// keys of ranks 0 .. k-1 land in out[] in order, with no rounds.  Exhausted
+// ranks are filled as block_select fills them.  Up to kRankMax valid keys (one
+// per thread: the refinement levels' at most 8 K children); above that -- the
+// coarse level's merge of the chunk candidates -- it runs block_select, which
+// measured faster there than n^2 comparisons on one SM.
+constexpr int kRankMax = kSelThreads;
+__device__ void block_select_ranked(const Key (&mine)[kPerThread], int k, Cand *out) {
+    __shared__ Key all[kRankMax];
+    __shared__ int nall;
+    if (threadIdx.x == 0) nall = 0;
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < kPerThread; ++e)
+        if (mine[e].pos >= 0) {
+            const int j = atomicAdd(&nall, 1);
+            if (j < kRankMax) all[j] = mine[e];
+        }
+    __syncthreads();
+    const int n = nall;
+    __syncthreads();  // every thread has read nall before a later call resets it
+    if (n > kRankMax) {  // uniform
+        block_select(mine, k, out);
+        return;
+    }
+    if ((int)threadIdx.x < n) {
+        const Key me = all[threadIdx.x];
+        int rank = 0;
+#pragma unroll 8
+        for (int j = 0; j < n; ++j) rank += better(all[j], me);
+        if (rank < k) out[rank] = Cand{key_score(me.key), me.idx, me.pos, 0};
+    }
+    const int r = (int)threadIdx.x;
+    if (r >= n && r < k)  // exhausted: the first empty rank holds the "none" key, the rest are blank
+        out[r] = r == n ? Cand{key_score(0ull), INT64_MAX, -1, 0} : Cand{0.0, -1, -1, 0};
+    __syncthreads();
+}
+
 // Children of one problem's kept cells: the octants of each kept cell at the
 // next level that meet the ball, written to the next level's table in (rank,
 // octant) order (an ordered block-wide compaction, 8 candidates per kept cell).
@@ -205,7 +245,7 @@ __global__ void __launch_bounds__(kSelThreads) topk_phase2(const ProbRef *__rest
             mine[e].pos = c.pos;
         }
         __syncthreads();
-        block_select(mine, top_k, tmp);
+        block_select_ranked(mine, top_k, tmp);
         __syncthreads();
         if (threadIdx.x == 0) {
             int nk = 0;
@@ -257,7 +297,7 @@ __global__ void __launch_bounds__(kSelThreads) select_small_kernel(const ProbRef
     }
     __shared__ Cand sel[kMaxTopK];
     __shared__ int nsel;
-    block_select(mine, top_k, sel);
+    block_select_ranked(mine, top_k, sel);
     __syncthreads();
     if (threadIdx.x == 0) {
         int nk = 0;

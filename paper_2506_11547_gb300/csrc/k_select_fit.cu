@@ -672,9 +672,17 @@ __device__ void fit_solve_warp(int k, int p, int t, int refit_iters, const ProbR
     }
     const double *part = slice_part + 11 * slice_off[p];
     const int64_t nslices = (P.n + kFitSlice - 1) / kFitSlice;
-    if (lane < 11) {  // slices summed in index order
+    if (lane < 11) {  // slices summed in index order, eight loads in flight at a time
         double acc = 0.0;
-        for (int64_t sl = 0; sl < nslices; ++sl) acc += __ldcg(part + 11 * sl + lane);
+        int64_t sl = 0;
+        for (; sl + 8 <= nslices; sl += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(part + 11 * (sl + u) + lane);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc += v[u];
+        }
+        for (; sl < nslices; ++sl) acc += __ldcg(part + 11 * sl + lane);
         Btot[lane] = acc;
     }
     __syncwarp();
@@ -818,23 +826,42 @@ __global__ void __launch_bounds__(kFitSmallThreads) fit_small_kernel(
     for (int t = 0; t <= refit_iters; ++t) {
         double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         int cnt = 0, chg = 0;
-        for (int64_t i = threadIdx.x; i < n; i += kFitSmallThreads) {
-            const float4 p0 = pr[2 * i], p1 = pr[2 * i + 1];
-            const bool in = recheck_v(R0, R1, R2, p0, p1) <= thr;
-            if (t > 0) chg += in != (mem[i] != 0);
-            mem[i] = in;
-            if (in) {
-                ++cnt;
-                const double a0 = p0.x, a1 = p0.y, a2 = p0.z, b0 = p0.w, b1 = p1.x, b2 = p1.y;
-                acc[0] = fma(b0, a0, acc[0]);
-                acc[1] = fma(b0, a1, acc[1]);
-                acc[2] = fma(b0, a2, acc[2]);
-                acc[3] = fma(b1, a0, acc[3]);
-                acc[4] = fma(b1, a1, acc[4]);
-                acc[5] = fma(b1, a2, acc[5]);
-                acc[6] = fma(b2, a0, acc[6]);
-                acc[7] = fma(b2, a1, acc[7]);
-                acc[8] = fma(b2, a2, acc[8]);
+        // pairs i, i + kFitSmallThreads, ... in that order; the records (and the
+        // previous membership bytes) of four consecutive ones are loaded first, so
+        // their loads are in flight together
+        for (int64_t i0 = threadIdx.x; i0 < n; i0 += 4 * kFitSmallThreads) {
+            float4 q0[4], q1[4];
+            uint8_t was[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + (int64_t)u * kFitSmallThreads;
+                if (i < n) {
+                    q0[u] = pr[2 * i];
+                    q1[u] = pr[2 * i + 1];
+                    was[u] = mem[i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + (int64_t)u * kFitSmallThreads;
+                if (i >= n) break;
+                const float4 p0 = q0[u], p1 = q1[u];
+                const bool in = recheck_v(R0, R1, R2, p0, p1) <= thr;
+                if (t > 0) chg += in != (was[u] != 0);
+                mem[i] = in;
+                if (in) {
+                    ++cnt;
+                    const double a0 = p0.x, a1 = p0.y, a2 = p0.z, b0 = p0.w, b1 = p1.x, b2 = p1.y;
+                    acc[0] = fma(b0, a0, acc[0]);
+                    acc[1] = fma(b0, a1, acc[1]);
+                    acc[2] = fma(b0, a2, acc[2]);
+                    acc[3] = fma(b1, a0, acc[3]);
+                    acc[4] = fma(b1, a1, acc[4]);
+                    acc[5] = fma(b1, a2, acc[5]);
+                    acc[6] = fma(b2, a0, acc[6]);
+                    acc[7] = fma(b2, a1, acc[7]);
+                    acc[8] = fma(b2, a2, acc[8]);
+                }
             }
         }
 #pragma unroll

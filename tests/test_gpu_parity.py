@@ -159,6 +159,31 @@ def test_batched_equals_alone_and_deterministic():
                    (x.best_count, x.inliers, x.best_cell, x.tests, x.rechecked)
 
 
+def test_large_problems_fitted_together_equal_alone():
+    """Three problems above 32768 pairs, fitted together in whole-GPU passes
+    (their slices in one flat list), and two small ones in the same call: each
+    result equals the problem solved alone, bit for bit, and the large ones
+    match the oracle (same winning cell, rotation within 1e-4 rad)."""
+    import oracle
+    probs = [synth.make_problem(n, rho=0.9, sigma=0.01, delta=0.03, seed=s)
+             for n, s in ((40000, 21), (50, 22), (70000, 23), (5000, 24), (33000, 25))]
+    args = [(dev(p.a), dev(p.b), p.delta) for p in probs]
+    with rv.Context(grid_n=32, levels=2) as ctx:
+        batch = ctx.solve(args)
+        alone = [ctx.solve([x])[0] for x in args]
+    for rb, ra in zip(batch, alone):
+        assert np.array_equal(rb.q, ra.q)
+        assert (rb.best_count, rb.inliers, rb.best_cell, rb.refits) == (ra.best_count, ra.inliers, ra.best_cell,
+                                                                        ra.refits)
+    for p, r in zip(probs, batch):
+        if p.n <= 32768:
+            continue
+        o = oracle.solve(p.a, p.b, f32(p.delta), grid_n=32, levels=2, nthreads=NTHREADS, trace=False)
+        assert r.status == o.status == 0
+        assert r.best_cell == o.best_cell
+        assert quat_angle(r.q, o.q) < ROT_TOL
+
+
 def test_graph_replay_with_new_inputs():
     """The captured pipeline is replayed for a second solve of the same shape
     with different data; results must be those of the new data."""

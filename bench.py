@@ -185,9 +185,10 @@ def percentile(xs, p):
     return s[k]
 
 
-def cpu_oracle_rate(p, grid_n, seconds: float, threads: int):
+def cpu_oracle_rate(p, grid_n, seconds: float, threads: int, m_hint: int = 0):
     """Oracle (FP64 C, as it stands) vote over a bounded sample of coarse cells:
-    tests/s on `threads` host threads."""
+    tests/s on `threads` host threads.  m_hint > 0: the sample size a previous
+    call settled on (skips the calibration)."""
     import numpy as np
     import oracle
     cells = oracle.level_cells(grid_n)
@@ -196,11 +197,14 @@ def cpu_oracle_rate(p, grid_n, seconds: float, threads: int):
     # calibrate on a few cells, then size the sample to ~seconds; the short
     # calibration carries fixed costs, so a sample that ends well short of the
     # target is rescaled (at most twice) and timed again
-    m0 = max(threads, 8)
-    t0 = time.perf_counter()
-    oracle.vote_cells(p.a, p.b, float(np.float32(p.delta)), grid_n, cells[order[:m0]], nthreads=threads)
-    dt0 = max(1e-3, time.perf_counter() - t0)
-    m = int(min(len(cells), max(m0, m0 * seconds / dt0)))
+    if m_hint > 0:
+        m = int(min(len(cells), m_hint))
+    else:
+        m0 = max(threads, 8)
+        t0 = time.perf_counter()
+        oracle.vote_cells(p.a, p.b, float(np.float32(p.delta)), grid_n, cells[order[:m0]], nthreads=threads)
+        dt0 = max(1e-3, time.perf_counter() - t0)
+        m = int(min(len(cells), max(m0, m0 * seconds / dt0)))
     for attempt in range(3):
         t0 = time.perf_counter()
         oracle.vote_cells(p.a, p.b, float(np.float32(p.delta)), grid_n, cells[order[:m]], nthreads=threads)
@@ -562,8 +566,9 @@ def run_reference(args):
     for _ in range(args.warmup):
         cpu_oracle_rate(p, grid_n, per_step / 4, threads)
     rates, samples, secs = [], [], []
-    for _ in range(args.steps):
-        r, m, dt = cpu_oracle_rate(p, grid_n, per_step, threads)
+    m = 0
+    for _ in range(args.steps):  # the first step sizes the sample; the others reuse that size
+        r, m, dt = cpu_oracle_rate(p, grid_n, per_step, threads, m_hint=m)
         rates.append(r)
         samples.append(m)
         secs.append(dt)

@@ -7,6 +7,7 @@ octant children and the Eq. (stack) eigenvector fit with its refit rule).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import dataclasses
 import os
@@ -19,7 +20,7 @@ __all__ = [
     "lib", "pair_M", "pair_S", "quad", "quat_to_R", "cell_exists", "cell_geom", "tau",
     "level_cells", "vote_cells", "rank", "jacobi4", "canonical", "solve", "OracleResult",
     "AMBIG", "cell_of_point", "fit_cell", "alg1_basis", "alg1_cell", "alg1_table", "alg1", "alg1_centre",
-    "alg1_peaks", "pose_pairs", "pose_translation", "pose",
+    "alg1_peaks", "pose_pairs", "pose_translation", "pose", "using_library",
 ]
 
 AMBIG = 1e-6
@@ -44,60 +45,78 @@ class _Trace(C.Structure):
                 ("topk_score", C.c_void_p), ("nkept", C.c_void_p)]
 
 
+def _configure(L):
+    """Argument and result types of the C entry points."""
+    L.rvo_pair_M.argtypes = [_f32p, _f32p, _f64p]
+    L.rvo_pair_S.argtypes = [_f32p, _f32p, _f64p]
+    L.rvo_quad.argtypes = [_f64p, _f64p]
+    L.rvo_quad.restype = C.c_double
+    L.rvo_quat_to_R.argtypes = [_f64p, _f64p]
+    L.rvo_cell_exists.argtypes = [C.c_int, C.c_int64, C.c_int64, C.c_int64]
+    L.rvo_cell_exists.restype = C.c_int
+    L.rvo_cell_geom.argtypes = [C.c_int, C.c_int64, C.c_int64, C.c_int64, _f64p, C.POINTER(C.c_double)]
+    L.rvo_cell_geom_chart.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, _f64p,
+                                      C.POINTER(C.c_double)]
+    L.rvo_tau.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.rvo_tau.restype = C.c_double
+    L.rvo_level_cells.argtypes = [C.c_int, C.c_void_p]
+    L.rvo_level_cells.restype = C.c_int64
+    L.rvo_vote_cells.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int, _i64p, C.c_int64,
+                                 _i32p, _i32p, _f64p, C.c_int]
+    L.rvo_vote_cells.restype = C.c_int
+    L.rvo_rank.argtypes = [_i32p, _f64p, _i64p, C.c_int64, C.c_int64, C.c_int, C.c_int64, _i64p, _f64p]
+    L.rvo_rank.restype = C.c_int64
+    L.rvo_jacobi4.argtypes = [_f64p, _f64p, _f64p]
+    L.rvo_canonical.argtypes = [_f64p]
+    L.rvo_solve.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
+                            C.c_int, C.c_int, C.c_int, C.POINTER(_Result), C.POINTER(_Trace)]
+    L.rvo_solve.restype = C.c_int
+    L.rvo_fit_cell.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int, C.c_int64, C.c_int,
+                               C.POINTER(_Result)]
+    L.rvo_fit_cell.restype = C.c_int
+    L.rvo_alg1_basis.argtypes = [_f32p, _f32p, _f64p, _f64p]
+    L.rvo_alg1_basis.restype = C.c_int
+    L.rvo_alg1_cell.argtypes = [_f64p, _f64p, C.c_double, C.c_double, C.c_int]
+    L.rvo_alg1_cell.restype = C.c_int64
+    L.rvo_alg1_table.argtypes = [C.c_int, _f64p]
+    L.rvo_alg1_table.restype = None
+    L.rvo_alg1.argtypes = [_f32p, _f32p, C.c_int64, _f64p, C.c_int, C.c_int, _i32p, C.POINTER(C.c_int64),
+                           C.POINTER(C.c_int32), _f64p]
+    L.rvo_alg1.restype = C.c_int64
+    L.rvo_alg1_centre.argtypes = [C.c_int, C.c_int64, _f64p]
+    L.rvo_alg1_centre.restype = None
+    L.rvo_alg1_peaks.argtypes = [_i32p, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_double, _i64p, _i32p, _f64p,
+                                 C.POINTER(C.c_int32)]
+    L.rvo_alg1_peaks.restype = C.c_int
+    L.rvo_pose_pairs.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                 C.c_int64]
+    L.rvo_pose_pairs.restype = C.c_int64
+    L.rvo_pose_translation.argtypes = [_f32p, _f32p, C.c_int64, _f64p, C.c_double, C.c_int, _f64p,
+                                       C.POINTER(C.c_int64)]
+    L.rvo_pose_translation.restype = C.c_int32
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        L.rvo_pair_M.argtypes = [_f32p, _f32p, _f64p]
-        L.rvo_pair_S.argtypes = [_f32p, _f32p, _f64p]
-        L.rvo_quad.argtypes = [_f64p, _f64p]
-        L.rvo_quad.restype = C.c_double
-        L.rvo_quat_to_R.argtypes = [_f64p, _f64p]
-        L.rvo_cell_exists.argtypes = [C.c_int, C.c_int64, C.c_int64, C.c_int64]
-        L.rvo_cell_exists.restype = C.c_int
-        L.rvo_cell_geom.argtypes = [C.c_int, C.c_int64, C.c_int64, C.c_int64, _f64p, C.POINTER(C.c_double)]
-        L.rvo_cell_geom_chart.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, _f64p,
-                                          C.POINTER(C.c_double)]
-        L.rvo_tau.argtypes = [C.c_double, C.c_double, C.c_double]
-        L.rvo_tau.restype = C.c_double
-        L.rvo_level_cells.argtypes = [C.c_int, C.c_void_p]
-        L.rvo_level_cells.restype = C.c_int64
-        L.rvo_vote_cells.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int, _i64p, C.c_int64,
-                                     _i32p, _i32p, _f64p, C.c_int]
-        L.rvo_vote_cells.restype = C.c_int
-        L.rvo_rank.argtypes = [_i32p, _f64p, _i64p, C.c_int64, C.c_int64, C.c_int, C.c_int64, _i64p, _f64p]
-        L.rvo_rank.restype = C.c_int64
-        L.rvo_jacobi4.argtypes = [_f64p, _f64p, _f64p]
-        L.rvo_canonical.argtypes = [_f64p]
-        L.rvo_solve.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
-                                C.c_int, C.c_int, C.c_int, C.POINTER(_Result), C.POINTER(_Trace)]
-        L.rvo_solve.restype = C.c_int
-        L.rvo_fit_cell.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_int, C.c_int, C.c_int64, C.c_int,
-                                   C.POINTER(_Result)]
-        L.rvo_fit_cell.restype = C.c_int
-        L.rvo_alg1_basis.argtypes = [_f32p, _f32p, _f64p, _f64p]
-        L.rvo_alg1_basis.restype = C.c_int
-        L.rvo_alg1_cell.argtypes = [_f64p, _f64p, C.c_double, C.c_double, C.c_int]
-        L.rvo_alg1_cell.restype = C.c_int64
-        L.rvo_alg1_table.argtypes = [C.c_int, _f64p]
-        L.rvo_alg1_table.restype = None
-        L.rvo_alg1.argtypes = [_f32p, _f32p, C.c_int64, _f64p, C.c_int, C.c_int, _i32p, C.POINTER(C.c_int64),
-                               C.POINTER(C.c_int32), _f64p]
-        L.rvo_alg1.restype = C.c_int64
-        L.rvo_alg1_centre.argtypes = [C.c_int, C.c_int64, _f64p]
-        L.rvo_alg1_centre.restype = None
-        L.rvo_alg1_peaks.argtypes = [_i32p, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_double, _i64p, _i32p, _f64p,
-                                     C.POINTER(C.c_int32)]
-        L.rvo_alg1_peaks.restype = C.c_int
-        L.rvo_pose_pairs.argtypes = [_f32p, _f32p, C.c_int64, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
-                                     C.c_int64]
-        L.rvo_pose_pairs.restype = C.c_int64
-        L.rvo_pose_translation.argtypes = [_f32p, _f32p, C.c_int64, _f64p, C.c_double, C.c_int, _f64p,
-                                           C.POINTER(C.c_int64)]
-        L.rvo_pose_translation.restype = C.c_int32
-        _lib = L
+        _lib = _configure(C.CDLL(_build.build()))
     return _lib
+
+
+@contextlib.contextmanager
+def using_library(path: str):
+    """Inside the block every wrapper calls the oracle library at `path` (a
+    build of a modified copy of rv_oracle.c), then the regular build again:
+    for the tests that plant a mistake in the oracle and check that a pin
+    catches it."""
+    global _lib
+    saved = lib()
+    _lib = _configure(C.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 def _v3(x) -> np.ndarray:

@@ -2,9 +2,9 @@
 
 Each case compiles a copy of the oracle (rv_oracle.c) with one plausible
 mistake: a transposed operand, a wrong sign, a reversed tie order, a dropped
-term, the wrong threshold, or swapped axes. It then runs the pins that guard
-that part and checks that at least one of them fails. This is evidence that
-the pins would catch such a mistake in the oracle itself.
+term, the wrong threshold, swapped axes, or a wrong radius. It then runs the
+pins that guard that part and checks that at least one of them fails. This is
+evidence that the pins would catch such a mistake in the oracle itself.
 
 The copies are built in a temporary directory with the oracle's own compiler
 flags. The oracle's source and its regular build are not touched.
@@ -19,6 +19,8 @@ import oracle
 from oracle import build as oracle_build
 from tests import test_oracle_alg1_pins as alg1_pins
 from tests import test_oracle_pins as pins
+from tests import test_oracle_pose_pins as pose_pins
+from tests import test_oracle_stereo_pins as stereo_pins
 
 CASES = [
     ("App. A product M = L(a)^T L'(b) with L(a) not transposed",
@@ -44,6 +46,23 @@ CASES = [
      "    return (i[0] * n + i[1]) * n + i[2];\n}\n\n/* The whole of Alg. 1",
      [alg1_pins.test_projection_of_the_lower_half_lands_in_the_unit_ball_and_inverts,
       alg1_pins.test_counts_sum_to_samples_and_noise_free_argmax_finds_the_rotation]),
+    ("Alg. 1 basis q_b2 = [0, b] q_b1 with one cross-product term of the wrong sign",
+     "    q2[1] = w * b0 + (b1 * vz - b2 * vy);", "    q2[1] = w * b0 - (b1 * vz - b2 * vy);",
+     [alg1_pins.test_every_sample_lies_on_the_pairs_quaternion_circle,
+      alg1_pins.test_basis_is_orthonormal_and_q_b1_is_the_minimal_rotation]),
+    ("peak suppression by cos(theta) instead of cos(theta / 2)",
+     "    const double cth = cos(theta / 2.0);", "    const double cth = cos(theta);",
+     [alg1_pins.test_peaks_obey_the_greedy_suppression_invariants]),
+    ("rigid-pose length check without the absolute value",
+     "fabs(lm - ln) <= mu", "(lm - ln) <= mu",
+     [pose_pins.test_kept_pairs_equal_a_direct_evaluation]),
+    ("stereographic inverse projection with w of the wrong sign",
+     "    q[3] = (c2 - 1.0) / den;\n    *chord = sqrt(3.0) * h / sqrt((1.0 + minv2) * den);",
+     "    q[3] = (1.0 - c2) / den;\n    *chord = sqrt(3.0) * h / sqrt((1.0 + minv2) * den);",
+     [stereo_pins.test_stereo_centre_is_the_inverse_projection]),
+    ("stereographic cell radius from the centre's conformal factor instead of the box's largest",
+     "    *chord = sqrt(3.0) * h / sqrt((1.0 + minv2) * den);", "    *chord = sqrt(3.0) * h / sqrt((1.0 + c2) * den);",
+     [stereo_pins.test_stereo_radius_covers_the_box_and_is_not_loose]),
 ]
 
 

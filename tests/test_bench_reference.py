@@ -1,6 +1,7 @@
-"""The benchmark's reference arm on CPU: `bench.py --impl reference` times the
-FP64 oracle on the host cores and prints one JSON line with the metric, unit and
-config of the measured arm; under a multi-rank launch only rank 0 prints."""
+"""Benchmark host logic on CPU.  The reference arm (`bench.py --impl reference`)
+times the FP64 oracle on the host cores and prints one JSON line with the
+metric, unit and config of the measured arm; under a multi-rank launch only
+rank 0 prints.  The clock record parses the sampled nvidia-smi lines."""
 import json
 import os
 import subprocess
@@ -36,3 +37,25 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, "--steps", "1", "--warmup", "1")
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_clock_summary_reports_median_clock_and_active_reasons():
+    """The clock record beside each benchmark number: median SM clock under load,
+    the maximum, and every throttle reason seen active (samples taken before the
+    timed region are skipped)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    cs = bench.ClockSampler(0)
+    cs.lines = ["1200, 2070, 300.0, 0x0, Not Active, Not Active, Not Active, Not Active",  # before the region
+                "2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+                "2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "garbage line"]
+    cs.skip = 1
+    s = cs.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    cs.lines = ["1500, 2070, 1000.0, 0x8, Active, Not Active, Active, Not Active"]
+    cs.skip = 0
+    assert cs.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]

@@ -10,20 +10,24 @@
 // return, which keep an exact record of the wraps.
 //
 // Launches per problem, on the context's stream:
-//   alg1_prep_kernel    zeroes the counters (2 n^3 bytes) and the wrap record
-//             and writes each pair's circle basis: FP64 (the IEEE operation
-//             sequence of the formulas) and its FP32 rounding
+//   alg1_prep_kernel    zeroes the counters (only the ball region's words
+//             when the words outside it are known to be zero, else all 2 n^3
+//             bytes) and the wrap record, and writes each pair's circle basis:
+//             FP64 (the IEEE operation sequence of the formulas) and its FP32
+//             rounding
 //   alg1_vote_kernel<false>  persistent; the N J samples in FP32, 32
 //             consecutive samples per warp instruction (coalesced angle-table
 //             reads), four independent samples per thread, one return-less
 //             atomic add each.  Samples that need FP64 go to a per-warp
 //             shared-memory queue that the warp empties 32 at a time, so FP64
 //             work runs in full warps
-//   alg1_argmax_kernel<., false>  (count, -index) maximum over the accumulator
-//             (with peaks: also the count histogram) and the sum of the
-//             counts; the last block writes the result (inverse projection,
-//             canonical sign, rotation matrix) and sets path 1 when that sum
-//             misses the samples cast
+//   alg1_argmax_kernel<., false>  (count, -index) maximum over the ball
+//             region's words (n a multiple of 8; otherwise every word), with
+//             peaks also the count histogram, and the sum of the counts; the
+//             last block writes the result (inverse projection, canonical
+//             sign, rotation matrix) and sets path 1 when that sum misses the
+//             samples cast (a counter wrapped, or a count fell outside the
+//             region)
 //   gated on path 1 (launched when N J >= 65536, returning at once
 //             otherwise): alg1_rezero_kernel, alg1_vote_kernel<true> (atomics
 //             with return and the wrap record), alg1_argmax_kernel<., true>

@@ -2,14 +2,17 @@
 """Benchmark of the rotation-voting hot path on GB300.
 
 One step = one full solve (pair step, vote on every level, top-K, children,
-fit) of the 1e5-pair workload: 99% outliers, sigma 0.01, delta 0.03,
-64^3 coarse grid + 3 levels of 2x2x2 refinement of the top 16 cells.
+fit) of the paper-scale workload: 1e6 pairs, 99% outliers, sigma 0.005,
+delta 0.03, 128^3 coarse grid + 3 levels of 2x2x2 refinement of the top 16
+cells (1.14e12 cell tests), in the FP16 hi/lo tensor-core form.
 
 Prints ONE JSON line: metric / value (cell-correspondence tests per second,
 whole job), rotations/s, p50/p99 solve latency, e2e through the C ABI with
 pinned host buffers, the dominant kernel's roofline, clocks, and the oracle's
-CPU baseline.  `--impl reference` times the FP64 oracle on the host cores
-instead (the reference arm).
+CPU baseline; beside them the other precision forms on the same workload and
+the 1e5-pair, 64^3 + 3-level workload in the plain FP32 form.
+`--impl reference` times the FP64 oracle on the host cores instead (the
+reference arm).
 """
 from __future__ import annotations
 
@@ -28,26 +31,40 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-correspondence tests/sec and rotations/sec at 1 GB300; p50/p99 solve latency"
 UNIT = "cell-correspondence tests/s"
-WORKLOAD = "fp32_n1e5_64L3"
-WORKLOAD_DESC = ("N=1e5 float32 unit pairs, 99% uniform outliers, inlier noise sigma=0.01, delta=0.03 rad; "
-                 "64^3 coarse grid over the vector-part ball (146,864 cells) + 3 levels of 2x2x2 "
-                 "subdivision of the top-16 cells; exact counts, EXCESS ranking, FP64 fit with 8 refits")
+WORKLOAD = "lowp_n1e6_128L3"
+PRECISION = "fp16x2"
+WORKLOAD_DESCS = {
+    "lowp_n1e6_128L3": ("N=1e6 float32 unit pairs, 99% uniform outliers, inlier noise sigma=0.005, delta=0.03 rad; "
+                        "128^3 coarse grid over the vector-part ball (1,136,840 cells) + 3 levels of 2x2x2 "
+                        "subdivision of the top-16 cells; exact counts, EXCESS ranking, FP64 fit with 8 refits"),
+    "fp32_n1e5_64L3": ("N=1e5 float32 unit pairs, 99% uniform outliers, inlier noise sigma=0.01, delta=0.03 rad; "
+                       "64^3 coarse grid over the vector-part ball (146,864 cells) + 3 levels of 2x2x2 "
+                       "subdivision of the top-16 cells; exact counts, EXCESS ranking, FP64 fit with 8 refits"),
+    "small_n1e3_32": ("N=1e3 float32 unit pairs, 90% uniform outliers, inlier noise sigma=0.01, delta=0.03 rad; "
+                      "32^3 grid, no refinement; exact counts, FP64 fit with 8 refits"),
+}
 FLOPS_PER_TEST = 20.0  # algorithmic: 10 multiply-adds of the (cell monomials . pair S entries) contraction
-# DRAM bytes (read + write) of one coarse-vote launch of the default workload, from one ncu capture
-# (profiles/vote_simt2_fp32_n1e5_64L3.md, profiles/vote_tc_fp16x2_n1e5_64L3.md).  A figure stands
-# only while the kernel's source file hashes to the value it was captured with.
+K16_FLOPS_PER_TEST = 32.0  # the contraction with K padded to 16 (one kind::f16 MMA K step)
+# The tensor-core epilogue's CUDA-core bound: per 8 tests it issues 4 sign-byte permutes, 2
+# three-input adds and 4 three-input |D| minima, 1.25 ALU-pipe instructions per test, on an ALU
+# pipe of 64 lanes per SM per clock: 152 x 64 x f_max / 1.25 tests/s.
+EPI_ALU_INSTR_PER_TEST = 1.25
+EPI_ALU_LANES_PER_SM = 64
+# DRAM bytes (read + write) of one coarse-vote launch, from one ncu capture of the workload and
+# precision named in the key.  A figure stands only while the kernel's source file hashes to the
+# value it was captured with; otherwise the line reports null.
 NCU_TRAFFIC = {
-    "fp32": (17163776, "k_vote_simt.cu", "d52c7728ebbc0e1fbfd454867409765a97ca859fbf31c2dea502e38392acd269"),
-    "fp16x2": (26736128, "k_vote_tc.cu", "052eb2a7a37a24cb8693af1f163ddbbf00cad21ef292a824f5c62bc2f74d8b3a"),
+    ("fp32_n1e5_64L3", "fp32"): (17163776, "k_vote_simt.cu",
+                                 "d52c7728ebbc0e1fbfd454867409765a97ca859fbf31c2dea502e38392acd269"),
 }
 
 
 def ncu_traffic(precision: str, workload: str):
-    """Captured DRAM bytes per coarse-vote launch, or None (other workload, or kernel changed)."""
+    """Captured DRAM bytes per coarse-vote launch, or None (not captured, or kernel changed)."""
     import hashlib
-    if workload != WORKLOAD or precision not in NCU_TRAFFIC:
+    if (workload, precision) not in NCU_TRAFFIC:
         return None
-    nbytes, src, digest = NCU_TRAFFIC[precision]
+    nbytes, src, digest = NCU_TRAFFIC[(workload, precision)]
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2506_11547_gb300", "csrc", src)
     try:
         ok = hashlib.sha256(open(path, "rb").read()).hexdigest() == digest
@@ -59,10 +76,10 @@ def ncu_traffic(precision: str, workload: str):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--precision", default=PRECISION)
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extra", action="store_true",
@@ -395,40 +412,6 @@ def tensor_pipe_fraction(rv, prec, grid_n, levels, a_d, b_d, delta, stream, flus
             "peak_source": f"dense bf16 tensor burst ({peak_src}); fp16 dense has the same nominal rate"}
 
 
-def bench_paper_scale(rv, synth, torch, stream, flush, reps: int = 3):
-    """The precision forms at the paper's scale: 1e6 pairs, 99% outliers, sigma 0.005, delta 0.03,
-    128^3 + 3 levels (1.14e12 cell tests per solve).  Device time per solve (L2 flushed before
-    each), the angle to the true rotation, and how many tests the FP32 re-check decided."""
-    p, g, L = synth.config_problem("lowp_n1e6_128L3")
-    a_d, b_d = torch.from_numpy(p.a).cuda(), torch.from_numpy(p.b).cuda()
-    arr = (rv.rot_vote_problem * 1)()
-    arr[0], keep = rv.problem(a_d, b_d, p.delta)
-    out = (rv.rot_vote_result * 1)()
-    res = {}
-    for prec in ("fp16x2", "bf16x2", "fp16", "bf16", "fp32"):
-        ctx = rv.Context(grid_n=g, levels=L, precision=prec, cuda_stream=stream.cuda_stream)
-        for _ in range(2):
-            ctx.solve_raw(arr, 1, out)
-        ts = []
-        for _ in range(reps):
-            flush.zero_()
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s0.record(stream)
-            ctx.solve_raw(arr, 1, out)
-            s1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(s0.elapsed_time(s1))
-        ctx.close()
-        r = rv.Result.of(out[0])
-        ms = sum(ts) / len(ts)
-        res[prec] = {"value": r.tests / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms, "tests": r.tests,
-                     "rechecked": r.rechecked, "ambiguous": r.ambiguous, "status": r.status,
-                     "angle_to_truth_rad": _angle(r.q, p.q_true)}
-    res["workload"] = ("1e6 pairs, 99% outliers, sigma 0.005, delta 0.03; 128^3 coarse grid (1,136,840 cells) "
-                       "+ 3 levels; one solve per call")
-    return res
-
-
 def bench_pose(rv, synth, torch, stream, flush, reps: int = 5):
     """Rigid pose (Sec. 4.5) on the paper's default synthetic setting (Sec. 5.4.1): N = 5000,
     90% outliers, noise 0.01; mu_t = 0.04; rotation vote 32^3 + 2 levels, delta = 0.03; the
@@ -578,7 +561,7 @@ def run_reference(args):
         "metric": METRIC, "impl": "reference", "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": WORKLOAD_DESC},
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESCS.get(args.workload, args.workload)},
         "ms_per_step": 1e3 * total_tests / value / args.steps,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"per step {sum(secs) / len(secs):.1f} s: the FP64 oracle's vote of {samples[0]} "
@@ -699,42 +682,14 @@ def main():
     e2e_value = whole_job_rate(tests_per_step, args.steps, ws, e2e_s)
     h2d = 2 * p.n * 3 * 4
     d2h = ctypes.sizeof(rv.rot_vote_result) + 4  # result struct + device error word
+    ctx.close()
 
     # ---- roofline of the dominant kernel (profiled solves on the same stream) ----
-    prof = rv.Context(grid_n=grid_n, levels=levels, precision=args.precision, cuda_stream=stream.cuda_stream,
-                      keep_trace=2)
-    stage_ms = {}
-    n_prof = 5
-    launches = 0
-    for _ in range(n_prof + 1):
-        flush.zero_()
-        prof.solve([(a_d, b_d, p.delta)])
-        st = prof.stage_times()
-        launches = sum(k for _, _, _, k in st)  # kernels one solve launches
-        for kind, lev, ms, _ in st:
-            stage_ms.setdefault((kind, lev), []).append(ms)
-    n_cells0 = len(prof.level_trace(0, 0)[0])
-    prof.close()
-    stage_avg = {k: sum(v[1:]) / len(v[1:]) for k, v in stage_ms.items()}
-    dom = max(stage_avg, key=stage_avg.get)
     peaks, peak_src = load_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    tests_dom = (n_cells0 * p.n) if dom == ("vote", 0) else None
-    roofline = None
-    if tests_dom:
-        achieved = FLOPS_PER_TEST * tests_dom / (stage_avg[dom] / 1e3) / 1e12
-        if args.precision == "fp32":
-            peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            bound, note = "alu", f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flops x {peaks.get('sm_max_mhz')} MHz"
-        else:
-            peak = peaks["bf16_tflops"]
-            bound, note = "tensor", f"dense bf16 tensor peak ({peak_src})"
-        roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": ncu_traffic(args.precision, args.workload), "traffic_unit": "B per launch",
-                    "kernel": f"{dom[0]} level {dom[1]}", "kernel_ms": stage_avg[dom],
-                    "flops_per_test": FLOPS_PER_TEST, "tests_per_launch": tests_dom, "peak_source": note,
-                    "executed_fma_per_test": 9 if args.precision == "fp32" else None,
-                    "share_of_step": stage_avg[dom] / sum(stage_avg.values())}
+    stage_avg, launches, n_cells0 = stage_profile(rv, grid_n, levels, args.precision, a_d, b_d, p.delta, stream,
+                                                  flush)
+    roofline = roofline_of(stage_avg, n_cells0 * p.n, args.precision, args.workload, peaks, peak_src, sms)
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
@@ -745,67 +700,48 @@ def main():
                "sample": f"{m} random coarse cells x {p.n} pairs of this workload's level 0 ({dt:.1f} s, "
                          f"FP64 C oracle, threads over cells)"}
 
-    # ---- the precision forms on the same workload (device-timed the same way) ----
+    # ---- the other precision forms on the same workload (device-timed the same way) ----
     extra = None
-    if not args.no_extra and args.precision == "fp32":
+    if not args.no_extra and ws == 1:
         extra = {}
-        for prec in ("fp16x2", "bf16x2", "fp16"):
-            cx = rv.Context(grid_n=grid_n, levels=levels, precision=prec, cuda_stream=stream.cuda_stream)
-            for _ in range(3):
-                cx.solve_raw(arr, 1, out)
-            ts = []
-            for _ in range(max(3, args.steps // 2)):
-                flush.zero_()
-                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                s0.record(stream)
-                cx.solve_raw(arr, 1, out)
-                s1.record(stream)
-                torch.cuda.synchronize()
-                ts.append(s0.elapsed_time(s1))
-            rr = rv.Result.of(out[0])
-            extra[prec] = {"value": tests_per_step / (sum(ts) / len(ts) / 1e3), "unit": UNIT,
-                           "ms_per_step": sum(ts) / len(ts), "rechecked": rr.rechecked,
-                           "same_result_as_fp32": bool(rr.best_cell == res0.best_cell and
-                                                       list(rr.q) == list(res0.q)),
-                           "tensor_pipe": tensor_pipe_fraction(rv, prec, grid_n, levels, a_d, b_d, p.delta, stream,
-                                                               flush, n_cells0 * p.n, peaks, peak_src)}
-            cx.close()
-        # the same workload in the stereographic chart (Sec. 4.3.1), FP32 form
-        cx = rv.Context(grid_n=grid_n, levels=levels, precision="fp32", chart="stereographic",
-                        cuda_stream=stream.cuda_stream)
-        for _ in range(3):
-            cx.solve_raw(arr, 1, out)
-        ts = []
-        for _ in range(max(3, args.steps // 2)):
-            flush.zero_()
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s0.record(stream)
-            cx.solve_raw(arr, 1, out)
-            s1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(s0.elapsed_time(s1))
-        rr = rv.Result.of(out[0])
-        extra["stereographic_fp32"] = {"value": rr.tests / (sum(ts) / len(ts) / 1e3), "unit": UNIT,
-                                       "ms_per_step": sum(ts) / len(ts), "tests_per_step": rr.tests,
-                                       "angle_to_truth_rad": _angle(rr.q, p.q_true)}
-        cx.close()
+        for prec in [x for x in ("fp16", "bf16", "bf16x2", "fp32") if x != args.precision]:
+            m = measure_form(rv, torch, prec, grid_n, levels, arr, out, stream, flush, max(3, args.steps // 4))
+            rr = m.pop("result")
+            m["same_result"] = bool(rr.best_cell == res0.best_cell and list(rr.q) == list(res0.q) and
+                                    rr.best_count == res0.best_count and rr.ambiguous == res0.ambiguous)
+            if prec != "fp32":
+                m["tensor_pipe"] = tensor_pipe_fraction(rv, prec, grid_n, levels, a_d, b_d, p.delta, stream, flush,
+                                                        n_cells0 * p.n, peaks, peak_src)
+            extra[prec] = m
+        extra["note"] = ("K = 16 forms (fp16, bf16): operands rounded once to 16 bits, the contraction's A = "
+                         "[m, -tau_hi, -tau_lo], band = each cell's rigorous bound; hi/lo forms (fp16x2, bf16x2): "
+                         "K = 32 split operands, a far narrower rigorous band (reading C11); every form gives the "
+                         "same exact counts")
 
-    batched = serving = alg1 = pose = paper_scale = None
+    # ---- the 1e5-pair, 64^3 + 3-level workload: the plain FP32 form and the FP16 hi/lo form ----
+    scale1 = None
+    if not args.no_extra and ws == 1 and args.workload != "fp32_n1e5_64L3":
+        scale1 = bench_scale1(rv, synth, torch, stream, flush, peaks, peak_src, sms, max(5, args.steps))
+
+    batched = serving = alg1 = pose = None
     if not args.no_extra and ws == 1:
         batched = bench_batched(rv, synth, torch, stream, flush)
         serving = bench_serving(rv, synth, torch, args.serve_seconds)
         alg1 = bench_alg1(rv, synth, torch, stream, flush, peaks)
         pose = bench_pose(rv, synth, torch, stream, flush)
-        paper_scale = bench_paper_scale(rv, synth, torch, stream, flush)
 
     lat = per
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else args.precision, "data": "synthetic",
-        "config": {"workload": args.workload, "desc": WORKLOAD_DESC, "precision": args.precision,
-                   "tests_per_step": tests_per_step, "l2": "flushed before every timed step (256 MiB write)",
-                   "parallelism": f"independent problem per GPU x{ws}"},
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESCS.get(args.workload, args.workload),
+                   "precision": args.precision, "tests_per_step": tests_per_step,
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"independent problem per GPU x{ws}",
+                   "form": ("FP16 hi/lo split operands (K = 32) on tcgen05 with FP32 accumulation in TMEM, rigorous "
+                            "per-cell re-check band, FP32 re-check, FP64 decision within 2e-6 of the threshold "
+                            "(the hi/lo reading of C11)" if args.precision.endswith("x2") else args.precision)},
         "rotations_per_s": ws * args.steps / (elapsed / 1e3),
         "latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "mean": ms_per_step},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -814,22 +750,132 @@ def main():
         "roofline": roofline,
         "stage_ms": {f"{k[0]}:{k[1]}": v for k, v in sorted(stage_avg.items(), key=lambda x: -x[1])},
         "precision_forms": extra,
+        "fp32_n1e5_64L3": scale1,
         "batched": batched,
         "serving": serving,
         "alg1": alg1,
         "pose": pose,
-        "paper_scale": paper_scale,
         "clocks": clocks,
         "cpu_baseline": cpu,
-        "result": {"status": res0.status, "angle_to_truth_rad": None, "rechecked": res0.rechecked,
-                   "ambiguous": res0.ambiguous},
+        "result": {"status": res0.status, "angle_to_truth_rad": _angle(res0.q, p.q_true),
+                   "rechecked": res0.rechecked, "resolved_fp64": res0.resolved, "ambiguous": res0.ambiguous,
+                   "best_cell": res0.best_cell, "best_count": res0.best_count, "inliers": res0.inliers},
     }
-    line["result"]["angle_to_truth_rad"] = _angle(res0.q, p.q_true)
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def stage_profile(rv, grid_n, levels, prec, a_d, b_d, delta, stream, flush, n_prof: int = 5):
+    """Per-stage device times (event pairs on the launching stream, mean of n_prof solves after
+    one, L2 flushed before each), the kernels one solve launches, and the coarse cell count."""
+    prof = rv.Context(grid_n=grid_n, levels=levels, precision=prec, cuda_stream=stream.cuda_stream, keep_trace=2)
+    stage_ms = {}
+    launches = 0
+    for _ in range(n_prof + 1):
+        flush.zero_()
+        prof.solve([(a_d, b_d, delta)])
+        st = prof.stage_times()
+        launches = sum(k for _, _, _, k in st)
+        for kind, lev, ms, _ in st:
+            stage_ms.setdefault((kind, lev), []).append(ms)
+    n_cells0 = len(prof.level_trace(0, 0)[0])
+    prof.close()
+    return {k: sum(v[1:]) / len(v[1:]) for k, v in stage_ms.items()}, launches, n_cells0
+
+
+def roofline_of(stage_avg, tests0, prec, workload, peaks, peak_src, sms):
+    """The dominant stage (the coarse vote) against its pipe: the FP32 FMA pipe for the plain form;
+    for the tensor-core forms the dense 16-bit tensor peak (measured bf16 burst; fp16 has the same
+    nominal rate), with the epilogue's CUDA-core bound beside it."""
+    dom = max(stage_avg, key=stage_avg.get)
+    if dom != ("vote", 0):
+        return None
+    t = stage_avg[dom] / 1e3
+    achieved = FLOPS_PER_TEST * tests0 / t / 1e12
+    f_mhz = peaks.get("sm_max_mhz", 2070.0)
+    r = {"achieved": achieved, "unit": "TFLOP/s", "traffic": ncu_traffic(prec, workload),
+         "traffic_unit": "B per launch", "kernel": "vote level 0", "kernel_ms": stage_avg[dom],
+         "flops_per_test": FLOPS_PER_TEST, "tests_per_launch": tests0,
+         "share_of_step": stage_avg[dom] / sum(stage_avg.values())}
+    if prec == "fp32":
+        peak = sms * 128 * 2 * f_mhz * 1e6 / 1e12
+        r.update(bound="alu", peak=peak, frac=achieved / peak, executed_fma_per_test=9,
+                 peak_source=f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flops x {f_mhz} MHz")
+    else:
+        peak = peaks["bf16_tflops"]
+        k = 32 if prec.endswith("x2") else 16
+        epi = sms * EPI_ALU_LANES_PER_SM * f_mhz * 1e6 / EPI_ALU_INSTR_PER_TEST
+        r.update(bound="tensor", peak=peak, frac=achieved / peak,
+                 peak_source=f"dense bf16 tensor burst ({peak_src}); fp16 dense has the same nominal rate",
+                 frac_k16=K16_FLOPS_PER_TEST * tests0 / t / 1e12 / peak,
+                 frac_executed_mma=2 * k * tests0 / t / 1e12 / peak, mma_flops_per_test=2 * k,
+                 epilogue={"bound": "alu", "tests_per_s": tests0 / t, "peak_tests_per_s": epi,
+                           "frac": tests0 / t / epi,
+                           "peak_source": (f"{sms} SMs x {EPI_ALU_LANES_PER_SM} ALU lanes x {f_mhz} MHz / "
+                                           f"{EPI_ALU_INSTR_PER_TEST} ALU instructions per test")})
+    return r
+
+
+def measure_form(rv, torch, prec, grid_n, levels, arr, out, stream, flush, reps):
+    """Device time per solve of one precision form (L2 flushed before each), after its autotune."""
+    cx = rv.Context(grid_n=grid_n, levels=levels, precision=prec, cuda_stream=stream.cuda_stream)
+    for _ in range(3):
+        cx.solve_raw(arr, 1, out)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        cx.solve_raw(arr, 1, out)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(s0.elapsed_time(s1))
+    cx.close()
+    rr = rv.Result.of(out[0])
+    ms = sum(ts) / len(ts)
+    return {"value": rr.tests / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "tests_per_step": rr.tests,
+            "rechecked": rr.rechecked, "resolved_fp64": rr.resolved, "ambiguous": rr.ambiguous, "result": rr}
+
+
+def bench_scale1(rv, synth, torch, stream, flush, peaks, peak_src, sms, reps):
+    """The 1e5-pair, 99%-outlier, 64^3 + 3-level workload: the plain FP32 CUDA-core form (the
+    baseline the precision forms must beat) and the FP16 hi/lo tensor-core form, each with its
+    coarse vote against its pipe; and the same workload in the stereographic chart (FP32)."""
+    p, g, L = synth.config_problem("fp32_n1e5_64L3")
+    a_d, b_d = torch.from_numpy(p.a).cuda(), torch.from_numpy(p.b).cuda()
+    arr = (rv.rot_vote_problem * 1)()
+    arr[0], keep = rv.problem(a_d, b_d, p.delta)
+    out = (rv.rot_vote_result * 1)()
+    res = {}
+    for prec in ("fp32", "fp16x2"):
+        m = measure_form(rv, torch, prec, g, L, arr, out, stream, flush, reps)
+        rr = m.pop("result")
+        st, launches, nc0 = stage_profile(rv, g, L, prec, a_d, b_d, p.delta, stream, flush)
+        m.update(angle_to_truth_rad=_angle(rr.q, p.q_true), kernels_per_step=launches,
+                 stage_ms={f"{k[0]}:{k[1]}": v for k, v in sorted(st.items(), key=lambda x: -x[1])},
+                 roofline=roofline_of(st, nc0 * p.n, prec, "fp32_n1e5_64L3", peaks, peak_src, sms))
+        res[prec] = m
+    cx = rv.Context(grid_n=g, levels=L, precision="fp32", chart="stereographic", cuda_stream=stream.cuda_stream)
+    for _ in range(3):
+        cx.solve_raw(arr, 1, out)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        cx.solve_raw(arr, 1, out)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(s0.elapsed_time(s1))
+    rr = rv.Result.of(out[0])
+    cx.close()
+    res["stereographic_fp32"] = {"value": rr.tests / (sum(ts) / len(ts) / 1e3), "unit": UNIT,
+                                 "ms_per_step": sum(ts) / len(ts), "tests_per_step": rr.tests,
+                                 "angle_to_truth_rad": _angle(rr.q, p.q_true)}
+    res["workload"] = WORKLOAD_DESCS["fp32_n1e5_64L3"]
+    return res
 
 
 if __name__ == "__main__":

@@ -20,10 +20,15 @@
  * eigenvector of sum_{inliers} S_i -- the least-squares solution of the
  * stacked system Q q = 0 of Eq. (stack), Sec. 4.2.
  *
- * Vote counts are exact: every (cell, pair) decision equals the decision of
- * an FP64 evaluation of q^T S_i q <= tau, except for pairs within 1e-6 of the
- * threshold, which are counted as the FP32 re-check decides and reported in
- * rot_vote_result.ambiguous.
+ * Vote counts are exact: every (cell, pair) decision is that of the FP64
+ * evaluation of q^T S_i q <= tau written as the definition's sequence of
+ * IEEE double operations (App. A's M = L(a)^T L'(b) summed over k, S =
+ * (I - M)/2, v = sum over (r, c) of q_r S_rc q_c, tau = sin^2(delta + r_c)).
+ * A fast value (FP32, or FP16/BF16 on the tensor cores) decides a test when it
+ * lies outside a rigorous error band of the threshold, an FP32 re-check when
+ * it lies inside, and the FP64 evaluation itself when the re-check lies within
+ * 2e-6 of the threshold.  Tests with |v - tau| <= 1e-6 in FP64 are counted as
+ * that evaluation decides and reported in rot_vote_result.ambiguous.
  *
  * Conventions
  *   - Quaternions are (w, x, y, z), scalar first; rotation matrices are
@@ -72,7 +77,9 @@ typedef enum {
 /* Arithmetic of the dominant (cell, pair) contraction.  All modes give the
  * same exact counts; they differ in speed and in how many tests need the
  * FP32 re-check.
- *   FP32    -- CUDA-core FP32 FMA form, 10 multiply-adds per test.
+ *   FP32    -- CUDA-core FP32 form: 9 fused multiply-adds per test, the cell's
+ *              rotation against the pair's outer product b a^T (App. A's
+ *              bilinear form q^T M q = b^T R(q) a).
  *   FP16    -- tcgen05 tensor-core form, monomials and S entries in FP16
  *              (K = 10 + 2 threshold columns, padded to 16), FP32
  *              accumulation in tensor memory.
@@ -147,10 +154,12 @@ typedef struct {
     int32_t refits;       /* refit iterations performed */
     int64_t tests;        /* (cell, pair) tests over all levels */
     int64_t rechecked;    /* tests re-evaluated by the FP32 re-check */
-    int64_t ambiguous;    /* re-checked tests within 1e-6 of the threshold */
+    int64_t ambiguous;    /* tests with |v - tau| <= 1e-6 in FP64 (decided by the FP64 evaluation) */
     int32_t status;       /* rot_vote_status of this problem */
     float ms_gpu;         /* device time of the solve call that produced it (batched: the batch) */
     float latency_ms;     /* serving: submit -> completion observed; else 0 */
+    int64_t resolved;     /* re-checked tests within 2e-6 of the threshold in FP32, decided by the
+                             FP64 evaluation of q^T S q <= tau */
 } rot_vote_result;
 
 /* Create a context on the current CUDA device.  cfg may be NULL (all defaults).
@@ -203,6 +212,24 @@ typedef struct {
 
 int rot_vote_stage_times(rot_vote_ctx *ctx, rot_vote_stage *out, int cap, int *count);
 
+/* Diagnostic of the serving loop (rot_vote_submit / rot_vote_poll): the
+ * device-time span of every serving batch completed so far on the context,
+ * in completion order (at most the last 65536).  t_start_ms / t_end_ms are
+ * the times of the events recorded on the wave's stream before the batch's
+ * first launch and after its last, in ms after serving started (the first
+ * submit); two batches overlapped on the device when their spans intersect.
+ * The paper has no counterpart: this measures the build's continuous
+ * batching.  Writes up to cap spans (the oldest first) and their total count.
+ * Returns OK or EINVAL. */
+typedef struct {
+    float t_start_ms;
+    float t_end_ms;
+    int32_t wave;      /* serving wave (stream) that ran the batch */
+    int32_t problems;  /* problems in the batch */
+} rot_vote_batch_span;
+
+int rot_vote_serve_spans(rot_vote_ctx *ctx, rot_vote_batch_span *out, int cap, int *count);
+
 /* Destroy a context: waits for in-flight work, frees its memory. */
 void rot_vote_destroy(rot_vote_ctx *ctx);
 
@@ -225,26 +252,31 @@ const char *rot_vote_last_error(const rot_vote_ctx *ctx);
  * of cudaFree.
  *
  * Arguments
- *   a, b    device (or managed) float32 [n][3], unit vectors, b_i ~ R a_i
+ *   a, b    float32 [n][3] unit vectors, b_i ~ R a_i, in device memory of the
+ *           current device (or managed memory)
  *   n       2 <= n <= ROT_VOTE_STATIC_MAX_PAIRS
  *   delta   inlier angle threshold, 0 < delta < pi/2 (rounded to float, as in
  *           rot_vote_problem)
  *   grid_n  grid side, a power of two in [2, 2^20]
- *   cells   device int64 [ncells] linear cell indices; each cell's box must
+ *   cells   int64 [ncells] linear cell indices (current device); each cell's box must
  *           meet the unit ball (a cell of the level table)
  *   ncells  1 <= ncells <= ROT_VOTE_STATIC_MAX_CELLS
- *   counts  device int32 [ncells], written (the call zeroes it first)
+ *   counts  int32 [ncells] (current device), written (the call zeroes it first)
  *   cuda_stream  cudaStream_t to run on (NULL = the legacy default stream)
  * The call runs on the current device and returns after the counts are
  * written (it synchronises cuda_stream).  The caller owns every buffer.
  *
  * Returns OK; ETOOLARGE (n or ncells above the limits, nothing launched);
- * EINVAL (bad argument, a pointer that is not device memory, a non-unit or
+ * EINVAL (bad argument, a pointer that is not memory of the current device
+ * nor managed memory, a non-unit or
  * non-finite input vector, or a cell index outside the level table -- counts
  * are then unspecified); ECUDA.
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the process; make that first call
+ * before any stream capture.  cudaDeviceReset on that device unloads the
+ * module and may move the array, so after a reset the entry point must not be
+ * called again in that process.
  * Every call on a device shares the one array and leaves its contents behind;
  * each call rewrites everything it reads before reading it.  Calls whose work
  * overlaps on the GPU (other host threads, other streams) race on the array:

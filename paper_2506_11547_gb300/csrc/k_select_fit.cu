@@ -372,8 +372,22 @@ __device__ __forceinline__ int block_excl_scan(int v, int *total) {
     return base + x - v;
 }
 
-// One slice of a fit pass: membership by the FP32 re-check
-// (|b - R a|^2/4 - c <= thr) for pairs [base, base + kFitSlice), stored in
+// Membership of one pair in a fit pass: q^T S_i q <= thr for the pass's q
+// (the winning cell's centre and threshold, or the previous iterate and
+// sin^2(delta)), by the FP32 re-check (|b - R a|^2/4 - c against fl32(thr))
+// and, within kBand64 of the threshold, by the FP64 evaluation with q and the
+// FP64 threshold -- so the winner's voters are exactly the pairs its vote
+// counted.
+__device__ __forceinline__ bool member_test(const float4 &R0, const float4 &R1, const float4 &R2, float thr,
+                                            const double4_32a &qm, double thr64, const float4 &p0,
+                                            const float4 &p1) {
+    const float v = recheck_v(R0, R1, R2, p0, p1);
+    if (!(fabsf(v - thr) <= kBand64)) return v <= thr;
+    return (decide_fp64(qm, thr64, p0, p1) & 1) != 0;
+}
+
+// One slice of a fit pass: membership (member_test) for pairs
+// [base, base + kFitSlice), stored in
 // mem[]; members compacted in index order, thread t summing the b a^T of
 // members t, t + kFitThreads, ... in FP64, and the thread sums reduced by a
 // fixed pairwise tree in shared memory.  The tree skips a partner whose whole
@@ -382,8 +396,8 @@ __device__ __forceinline__ int block_excl_scan(int v, int *total) {
 // tree.  Writes the slice's 9 sums, member count and changed count to
 // part[0..10] (thread 0).  Depends only on the slice.
 __device__ void fit_slice(const float4 *__restrict__ pr, uint8_t *mem, int64_t n, int64_t base, const float4 &R0,
-                          const float4 &R1, const float4 &R2, float thr, bool first, int *list,
-                          double (*red)[kFitThreads / 2], double *part) {
+                          const float4 &R1, const float4 &R2, float thr, const double4_32a &qm, double thr64,
+                          bool first, int *list, double (*red)[kFitThreads / 2], double *part) {
     int mine[kFitPer];
     int cnt = 0, chg = 0;
 #pragma unroll
@@ -391,7 +405,7 @@ __device__ void fit_slice(const float4 *__restrict__ pr, uint8_t *mem, int64_t n
         const int64_t i = base + (int64_t)e * kFitThreads + threadIdx.x;
         mine[e] = -1;
         if (i < n) {
-            const bool in = recheck_v(R0, R1, R2, pr[2 * i], pr[2 * i + 1]) <= thr;
+            const bool in = member_test(R0, R1, R2, thr, qm, thr64, pr[2 * i], pr[2 * i + 1]);
             if (!first) chg += in != (mem[i] != 0);
             mem[i] = in;
             if (in) mine[cnt++] = (int)(i - base);
@@ -496,14 +510,75 @@ __device__ void jacobi4_f32(float A[4][4], float V[4][4]) {
     }
 }
 
+// Cyclic Jacobi in FP64 on a symmetric 4x4 (one thread): the textbook
+// rotation zeroing A_pq with t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)),
+// theta = (A_qq - A_pp) / (2 A_pq), c = 1 / sqrt(t^2 + 1), s = t c, applied to
+// A from both sides and to V, sweeping (p, q) in row order until the
+// off-diagonal sum of squares is at most 1e-40 of the diagonal's (or 50
+// sweeps).  Writes the unit eigenvector of the smallest eigenvalue to q and
+// returns whether the two smallest eigenvalues differ by more than 1e-12 tr.
+__device__ __noinline__ bool jacobi4_f64_smallest(const double (*Ain)[4], double tr, double q[4]) {
+    double A[4][4], V[4][4];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            A[r][c] = Ain[r][c];
+            V[r][c] = r == c ? 1.0 : 0.0;
+        }
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int r = 0; r < 4; ++r) {
+            dia += A[r][r] * A[r][r];
+            for (int c = r + 1; c < 4; ++c) off += A[r][c] * A[r][c];
+        }
+        if (!(off > 1e-40 * dia) || off < 1e-300) break;
+        for (int p = 0; p < 3; ++p)
+            for (int qq = p + 1; qq < 4; ++qq) {
+                const double apq = A[p][qq];
+                if (apq == 0.0) continue;
+                const double th = (A[qq][qq] - A[p][p]) / (2.0 * apq);
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < 4; ++k) {  // A <- A J, V <- V J
+                    const double akp = A[k][p], akq = A[k][qq];
+                    A[k][p] = c * akp - sn * akq;
+                    A[k][qq] = sn * akp + c * akq;
+                    const double vkp = V[k][p], vkq = V[k][qq];
+                    V[k][p] = c * vkp - sn * vkq;
+                    V[k][qq] = sn * vkp + c * vkq;
+                }
+                for (int k = 0; k < 4; ++k) {  // A <- J^T A
+                    const double apk = A[p][k], aqk = A[qq][k];
+                    A[p][k] = c * apk - sn * aqk;
+                    A[qq][k] = sn * apk + c * aqk;
+                }
+            }
+    }
+    int i0 = 0;
+    for (int k = 1; k < 4; ++k)
+        if (A[k][k] < A[i0][i0]) i0 = k;
+    double l1 = DBL_MAX;
+    for (int k = 0; k < 4; ++k)
+        if (k != i0 && A[k][k] < l1) l1 = A[k][k];
+    double n2 = 0.0;
+    for (int r = 0; r < 4; ++r) n2 += V[r][i0] * V[r][i0];
+    const double inv = 1.0 / sqrt(n2);
+    for (int r = 0; r < 4; ++r) q[r] = V[r][i0] * inv;
+    return (l1 - A[i0][i0]) > 1e-12 * tr;
+}
+
 // Smallest eigenpair of the symmetric 4x4 A (FP64, in shared memory), called
-// by one whole warp.  An FP32 Jacobi gives the basis u_0..u_3 (~1e-7); lane j
-// < 4 then takes the FP64 Rayleigh quotient lam_j = u_j^T A u_j / u_j^T u_j
-// (second-order accurate, ~1e-14 relative), and the smallest vector v gets two
-// FP64 first-order corrections v += sum_{j != i0} u_j (u_j^T r) / ((lam_i0 -
-// lam_j) u_j^T u_j), r = A v - (v^T A v / v^T v) v, which bring it to ~1e-14.
+// by one whole warp.  An FP32 Jacobi gives the basis u_0..u_3 (~1e-7); lane
+// j < 4 then takes the FP64 Rayleigh quotient lam_j = u_j^T A u_j / u_j^T u_j
+// (second-order accurate, ~1e-14 relative).
+//   - Gap lam_1 - lam_0 above 1e-6 tr(A): the smallest vector v gets two FP64
+//     first-order corrections v += sum_{j != i0} u_j (u_j^T r) / ((lam_i0 -
+//     lam_j) u_j^T u_j), r = A v - (v^T A v / v^T v) v, which bring it to
+//     ~1e-14.
+//   - Smaller gap: the FP32 basis may mix the two eigenvectors and the
+//     corrections need not converge, so the full FP64 Jacobi above decides:
+//     its eigenvector, and its eigenvalues for the degeneracy test.
 // Writes q (unit, on every lane) and returns whether the gap between the two
-// smallest eigenvalues exceeds 1e-12 tr(A) (else q is the uncorrected u_i0).
+// smallest eigenvalues exceeds 1e-12 tr(A).
 __device__ bool eig4_smallest(const double (*A)[4], float (*Vs)[4], double q[4]) {
     const int lane = threadIdx.x & 31;
     if (lane == 0) {
@@ -531,7 +606,15 @@ __device__ bool eig4_smallest(const double (*A)[4], float (*Vs)[4], double q[4])
     for (int k = 0; k < 4; ++k)
         if (k != i0 && lams[k] < l1) l1 = lams[k];
     const double tr = A[0][0] + A[1][1] + A[2][2] + A[3][3];
-    const bool gap_ok = (l1 - lams[i0]) > 1e-12 * tr;
+    if (!((l1 - lams[i0]) > 1e-6 * tr)) {  // warp-uniform: lams, i0, l1 and tr agree on every lane
+        double qv[4] = {0.0, 0.0, 0.0, 0.0};
+        int ok = 0;
+        if (lane == 0) ok = jacobi4_f64_smallest(A, tr, qv) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        for (int r = 0; r < 4; ++r) q[r] = __shfl_sync(0xffffffffu, qv[r], 0);
+        return ok != 0;
+    }
+    const bool gap_ok = true;
     double v[4];
     for (int r = 0; r < 4; ++r) v[r] = __shfl_sync(0xffffffffu, u[r], i0);
     if (gap_ok) {
@@ -648,6 +731,7 @@ __device__ void fit_result(int p, const LevelRef &L, int wpos, int last, const F
     r.tests = (int64_t)stats[p].tests;
     r.rechecked = (int64_t)stats[p].rechecked;
     r.ambiguous = (int64_t)stats[p].ambiguous;
+    r.resolved = (int64_t)stats[p].resolved;
     r.status = stats[p].invalid ? ROT_VOTE_EINVAL : sh.status;
     r.ms_gpu = 0.f;
     r.latency_ms = 0.f;
@@ -751,19 +835,24 @@ __global__ void __launch_bounds__(kFitThreads, 2) fit_iter_kernel(
         }
         float4 R0, R1, R2;
         float thr;
+        double4_32a qm;
+        double thr64;
         if (t == 0) {
             R0 = L.cells.R32[3 * wpos];
             R1 = L.cells.R32[3 * wpos + 1];
             R2 = L.cells.R32[3 * wpos + 2];
-            thr = (float)tau_cs(P.sin_d, P.cos_d, L.cells.trig[wpos]);
+            qm = L.cells.q[wpos];
+            thr64 = tau_cs(P.sin_d, P.cos_d, L.cells.trig[wpos]);
         } else {
             const double q[4] = {state[k].q[0], state[k].q[1], state[k].q[2], state[k].q[3]};
             R32_of(q, R0, R1, R2);
-            thr = (float)(P.sin_d * P.sin_d);
+            qm = make_double4_32a(q[0], q[1], q[2], q[3]);
+            thr64 = dmul(P.sin_d, P.sin_d);
         }
+        thr = (float)thr64;
         const int64_t sl = f - big_soff[k];
-        fit_slice(pool.pr + 2 * P.pool_off, member + P.pool_off, P.n, sl * kFitSlice, R0, R1, R2, thr, t == 0, list,
-                  red, slice_part + 11 * (slice_off[p] + sl));
+        fit_slice(pool.pr + 2 * P.pool_off, member + P.pool_off, P.n, sl * kFitSlice, R0, R1, R2, thr, qm, thr64,
+                  t == 0, list, red, slice_part + 11 * (slice_off[p] + sl));
         if (threadIdx.x == 0) {
             __threadfence();  // this slice's sums are visible before it is counted
             last_block = atomicAdd(&done_cnt[k], 1) == (int)(big_soff[k + 1] - big_soff[k]) - 1;
@@ -819,9 +908,11 @@ __global__ void __launch_bounds__(kFitSmallThreads) fit_small_kernel(
         const double4_32a q4 = L.cells.q[wpos];
         qc[0] = q4.x; qc[1] = q4.y; qc[2] = q4.z; qc[3] = q4.w;
     }
-    const float thr_refit = (float)(P.sin_d * P.sin_d);
+    const double thr_refit = dmul(P.sin_d, P.sin_d);
     float4 R0 = L.cells.R32[3 * wpos], R1 = L.cells.R32[3 * wpos + 1], R2 = L.cells.R32[3 * wpos + 2];
-    float thr = (float)tau_cs(P.sin_d, P.cos_d, L.cells.trig[wpos]);
+    double4_32a qm = L.cells.q[wpos];
+    double thr64 = tau_cs(P.sin_d, P.cos_d, L.cells.trig[wpos]);
+    float thr = (float)thr64;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int t = 0; t <= refit_iters; ++t) {
         double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -846,7 +937,7 @@ __global__ void __launch_bounds__(kFitSmallThreads) fit_small_kernel(
                 const int64_t i = i0 + (int64_t)u * kFitSmallThreads;
                 if (i >= n) break;
                 const float4 p0 = q0[u], p1 = q1[u];
-                const bool in = recheck_v(R0, R1, R2, p0, p1) <= thr;
+                const bool in = member_test(R0, R1, R2, thr, qm, thr64, p0, p1);
                 if (t > 0) chg += in != (was[u] != 0);
                 mem[i] = in;
                 if (in) {
@@ -890,7 +981,9 @@ __global__ void __launch_bounds__(kFitSmallThreads) fit_small_kernel(
         if (sh.done) break;
         const double q[4] = {sh.q[0], sh.q[1], sh.q[2], sh.q[3]};
         R32_of(q, R0, R1, R2);
-        thr = thr_refit;
+        qm = make_double4_32a(q[0], q[1], q[2], q[3]);
+        thr64 = thr_refit;
+        thr = (float)thr64;
         __syncthreads();  // sh is read before warp 0 rewrites it
     }
     if (threadIdx.x == 0) fit_result(p, L, wpos, last, sh, stats, results);

@@ -7,7 +7,8 @@
 // 1 - 2 tau_c in shared memory once, and tests its pair against every cell
 // with the FP32 chain d = fma-chain(-R_c, b a^T, 1 - 2 tau_c) of the plain
 // form (k_vote_simt.cu).  Tests with |d| <= kBandR take the FP32 re-check
-// |b - R_c a|^2/4 - c, so the counts are the exact counts of every precision
+// |b - R_c a|^2/4 - c, and those within kBand64 of the threshold the FP64
+// resolution pass, so the counts are the exact counts of every precision
 // form.  Per cell, a warp's 32 votes are summed by a ballot and a population
 // count into a shared-memory counter, added to the level's counts once per
 // block.  Padding pairs do not vote.
@@ -25,7 +26,7 @@ __global__ void __launch_bounds__(kSmallThreads) vote_small_kernel(const ProbRef
                                                                    const int2 *__restrict__ tiles, int ntiles,
                                                                    const LevelRef *__restrict__ lref,
                                                                    int level_stride, int level, PairPool pool,
-                                                                   ProbStats *stats) {
+                                                                   ProbStats *stats, AmbQueue amb) {
     __shared__ float4 sm[kSmallMaxCells * 3];  // -R (9), c0 = 1 - 2 tau, tau (3 float4 per cell)
     __shared__ int scnt[kSmallMaxCells];
     static_assert(sizeof(float4) * kSmallMaxCells * 3 + sizeof(int) * kSmallMaxCells <= 48 * 1024, "static smem");
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(kSmallThreads) vote_small_kernel(const ProbRef
     const int64_t g = P.pool_off + i;
     const float4 s0 = pool.p32[3 * g], s1 = pool.p32[3 * g + 1], s2 = pool.p32[3 * g + 2];
     const int lane = threadIdx.x & 31;
-    unsigned rechecked = 0, ambiguous = 0;
+    unsigned rechecked = 0, ambiguous = 0, resolved = 0;
     for (int c = 0; c < nc; ++c) {
         const float4 m0 = sm[3 * c], m1 = sm[3 * c + 1], m2 = sm[3 * c + 2];
         const float tau = m2.z;
@@ -66,10 +67,13 @@ __global__ void __launch_bounds__(kSmallThreads) vote_small_kernel(const ProbRef
         bool vote = real && (__float_as_uint(x) >> 31);
         if (real && fabsf(x) <= kBandR) {  // rare: the FP32 re-check decides
             const float4 R0 = L.cells.R32[3 * c], R1 = L.cells.R32[3 * c + 1], R2 = L.cells.R32[3 * c + 2];
-            const float v = recheck_v(R0, R1, R2, pool.pr[2 * g], pool.pr[2 * g + 1]);
-            vote = v <= tau;
+            const float4 p0 = pool.pr[2 * g], p1 = pool.pr[2 * g + 1];
+            const float v = recheck_v(R0, R1, R2, p0, p1);
+            const int dec = decide_or_defer(v, tau, L, c, P, tl.x, g, p0, p1, amb);
+            vote = dec & 1;
             ++rechecked;
-            ambiguous += fabsf(v - tau) <= kAmbig;
+            ambiguous += (dec >> 1) & 1;
+            resolved += (dec >> 2) & 1;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, vote);
         if (lane == 0 && bal) atomicAdd(&scnt[c], __popc(bal));
@@ -79,18 +83,22 @@ __global__ void __launch_bounds__(kSmallThreads) vote_small_kernel(const ProbRef
         if (scnt[c]) atomicAdd(&L.counts[c], scnt[c]);
     const unsigned rc = __reduce_add_sync(0xffffffffu, rechecked);
     const unsigned am = __reduce_add_sync(0xffffffffu, ambiguous);
+    const unsigned rs = __reduce_add_sync(0xffffffffu, resolved);
     if (lane == 0) {
         if (rc) atomicAdd(&stats[tl.x].rechecked, (unsigned long long)rc);
         if (am) atomicAdd(&stats[tl.x].ambiguous, (unsigned long long)am);
+        if (rs) atomicAdd(&stats[tl.x].resolved, (unsigned long long)rs);
     }
 }
 
 }  // namespace
 
 cudaError_t launch_vote_small(const ProbRef *probs, const int2 *tiles, int ntiles, const LevelRef *lref,
-                              int level_stride, int level, PairPool pool, ProbStats *stats, cudaStream_t s) {
+                              int level_stride, int level, PairPool pool, ProbStats *stats, AmbQueue amb,
+                              cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    vote_small_kernel<<<ntiles, kSmallThreads, 0, s>>>(probs, tiles, ntiles, lref, level_stride, level, pool, stats);
+    vote_small_kernel<<<ntiles, kSmallThreads, 0, s>>>(probs, tiles, ntiles, lref, level_stride, level, pool, stats,
+                                                       amb);
     return cudaGetLastError();
 }
 

@@ -10,7 +10,8 @@
 // |D| <= band_c, a rigorous per-cell bound on |D - (v - tau)_exact| (operand
 // rounding to 16 bits, the FP32 pair step, FP32 accumulation).  Flagged tests
 // are re-evaluated with the FP32 re-check |b - R_c a|^2/4 - c_i, whose error
-// is below 7e-7, so every decision with |v - tau| > 1e-6 is the FP64 one.
+// is below 7e-7; those within kBand64 = 2e-6 of the threshold go to the FP64
+// resolution pass (k_resolve64.cu), so every decision is the FP64 one.
 //
 // One persistent CTA per SM.  The MMA unit is U = 256 or 128 pairs (N of one
 // tcgen05.mma) and TMEM holds 512 / U accumulator stages of U columns:
@@ -60,18 +61,23 @@ constexpr int kBTileBytesMax = kPairTile * 32 * 2; // 256 rows x K = 32 x 2 B
 constexpr int kALbo = 128 * 16, kBLbo = kPairTile * 16;
 // Deferred re-check state, per epilogue warp / warpgroup (after the barriers):
 //   queue   kQCap entries {pair offset in the item, lane | sign << 5} per warp
-//   rows    R (9), tau, pad per cell row, per warpgroup
+//   defer   kDCap entries {pair offset in the item, cell row} per warp: tests
+//           whose re-check lies within kBand64 of tau, staged for the FP64 pass
+//   rows    R (9), tau, table position, pad per cell row, per warpgroup
 //   corr    count correction per cell row, per warpgroup
 constexpr int kQCap = 64;
 constexpr int kMaxG = 4;
 constexpr size_t kQueueBytes = (size_t)4 * kMaxG * kQCap * 8;
 constexpr size_t kRowBytes = (size_t)kMaxG * 128 * 12 * 4;
 constexpr size_t kCorrBytes = (size_t)kMaxG * 128 * 4;
+constexpr int kDCap = 64;
+constexpr size_t kDeferBytes = (size_t)4 * kMaxG * kDCap * 8;
 constexpr size_t kBarBytes = 1024;
 // 1024 B alignment slack + A (2 stages) + B (kNB stages) + barriers/flags + re-check state.
 // Over 116 KB, so one CTA per SM (each holds all 512 TMEM columns).
 constexpr size_t kSmemBytes =
-    1024 + 2 * kATileBytesMax + kNB * kBTileBytesMax + kBarBytes + kQueueBytes + kRowBytes + kCorrBytes;
+    1024 + 2 * kATileBytesMax + kNB * kBTileBytesMax + kBarBytes + kQueueBytes + kRowBytes + kCorrBytes +
+    kDeferBytes;
 static_assert(kSmemBytes > 116 * 1024 && kSmemBytes <= 227 * 1024, "shared memory budget");
 static_assert((2 * kNB + 2 * kMaxAcc + 5) * 8 + 8 + 16 <= (int)kBarBytes, "barrier area");
 constexpr uint64_t kWaitNs = 2000000000ull;
@@ -358,7 +364,7 @@ template <int G, int KSTEPS, bool BF16, int CH, int U>
 __global__ void __launch_bounds__(128 + 128 * G, 1)
     vote_tc_kernel(const VoteItem *__restrict__ items, int n_items, const ProbRef *__restrict__ probs,
                    const LevelRef *__restrict__ lref, int level_stride, int level, PairPool pool, ProbStats *stats,
-                   float band_req, int *err_flag, uint64_t wait_ns, int test_stall) {
+                   float band_req, int *err_flag, uint64_t wait_ns, int test_stall, AmbQueue amb) {
     // Every warpgroup drains every stage, in unit order, so no wait ever runs
     // more than one phase ahead of its stage (an mbarrier parity wait could not
     // tell phase k+1 from a pending phase k).
@@ -383,6 +389,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
     uint2 *q_all = (uint2 *)rq;
     float *rows_all = (float *)(rq + kQueueBytes);
     int *corr_all = (int *)(rq + kQueueBytes + kRowBytes);
+    uint2 *d_all = (uint2 *)(rq + kQueueBytes + kRowBytes + kCorrBytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -508,6 +515,8 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
         const int q = warp & 3;               // TMEM lane quarter this warp may access
         const int row = 32 * q + lane;        // cell row of this thread
         uint2 *qw = q_all + (size_t)(warp - 4) * kQCap;  // this warp's re-check queue
+        uint2 *dw = d_all + (size_t)(warp - 4) * kDCap;  // this warp's FP64 staging
+        bool amb_full = false;  // this warp found the FP64 queue full: decide in place from now on
         float *rows = rows_all + (size_t)g * 128 * 12;   // this warpgroup's row table
         int *corr = corr_all + g * 128;
         int64_t j = 0;
@@ -529,7 +538,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 band = fmaxf(cell_band<KSTEPS, BF16>(m), band_req);
             }
             int cnt = 0;
-            unsigned rechecked = 0, ambiguous = 0;
+            unsigned rechecked = 0, ambiguous = 0, resolved = 0;
             {  // the cell's rotation and threshold, for re-checks of this row by any lane of the warp
                 float4 R0 = make_float4(0, 0, 0, 0), R1 = R0, R2 = R0;
                 if (valid) {
@@ -540,26 +549,68 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 float4 *rr = reinterpret_cast<float4 *>(rows + row * 12);
                 rr[0] = R0;
                 rr[1] = R1;
-                rr[2] = make_float4(R2.x, tau, 0.f, 0.f);
+                rr[2] = make_float4(R2.x, tau, __int_as_float(valid ? pos : 0), 0.f);
                 corr[row] = 0;
             }
             __syncwarp();
             int qn = 0;  // entries in this warp's queue (warp-uniform)
+            int dn = 0;  // entries in this warp's FP64 staging (warp-uniform)
             const int64_t gbase = v.P.pool_off + v.W.pair_begin;
-            // drains the queue: one entry per lane, loads issued in parallel
+            const uint32_t lt = (1u << lane) - 1u;
+            // hands the staged tests to the FP64 pass with one atomic for the warp; when the
+            // queue is full, decides them here in FP64, one test per lane
+            auto defer_flush = [&]() {
+                int base = 0;
+                if (lane == 0) base = amb_full ? amb.cap : atomicAdd(amb.count, dn);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                const bool room = base <= amb.cap - dn;
+                amb_full = !room;
+                for (int k = lane; k < dn; k += 32) {
+                    const uint2 e = dw[k];
+                    const int cpos = __float_as_int(rows[e.y * 12 + 10]);
+                    const int64_t gp = gbase + (int64_t)e.x;
+                    if (room) {
+                        amb.q[base + k] = Amb64{v.W.prob, cpos, gp};
+                    } else {
+                        const int dec = decide_cell_fp64(v.L.cells.q + cpos, v.L.cells.trig + cpos, v.P.sin_d,
+                                                         v.P.cos_d, pool.pr[2 * gp], pool.pr[2 * gp + 1]);
+                        atomicAdd(&corr[e.y], dec & 1);
+                        ambiguous += (dec >> 1) & 1;
+                        ++resolved;
+                    }
+                }
+                __syncwarp();
+                dn = 0;
+            };
+            // drains the re-check queue: one entry per lane, loads issued in parallel; the
+            // tests within kBand64 of tau are staged for the FP64 pass (their sign-bit vote
+            // removed here, their vote added there)
             auto flush = [&]() {
-                for (int k = lane; k < qn; k += 32) {
-                    const uint2 en = qw[k];
-                    const int rrow = 32 * q + (int)(en.y & 31u);
-                    const float4 *rr = reinterpret_cast<const float4 *>(rows + rrow * 12);
-                    const float4 R0 = rr[0], R1 = rr[1], R2x = rr[2];
-                    const float rtau = R2x.y;
-                    const int64_t gp = gbase + (int64_t)en.x;
-                    const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
-                    const float vv = recheck_v(R0, R1, make_float4(R2x.x, 0.f, 0.f, 0.f), p0, p1);
-                    atomicAdd(&corr[rrow], (int)(vv <= rtau) - (int)(en.y >> 5));
-                    ++rechecked;
-                    ambiguous += fabsf(vv - rtau) <= kAmbig;
+                for (int k0 = 0; k0 < qn; k0 += 32) {
+                    const int k = k0 + lane;
+                    bool in_band = false;
+                    uint32_t poff = 0, rrow = 0;
+                    if (k < qn) {
+                        const uint2 en = qw[k];
+                        rrow = 32 * q + (en.y & 31u);
+                        poff = en.x;
+                        const float4 *rr = reinterpret_cast<const float4 *>(rows + rrow * 12);
+                        const float4 R0 = rr[0], R1 = rr[1], R2x = rr[2];
+                        const float rtau = R2x.y;
+                        const int64_t gp = gbase + (int64_t)en.x;
+                        const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
+                        const float vv = recheck_v(R0, R1, make_float4(R2x.x, 0.f, 0.f, 0.f), p0, p1);
+                        in_band = fabsf(vv - rtau) <= kBand64;
+                        atomicAdd(&corr[rrow], (in_band ? 0 : (int)(vv <= rtau)) - (int)(en.y >> 5));
+                        ++rechecked;
+                    }
+                    const uint32_t bal = __ballot_sync(0xffffffffu, in_band);
+                    if (bal != 0) {
+                        if (in_band) dw[dn + __popc(bal & lt)] = make_uint2(poff, rrow);
+                        dn += __popc(bal);
+                        __syncwarp();
+                        if (dn > kDCap - 32) defer_flush();
+                    }
                 }
                 __syncwarp();
                 qn = 0;
@@ -594,7 +645,6 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                         sm |= (r[e] >> 31) << e;
                     }
                 }
-                const uint32_t lt = (1u << lane) - 1u;
                 for (;;) {
                     const bool has = fm != 0;
                     const uint32_t bal = __ballot_sync(0xffffffffu, has);
@@ -657,13 +707,16 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 if (lane == 0) mbar_arrive(&acc_empty[stage]);
             }
             if (qn > 0) flush();
+            if (dn > 0) defer_flush();
             cnt += corr[row];
             if (valid && cnt != 0) atomicAdd(&v.L.counts[pos], cnt);
             const unsigned rc = __reduce_add_sync(0xffffffffu, rechecked);
             const unsigned am = __reduce_add_sync(0xffffffffu, ambiguous);
+            const unsigned rs = __reduce_add_sync(0xffffffffu, resolved);
             if (lane == 0) {
                 if (rc) atomicAdd(&stats[v.W.prob].rechecked, (unsigned long long)rc);
                 if (am) atomicAdd(&stats[v.W.prob].ambiguous, (unsigned long long)am);
+                if (rs) atomicAdd(&stats[v.W.prob].resolved, (unsigned long long)rs);
             }
         }
     }
@@ -707,13 +760,13 @@ cudaError_t prepare_all() {
 template <int KSTEPS, bool BF16>
 cudaError_t launch_v(int variant, const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                      int level_stride, int level, PairPool pool, ProbStats *stats, float band_req, int grid,
-                     int *err_flag, int test_stall, cudaStream_t s) {
+                     int *err_flag, int test_stall, AmbQueue amb, cudaStream_t s) {
     switch (variant) {
 #define RV_CASE(G_, CH_, U_, V_)                                                                             \
     case V_:                                                                                                 \
         vote_tc_kernel<G_, KSTEPS, BF16, CH_, U_><<<grid, 128 + 128 * G_, kSmemBytes, s>>>(                  \
             items, n_items, probs, lref, level_stride, level, pool, stats, band_req, err_flag,               \
-            test_stall ? 1000000ull : kWaitNs, test_stall);                                                   \
+            test_stall ? 1000000ull : kWaitNs, test_stall, amb);                                              \
         return cudaGetLastError();
         RV_TC_VARIANTS(RV_CASE)
 #undef RV_CASE
@@ -735,12 +788,13 @@ cudaError_t prepare_vote_tc() {
 
 cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                            int level_stride, int level, PairPool pool, ProbStats *stats, int prec, float band_req,
-                           int variant, int grid_blocks, int *err_flag, int test_stall, cudaStream_t s) {
+                           int variant, int grid_blocks, int *err_flag, int test_stall, AmbQueue amb,
+                           cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
     const int grid = grid_blocks < n_items ? grid_blocks : n_items;
 #define RV_TC_G(KS_, BF_) \
     launch_v<KS_, BF_>(variant, items, n_items, probs, lref, level_stride, level, pool, stats, band_req, grid, \
-                       err_flag, test_stall, s)
+                       err_flag, test_stall, amb, s)
     switch (prec) {
     case ROT_PREC_FP16: return RV_TC_G(1, false);
     case ROT_PREC_BF16: return RV_TC_G(1, true);

@@ -292,7 +292,18 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     const size_t o_nkept = reserve(sizeof(int32_t) * (size_t)P * S);
     const size_t o_err = reserve(sizeof(int) * 4);
     const size_t o_ictr = reserve(sizeof(int) * (size_t)S);  // per-level work-item counters (CUDA-core vote)
+    const size_t o_ambcnt = reserve(sizeof(int) * (size_t)S);  // per-level FP64-queue lengths
     const size_t z1 = align_up(off, 256);
+    // FP64 resolution queue: room for 8e-6 of the largest level's tests (uniform outliers put
+    // 4e-6 of them within the band) + 64k; a full queue makes the vote decide the rest itself
+    int64_t lev_tests = 0, tests_l0 = 0, pairs_all = 0;
+    for (int k = 0; k < P; ++k) {
+        tests_l0 += (int64_t)pl.probs_h[k].n * gt[k]->ncells;
+        pairs_all += pl.probs_h[k].n;
+    }
+    lev_tests = std::max<int64_t>(tests_l0, pairs_all * (int64_t)child_cap);
+    pl.amb_cap = (int)std::min<int64_t>((int64_t)1 << 25, (int64_t)(8e-6 * (double)lev_tests) + 65536);
+    const size_t o_amb = reserve(sizeof(Amb64) * (size_t)pl.amb_cap);
     const size_t o_kept = reserve(sizeof(int32_t) * (size_t)P * S * K);
     const size_t o_cand = reserve(sizeof(Cand) * ((size_t)P * pl.chunks_per_prob * K + (size_t)P * K));
     const size_t o_res = reserve(sizeof(rot_vote_result) * P);
@@ -363,6 +374,8 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     pl.d_fcnt = (int *)(B + o_fcnt);
     pl.d_err = (int *)(B + o_err);
     pl.d_ictr = (int *)(B + o_ictr);
+    pl.d_ambcnt = (int *)(B + o_ambcnt);
+    pl.d_amb = (Amb64 *)(B + o_amb);
 
     // pair-prep tiles
     pl.tiles_h.clear();
@@ -526,12 +539,15 @@ int Context::enqueue_pipeline(Wave &w) {
     // levels (<= 8 top_k cells per problem): the pair-major vote and a one-block
     // top-K.  Each ranking step also writes the next level's children.
     for (int lev = 0; lev < S && e == cudaSuccess; ++lev) {
-        mark(1, lev, 1);
+        mark(1, lev, 2);  // the vote and its FP64 resolution pass
         if (lev == 0)
             e = launch_vote(w, lev, pl.variant);
         else
             e = launch_vote_small(pl.d_probs, pl.d_tiles, (int)pl.tiles_h.size(), pl.d_lref, S, lev, pl.pool,
-                                  pl.d_stats, w.stream);
+                                  pl.d_stats, pl.amb(lev), w.stream);
+        if (e == cudaSuccess)
+            e = launch_resolve64(pl.amb(lev), pl.d_probs, pl.d_lref, S, lev, pl.pool, pl.d_stats, 4 * sm_count,
+                                 w.stream);
         done();
         mark(2, lev, lev == 0 ? 2 : 1);
         if (e == cudaSuccess) {
@@ -563,9 +579,10 @@ cudaError_t Context::launch_vote(Wave &w, int lev, int variant) {
     const int nit = (int)pl.items_h[lev].size();
     if (pl.pool.tc_k)
         return launch_vote_tc(pl.d_items[lev], nit, pl.d_probs, pl.d_lref, pl.stride, lev, pl.pool, pl.d_stats,
-                              pl.prec, cfg.recheck_band, variant, pl.grid_blocks, pl.d_err, w.stall, w.stream);
+                              pl.prec, cfg.recheck_band, variant, pl.grid_blocks, pl.d_err, w.stall, pl.amb(lev),
+                              w.stream);
     return launch_vote_simt(pl.d_items[lev], nit, pl.d_probs, pl.d_lref, pl.stride, lev, pl.pool, pl.d_stats, variant,
-                            pl.grid_blocks, pl.d_ictr + lev, w.stream);
+                            pl.grid_blocks, pl.d_ictr + lev, pl.amb(lev), w.stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -866,6 +883,19 @@ int Wave::init(cudaStream_t s, bool own) {
     return ROT_VOTE_OK;
 }
 
+// Gives the workspace back (an idle wave only): the serving scheduler does this
+// when a request does not fit the budget while every other wave is idle.
+void Wave::free_workspace(Context &ctx) {
+    if (!base) return;
+    cudaStreamSynchronize(stream);
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    graph_exec = nullptr;
+    cudaFree(base);
+    ctx.bytes_held -= cap;
+    base = nullptr;
+    cap = 0;
+}
+
 void Wave::release(Context &ctx) {
     if (stream) cudaStreamSynchronize(stream);
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -998,7 +1028,9 @@ int rot_vote_create(const rot_vote_config *cfg_in, rot_vote_ctx **out) {
 
 int rot_vote_solve(rot_vote_ctx *ctx, const rot_vote_problem *p, int n_problems, rot_vote_result *out) {
     if (!ctx || !p || !out || n_problems < 1) return ROT_VOTE_EINVAL;
-    return reinterpret_cast<Context *>(ctx)->solve(p, n_problems, out);
+    Context *c = reinterpret_cast<Context *>(ctx);
+    std::lock_guard<std::mutex> g(c->launch_mu);
+    return c->solve(p, n_problems, out);
 }
 
 int rot_vote_submit(rot_vote_ctx *ctx, const rot_vote_problem *p, uint64_t *ticket) {
@@ -1014,12 +1046,21 @@ int rot_vote_poll(rot_vote_ctx *ctx, uint64_t ticket, rot_vote_result *out, int 
 int rot_vote_level_trace(rot_vote_ctx *ctx, int problem, int level, int64_t *idx, int32_t *count, int64_t cap,
                          int64_t *ncells, int64_t *kept_idx, int32_t *nkept) {
     if (!ctx) return ROT_VOTE_EINVAL;
-    return reinterpret_cast<Context *>(ctx)->level_trace(problem, level, idx, count, cap, ncells, kept_idx, nkept);
+    Context *c = reinterpret_cast<Context *>(ctx);
+    std::lock_guard<std::mutex> g(c->launch_mu);
+    return c->level_trace(problem, level, idx, count, cap, ncells, kept_idx, nkept);
 }
 
 int rot_vote_stage_times(rot_vote_ctx *ctx, rot_vote_stage *out, int cap, int *count) {
     if (!ctx || (!out && cap > 0)) return ROT_VOTE_EINVAL;
-    return reinterpret_cast<Context *>(ctx)->stage_times(out, cap, count);
+    Context *c = reinterpret_cast<Context *>(ctx);
+    std::lock_guard<std::mutex> g(c->launch_mu);
+    return c->stage_times(out, cap, count);
+}
+
+int rot_vote_serve_spans(rot_vote_ctx *ctx, rot_vote_batch_span *out, int cap, int *count) {
+    if (!ctx || !count || (!out && cap > 0) || cap < 0) return ROT_VOTE_EINVAL;
+    return reinterpret_cast<Context *>(ctx)->serve_spans(out, cap, count);
 }
 
 void rot_vote_destroy(rot_vote_ctx *ctx) {

@@ -1245,5 +1245,7 @@ int Context::alg1(const rot_vote_alg1_problem *p, int np, rot_vote_alg1_result *
 extern "C" int rot_vote_alg1(rot_vote_ctx *ctx, const rot_vote_alg1_problem *p, int n_problems,
                              rot_vote_alg1_result *out) {
     if (!ctx || !p || !out || n_problems < 1) return ROT_VOTE_EINVAL;
-    return reinterpret_cast<rv::Context *>(ctx)->alg1(p, n_problems, out);
+    rv::Context *c = reinterpret_cast<rv::Context *>(ctx);
+    std::lock_guard<std::mutex> g(c->launch_mu);
+    return c->alg1(p, n_problems, out);
 }

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rv_internal.h"
+
 namespace rv {
 
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
@@ -228,6 +230,115 @@ __device__ __forceinline__ float recheck_v(const float4 &R0, const float4 &R1, c
     const float e0 = p0.w - ra0, e1 = p1.x - ra1, e2 = p1.y - ra2;
     const float e2s = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
     return fmaf(0.25f, e2s, -p1.z);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 resolution of the tests next to the threshold.
+//
+// A test is ambiguous when |v - tau| <= 1e-6 in FP64 (v = q_c^T S_i q_c).  The
+// FP32 re-check value v32 is within 7e-7 of the exact real v, and tau32 =
+// fl32(tau) within 6e-8 of tau, so once |v32 - tau32| > kBand64 = 2e-6 the
+// test is not ambiguous and v32 <= tau32 is the FP64 decision.  Inside that
+// band the test is evaluated in IEEE double, one rounded operation at a time
+// in the order of the definition:
+//   1. the products a_j b_k of the float32 inputs (exact in double);
+//   2. M = L(a)^T L'(b) of App. A, entry (r, c) accumulated over k = 0..3
+//      from 0.0 (the products that are structurally zero add nothing);
+//   3. S = (I - M) / 2 (Lemma 1: S = I - P);
+//   4. v = sum over (r, c) in row-major order of (q_r S_rc) q_c, from 0.0;
+// and it votes iff v <= tau, tau = sin^2(delta + r_c) from the cell's FP64
+// (cos r, sin r).  Every such value is the unique IEEE result of those
+// operations, so the decision and the ambiguity flag are those of any FP64
+// program that writes the definition in that order.
+// ---------------------------------------------------------------------------
+constexpr float kBand64 = 2e-6f;  // |v32 - tau32| <= this: decided in FP64
+constexpr double kAmbig64 = 1e-6; // |v - tau| <= this (FP64): reported ambiguous
+
+static __device__ __noinline__ double quad_fp64(double q0, double q1, double q2, double q3, const float4 &p0,
+                                         const float4 &p1) {
+    const double a0 = p0.x, a1 = p0.y, a2 = p0.z, b0 = p0.w, b1 = p1.x, b2 = p1.y;
+    // p_jk = a_j b_k, exact (24-bit significands)
+    const double p00 = dmul(a0, b0), p01 = dmul(a0, b1), p02 = dmul(a0, b2);
+    const double p10 = dmul(a1, b0), p11 = dmul(a1, b1), p12 = dmul(a1, b2);
+    const double p20 = dmul(a2, b0), p21 = dmul(a2, b1), p22 = dmul(a2, b2);
+    // M_rc = sum_k L(a)_kr L'(b)_kc: the non-zero products in k order
+    const double m00 = dadd(dadd(p00, p11), p22);
+    const double m01 = dsub(p12, p21);            // k = 2: a1 b2, k = 3: -a2 b1
+    const double m02 = dsub(p20, p02);            // k = 1: -a0 b2, k = 3: a2 b0
+    const double m03 = dsub(p01, p10);            // k = 1: a0 b1, k = 2: -a1 b0
+    const double m11 = dsub(dsub(p00, p22), p11); // k = 0, 2, 3
+    const double m12 = dadd(p01, p10);
+    const double m13 = dadd(p02, p20);
+    const double m22 = dsub(dsub(p11, p22), p00); // k = 0, 1, 3
+    const double m23 = dadd(p12, p21);
+    const double m33 = dsub(dsub(p22, p11), p00); // k = 0, 1, 2
+    // S = (I - M) / 2; M is symmetric entry by entry (two-term sums commute)
+    const double s00 = dmul(dsub(1.0, m00), 0.5), s11 = dmul(dsub(1.0, m11), 0.5);
+    const double s22 = dmul(dsub(1.0, m22), 0.5), s33 = dmul(dsub(1.0, m33), 0.5);
+    const double s01 = dmul(dsub(0.0, m01), 0.5), s02 = dmul(dsub(0.0, m02), 0.5);
+    const double s03 = dmul(dsub(0.0, m03), 0.5), s12 = dmul(dsub(0.0, m12), 0.5);
+    const double s13 = dmul(dsub(0.0, m13), 0.5), s23 = dmul(dsub(0.0, m23), 0.5);
+    const double q[4] = {q0, q1, q2, q3};
+    const double S[16] = {s00, s01, s02, s03, s01, s11, s12, s13, s02, s12, s22, s23, s03, s13, s23, s33};
+    double v = 0.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v = dadd(v, dmul(dmul(q[r], S[4 * r + c]), q[c]));
+    return v;
+}
+
+// The FP64 decision of one test against an FP64 threshold: bit 0 vote, bit 1
+// ambiguous.
+__device__ __forceinline__ int decide_fp64(const double4_32a &q, double tau64, const float4 &p0, const float4 &p1) {
+    const double v = quad_fp64(q.x, q.y, q.z, q.w, p0, p1);
+    return (v <= tau64 ? 1 : 0) | (fabs(dsub(v, tau64)) <= kAmbig64 ? 2 : 0);
+}
+
+// The FP64 decision of one test of a level-table cell (its centre qc and
+// (cos r, sin r) trig; the pair's re-check record p0, p1), kept out of line so
+// that the vote kernels' registers do not see it.
+static __device__ __noinline__ int decide_cell_fp64(const double4_32a *qc, const double2 *trig, double sin_d,
+                                                    double cos_d, float4 p0, float4 p1) {
+    return decide_fp64(*qc, tau_cs(sin_d, cos_d, *trig), p0, p1);
+}
+
+// Appends one in-band test to the FP64 resolution queue; the lanes of a warp
+// that call it together share one atomic.  Returns false -- the caller then
+// decides the test itself -- when there is no queue or it is full (a full
+// queue takes no further atomics, so its counter never runs far past cap).
+__device__ __forceinline__ bool defer64(const AmbQueue &Q, int prob, int pos, int64_t gp) {
+    if (Q.q == nullptr || *(volatile int *)Q.count >= Q.cap) return false;
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(Q.count, __popc(act));
+    base = __shfl_sync(act, base, leader);
+    const int slot = base + __popc(act & ((1u << lane) - 1u));
+    if (slot >= Q.cap) return false;
+    Q.q[slot] = Amb64{prob, pos, gp};
+    return true;
+}
+
+// The decision of one re-checked test of a level-table cell: bit 0 vote, bit 1
+// ambiguous, bit 2 set when the FP64 evaluation decided it.  The cell's FP64
+// centre qc and (cos r, sin r) trig are read only inside the band, where the
+// threshold is rebuilt in FP64 from them (tau_cs, the table's own operations).
+__device__ __forceinline__ int decide_test(float v32, float tau32, const double4_32a *qc, const double2 *trig,
+                                           double sin_d, double cos_d, const float4 &p0, const float4 &p1) {
+    if (!(fabsf(v32 - tau32) <= kBand64)) return v32 <= tau32 ? 1 : 0;
+    return 4 | decide_fp64(*qc, tau_cs(sin_d, cos_d, *trig), p0, p1);
+}
+
+// The same decision, with an in-band test deferred to the FP64 pass when the
+// queue takes it: then the result is 8 (no vote counted here).
+__device__ __forceinline__ int decide_or_defer(float v32, float tau32, const LevelRef &L, int pos, const ProbRef &P,
+                                               int prob, int64_t gp, const float4 &p0, const float4 &p1,
+                                               const AmbQueue &Q) {
+    if (!(fabsf(v32 - tau32) <= kBand64)) return v32 <= tau32 ? 1 : 0;
+    if (defer64(Q, prob, pos, gp)) return 8;
+    return 4 | decide_cell_fp64(L.cells.q + pos, L.cells.trig + pos, P.sin_d, P.cos_d, p0, p1);
 }
 
 }  // namespace rv

@@ -13,7 +13,6 @@ constexpr int kMaxLevels = 12;      // refinement levels per problem
 constexpr int kMaxTopK = 64;
 constexpr int kPairTile = 256;      // pairs per pool tile (tensor-core B tile rows = MMA N)
 constexpr int kCellTile = 128;      // cells per tensor-core A tile (TMEM lanes)
-constexpr float kAmbig = 1e-6f;     // |v - tau| below this: the decision is reported ambiguous
 constexpr float kBandR = 5e-6f;     // FP32 form: |d| band, d = fma-chain(-R_c, b a^T, 1 - 2 tau) ~ 2 (v - tau)
 constexpr int kSelChunk = 4096;     // cells per top-K phase-1 block
 constexpr int kSimtItemCells = 1024; // cells per CUDA-core vote work item (any cells-per-thread variant)
@@ -62,6 +61,7 @@ struct ProbStats {
     unsigned long long tests;
     unsigned long long rechecked;
     unsigned long long ambiguous;
+    unsigned long long resolved;  // tests decided by the FP64 evaluation
     int32_t invalid;     // input validation failed
     int32_t pad;
 };
@@ -99,6 +99,25 @@ struct PairPool {
     float4 *p2x = nullptr;
 };
 
+// A (cell, pair) test whose FP32 re-check lands within kBand64 of the
+// threshold, deferred to the FP64 resolution pass: problem, position in the
+// level table, pool index of the pair.  The vote kernels leave such a test
+// uncounted; resolve64 counts it.
+struct Amb64 {
+    int32_t prob;
+    int32_t pos;
+    int64_t gp;
+};
+
+// The deferred tests of one level: q[0 .. min(*count, cap)).  q == nullptr (or
+// a full queue): the vote kernel decides the test in FP64 itself.
+struct AmbQueue {
+    Amb64 *q = nullptr;
+    int *count = nullptr;  // zeroed before the level's vote
+    int cap = 0;
+    int pad = 0;
+};
+
 // ---- launchers (each returns cudaGetLastError() of its launch) ----
 
 // Coarse table of an n^3 grid from its non-empty rows {first table position, ix_lo, ix_hi, iz*n + iy}.
@@ -115,7 +134,7 @@ cudaError_t launch_pair_prep(const ProbRef *probs, const int2 *tiles, int ntiles
 // items in grid-stride order.
 cudaError_t launch_vote_simt(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                              int level_stride, int level, PairPool pool, ProbStats *stats, int variant,
-                             int grid_blocks, int *item_counter, cudaStream_t s);
+                             int grid_blocks, int *item_counter, AmbQueue amb, cudaStream_t s);
 
 // Vote, tcgen05 tensor-core form. prec: ROT_PREC_FP16 .. BF16X2; variant = epilogue
 // warpgroups (2 or 4), plus 10 for 16-column instead of 32-column TMEM chunks, plus
@@ -126,7 +145,8 @@ cudaError_t launch_vote_simt(const VoteItem *items, int n_items, const ProbRef *
 // *err_flag and leave the context usable.
 cudaError_t launch_vote_tc(const VoteItem *items, int n_items, const ProbRef *probs, const LevelRef *lref,
                            int level_stride, int level, PairPool pool, ProbStats *stats, int prec, float band_req,
-                           int variant, int grid_blocks, int *err_flag, int test_stall, cudaStream_t s);
+                           int variant, int grid_blocks, int *err_flag, int test_stall, AmbQueue amb,
+                           cudaStream_t s);
 
 // Once per process/device, outside stream capture: kernel attributes of the tensor-core vote.
 cudaError_t prepare_vote_tc();
@@ -148,7 +168,15 @@ cudaError_t launch_select_small(const ProbRef *probs, int nprob, const LevelRef 
 // Vote of a refinement level, pair-major (one block per 256-pair tile of the
 // pair step's tile list); FP32 chain + FP32 re-check, exact counts in every form.
 cudaError_t launch_vote_small(const ProbRef *probs, const int2 *tiles, int ntiles, const LevelRef *lref,
-                              int level_stride, int level, PairPool pool, ProbStats *stats, cudaStream_t s);
+                              int level_stride, int level, PairPool pool, ProbStats *stats, AmbQueue amb,
+                              cudaStream_t s);
+
+// The FP64 resolution pass of one level's deferred tests (after its vote): each
+// test decided by the FP64 evaluation, its vote added to the cell's count, the
+// problem's ambiguous and resolved statistics updated.  grid_blocks blocks
+// stride over the queue (its length is read on the device).
+cudaError_t launch_resolve64(AmbQueue amb, const ProbRef *probs, const LevelRef *lref, int level_stride, int level,
+                             PairPool pool, ProbStats *stats, int grid_blocks, cudaStream_t s);
 
 // Fit state of a large problem between its passes.
 struct FitState {

@@ -514,5 +514,7 @@ int Context::pose(const rot_vote_pose_problem *p, int np, rot_vote_pose_result *
 extern "C" int rot_vote_pose(rot_vote_ctx *ctx, const rot_vote_pose_problem *p, int n_problems,
                              rot_vote_pose_result *out) {
     if (!ctx || !p || !out || n_problems < 1) return ROT_VOTE_EINVAL;
-    return reinterpret_cast<rv::Context *>(ctx)->pose(p, n_problems, out);
+    rv::Context *c = reinterpret_cast<rv::Context *>(ctx);
+    std::lock_guard<std::mutex> g(c->launch_mu);
+    return c->pose(p, n_problems, out);
 }

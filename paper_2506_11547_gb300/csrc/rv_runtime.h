@@ -68,6 +68,16 @@ struct Plan {
     int *d_fcnt = nullptr;  // per large problem: slices of the current fit iteration written
     int *d_err = nullptr;
     int *d_ictr = nullptr;  // per-level work-item counters of the CUDA-core vote (zeroed per solve)
+    Amb64 *d_amb = nullptr; // tests deferred to the FP64 resolution pass (reused level after level)
+    int *d_ambcnt = nullptr;  // per-level queue lengths (zeroed per solve)
+    int amb_cap = 0;
+    AmbQueue amb(int lev) const {
+        AmbQueue q;
+        q.q = d_amb;
+        q.count = d_ambcnt + lev;
+        q.cap = amb_cap;
+        return q;
+    }
 };
 
 class Context;
@@ -90,7 +100,8 @@ struct Wave {
     void *graph_base = nullptr;
     Plan plan;
     // serving bookkeeping
-    bool busy = false;
+    bool busy = false;       // a batch is admitted to this wave (being launched, or in flight)
+    bool launching = false;  // the scheduler is launching it with the context lock released
     int stall = 0;  // fault injection for this batch (see Context::test_stall)
     std::vector<uint64_t> tickets;
     std::vector<double> t_submit;
@@ -100,6 +111,7 @@ struct Wave {
     int ensure_pinned(size_t bytes);
     int ensure_stage(size_t bytes);
     int ensure_results(int n);
+    void free_workspace(Context &ctx);
     void release(Context &ctx);
 };
 
@@ -144,8 +156,14 @@ class Context {
     void *a1_hdr_h = nullptr;
     cudaEvent_t a1_ev[2] = {nullptr, nullptr};
 
+    // Every launch, and the state launches share (workspaces, grid tables, tuning,
+    // traces, last_error), is taken under launch_mu.  The serving state below is
+    // guarded by mu, which is never held across a launch, so rot_vote_submit and
+    // rot_vote_poll do not wait for the scheduler's launches.  No code holds both.
+    std::mutex launch_mu;
+
     // serving
-    std::mutex mu;          // guards everything below and every launch
+    std::mutex mu;          // guards everything below
     std::condition_variable cv;
     std::deque<Pending> queue;
     std::vector<Wave> waves;
@@ -155,6 +173,9 @@ class Context {
     bool stop = false;
     std::thread sched;
     bool sched_started = false;
+    cudaEvent_t serve_ref = nullptr;          // recorded when serving starts: the origin of batch spans
+    std::vector<rot_vote_batch_span> spans;   // device-time span of every completed serving batch
+    static constexpr size_t kMaxSpans = 1 << 16;
 
     int init(const rot_vote_config &c);
     void shutdown();
@@ -185,6 +206,7 @@ class Context {
     int submit(const rot_vote_problem &p, uint64_t *ticket);
     int poll(uint64_t ticket, rot_vote_result *out, int timeout_us);
     void sched_loop();
+    int serve_spans(rot_vote_batch_span *out, int cap, int *count);
 };
 
 double now_s();

@@ -105,6 +105,7 @@ __global__ void static_setup_kernel(StaticArgs A) {
             S.tests = 0;
             S.rechecked = 0;
             S.ambiguous = 0;
+            S.resolved = 0;
             S.invalid = 0;
             S.pad = 0;
             *reinterpret_cast<ProbStats *>(base + kOffStats) = S;
@@ -162,13 +163,16 @@ cudaError_t static_base(unsigned char **out) {
     return cudaSuccess;
 }
 
-bool device_accessible(const void *p) {
+// Memory the kernels on device `dev` may read and write: that device's own
+// memory, or managed memory.
+bool device_accessible(const void *p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -184,7 +188,10 @@ extern "C" int rot_vote_count_cells_static(const float *a, const float *b, int64
     if (n > kStaticMaxPairs || ncells > kStaticMaxCells) return ROT_VOTE_ETOOLARGE;
     if (!(delta > 0.0) || !(delta < 1.5707963)) return ROT_VOTE_EINVAL;
     if (grid_n < 2 || grid_n > (1 << 20) || (grid_n & (grid_n - 1)) != 0) return ROT_VOTE_EINVAL;
-    if (!device_accessible(a) || !device_accessible(b) || !device_accessible(cells) || !device_accessible(counts))
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ROT_VOTE_ECUDA;
+    if (!device_accessible(a, dev) || !device_accessible(b, dev) || !device_accessible(cells, dev) ||
+        !device_accessible(counts, dev))
         return ROT_VOTE_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     unsigned char *base = nullptr;
@@ -229,7 +236,7 @@ extern "C" int rot_vote_count_cells_static(const float *a, const float *b, int64
                              stats, s);
     if (e == cudaSuccess)
         e = launch_vote_simt(reinterpret_cast<const VoteItem *>(base + kOffItems), A.nitems, probs, lref, 1, 0, pool,
-                             stats, 4, A.nitems, nullptr, s);
+                             stats, 4, A.nitems, nullptr, AmbQueue{}, s);
     // header slots back to the host: ProbStats.invalid and the bad-cell flag
     unsigned char hdr[1024];
     if (e == cudaSuccess) e = cudaMemcpyAsync(hdr, base, sizeof hdr, cudaMemcpyDeviceToHost, s);

@@ -41,7 +41,7 @@ class rot_vote_result(C.Structure):
     _fields_ = [("q", C.c_double * 4), ("R", C.c_double * 9), ("best_count", C.c_int32), ("inliers", C.c_int32),
                 ("best_cell", C.c_int64), ("best_level", C.c_int32), ("refits", C.c_int32), ("tests", C.c_int64),
                 ("rechecked", C.c_int64), ("ambiguous", C.c_int64), ("status", C.c_int32), ("ms_gpu", C.c_float),
-                ("latency_ms", C.c_float)]
+                ("latency_ms", C.c_float), ("resolved", C.c_int64)]
 
 
 ALG1_MAX_PEAKS, ALG1_PEAK_CANDIDATES = 64, 16384
@@ -80,6 +80,10 @@ class rot_vote_stage(C.Structure):
     _fields_ = [("kind", C.c_int32), ("level", C.c_int32), ("ms", C.c_float), ("kernels", C.c_int32)]
 
 
+class rot_vote_batch_span(C.Structure):
+    _fields_ = [("t_start_ms", C.c_float), ("t_end_ms", C.c_float), ("wave", C.c_int32), ("problems", C.c_int32)]
+
+
 STAGE_KIND = {0: "pair_prep", 1: "vote", 2: "topk", 3: "children", 4: "fit", 5: "alg1_zero", 6: "alg1_vote",
               7: "alg1_argmax"}
 
@@ -87,7 +91,7 @@ _lib = None
 
 EXPORTS = ("rot_vote_create", "rot_vote_solve", "rot_vote_submit", "rot_vote_poll", "rot_vote_level_trace",
            "rot_vote_stage_times", "rot_vote_destroy", "rot_vote_last_error", "rot_vote_count_cells_static",
-           "rot_vote_alg1", "rot_vote_pose")
+           "rot_vote_alg1", "rot_vote_pose", "rot_vote_serve_spans")
 
 
 def load(path: str = LIB_PATH):
@@ -111,6 +115,8 @@ def load(path: str = LIB_PATH):
     L.rot_vote_level_trace.restype = C.c_int
     L.rot_vote_stage_times.argtypes = [C.c_void_p, C.POINTER(rot_vote_stage), C.c_int, C.POINTER(C.c_int)]
     L.rot_vote_stage_times.restype = C.c_int
+    L.rot_vote_serve_spans.argtypes = [C.c_void_p, C.POINTER(rot_vote_batch_span), C.c_int, C.POINTER(C.c_int)]
+    L.rot_vote_serve_spans.restype = C.c_int
     L.rot_vote_destroy.argtypes = [C.c_void_p]
     L.rot_vote_destroy.restype = None
     L.rot_vote_last_error.argtypes = [C.c_void_p]
@@ -143,13 +149,14 @@ class Result:
     status: int
     ms_gpu: float
     latency_ms: float
+    resolved: int = 0
 
     @staticmethod
     def of(r: rot_vote_result) -> "Result":
         return Result(q=np.array(r.q[:]), R=np.array(r.R[:]).reshape(3, 3), best_count=r.best_count,
                       inliers=r.inliers, best_cell=r.best_cell, best_level=r.best_level, refits=r.refits,
                       tests=r.tests, rechecked=r.rechecked, ambiguous=r.ambiguous, status=r.status,
-                      ms_gpu=r.ms_gpu, latency_ms=r.latency_ms)
+                      ms_gpu=r.ms_gpu, latency_ms=r.latency_ms, resolved=r.resolved)
 
 
 @dataclasses.dataclass
@@ -385,6 +392,14 @@ class Context:
         self._check(self._L.rot_vote_stage_times(self._h, buf, 256, C.byref(n)))
         return [(STAGE_KIND[buf[k].kind], buf[k].level, buf[k].ms, buf[k].kernels) for k in range(min(n.value, 256))]
 
+    def serve_spans(self, cap: int = 1 << 16):
+        """[(t_start_ms, t_end_ms, wave, problems)] of every completed serving batch: device-time
+        spans from the serving start, in completion order."""
+        buf = (rot_vote_batch_span * cap)()
+        n = C.c_int()
+        self._check(self._L.rot_vote_serve_spans(self._h, buf, cap, C.byref(n)))
+        return [(buf[k].t_start_ms, buf[k].t_end_ms, buf[k].wave, buf[k].problems) for k in range(min(n.value, cap))]
+
     def close(self):
         if getattr(self, "_h", None):
             self._L.rot_vote_destroy(self._h)
@@ -403,6 +418,24 @@ class Context:
             pass
 
 
+def check_static_args(a, b, cells, counts) -> None:
+    """Shapes and devices of count_cells_static's tensors, checked before anything is
+    launched: a and b [n, 3] with the same n, cells and counts 1-D of the same length,
+    all on one CUDA device, the current one (raises ValueError otherwise)."""
+    if a.dim() != 2 or a.shape[1] != 3 or tuple(b.shape) != tuple(a.shape):
+        raise ValueError(f"a and b must both be [n, 3]; got {tuple(a.shape)} and {tuple(b.shape)}")
+    if cells.dim() != 1 or tuple(counts.shape) != tuple(cells.shape):
+        raise ValueError(f"cells and counts must be 1-D of one length; got {tuple(cells.shape)} and "
+                         f"{tuple(counts.shape)}")
+    devs = {(t.device.type, t.device.index) for t in (a, b, cells, counts)}
+    if len(devs) != 1 or next(iter(devs))[0] != "cuda":
+        raise ValueError(f"a, b, cells and counts must be on one CUDA device; got {sorted(map(str, devs))}")
+    import torch
+    if next(iter(devs))[1] != torch.cuda.current_device():
+        raise ValueError(f"the tensors are on cuda:{next(iter(devs))[1]}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+
+
 def count_cells_static(a, b, delta: float, grid_n: int, cells, counts, cuda_stream: int = 0) -> int:
     """rot_vote_count_cells_static: vote counts of the listed cells into `counts`
     with no device allocation.  a, b: device float32 [n, 3]; cells: device int64
@@ -410,6 +443,7 @@ def count_cells_static(a, b, delta: float, grid_n: int, cells, counts, cuda_stre
     for t, dt in ((a, "torch.float32"), (b, "torch.float32"), (cells, "torch.int64"), (counts, "torch.int32")):
         if str(t.dtype) != dt or not t.is_contiguous():
             raise TypeError(f"expected a contiguous {dt} device tensor")
+    check_static_args(a, b, cells, counts)
     return int(load().rot_vote_count_cells_static(a.data_ptr(), b.data_ptr(), int(a.shape[0]), float(delta),
                                                   int(grid_n), cells.data_ptr(), int(cells.shape[0]),
                                                   counts.data_ptr(), int(cuda_stream) or None))

@@ -33,6 +33,7 @@ __all__ = [
     "make_multi_problem",
     "PoseProblem",
     "make_pose_problem",
+    "make_bundle_problem",
     "SEED_BASE",
 ]
 
@@ -119,6 +120,27 @@ def make_problem(n: int, rho: float, sigma: float, delta: float, seed: int,
     return Problem(a=a.astype(np.float32), b=b.astype(np.float32), q_true=q,
                    R_true=R, outlier=outlier, delta=float(delta),
                    sigma=float(sigma), rho=float(rho))
+
+
+def make_bundle_problem(n: int, spread: float, seed: int, about_axis: bool = False) -> Problem:
+    """Noise-free correspondences whose observations a_i form a narrow bundle:
+    a_i = normalize(a0 + spread * N(0, I3)), b_i = R a_i.  With a bundle the
+    rotation about a0 is barely constrained, so the inlier set is close to the
+    degenerate case of all-parallel observations (the smaller the spread, the
+    closer).  about_axis=True takes a0 along the rotation axis itself, where
+    b_i ~ a_i (the pairs of the paper's same-axis setting, Table I); otherwise
+    a0 is a uniform direction."""
+    rng = np.random.default_rng(seed)
+    q, R = _random_rotation(rng)
+    if about_axis:
+        v = q[1:]
+        a0 = v / np.linalg.norm(v)
+    else:
+        a0 = _normalize_rows(rng.standard_normal((1, 3)))[0]
+    a = _normalize_rows(a0[None, :] + spread * rng.standard_normal((n, 3)))
+    b = _normalize_rows(a @ R.T)
+    return Problem(a=a.astype(np.float32), b=b.astype(np.float32), q_true=q, R_true=R,
+                   outlier=np.zeros(n, dtype=bool), delta=0.03, sigma=0.0, rho=0.0)
 
 
 # Synthetic workload shapes (Sec. 5.3.1 of the paper: N up to 1e6, outlier

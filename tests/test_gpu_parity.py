@@ -1,8 +1,10 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Counts: every cell's count equals the oracle's except by at most the number
-of that cell's tests within 1e-6 of the threshold (the oracle reports them).
-Ranking: kept cells equal the oracle's (near-ties within 1e-9 may swap).
+Counts: every cell's count equals the oracle's, at every level (the tests
+within 2e-6 of the threshold are decided by the FP64 evaluation, in the
+oracle's order of operations).
+Ranking: the kept cells equal the oracle's, in rank order.
+Ambiguous tests (|v - tau| <= 1e-6 in FP64): the same total as the oracle's.
 Rotation: within 1e-4 rad of the oracle's.
 """
 import os
@@ -31,21 +33,13 @@ def dev(x):
 
 def check_counts(gpu_idx, gpu_cnt, lev):
     assert np.array_equal(gpu_idx, lev["idx"]), "level tables differ"
-    d = np.abs(gpu_cnt.astype(np.int64) - lev["count"].astype(np.int64))
-    bad = np.nonzero(d > lev["amb"])[0]
-    assert len(bad) == 0, f"{len(bad)} cells differ beyond ambiguity, e.g. pos {bad[:5]}"
+    bad = np.nonzero(gpu_cnt.astype(np.int64) != lev["count"].astype(np.int64))[0]
+    assert len(bad) == 0, (f"{len(bad)} of {len(gpu_cnt)} cells differ, e.g. pos {bad[:5]}: "
+                           f"gpu {gpu_cnt[bad[:5]]} oracle {lev['count'][bad[:5]]} amb {lev['amb'][bad[:5]]}")
 
 
-def check_kept(gpu_kept, lev, n_pairs):
-    want = lev["topk_idx"]
-    if np.array_equal(gpu_kept, want):
-        return
-    # allow swaps only among near-ties of the oracle's scores
-    assert len(gpu_kept) == len(want)
-    sc = dict(zip(lev["idx"].tolist(), (lev["count"] - n_pairs * lev["tau"]).tolist()))
-    ws = np.array([sc[i] for i in want])
-    gs = np.array([sc[i] for i in gpu_kept])
-    assert np.allclose(np.sort(ws), np.sort(gs), atol=1e-9) and np.max(np.abs(ws - gs)) < 1e-9 + 2 * lev["amb"].max()
+def check_kept(gpu_kept, lev):
+    assert np.array_equal(gpu_kept, lev["topk_idx"]), (gpu_kept, lev["topk_idx"])
 
 
 def run_both(p, grid_n, levels, precision="fp32", top_k=16, rank_mode="excess", refit=8, device=True, shape=0,
@@ -65,12 +59,15 @@ def assert_parity(p, r, tr, o, levels):
     for lev in range(levels + 1):
         idx, cnt, kept = tr[lev]
         check_counts(idx, cnt, o.levels[lev])
-        check_kept(kept, o.levels[lev], p.n)
+        check_kept(kept, o.levels[lev])
     assert r.status == o.status
     assert r.best_cell == o.best_cell
-    assert abs(r.best_count - o.best_count) <= o.levels[-1]["amb"].max()
+    assert r.best_count == o.best_count
+    assert r.ambiguous == o.ambiguous, (r.ambiguous, o.ambiguous)
+    assert r.resolved >= r.ambiguous
     assert quat_angle(r.q, o.q) < ROT_TOL
     assert r.tests == o.tests
+    assert (r.inliers, r.refits) == (o.inliers, o.refits)
     assert r.q[0] >= 0
 
 
@@ -78,7 +75,6 @@ def test_small_workload_every_cell():
     p, g, L = synth.config_problem("small_n1e3_32")
     r, tr, o = run_both(p, g, L)
     assert_parity(p, r, tr, o, L)
-    assert abs(r.inliers - o.inliers) <= 2
 
 
 def test_multilevel_every_level():

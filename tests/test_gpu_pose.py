@@ -4,8 +4,8 @@ the FP64 oracle.
 - Kept pairs: bit-exact. Same pairs, same order, same float32 unit vectors:
   each length decision equals the IEEE double definition.
 - Rotation: the rotation-vote parity bar on those identical inputs:
-  - the same winning cell;
-  - counts within the ambiguous tests;
+  - the same winning cell and the same count;
+  - the same number of ambiguous tests;
   - 1e-4 rad.
 - Translation: each side votes with its own rotation. Where the two rotations
   agree to 1e-12, the winning cell and its count agree exactly, up to a
@@ -51,7 +51,8 @@ def check(r, g_pairs, o_pairs, o):
     K = r.pairs_kept
     assert np.array_equal(g_pairs[0][:K], o_pairs[0]) and np.array_equal(g_pairs[1][:K], o_pairs[1])
     assert r.rot.best_cell == o_rot.best_cell
-    assert abs(r.rot.best_count - o_rot.best_count) <= max(1, o_rot.ambiguous)
+    assert r.rot.best_count == o_rot.best_count
+    assert r.rot.ambiguous == o_rot.ambiguous
     assert quat_angle(r.rot.q, o_rot.q) < 1e-4
     assert r.rot.tests == o_rot.tests
     if quat_angle(r.rot.q, o_rot.q) < 1e-12:

@@ -1,13 +1,17 @@
 """rot_vote_count_cells_static (the entry point that allocates no device
 memory), called through the C ABI, against the counts of a context's solve
-(rot_vote_solve in the FP32 form, level-0 trace) on the same inputs.  Both run
-the same vote, so the counts must be identical, call after call: the cases run
-back to back on the shared static scratch, larger problem after smaller and
-smaller after larger, up to both size limits."""
+(rot_vote_solve in the FP32 form, level-0 trace) on the same inputs and
+against the oracle's counts of the same cells.  All three count exactly, so
+the counts must be identical, call after call: the cases run back to back on
+the shared static scratch, larger problem after smaller and smaller after
+larger, up to both size limits."""
+import os
+
 import numpy as np
 import pytest
 
 from paper_2506_11547_gb300 import synth
+from tests._util import f32
 
 pytestmark = pytest.mark.gpu
 
@@ -44,10 +48,13 @@ def test_static_counts_equal_solve_counts_call_after_call():
         (synth.make_problem(3001, rho=0.8, sigma=0.01, delta=0.02, seed=903), 32, rv.STATIC_MAX_CELLS),
         (synth.make_problem(129, rho=0.3, sigma=0.01, delta=0.04, seed=904), 8, None),
     ]
+    import oracle
     for p, g, keep in cases:
         idx, cnt = _solve_level0(p, g)
         if keep is not None:
             idx, cnt = idx[:keep], cnt[:keep]
+        oc, _, _ = oracle.vote_cells(p.a, p.b, f32(p.delta), g, idx, nthreads=max(1, os.cpu_count() or 1))
+        assert np.array_equal(cnt, oc)
         rc, got = _static_counts(p, g, idx)
         assert rc == rv.OK
         assert np.array_equal(got, cnt)

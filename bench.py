@@ -525,16 +525,43 @@ def bench_serving(rv, synth, torch, seconds: float, rate_hz: float = 2000.0, dis
     t_sub = time.perf_counter() - t0
     finished.set()
     th.join()
+    spans = ctx.serve_spans()
     ctx.close()
     span = max(done_t) - t0
     return {"rotations_per_s": len(lat) / span, "offered_per_s": total / t_sub,
             "tests_per_s": tests[0] / span, "unit": "rotations/s",
             "latency_ms": {"p50": percentile(lat, 50), "p90": percentile(lat, 90), "p99": percentile(lat, 99),
                            "max": max(lat)},
-            "completed": len(lat), "refused_eagain": refused[0],
+            "completed": len(lat), "refused_eagain": refused[0], "overlap": span_overlap(spans),
             "workload": ("Poisson %.0f/s for %.1f s; N log-uniform [100, 1e5], outliers U[0.8, 0.99], sigma 0.01, "
                          "delta 0.03; 32^3 + 2 levels; fp16x2; %d distinct problems cycled; after a 1 s warm-up at the same "
                          "rate; latency = submit to result ready (library clock)" % (rate_hz, seconds, distinct))}
+
+
+def span_overlap(spans):
+    """How much the serving batches overlapped on the device, from their device-time spans
+    (t_start_ms, t_end_ms, wave, problems): the mean number of batches in flight over the time
+    any was, and the share of that time with two or more in flight."""
+    if not spans:
+        return None
+    ev = sorted([(s[0], 1) for s in spans] + [(s[1], -1) for s in spans])
+    busy = multi = 0.0
+    depth, prev = 0, ev[0][0]
+    for t, d in ev:
+        if depth > 0:
+            busy += t - prev
+        if depth > 1:
+            multi += t - prev
+        depth += d
+        prev = t
+    total = sum(s[1] - s[0] for s in spans)
+    return {"batches": len(spans), "waves_used": len({s[2] for s in spans}),
+            "mean_batch_problems": sum(s[3] for s in spans) / len(spans),
+            "mean_in_flight": total / busy if busy > 0 else None,
+            "share_two_or_more": multi / busy if busy > 0 else None,
+            "note": ("spans run from a batch's first to its last event on its wave's stream: overlapping spans "
+                     "mean both batches' work was in flight together; the tcgen05 vote holds a whole SM, so "
+                     "two waves' coarse votes share no SM")}
 
 
 def run_reference(args):

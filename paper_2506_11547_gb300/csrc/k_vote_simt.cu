@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, 4) vote_simt_kernel(const VoteItem *
             const int ntiles = (W.pair_end - W.pair_begin) / kTP;
             const int nvalid = (int)min((int64_t)(W.pair_end - W.pair_begin), P.n - W.pair_begin);
             const float4 *src = pool.p32 + 3 * g0;
-            unsigned rechecked = 0, ambiguous = 0, resolved = 0;
+            unsigned rechecked = 0;
 
             auto load_tile = [&](int buf, int t) {
                 const float4 *gsrc = src + (int64_t)t * kTP * 3;
@@ -158,11 +158,9 @@ __global__ void __launch_bounds__(kThreads, 4) vote_simt_kernel(const VoteItem *
                                 const float4 R0 = L.cells.R32[3 * pos[k]], R1 = L.cells.R32[3 * pos[k] + 1],
                                              R2 = L.cells.R32[3 * pos[k] + 2];
                                 const float v = recheck_v(R0, R1, R2, q0, q1);
-                                const int dec = decide_or_defer(v, tau[k], L, pos[k], P, W.prob, gp, q0, q1, amb);
+                                const int dec = decide_or_defer(v, tau[k], L, pos[k], W.prob, gp, amb);
                                 cnt[k] += (dec & 1) - (int)(__float_as_uint(d[k]) >> 31);
                                 ++rechecked;
-                                ambiguous += (dec >> 1) & 1;
-                                resolved += (dec >> 2) & 1;
                             }
                         }
                     }
@@ -173,13 +171,7 @@ __global__ void __launch_bounds__(kThreads, 4) vote_simt_kernel(const VoteItem *
             for (int k = 0; k < CPT; ++k)
                 if (pos[k] < cell_end && cnt[k] != 0) atomicAdd(&L.counts[pos[k]], cnt[k]);
             const unsigned rc = __reduce_add_sync(0xffffffffu, rechecked);
-            const unsigned am = __reduce_add_sync(0xffffffffu, ambiguous);
-            const unsigned rs = __reduce_add_sync(0xffffffffu, resolved);
-            if ((threadIdx.x & 31) == 0) {
-                if (rc) atomicAdd(&stats[W.prob].rechecked, (unsigned long long)rc);
-                if (am) atomicAdd(&stats[W.prob].ambiguous, (unsigned long long)am);
-                if (rs) atomicAdd(&stats[W.prob].resolved, (unsigned long long)rs);
-            }
+            if ((threadIdx.x & 31) == 0 && rc) atomicAdd(&stats[W.prob].rechecked, (unsigned long long)rc);
         }
     }
 }
@@ -210,40 +202,6 @@ __device__ __forceinline__ float min3_abs(float m, float x, float y) {
 }
 
 constexpr int kPP = kTP / 2;  // pair-pairs per shared-memory tile (5 float4 each)
-constexpr int kSDCap = 64;    // per-warp staging of tests for the FP64 pass
-
-// Hands a warp's staged tests (cell position, pair offset from g0), whose FP32
-// re-check lies within kBand64 of the threshold, to the FP64 pass with one
-// atomic; when the queue is full (full != 0 on entry, or no room), decides them
-// here in FP64, one per lane, and adds their votes to the counts.  Called by
-// the whole warp; kept out of line so that the vote loop's registers do not
-// see it.  Returns the tests decided here | their ambiguous ones << 8 | the
-// queue-full state << 16.
-static __device__ __noinline__ unsigned simt_defer_flush(const int2 *dq, int dn, AmbQueue amb, int full, int prob,
-                                                         int64_t g0, const double4_32a *cq, const double2 *ctrig,
-                                                         int32_t *counts, double sin_d, double cos_d,
-                                                         const float4 *pr) {
-    const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == 0) base = (full || !amb.q) ? amb.cap : atomicAdd(amb.count, dn);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    const bool room = amb.q && base <= amb.cap - dn;
-    unsigned here = 0, am = 0;
-    for (int k = lane; k < dn; k += 32) {
-        const int2 e = dq[k];
-        const int64_t gp = g0 + e.y;
-        if (room) {
-            amb.q[base + k] = Amb64{prob, e.x, gp};
-        } else {
-            const int dec = decide_cell_fp64(cq + e.x, ctrig + e.x, sin_d, cos_d, pr[2 * gp], pr[2 * gp + 1]);
-            if (dec & 1) atomicAdd(&counts[e.x], 1);
-            am += (dec >> 1) & 1;
-            ++here;
-        }
-    }
-    __syncwarp();
-    return here | (am << 8) | ((room ? 0u : 1u) << 16);
-}
 
 template <int CPT, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) vote_simt2_kernel(const VoteItem *__restrict__ items, int n_items,
@@ -253,9 +211,6 @@ __global__ void __launch_bounds__(kThreads, MINB) vote_simt2_kernel(const VoteIt
                                                               int *item_counter, AmbQueue amb) {
     __shared__ __align__(16) float4 sh[2][kPP * 5];
     __shared__ int s_item;
-    __shared__ int2 sdq[kThreads / 32][kSDCap];  // tests staged for the FP64 pass, per warp
-    int2 *dq = sdq[threadIdx.x >> 5];
-    int dfull = 0;  // this warp found the FP64 queue full
     int stride_it = blockIdx.x;
     for (int it = next_item(item_counter, stride_it, &s_item); it < n_items;
          it = next_item(item_counter, stride_it, &s_item)) {
@@ -267,7 +222,6 @@ __global__ void __launch_bounds__(kThreads, MINB) vote_simt2_kernel(const VoteIt
         if (W.cell_begin >= ncell) continue;
         const int cell_end = min(ncell, W.cell_begin + kSimtItemCells);
         for (int sub = W.cell_begin; sub < cell_end; sub += CPT * kThreads) {
-            int dn = 0;  // staged tests of this warp (warp-uniform)
             uint64_t mm[CPT][9], nt[CPT];  // (-R_jk, -R_jk) and (c0, c0)
             float nr[CPT][9], tau[CPT], c0[CPT];
             int cnt[CPT], pos[CPT];
@@ -284,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, MINB) vote_simt2_kernel(const VoteIt
             const int ntiles = (W.pair_end - W.pair_begin) / kTP;
             const int nvalid = (int)min((int64_t)(W.pair_end - W.pair_begin), P.n - W.pair_begin);
             const float4 *src = pool.p2x + (g0 >> 1) * 5;
-            unsigned rechecked = 0, ambiguous = 0, resolved = 0;
+            unsigned rechecked = 0;
             auto load_tile = [&](int buf, int t) {
                 const float4 *gsrc = src + (int64_t)t * kPP * 5;
                 for (int e = threadIdx.x; e < kPP * 5; e += kThreads) cp_async16(&sh[buf][e], gsrc + e);
@@ -357,46 +311,31 @@ __global__ void __launch_bounds__(kThreads, MINB) vote_simt2_kernel(const VoteIt
                             const float tb = __shfl_sync(0xffffffffu, tau[k], src_lane);
                             const int pb = __shfl_sync(0xffffffffu, pos[k], src_lane);
                             int corr = 0;
-                            for (int i0 = 0; i0 < jn; i0 += 32) {  // warp-uniform trip count
-                                const int i = i0 + lane;
-                                bool in_band = false;
-                                if (i < jn) {
-                                    // P_t of pair i at float 20 (i/2) + 4 (t/2) + 2 (t%2) + i%2
-                                    const float *q = Sf + 20 * (i >> 1) + (i & 1);
-                                    float x = fmaf(rb[0], q[0], cb);
-                                    x = fmaf(rb[1], q[2], x);
-                                    x = fmaf(rb[2], q[4], x);
-                                    x = fmaf(rb[3], q[6], x);
-                                    x = fmaf(rb[4], q[8], x);
-                                    x = fmaf(rb[5], q[10], x);
-                                    x = fmaf(rb[6], q[12], x);
-                                    x = fmaf(rb[7], q[14], x);
-                                    x = fmaf(rb[8], q[16], x);
-                                    if (fabsf(x) <= kBandR) {
-                                        const int64_t gp = g0 + (int64_t)t * kTP + i;
-                                        const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
-                                        const float4 R0 = L.cells.R32[3 * pb], R1 = L.cells.R32[3 * pb + 1],
-                                                     R2 = L.cells.R32[3 * pb + 2];
-                                        const float v = recheck_v(R0, R1, R2, p0, p1);
-                                        in_band = fabsf(v - tb) <= kBand64;  // then decided by the FP64 pass
-                                        corr += (in_band ? 0 : (int)(v <= tb)) - (int)(__float_as_uint(x) >> 31);
-                                        ++rechecked;
+                            for (int i = lane; i < jn; i += 32) {
+                                // P_t of pair i at float 20 (i/2) + 4 (t/2) + 2 (t%2) + i%2
+                                const float *q = Sf + 20 * (i >> 1) + (i & 1);
+                                float x = fmaf(rb[0], q[0], cb);
+                                x = fmaf(rb[1], q[2], x);
+                                x = fmaf(rb[2], q[4], x);
+                                x = fmaf(rb[3], q[6], x);
+                                x = fmaf(rb[4], q[8], x);
+                                x = fmaf(rb[5], q[10], x);
+                                x = fmaf(rb[6], q[12], x);
+                                x = fmaf(rb[7], q[14], x);
+                                x = fmaf(rb[8], q[16], x);
+                                if (fabsf(x) <= kBandR) {
+                                    const int64_t gp = g0 + (int64_t)t * kTP + i;
+                                    const float4 p0 = pool.pr[2 * gp], p1 = pool.pr[2 * gp + 1];
+                                    const float4 R0 = L.cells.R32[3 * pb], R1 = L.cells.R32[3 * pb + 1],
+                                                 R2 = L.cells.R32[3 * pb + 2];
+                                    const float v = recheck_v(R0, R1, R2, p0, p1);
+                                    int vote = v <= tb;
+                                    ++rechecked;
+                                    if (fabsf(v - tb) <= kBand64) {  // decided by the FP64 pass
+                                        vote = 0;
+                                        defer_or_flag(amb, L.counts, W.prob, pb, gp);
                                     }
-                                }
-                                const uint32_t bal = __ballot_sync(0xffffffffu, in_band);
-                                if (bal != 0) {
-                                    if (in_band) dq[dn + __popc(bal & ((1u << lane) - 1u))] = make_int2(pb, t * kTP + i);
-                                    dn += __popc(bal);
-                                    __syncwarp();
-                                    if (dn > kSDCap - 32) {
-                                        const unsigned f = simt_defer_flush(dq, dn, amb, dfull, W.prob, g0, L.cells.q,
-                                                                            L.cells.trig, L.counts, P.sin_d, P.cos_d,
-                                                                            pool.pr);
-                                        resolved += f & 0xffu;
-                                        ambiguous += (f >> 8) & 0xffu;
-                                        dfull = (int)(f >> 16);
-                                        dn = 0;
-                                    }
+                                    corr += vote - (int)(__float_as_uint(x) >> 31);
                                 }
                             }
                             corr = __reduce_add_sync(0xffffffffu, corr);
@@ -406,24 +345,11 @@ __global__ void __launch_bounds__(kThreads, MINB) vote_simt2_kernel(const VoteIt
                 }
                 __syncthreads();
             }
-            if (dn > 0) {
-                const unsigned f = simt_defer_flush(dq, dn, amb, dfull, W.prob, g0, L.cells.q, L.cells.trig,
-                                                    L.counts, P.sin_d, P.cos_d, pool.pr);
-                resolved += f & 0xffu;
-                ambiguous += (f >> 8) & 0xffu;
-                dfull = (int)(f >> 16);
-            }
 #pragma unroll
             for (int k = 0; k < CPT; ++k)
                 if (pos[k] < cell_end && cnt[k] != 0) atomicAdd(&L.counts[pos[k]], cnt[k]);
             const unsigned rc = __reduce_add_sync(0xffffffffu, rechecked);
-            const unsigned am = __reduce_add_sync(0xffffffffu, ambiguous);
-            const unsigned rs = __reduce_add_sync(0xffffffffu, resolved);
-            if ((threadIdx.x & 31) == 0) {
-                if (rc) atomicAdd(&stats[W.prob].rechecked, (unsigned long long)rc);
-                if (am) atomicAdd(&stats[W.prob].ambiguous, (unsigned long long)am);
-                if (rs) atomicAdd(&stats[W.prob].resolved, (unsigned long long)rs);
-            }
+            if ((threadIdx.x & 31) == 0 && rc) atomicAdd(&stats[W.prob].rechecked, (unsigned long long)rc);
         }
     }
 }

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kSmallThreads) vote_small_kernel(const ProbRef
     const int64_t g = P.pool_off + i;
     const float4 s0 = pool.p32[3 * g], s1 = pool.p32[3 * g + 1], s2 = pool.p32[3 * g + 2];
     const int lane = threadIdx.x & 31;
-    unsigned rechecked = 0, ambiguous = 0, resolved = 0;
+    unsigned rechecked = 0;
     for (int c = 0; c < nc; ++c) {
         const float4 m0 = sm[3 * c], m1 = sm[3 * c + 1], m2 = sm[3 * c + 2];
         const float tau = m2.z;
@@ -69,11 +69,9 @@ __global__ void __launch_bounds__(kSmallThreads) vote_small_kernel(const ProbRef
             const float4 R0 = L.cells.R32[3 * c], R1 = L.cells.R32[3 * c + 1], R2 = L.cells.R32[3 * c + 2];
             const float4 p0 = pool.pr[2 * g], p1 = pool.pr[2 * g + 1];
             const float v = recheck_v(R0, R1, R2, p0, p1);
-            const int dec = decide_or_defer(v, tau, L, c, P, tl.x, g, p0, p1, amb);
+            const int dec = decide_or_defer(v, tau, L, c, tl.x, g, amb);
             vote = dec & 1;
             ++rechecked;
-            ambiguous += (dec >> 1) & 1;
-            resolved += (dec >> 2) & 1;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, vote);
         if (lane == 0 && bal) atomicAdd(&scnt[c], __popc(bal));
@@ -82,13 +80,7 @@ __global__ void __launch_bounds__(kSmallThreads) vote_small_kernel(const ProbRef
     for (int c = threadIdx.x; c < nc; c += kSmallThreads)
         if (scnt[c]) atomicAdd(&L.counts[c], scnt[c]);
     const unsigned rc = __reduce_add_sync(0xffffffffu, rechecked);
-    const unsigned am = __reduce_add_sync(0xffffffffu, ambiguous);
-    const unsigned rs = __reduce_add_sync(0xffffffffu, resolved);
-    if (lane == 0) {
-        if (rc) atomicAdd(&stats[tl.x].rechecked, (unsigned long long)rc);
-        if (am) atomicAdd(&stats[tl.x].ambiguous, (unsigned long long)am);
-        if (rs) atomicAdd(&stats[tl.x].resolved, (unsigned long long)rs);
-    }
+    if (lane == 0 && rc) atomicAdd(&stats[tl.x].rechecked, (unsigned long long)rc);
 }
 
 }  // namespace

@@ -71,7 +71,7 @@ constexpr size_t kQueueBytes = (size_t)4 * kMaxG * kQCap * 8;
 constexpr size_t kRowBytes = (size_t)kMaxG * 128 * 12 * 4;
 constexpr size_t kCorrBytes = (size_t)kMaxG * 128 * 4;
 constexpr int kDCap = 64;
-constexpr size_t kDeferBytes = (size_t)4 * kMaxG * kDCap * 8;
+constexpr size_t kDeferBytes = (size_t)4 * kMaxG * (kDCap * 8 + 16);  // entries + count + queue-full flag
 constexpr size_t kBarBytes = 1024;
 // 1024 B alignment slack + A (2 stages) + B (kNB stages) + barriers/flags + re-check state.
 // Over 116 KB, so one CTA per SM (each holds all 512 TMEM columns).
@@ -515,8 +515,12 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
         const int q = warp & 3;               // TMEM lane quarter this warp may access
         const int row = 32 * q + lane;        // cell row of this thread
         uint2 *qw = q_all + (size_t)(warp - 4) * kQCap;  // this warp's re-check queue
-        uint2 *dw = d_all + (size_t)(warp - 4) * kDCap;  // this warp's FP64 staging
-        bool amb_full = false;  // this warp found the FP64 queue full: decide in place from now on
+        // this warp's FP64 staging: kDCap entries, then its count and queue-full flag (in shared
+        // memory, so the cold path holds no register across the drain loop)
+        uint2 *const dw = d_all + (size_t)(warp - 4) * (kDCap + 2);
+        int *const dstate = reinterpret_cast<int *>(dw + kDCap);
+        if (lane == 0) dstate[0] = dstate[1] = 0;
+        __syncwarp();
         float *rows = rows_all + (size_t)g * 128 * 12;   // this warpgroup's row table
         int *corr = corr_all + g * 128;
         int64_t j = 0;
@@ -538,7 +542,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 band = fmaxf(cell_band<KSTEPS, BF16>(m), band_req);
             }
             int cnt = 0;
-            unsigned rechecked = 0, ambiguous = 0, resolved = 0;
+            unsigned rechecked = 0;
             {  // the cell's rotation and threshold, for re-checks of this row by any lane of the warp
                 float4 R0 = make_float4(0, 0, 0, 0), R1 = R0, R2 = R0;
                 if (valid) {
@@ -554,33 +558,31 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
             }
             __syncwarp();
             int qn = 0;  // entries in this warp's queue (warp-uniform)
-            int dn = 0;  // entries in this warp's FP64 staging (warp-uniform)
             const int64_t gbase = v.P.pool_off + v.W.pair_begin;
-            const uint32_t lt = (1u << lane) - 1u;
             // hands the staged tests to the FP64 pass with one atomic for the warp; when the
-            // queue is full, decides them here in FP64, one test per lane
+            // queue is full, flags their cells for the pass's recount instead
             auto defer_flush = [&]() {
+                const int dn = dstate[0];
                 int base = 0;
-                if (lane == 0) base = amb_full ? amb.cap : atomicAdd(amb.count, dn);
+                if (lane == 0) base = (dstate[1] || __ldcg(amb.ovf)) ? amb.cap : atomicAdd(amb.count, dn);
                 base = __shfl_sync(0xffffffffu, base, 0);
                 const bool room = base <= amb.cap - dn;
-                amb_full = !room;
+                __syncwarp();
+                if (lane == 0) {
+                    dstate[0] = 0;
+                    dstate[1] = room ? 0 : 1;
+                }
                 for (int k = lane; k < dn; k += 32) {
                     const uint2 e = dw[k];
                     const int cpos = __float_as_int(rows[e.y * 12 + 10]);
-                    const int64_t gp = gbase + (int64_t)e.x;
                     if (room) {
-                        amb.q[base + k] = Amb64{v.W.prob, cpos, gp};
+                        amb.q[base + k] = Amb64{v.W.prob, cpos, gbase + (int64_t)e.x};
                     } else {
-                        const int dec = decide_cell_fp64(v.L.cells.q + cpos, v.L.cells.trig + cpos, v.P.sin_d,
-                                                         v.P.cos_d, pool.pr[2 * gp], pool.pr[2 * gp + 1]);
-                        atomicAdd(&corr[e.y], dec & 1);
-                        ambiguous += (dec >> 1) & 1;
-                        ++resolved;
+                        atomicOr(&v.L.counts[cpos], kOvfBit);
+                        *amb.ovf = 1;
                     }
                 }
                 __syncwarp();
-                dn = 0;
             };
             // drains the re-check queue: one entry per lane, loads issued in parallel; the
             // tests within kBand64 of tau are staged for the FP64 pass (their sign-bit vote
@@ -606,10 +608,12 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     }
                     const uint32_t bal = __ballot_sync(0xffffffffu, in_band);
                     if (bal != 0) {
-                        if (in_band) dw[dn + __popc(bal & lt)] = make_uint2(poff, rrow);
-                        dn += __popc(bal);
+                        const int dn = dstate[0];
+                        if (in_band) dw[dn + __popc(bal & ((1u << lane) - 1u))] = make_uint2(poff, rrow);
                         __syncwarp();
-                        if (dn > kDCap - 32) defer_flush();
+                        if (lane == 0) dstate[0] = dn + __popc(bal);
+                        __syncwarp();
+                        if (dn + __popc(bal) > kDCap - 32) defer_flush();
                     }
                 }
                 __syncwarp();
@@ -652,7 +656,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     if (has) {
                         const int e = __ffs((int)fm) - 1;
                         fm &= fm - 1;
-                        qw[qn + __popc(bal & lt)] =
+                        qw[qn + __popc(bal & ((1u << lane) - 1u))] =
                             make_uint2((uint32_t)(poff + e), (uint32_t)lane | (((sm >> e) & 1u) << 5));
                     }
                     qn += __popc(bal);
@@ -707,17 +711,11 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 if (lane == 0) mbar_arrive(&acc_empty[stage]);
             }
             if (qn > 0) flush();
-            if (dn > 0) defer_flush();
+            if (dstate[0] > 0) defer_flush();
             cnt += corr[row];
             if (valid && cnt != 0) atomicAdd(&v.L.counts[pos], cnt);
             const unsigned rc = __reduce_add_sync(0xffffffffu, rechecked);
-            const unsigned am = __reduce_add_sync(0xffffffffu, ambiguous);
-            const unsigned rs = __reduce_add_sync(0xffffffffu, resolved);
-            if (lane == 0) {
-                if (rc) atomicAdd(&stats[v.W.prob].rechecked, (unsigned long long)rc);
-                if (am) atomicAdd(&stats[v.W.prob].ambiguous, (unsigned long long)am);
-                if (rs) atomicAdd(&stats[v.W.prob].resolved, (unsigned long long)rs);
-            }
+            if (lane == 0 && rc) atomicAdd(&stats[v.W.prob].rechecked, (unsigned long long)rc);
         }
     }
 

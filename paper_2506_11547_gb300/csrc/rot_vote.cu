@@ -292,7 +292,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     const size_t o_nkept = reserve(sizeof(int32_t) * (size_t)P * S);
     const size_t o_err = reserve(sizeof(int) * 4);
     const size_t o_ictr = reserve(sizeof(int) * (size_t)S);  // per-level work-item counters (CUDA-core vote)
-    const size_t o_ambcnt = reserve(sizeof(int) * (size_t)S);  // per-level FP64-queue lengths
+    const size_t o_ambcnt = reserve(sizeof(int) * 2 * (size_t)S);  // per level: FP64-queue length, full flag
     const size_t z1 = align_up(off, 256);
     // FP64 resolution queue: room for 8e-6 of the largest level's tests (uniform outliers put
     // 4e-6 of them within the band) + 64k; a full queue makes the vote decide the rest itself
@@ -303,6 +303,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     }
     lev_tests = std::max<int64_t>(tests_l0, pairs_all * (int64_t)child_cap);
     pl.amb_cap = (int)std::min<int64_t>((int64_t)1 << 25, (int64_t)(8e-6 * (double)lev_tests) + 65536);
+    if (test_amb_cap >= 0) pl.amb_cap = test_amb_cap;
     const size_t o_amb = reserve(sizeof(Amb64) * (size_t)pl.amb_cap);
     const size_t o_kept = reserve(sizeof(int32_t) * (size_t)P * S * K);
     const size_t o_cand = reserve(sizeof(Cand) * ((size_t)P * pl.chunks_per_prob * K + (size_t)P * K));
@@ -546,7 +547,7 @@ int Context::enqueue_pipeline(Wave &w) {
             e = launch_vote_small(pl.d_probs, pl.d_tiles, (int)pl.tiles_h.size(), pl.d_lref, S, lev, pl.pool,
                                   pl.d_stats, pl.amb(lev), w.stream);
         if (e == cudaSuccess)
-            e = launch_resolve64(pl.amb(lev), pl.d_probs, pl.d_lref, S, lev, pl.pool, pl.d_stats, 4 * sm_count,
+            e = launch_resolve64(pl.amb(lev), pl.d_probs, P, pl.d_lref, S, lev, pl.pool, pl.d_stats, 4 * sm_count,
                                  w.stream);
         done();
         mark(2, lev, lev == 0 ? 2 : 1);

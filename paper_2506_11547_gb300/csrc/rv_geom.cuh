@@ -295,50 +295,30 @@ __device__ __forceinline__ int decide_fp64(const double4_32a &q, double tau64, c
     return (v <= tau64 ? 1 : 0) | (fabs(dsub(v, tau64)) <= kAmbig64 ? 2 : 0);
 }
 
-// The FP64 decision of one test of a level-table cell (its centre qc and
-// (cos r, sin r) trig; the pair's re-check record p0, p1), kept out of line so
-// that the vote kernels' registers do not see it.
-static __device__ __noinline__ int decide_cell_fp64(const double4_32a *qc, const double2 *trig, double sin_d,
-                                                    double cos_d, float4 p0, float4 p1) {
-    return decide_fp64(*qc, tau_cs(sin_d, cos_d, *trig), p0, p1);
+// Hands one test whose FP32 re-check lies within kBand64 of its threshold to
+// the FP64 resolution pass: appends it to the level's queue, or, once the queue
+// is full, flags its cell (kOvfBit in its count) so that the pass recounts the
+// whole cell.  A full queue takes no further atomics, so its counter stays
+// within a few thousand of cap.  The caller counts no vote for the test.
+__device__ __forceinline__ void defer_or_flag(const AmbQueue &Q, int32_t *counts, int prob, int pos, int64_t gp) {
+    if (!__ldcg(Q.ovf)) {
+        const unsigned slot = (unsigned)atomicAdd(Q.count, 1);
+        if (slot < (unsigned)Q.cap) {
+            Q.q[slot] = Amb64{prob, pos, gp};
+            return;
+        }
+    }
+    atomicOr(&counts[pos], kOvfBit);
+    *Q.ovf = 1;
 }
 
-// Appends one in-band test to the FP64 resolution queue; the lanes of a warp
-// that call it together share one atomic.  Returns false -- the caller then
-// decides the test itself -- when there is no queue or it is full (a full
-// queue takes no further atomics, so its counter never runs far past cap).
-__device__ __forceinline__ bool defer64(const AmbQueue &Q, int prob, int pos, int64_t gp) {
-    if (Q.q == nullptr || *(volatile int *)Q.count >= Q.cap) return false;
-    const unsigned act = __activemask();
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(act) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(Q.count, __popc(act));
-    base = __shfl_sync(act, base, leader);
-    const int slot = base + __popc(act & ((1u << lane) - 1u));
-    if (slot >= Q.cap) return false;
-    Q.q[slot] = Amb64{prob, pos, gp};
-    return true;
-}
-
-// The decision of one re-checked test of a level-table cell: bit 0 vote, bit 1
-// ambiguous, bit 2 set when the FP64 evaluation decided it.  The cell's FP64
-// centre qc and (cos r, sin r) trig are read only inside the band, where the
-// threshold is rebuilt in FP64 from them (tau_cs, the table's own operations).
-__device__ __forceinline__ int decide_test(float v32, float tau32, const double4_32a *qc, const double2 *trig,
-                                           double sin_d, double cos_d, const float4 &p0, const float4 &p1) {
+// The decision of one re-checked test of a level-table cell: 1 vote, 0 no
+// vote, 8 handed to the FP64 pass (no vote counted here).
+__device__ __forceinline__ int decide_or_defer(float v32, float tau32, const LevelRef &L, int pos, int prob,
+                                               int64_t gp, const AmbQueue &Q) {
     if (!(fabsf(v32 - tau32) <= kBand64)) return v32 <= tau32 ? 1 : 0;
-    return 4 | decide_fp64(*qc, tau_cs(sin_d, cos_d, *trig), p0, p1);
-}
-
-// The same decision, with an in-band test deferred to the FP64 pass when the
-// queue takes it: then the result is 8 (no vote counted here).
-__device__ __forceinline__ int decide_or_defer(float v32, float tau32, const LevelRef &L, int pos, const ProbRef &P,
-                                               int prob, int64_t gp, const float4 &p0, const float4 &p1,
-                                               const AmbQueue &Q) {
-    if (!(fabsf(v32 - tau32) <= kBand64)) return v32 <= tau32 ? 1 : 0;
-    if (defer64(Q, prob, pos, gp)) return 8;
-    return 4 | decide_cell_fp64(L.cells.q + pos, L.cells.trig + pos, P.sin_d, P.cos_d, p0, p1);
+    defer_or_flag(Q, L.counts, prob, pos, gp);
+    return 8;
 }
 
 }  // namespace rv

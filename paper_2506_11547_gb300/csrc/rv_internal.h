@@ -114,9 +114,15 @@ struct Amb64 {
 struct AmbQueue {
     Amb64 *q = nullptr;
     int *count = nullptr;  // zeroed before the level's vote
+    int *ovf = nullptr;    // set when a test found the queue full (zeroed before the vote)
     int cap = 0;
     int pad = 0;
 };
+
+// Set in a cell's count when one of its tests found the FP64 queue full: the
+// resolution pass then recounts that cell from all of its pairs.  Counts stay
+// below 2^30 (problems hold fewer than 2^30 pairs).
+constexpr int32_t kOvfBit = 1 << 30;
 
 // ---- launchers (each returns cudaGetLastError() of its launch) ----
 
@@ -173,10 +179,12 @@ cudaError_t launch_vote_small(const ProbRef *probs, const int2 *tiles, int ntile
 
 // The FP64 resolution pass of one level's deferred tests (after its vote): each
 // test decided by the FP64 evaluation, its vote added to the cell's count, the
-// problem's ambiguous and resolved statistics updated.  grid_blocks blocks
-// stride over the queue (its length is read on the device).
-cudaError_t launch_resolve64(AmbQueue amb, const ProbRef *probs, const LevelRef *lref, int level_stride, int level,
-                             PairPool pool, ProbStats *stats, int grid_blocks, cudaStream_t s);
+// problem's ambiguous and resolved statistics updated; cells flagged with
+// kOvfBit (the queue was full) recounted from all of their pairs.
+// grid_blocks blocks stride over the queue (its length is read on the device)
+// and over the nprob problems' cells of the level.
+cudaError_t launch_resolve64(AmbQueue amb, const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride,
+                             int level, PairPool pool, ProbStats *stats, int grid_blocks, cudaStream_t s);
 
 // Fit state of a large problem between its passes.
 struct FitState {

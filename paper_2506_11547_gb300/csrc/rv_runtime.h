@@ -69,12 +69,13 @@ struct Plan {
     int *d_err = nullptr;
     int *d_ictr = nullptr;  // per-level work-item counters of the CUDA-core vote (zeroed per solve)
     Amb64 *d_amb = nullptr; // tests deferred to the FP64 resolution pass (reused level after level)
-    int *d_ambcnt = nullptr;  // per-level queue lengths (zeroed per solve)
+    int *d_ambcnt = nullptr;  // per level: queue length, then queue-full flag (zeroed per solve)
     int amb_cap = 0;
     AmbQueue amb(int lev) const {
         AmbQueue q;
         q.q = d_amb;
-        q.count = d_ambcnt + lev;
+        q.count = d_ambcnt + 2 * lev;
+        q.ovf = d_ambcnt + 2 * lev + 1;
         q.cap = amb_cap;
         return q;
     }
@@ -132,6 +133,8 @@ class Context {
     int test_fail_alloc = 0;  // fault injection: the k-th workspace allocation fails (ROT_VOTE_TEST_FAIL_ALLOC=k)
     int test_stall = 0;       // fault injection: in the next k solves the tensor-core copies never arrive and
                               // device waits are bounded by 1 ms (ROT_VOTE_TEST_STALL=k)
+    int test_amb_cap = -1;    // test hook: the FP64 queue holds k tests (ROT_VOTE_TEST_AMB_CAP=k), so that
+                              // the recount of the cells it could not take is exercised
     // per-kernel profiling (keep_trace == 2)
     std::vector<cudaEvent_t> prof_ev;
     std::vector<rot_vote_stage> prof;

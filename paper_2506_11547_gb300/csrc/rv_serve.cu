@@ -58,6 +58,7 @@ int Context::init(const rot_vote_config &c) {
     // fault-injection hooks for the failure tests (never set in normal use)
     if (const char *e = getenv("ROT_VOTE_TEST_FAIL_ALLOC")) test_fail_alloc = atoi(e);
     if (const char *e = getenv("ROT_VOTE_TEST_STALL")) test_stall = atoi(e);
+    if (const char *e = getenv("ROT_VOTE_TEST_AMB_CAP")) test_amb_cap = atoi(e);
     return ROT_VOTE_OK;
 }
 

@@ -2,12 +2,12 @@
 // cell list with every scratch buffer in one file-scope static device array,
 // so the call allocates no device memory.
 //
-// The call runs three launches on the caller's stream: a set-up kernel (header,
-// work lists, cell table, counts zeroed), the pair step (launch_pair_prep) and
-// the CUDA-core FP32 vote (launch_vote_simt), the same two kernels a solve
-// runs, here with their pair pool, cell table and work lists in the static
-// array.  It then reads back two flags (invalid pairs, invalid cells) and
-// returns.
+// The call runs four launches on the caller's stream: a set-up kernel (header,
+// work lists, cell table, counts zeroed), the pair step (launch_pair_prep), the
+// CUDA-core FP32 vote (launch_vote_simt) and its FP64 resolution pass
+// (launch_resolve64), the kernels a solve runs, here with their pair pool, cell
+// table, work lists and FP64 queue in the static array.  It then reads back two
+// flags (invalid pairs, invalid cells) and returns.
 #include <mutex>
 
 #include "rv_geom.cuh"
@@ -31,7 +31,7 @@ constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kOffProb = 0;
 constexpr size_t kOffLevel = 256;
 constexpr size_t kOffStats = 512;
-constexpr size_t kOffFlags = 768;  // int32 ncells, int32 bad_cell
+constexpr size_t kOffFlags = 768;  // int32 ncells, bad_cell, FP64-queue length, queue-full flag
 constexpr size_t kOffTiles = 1024;
 constexpr size_t kOffItems = al256(kOffTiles + sizeof(int2) * kStaticMaxTiles);
 constexpr size_t kOffS32 = al256(kOffItems + sizeof(VoteItem) * kStaticMaxItems);
@@ -42,7 +42,9 @@ constexpr size_t kOffTrig = al256(kOffChord + sizeof(double) * kStaticMaxCells);
 constexpr size_t kOffIdx = al256(kOffTrig + sizeof(double2) * kStaticMaxCells);
 constexpr size_t kOffM32 = al256(kOffIdx + sizeof(int64_t) * kStaticMaxCells);
 constexpr size_t kOffR32 = al256(kOffM32 + sizeof(float4) * 3 * kStaticMaxCells);
-constexpr size_t kOffEnd = al256(kOffR32 + sizeof(float4) * 3 * kStaticMaxCells);
+constexpr int kStaticAmbCap = 8192;  // tests within 2e-6 of the threshold (about 1100 expected at the limits)
+constexpr size_t kOffAmb = al256(kOffR32 + sizeof(float4) * 3 * kStaticMaxCells);
+constexpr size_t kOffEnd = al256(kOffAmb + sizeof(Amb64) * kStaticAmbCap);
 static_assert(sizeof(ProbRef) <= 256 && sizeof(LevelRef) <= 256 && sizeof(ProbStats) <= 256, "header slots");
 static_assert(kOffEnd <= (size_t)ROT_VOTE_STATIC_SCRATCH_BYTES, "static scratch layout exceeds its size");
 
@@ -216,7 +218,7 @@ extern "C" int rot_vote_count_cells_static(const float *a, const float *b, int64
     A.sin_d = sin((double)df);
     A.cos_d = cos((double)df);
 
-    cudaError_t e = cudaMemsetAsync(base + kOffFlags + sizeof(int32_t), 0, sizeof(int32_t), s);
+    cudaError_t e = cudaMemsetAsync(base + kOffFlags + sizeof(int32_t), 0, 3 * sizeof(int32_t), s);
     const int threads = 256;
     const int blocks = (ncells + threads - 1) / threads;
     if (e == cudaSuccess) {
@@ -234,9 +236,15 @@ extern "C" int rot_vote_count_cells_static(const float *a, const float *b, int64
     if (e == cudaSuccess)
         e = launch_pair_prep(probs, reinterpret_cast<const int2 *>(base + kOffTiles), A.ntiles, pool, ROT_PREC_FP32,
                              stats, s);
+    AmbQueue amb;
+    amb.q = reinterpret_cast<Amb64 *>(base + kOffAmb);
+    amb.count = reinterpret_cast<int *>(base + kOffFlags) + 2;
+    amb.ovf = reinterpret_cast<int *>(base + kOffFlags) + 3;
+    amb.cap = kStaticAmbCap;
     if (e == cudaSuccess)
         e = launch_vote_simt(reinterpret_cast<const VoteItem *>(base + kOffItems), A.nitems, probs, lref, 1, 0, pool,
-                             stats, 4, A.nitems, nullptr, AmbQueue{}, s);
+                             stats, 4, A.nitems, nullptr, amb, s);
+    if (e == cudaSuccess) e = launch_resolve64(amb, probs, 1, lref, 1, 0, pool, stats, 2 * kStaticMaxCells / 256, s);
     // header slots back to the host: ProbStats.invalid and the bad-cell flag
     unsigned char hdr[1024];
     if (e == cudaSuccess) e = cudaMemcpyAsync(hdr, base, sizeof hdr, cudaMemcpyDeviceToHost, s);

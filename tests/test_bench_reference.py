@@ -59,3 +59,17 @@ def test_clock_summary_reports_median_clock_and_active_reasons():
     cs.lines = ["1500, 2070, 1000.0, 0x8, Active, Not Active, Active, Not Active"]
     cs.skip = 0
     assert cs.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_serving_span_overlap_summary():
+    """The serving overlap record: mean batches in flight over the busy time and the
+    share of it with two or more batches in flight, from device-time spans."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod2", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    o = bench.span_overlap([(0.0, 10.0, 0, 2), (5.0, 12.0, 1, 3), (20.0, 25.0, 0, 1)])
+    assert o["batches"] == 3 and o["waves_used"] == 2 and o["mean_batch_problems"] == 2.0
+    assert abs(o["mean_in_flight"] - 22.0 / 17.0) < 1e-12
+    assert abs(o["share_two_or_more"] - 5.0 / 17.0) < 1e-12
+    assert bench.span_overlap([]) is None

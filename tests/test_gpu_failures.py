@@ -86,3 +86,19 @@ def test_ten_repeated_runs_are_bitwise_equal(prec):
             tr = [ctx.level_trace(0, lev) for lev in range(3)]
             for a, b in zip(tr0, tr):
                 assert all(np.array_equal(u, v) for u, v in zip(a, b))
+
+
+@pytest.mark.parametrize("cap", ["0", "16"])
+def test_full_fp64_queue_recounts_exactly(cap, monkeypatch):
+    """Host hook ROT_VOTE_TEST_AMB_CAP shrinks the FP64 resolution queue (0 or 16
+    tests), so the tests near the threshold that it cannot take flag their cells
+    and the resolution pass recounts those cells from all pairs.  Counts, kept
+    cells, ambiguous totals and the rotation must still equal the oracle's, in
+    the FP32 and the tensor-core forms."""
+    from tests.test_gpu_parity import assert_parity, run_both
+    monkeypatch.setenv("ROT_VOTE_TEST_AMB_CAP", cap)
+    p = synth.make_problem(20000, rho=0.9, sigma=0.01, delta=0.03, seed=41)
+    for prec in ("fp32", "fp16x2", "bf16"):
+        r, tr, o = run_both(p, 16, 2, precision=prec)
+        assert_parity(p, r, tr, o, 2)
+        assert r.resolved > 0

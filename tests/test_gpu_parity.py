@@ -283,3 +283,27 @@ def test_delta_extremes(delta):
     assert_parity(p, r, tr, o, 1)
     if delta == 1.5:
         assert all(int(c.min()) == p.n for _, c, _ in tr[:1])
+
+
+def test_batched_workload_4096_problems_sample_equals_oracle():
+    """The benchmark's batched workload at full scale: 4096 independent problems
+    (N log-uniform in [50, 2e4], outliers U[0.5, 0.95], noise U[0.001, 0.02],
+    delta = 3 sigma; 32^3 + 2 levels) in one call, FP16 hi/lo form.  A seeded
+    sample of 64 problems, including the smallest and the largest, must equal
+    the oracle's solve: the winning cell and its count, the ambiguous tests, the
+    tests, the inliers and the status; the rotation within 1e-4 rad."""
+    import oracle
+    probs = synth.batched_problems(4096)
+    args = [(dev(p.a), dev(p.b), p.delta) for p in probs]
+    with rv.Context(grid_n=32, levels=2, precision="fp16x2") as ctx:
+        res = ctx.solve(args)
+    ns = np.array([p.n for p in probs])
+    rng = np.random.default_rng(4096)
+    pick = set(rng.choice(len(probs), 62, replace=False).tolist()) | {int(ns.argmin()), int(ns.argmax())}
+    for k in sorted(pick):
+        p, r = probs[k], res[k]
+        o = oracle.solve(p.a, p.b, f32(p.delta), grid_n=32, levels=2, nthreads=NTHREADS, trace=False)
+        assert r.status == o.status, k
+        assert (r.best_cell, r.best_count, r.ambiguous, r.tests, r.inliers) == \
+               (o.best_cell, o.best_count, o.ambiguous, o.tests, o.inliers), k
+        assert quat_angle(r.q, o.q) < ROT_TOL, k

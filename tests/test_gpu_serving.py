@@ -159,15 +159,20 @@ def test_serving_admits_a_large_problem_under_a_small_memory_budget():
 
 
 def test_serving_spans_show_overlapping_waves():
-    """The batch spans of a burst: one per completed batch, with device start <=
-    end; batches admitted on different waves while others run are in flight at
-    the same time (their spans intersect)."""
+    """The batch spans of a stream: one per completed batch, with device start <=
+    end.  Requests arrive two at a time while earlier batches run, so they are
+    admitted onto other waves and are in flight at the same time (their spans
+    intersect).  (A burst submitted at once is one batch on one wave.)"""
     rng = np.random.default_rng(13)
-    ns = np.exp(rng.uniform(np.log(2000), np.log(30000), size=32)).astype(int)
+    ns = np.exp(rng.uniform(np.log(20000), np.log(60000), size=32)).astype(int)
     probs = [synth.make_problem(int(n), rho=0.9, sigma=0.01, delta=0.03, seed=900 + k) for k, n in enumerate(ns)]
     args = [(_dev(p.a), _dev(p.b), p.delta) for p in probs]
-    with rv.Context(grid_n=32, levels=2, precision="fp32", max_inflight=4) as ctx:
-        tickets = [ctx.submit(*x) for x in args]
+    with rv.Context(grid_n=32, levels=2, precision="fp32", max_inflight=64) as ctx:
+        ctx.solve([args[0]])  # tuning and the coarse table before the stream
+        tickets = []
+        for k in range(0, len(args), 2):
+            tickets += [ctx.submit(*x) for x in args[k:k + 2]]
+            time.sleep(0.0005)
         _drain(ctx, tickets)
         spans = ctx.serve_spans()
     assert sum(s[3] for s in spans) == len(args)

@@ -30,7 +30,7 @@ def _solve_level0(p, grid_n):
     with rv.Context(grid_n=grid_n, levels=0, precision="fp32", keep_trace=1) as ctx:
         r = ctx.solve([(_dev(p.a), _dev(p.b), p.delta)])[0]
         idx, cnt, _ = ctx.level_trace(0, 0)
-    assert r.status == rv.OK
+    assert r.status in (rv.OK, rv.EDEGENERATE)  # identical pairs make the fit degenerate
     return idx, cnt
 
 
@@ -41,12 +41,37 @@ def _static_counts(p, grid_n, idx):
     return rc, counts.cpu().numpy()
 
 
+def _at_threshold(n, grid_n, delta, seed):
+    """n copies of one pair whose test against one cell of the grid_n level lies on that
+    cell's threshold (q_c^T S q_c = tau_c up to float32 rounding): b is R(q_c) a turned by
+    2 asin(sqrt(tau_c)) about an axis normal to it.  All n tests of that cell fall within the
+    FP64 band, more than the entry point's FP64 queue holds, so the resolution pass must
+    recount the cell.  The cell's centre and threshold come from the oracle."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    cells = oracle.level_cells(grid_n)
+    idx = int(cells[len(cells) // 3])
+    ix, iy, iz = idx % grid_n, (idx // grid_n) % grid_n, idx // (grid_n * grid_n)
+    q, chord = oracle.cell_geom(grid_n, ix, iy, iz)
+    tau = oracle.tau(f32(delta), chord)
+    a = rng.standard_normal(3)
+    a /= np.linalg.norm(a)
+    ra = oracle.quat_to_R(q) @ a
+    axis = np.cross(ra, rng.standard_normal(3))
+    b = synth.rodrigues(axis, 2.0 * np.arcsin(np.sqrt(tau))) @ ra
+    pr = synth.make_problem(n, rho=0.0, sigma=0.0, delta=delta, seed=seed)
+    pr.a[:] = np.float32(a)
+    pr.b[:] = np.float32(b / np.linalg.norm(b))
+    return pr
+
+
 def test_static_counts_equal_solve_counts_call_after_call():
     cases = [
         (synth.make_problem(5000, rho=0.9, sigma=0.01, delta=0.03, seed=901), 16, None),
         (synth.make_problem(rv.STATIC_MAX_PAIRS, rho=0.5, sigma=0.01, delta=0.05, seed=902), 16, None),
         (synth.make_problem(3001, rho=0.8, sigma=0.01, delta=0.02, seed=903), 32, rv.STATIC_MAX_CELLS),
         (synth.make_problem(129, rho=0.3, sigma=0.01, delta=0.04, seed=904), 8, None),
+        (_at_threshold(rv.STATIC_MAX_PAIRS, 32, 0.05, seed=908), 32, rv.STATIC_MAX_CELLS),
     ]
     import oracle
     for p, g, keep in cases:

@@ -27,14 +27,14 @@
 //               [g U/G, (g+1) U/G) of every unit in turn, so each has all
 //               stages in flight; each thread owns one TMEM lane = one cell and
 //               reads 16 or 32 columns per tcgen05.ld, double-buffered so the
-//               next load is in flight while it counts the current one: sign
+//               next load is in flight while it counts the current one (and
+//               releases the stage as soon as its last load has completed): sign
 //               bits two per byte permute and the minimum of |D| two values per
-//               three-input minimum, with no warp vote per chunk.  Once per unit
-//               the warp votes on its chunks holding a value within the band
-//               (rare), reloads those from the stage it still holds and queues
-//               their tests in a per-warp shared-memory queue that is drained
-//               32 at a time (one lane per test), so no warp waits on one
-//               global load per flagged test.
+//               three-input minimum.  One warp vote per chunk: when a lane's
+//               chunk holds a value within the band (rare), the warp queues
+//               those tests from the registers it still holds into a per-warp
+//               shared-memory queue that is drained 32 at a time (one lane per
+//               test), so no warp waits on one global load per flagged test.
 // The autotuner picks U, G and the chunk width per workload.
 // Every mbarrier wait is bounded (2 s or 2^24 polls): on expiry the CTA sets
 // *err_flag, stops all roles, waits (bounded) for its own copies and MMAs,
@@ -620,23 +620,24 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 qn = 0;
             };
             // counts the CH values of one chunk: sign bits (D < 0) two per byte
-            // permute, summed two words per add; returns whether the chunk holds a
-            // value within the band (minimum of |D|, two values per three-input
-            // minimum).  No warp vote here, so consecutive chunks overlap.
+            // permute, added two words per add to tsum, which is decoded once per
+            // two chunks (at most 64 values, within the 126 sign_count allows);
+            // returns whether the chunk holds a value within the band (one chain
+            // of three-input minima of |D|, two values each).
+            uint32_t tsum = 0;
             auto chunk_count = [&](const uint32_t(&r)[CH]) -> uint32_t {
-                uint32_t t0 = 0, t1 = 0;
-                float m0 = 4.f, m1 = 4.f, m2 = 4.f, m3 = 4.f;  // min |D| (|D| <= 4)
+                float m = 4.f;  // min |D| (|D| <= 4)
 #pragma unroll
-                for (int e = 0; e < CH; e += 8) {
-                    t0 = t0 + sign_bytes2(r[e], r[e + 1]) + sign_bytes2(r[e + 2], r[e + 3]);
-                    t1 = t1 + sign_bytes2(r[e + 4], r[e + 5]) + sign_bytes2(r[e + 6], r[e + 7]);
-                    m0 = min3_abs(m0, __uint_as_float(r[e]), __uint_as_float(r[e + 1]));
-                    m1 = min3_abs(m1, __uint_as_float(r[e + 2]), __uint_as_float(r[e + 3]));
-                    m2 = min3_abs(m2, __uint_as_float(r[e + 4]), __uint_as_float(r[e + 5]));
-                    m3 = min3_abs(m3, __uint_as_float(r[e + 6]), __uint_as_float(r[e + 7]));
+                for (int e = 0; e < CH; e += 4) {
+                    tsum = tsum + sign_bytes2(r[e], r[e + 1]) + sign_bytes2(r[e + 2], r[e + 3]);
+                    m = min3_abs(m, __uint_as_float(r[e]), __uint_as_float(r[e + 1]));
+                    m = min3_abs(m, __uint_as_float(r[e + 2]), __uint_as_float(r[e + 3]));
                 }
-                cnt += sign_count(t0 + t1);
-                return fminf(fminf(m0, m1), fminf(m2, m3)) <= band ? 1u : 0u;
+                return m <= band ? 1u : 0u;
+            };
+            auto decode = [&]() {
+                cnt += sign_count(tsum);
+                tsum = 0;
             };
             // queues the tests within the band of one chunk (pair offset poff in
             // the item) for the FP32 re-check; hit: this lane's chunk holds one
@@ -681,34 +682,37 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 // CH-column chunks, double-buffered: the load of the next chunk is in
                 // flight while this one is counted
                 uint32_t ra[CH], rb[CH];
-                uint32_t hm = 0;  // bit c: this lane's chunk c holds a value within the band
                 tmem_ld(taddr, ra);
                 tmem_ld_wait(ra);
+                // the stage is released once this warp's last load of it has completed
+                auto release = [&]() {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[stage]);
+                };
                 if constexpr (kCols == CH) {
-                    hm = chunk_count(ra);
+                    release();
+                    const uint32_t h = chunk_count(ra);
+                    decode();
+                    if (__any_sync(0xffffffffu, h)) chunk_queue(ra, pbase, h);
                 } else {
 #pragma unroll 1
                     for (int c = 0; c < kCols / CH; c += 2) {
                         tmem_ld(taddr + (c + 1) * CH, rb);
-                        hm |= chunk_count(ra) << c;
+                        const uint32_t ha = chunk_count(ra);
+                        if (__any_sync(0xffffffffu, ha)) chunk_queue(ra, pbase + c * CH, ha);
                         tmem_ld_wait(rb);
                         const bool more = c + 2 < kCols / CH;
-                        if (more) tmem_ld(taddr + (c + 2) * CH, ra);
-                        hm |= chunk_count(rb) << (c + 1);
+                        if (more)
+                            tmem_ld(taddr + (c + 2) * CH, ra);
+                        else
+                            release();
+                        const uint32_t hb = chunk_count(rb);
+                        decode();
+                        if (__any_sync(0xffffffffu, hb)) chunk_queue(rb, pbase + (c + 1) * CH, hb);
                         if (more) tmem_ld_wait(ra);
                     }
                 }
-                // rare (one warp vote per unit): reload the flagged chunks from the
-                // stage, still held, and queue their tests within the band
-                for (uint32_t any = __reduce_or_sync(0xffffffffu, hm); any != 0; any &= any - 1) {
-                    const int c = __ffs((int)any) - 1;
-                    tmem_ld(taddr + c * CH, ra);
-                    tmem_ld_wait(ra);
-                    chunk_queue(ra, pbase + c * CH, (hm >> c) & 1u);
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acc_empty[stage]);
             }
             if (qn > 0) flush();
             if (dstate[0] > 0) defer_flush();

@@ -18,21 +18,6 @@ __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
 
-// Threshold of a cell: sin^2(delta + r) with r = 2 asin(x), x = min(1, chord/2),
-// and 1 once delta + r >= pi/2.  Uses cos r = 1 - 2x^2 and
-// sin r = 2x sqrt(1 - x^2), so no transcendental function is needed on the
-// device; sin(delta), cos(delta) come from the host once per problem.
-__device__ __forceinline__ double tau_of(double sin_d, double cos_d, double chord) {
-    double x = ddiv(chord, 2.0);
-    if (x > 1.0) x = 1.0;
-    const double cr = dsub(1.0, dmul(dmul(2.0, x), x));
-    const double sr = dmul(dmul(2.0, x), dsqrt(dsub(1.0, dmul(x, x))));
-    const double cos_sum = dsub(dmul(cos_d, cr), dmul(sin_d, sr));
-    if (cos_sum <= 0.0) return 1.0;
-    const double s = dadd(dmul(sin_d, cr), dmul(cos_d, sr));
-    return dmul(s, s);
-}
-
 // The delta-independent part of the threshold: cos r = 1 - 2x^2 and
 // sin r = 2x sqrt(1 - x^2) of r = 2 asin(x), x = min(1, chord/2).
 __device__ __forceinline__ double2 cell_trig(double chord) {
@@ -43,8 +28,11 @@ __device__ __forceinline__ double2 cell_trig(double chord) {
     return make_double2(cr, sr);
 }
 
-// tau = sin^2(delta + r) from the cell's (cos r, sin r): the same operations,
-// in the same order, as tau_of(), without its square root and division.
+// Threshold of a cell: tau = sin^2(delta + r) with r = 2 asin(x), x = min(1,
+// chord/2), and 1 once delta + r >= pi/2; from the cell's (cos r, sin r) =
+// (1 - 2x^2, 2x sqrt(1 - x^2)) (cell_trig), so no transcendental function is
+// needed on the device; sin(delta), cos(delta) come from the host once per
+// problem.
 __device__ __forceinline__ double tau_cs(double sin_d, double cos_d, double2 cs) {
     const double cos_sum = dsub(dmul(cos_d, cs.x), dmul(sin_d, cs.y));
     if (cos_sum <= 0.0) return 1.0;

@@ -523,14 +523,15 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
         __syncwarp();
         float *rows = rows_all + (size_t)g * 128 * 12;   // this warpgroup's row table
         int *corr = corr_all + g * 128;
-        int64_t j = 0;
+        // accumulator stage of the next unit and the parity of its phase, carried across items
+        int stage = 0;
+        uint32_t parity = 0;
+        const uint32_t tbase = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * kCols);
         bool ok = true;
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             ItemView v;
             if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
-            const int64_t j0 = j;  // first unit of the item
             const int nunits = kUPT * v.ntiles;
-            j += nunits;
             const int pos = v.W.cell_begin + row;
             const bool valid = pos < v.ncell;
             float tau = 0.f, band = -1.f;
@@ -665,22 +666,24 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     if (qn > kQCap - 32) flush();
                 }
             };
-            for (int t = 0; t < nunits; ++t) {
-                const int64_t jj = j0 + t;
-                const int stage = (int)(jj % kNAcc);
-                const uint32_t uc = (uint32_t)(jj / kNAcc);
+            int pbase = g * kCols;  // pair offset of this warpgroup's columns of the unit in the item
+            for (int t = 0; t < nunits; ++t, pbase += U) {
                 // warp-uniform outcome: every lane must reach the .sync.aligned tcgen05.ld below
-                if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[stage], uc & 1u, wctl))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[stage], parity, wctl))) {
                     fail();
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t taddr =
-                    tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(stage * U + g * kCols);
-                const int pbase = t * U + g * kCols;
+                const uint32_t taddr = tbase + (uint32_t)(stage * U);
+                uint64_t *const empty_bar = &acc_empty[stage];
+                if (++stage == kNAcc) {
+                    stage = 0;
+                    parity ^= 1u;
+                }
                 // CH-column chunks, double-buffered: the load of the next chunk is in
-                // flight while this one is counted
+                // flight while this one is counted (fully unrolled, so the chunk offsets
+                // are immediates and no loop bookkeeping runs per chunk)
                 uint32_t ra[CH], rb[CH];
                 tmem_ld(taddr, ra);
                 tmem_ld_wait(ra);
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 auto release = [&]() {
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&acc_empty[stage]);
+                    if (lane == 0) mbar_arrive(empty_bar);
                 };
                 if constexpr (kCols == CH) {
                     release();
@@ -696,7 +699,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     decode();
                     if (__any_sync(0xffffffffu, h)) chunk_queue(ra, pbase, h);
                 } else {
-#pragma unroll 1
+#pragma unroll
                     for (int c = 0; c < kCols / CH; c += 2) {
                         tmem_ld(taddr + (c + 1) * CH, rb);
                         const uint32_t ha = chunk_count(ra);

@@ -68,7 +68,8 @@ __device__ __forceinline__ int tc_off(int r, int k) {
 
 template <typename T16>
 __device__ __forceinline__ void write_tc_row(uint8_t *tile, int r, int K, const float s[10], bool pad) {
-    // B row of a pair: K = 16: [s(10), 1, 1, 0 x4]; K = 32: [s_hi(10), s_lo(10), s_hi(10), 1, 1]
+    // B row of a pair: K = 16: [s(10), 1, 1, lo(s_0)..lo(s_3)] (the padding carries the low
+    // halves of the four diagonal entries); K = 32: [s_hi(10), s_lo(10), s_hi(10), 1, 1]
     T16 v[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) v[k] = to16<T16>(0.f);
@@ -79,6 +80,8 @@ __device__ __forceinline__ void write_tc_row(uint8_t *tile, int r, int K, const 
             for (int k = 0; k < 10; ++k) v[k] = to16<T16>(s[k]);
             v[10] = to16<T16>(1.f);
             v[11] = to16<T16>(1.f);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[12 + k] = to16<T16>(s[k] - from16(v[k]));
         } else {
 #pragma unroll
             for (int k = 0; k < 10; ++k) {

@@ -1,9 +1,9 @@
 // k_vote_tc.cu -- the vote on the tcgen05 tensor cores (sm_103a).
 //
 // D[c][i] = sum_k A[c][k] B[i][k] with
-//   A row (cell c):  K = 16: [m(q_c) (10), -tau_hi, -tau_lo, 0 x4]
+//   A row (cell c):  K = 16: [m(q_c) (10), -tau_hi, -tau_lo, m_0..m_3]
 //                    K = 32: [m_hi (10), m_hi (10), m_lo (10), -tau_hi, -tau_lo]
-//   B row (pair i):  K = 16: [s_i (10), 1, 1, 0 x4]
+//   B row (pair i):  K = 16: [s_i (10), 1, 1, lo(s_0)..lo(s_3)]
 //                    K = 32: [s_hi (10), s_lo (10), s_hi (10), 1, 1]
 // so D = m.s - tau ~ q_c^T S_i q_c - tau_c, in FP32 in tensor memory.  The
 // cell votes for the pair iff D <= 0; the epilogue counts sign bits and flags
@@ -246,26 +246,47 @@ __device__ __forceinline__ float min3_abs(float m, float x, float y) {
     return r;
 }
 
-// Rigorous per-cell bound on |D - (v - tau)| (see the file comment).
+// Rigorous per-cell bound on |D - (v - tau)| (see the file comment).  smax_k
+// bounds |s_k| for unit a, b: 1 for the diagonal entries S00..S33, 1/2 for the
+// six others (each is half a cross-product component, or half of a0 b1 + a1 b0
+// and the like, and |a0 b1 + a1 b0| <= |a| |b| by Cauchy-Schwarz); the final
+// factor 1.25 covers inputs whose squared norms are within 1e-5 of 1.
 template <int KSTEPS, bool BF16>
 __device__ __forceinline__ float cell_band(const float m[10]) {
     const float u32 = 5.9604645e-8f;
     const float u16 = BF16 ? 3.90625e-3f : 4.8828125e-4f;
     const float sub = BF16 ? 0.f : 2.9802322e-8f;  // half the FP16 subnormal spacing
-    const float smax[10] = {1.f, 1.f, 1.f, 1.f, 0.5f, 0.5f, 0.5f, 1.f, 1.f, 1.f};
+    const float smax[10] = {1.f, 1.f, 1.f, 1.f, 0.5f, 0.5f, 0.5f, 0.5f, 0.5f, 0.5f};
+    const int K = 16 * KSTEPS;
+    const float accum = (14.f + 12.f * K) * u32 + 1e-6f;
     float msum = 0.f, mabs = 0.f;
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
         msum = fmaf(fabsf(m[k]), smax[k], msum);
         mabs += fabsf(m[k]);
     }
-    const int K = 16 * KSTEPS;
-    const float accum = (14.f + 12.f * K) * u32 + 1e-6f;
     float b;
-    if (KSTEPS == 1)
-        b = (2.f * u16 + u16 * u16 + 2.f * u32) * msum + sub * (mabs + 8.5f) + accum;
-    else
-        b = (3.f * u16 * u16 + u16 * u16 * u16 + 2.f * u32) * msum + 2.f * sub * (mabs + 8.5f) + accum;
+    if (KSTEPS == 1) {
+        // A holds m~ = m rounded to 16 bits, whose error is known exactly; B holds s
+        // rounded to 16 bits plus, in the padding columns, the low halves of the four
+        // diagonal entries.  D - (v - tau) = sum (m - m~) s + sum m~ (s - s_B) + ...:
+        // dm below, u16 |m~| smax for the six off-diagonal entries, u16^2 for the
+        // diagonal ones and for tau's hi/lo split; 2 u32 for the FP32 m, s and tau.
+        float dm = 0.f, mt_off = 0.f, mt_diag = 0.f;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+            const float mt = f16<BF16>(h16<BF16>(m[k]));
+            dm = fmaf(fabsf(m[k] - mt), smax[k], dm);
+            if (k < 4)
+                mt_diag += fabsf(mt);
+            else
+                mt_off = fmaf(fabsf(mt), smax[k], mt_off);
+        }
+        b = dm + u16 * mt_off + u16 * u16 * (mt_diag + 1.f) + 2.f * u32 * (msum + 1.f) +
+            2.f * sub * (mabs + 1.f) + accum;
+    } else {
+        b = (3.f * u16 * u16 + u16 * u16 * u16 + 2.f * u32) * msum + 2.f * sub * (mabs + 7.f) + accum;
+    }
     return b * 1.25f;
 }
 
@@ -331,6 +352,8 @@ __device__ __noinline__ void build_a_tiles(const VoteItem *__restrict__ items, i
                     for (int k = 0; k < 10; ++k) row[k] = h16<BF16>(m[k]);
                     row[10] = th ^ 0x8000u;  // -tau_hi
                     row[11] = tl ^ 0x8000u;  // -tau_lo
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) row[12 + k] = row[k];  // times the low halves of S00..S33
                 } else {
 #pragma unroll
                     for (int k = 0; k < 10; ++k) {

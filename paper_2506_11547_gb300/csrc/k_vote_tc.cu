@@ -28,9 +28,10 @@
 //               stages in flight; each thread owns one TMEM lane = one cell and
 //               reads 16 or 32 columns per tcgen05.ld, double-buffered so the
 //               next load is in flight while it counts the current one (and
-//               releases the stage as soon as its last load has completed): sign
-//               bits two per byte permute and the minimum of |D| two values per
-//               three-input minimum.  One warp vote per chunk: when a lane's
+//               releases the stage as soon as its last load has completed): the
+//               signs two per packed fma rounding toward -inf on the FMA pipe
+//               (sign_fma2) and the minimum of |D| two values per three-input
+//               minimum on the ALU pipe.  One warp vote per chunk: when a lane's
 //               chunk holds a value within the band (rare), the warp queues
 //               those tests from the registers it still holds into a per-warp
 //               shared-memory queue that is drained 32 at a time (one lane per
@@ -226,19 +227,24 @@ __device__ __forceinline__ float f16(uint16_t x) {
     return __half2float(__ushort_as_half(x));
 }
 
-// Sign bytes of two FP32 values, each twice: bytes [s(a), s(b), s(a), s(b)] with
-// s(x) = 0xFF if x's sign bit is set, else 0 (byte permute with sign replication).
-__device__ __forceinline__ uint32_t sign_bytes2(uint32_t a, uint32_t b) {
-    uint32_t r;
-    asm("prmt.b32 %0, %1, %2, 0xFBFB;" : "=r"(r) : "r"(a), "r"(b));
-    return r;
+// Sign counting on the FMA pipe.  A counter starts at 1.5; fma rounding toward
+// -inf of counter + d 2^-30 returns the counter lowered by exactly one ulp
+// (2^-23) when d < 0 (|d 2^-30| < 2^-23 for |d| < 2^7) and the counter itself
+// when d >= 0, -0 included.  Two counters per 64-bit register, two tests per
+// packed fma; while a counter stays in [1, 2) its decrement count is
+// bits(1.5f) - bits(counter).
+constexpr uint64_t kCnt0 = 0x3FC000003FC00000ull;  // (1.5f, 1.5f)
+constexpr uint64_t kTiny2 = 0x3080000030800000ull; // (2^-30, 2^-30)
+__device__ __forceinline__ uint64_t sign_fma2(uint32_t a, uint32_t b, uint64_t acc) {
+    uint64_t d;
+    asm("{\n .reg .b64 t;\n mov.b64 t, {%1, %2};\n fma.rm.f32x2 %0, t, %3, %4;\n}\n"
+        : "=l"(d)
+        : "r"(a), "r"(b), "l"(kTiny2), "l"(acc));
+    return d;
 }
-// Number of set sign bits among the 2k values whose sign_bytes2 words sum (mod 2^32)
-// to t, for k <= 63: t = 255 X with X = sum_i n_i 256^i (n_i <= 63 the count in
-// byte i, each value counted twice); 255 is odd, so X = t 255^-1 mod 2^32, and its
-// byte sum 2 (n_0 + n_1) is the top byte of X 0x01010101.  0xFBFCFDFF is
-// 255^-1 0x01010101 mod 2^32.
-__device__ __forceinline__ int sign_count(uint32_t t) { return (int)((t * 0xFBFCFDFFu) >> 25); }
+__device__ __forceinline__ int sign_fma2_count(uint64_t acc) {
+    return (int)(2u * 0x3FC00000u - (uint32_t)acc - (uint32_t)(acc >> 32));
+}
 // min(m, |x|, |y|) (three-input minimum).
 __device__ __forceinline__ float min3_abs(float m, float x, float y) {
     float r;
@@ -646,25 +652,25 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 __syncwarp();
                 qn = 0;
             };
-            // counts the CH values of one chunk: sign bits (D < 0) two per byte
-            // permute, added two words per add to tsum, which is decoded once per
-            // two chunks (at most 64 values, within the 126 sign_count allows);
+            // counts the CH values of one chunk: the tests with D < 0 into the two
+            // FMA-pipe counters of tsum (sign_fma2), decoded once per two chunks;
             // returns whether the chunk holds a value within the band (one chain
             // of three-input minima of |D|, two values each).
-            uint32_t tsum = 0;
+            uint64_t tsum = kCnt0;
             auto chunk_count = [&](const uint32_t(&r)[CH]) -> uint32_t {
                 float m = 4.f;  // min |D| (|D| <= 4)
 #pragma unroll
                 for (int e = 0; e < CH; e += 4) {
-                    tsum = tsum + sign_bytes2(r[e], r[e + 1]) + sign_bytes2(r[e + 2], r[e + 3]);
+                    tsum = sign_fma2(r[e], r[e + 1], tsum);
+                    tsum = sign_fma2(r[e + 2], r[e + 3], tsum);
                     m = min3_abs(m, __uint_as_float(r[e]), __uint_as_float(r[e + 1]));
                     m = min3_abs(m, __uint_as_float(r[e + 2]), __uint_as_float(r[e + 3]));
                 }
                 return m <= band ? 1u : 0u;
             };
             auto decode = [&]() {
-                cnt += sign_count(tsum);
-                tsum = 0;
+                cnt += sign_fma2_count(tsum);
+                tsum = kCnt0;
             };
             // queues the tests within the band of one chunk (pair offset poff in
             // the item) for the FP32 re-check; hit: this lane's chunk holds one
@@ -674,7 +680,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
 #pragma unroll
                     for (int e = 0; e < CH; ++e) {
                         fm |= (uint32_t)(fabsf(__uint_as_float(r[e])) <= band) << e;
-                        sm |= (r[e] >> 31) << e;
+                        sm |= (uint32_t)(__uint_as_float(r[e]) < 0.f) << e;
                     }
                 }
                 for (;;) {

@@ -490,6 +490,11 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
             int64_t j = 0;
             int i = 0;
             bool ok = true;
+            // B stage and accumulator stage of the next tile / unit with their phase parities,
+            // and the shared-memory descriptors (start address in bits 0-13: offsets add there)
+            int bs = 0, as = 0;
+            uint32_t bph = 0, aph = 0;
+            const uint64_t b_desc0 = sdesc(smem_u32(sB), kBLbo);
             for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
                 ItemView v;
                 if (!load_item(items, it, probs, lref, level_stride, level, v)) continue;
@@ -500,22 +505,17 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a_addr = smem_u32(sA + ab * kATileBytesMax);
+                const uint64_t a_desc = sdesc(smem_u32(sA + ab * kATileBytesMax), kALbo);
                 for (int t = 0; t < v.ntiles && ok; ++t, ++j) {
-                    const int bs = (int)(j % kNB);
-                    const uint32_t ub = (uint32_t)(j / kNB);
-                    if (!mbar_wait(&b_full[bs], ub & 1u, wctl)) {
+                    if (!mbar_wait(&b_full[bs], bph, wctl)) {
                         fail();
                         ok = false;
                         break;
                     }
-                    const uint32_t b_addr = smem_u32(sB + bs * kBTileBytesMax);
+                    const uint64_t b_desc = b_desc0 + (uint64_t)(bs * (kBTileBytesMax >> 4));
 #pragma unroll
                     for (int h = 0; h < kUPT; ++h) {  // rows [h U, (h+1) U) of the B tile: U / 8 groups of 128 B
-                        const int64_t u = kUPT * j + h;
-                        const int as = (int)(u % kNAcc);
-                        const uint32_t uc = (uint32_t)(u / kNAcc);
-                        if (!mbar_wait(&acc_empty[as], (uc & 1u) ^ 1u, wctl)) {
+                        if (!mbar_wait(&acc_empty[as], aph ^ 1u, wctl)) {
                             fail();
                             ok = false;
                             break;
@@ -524,12 +524,21 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                         const uint32_t d_tmem = tmem_base + (uint32_t)(as * U);
 #pragma unroll
                         for (int k = 0; k < KSTEPS; ++k)
-                            mma_f16(d_tmem, sdesc(a_addr + k * 2 * kALbo, kALbo),
-                                    sdesc(b_addr + h * (U / 8) * 128 + k * 2 * kBLbo, kBLbo), IDESC, k > 0 ? 1u : 0u);
+                            mma_f16(d_tmem, a_desc + (uint64_t)(k * (2 * kALbo >> 4)),
+                                    b_desc + (uint64_t)(h * (U / 8) * (128 >> 4) + k * (2 * kBLbo >> 4)), IDESC,
+                                    k > 0 ? 1u : 0u);
                         mma_commit(&acc_full[as]);
+                        if (++as == kNAcc) {
+                            as = 0;
+                            aph ^= 1u;
+                        }
                     }
                     if (!ok) break;
                     mma_commit(&b_empty[bs]);
+                    if (++bs == kNB) {
+                        bs = 0;
+                        bph ^= 1u;
+                    }
                 }
                 if (!ok) break;
                 mma_commit(&a_empty[ab]);

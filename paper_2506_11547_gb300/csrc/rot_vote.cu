@@ -123,6 +123,55 @@ int Context::cuda_fail(cudaError_t e, const char *what) {
 // ---------------------------------------------------------------------------
 static bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
+// The tensor-core vote takes items in grid-stride order (item i on CTA i mod
+// grid), so when the item count is not a multiple of the grid, the CTAs of the
+// last, partial round run one more item while the others idle.  This splits
+// the items of that round by pair range into pieces that spread its work over
+// every CTA: for k = 1..4 target pieces per CTA, each item becomes
+// round(tiles / piece) pieces (at least one, at least 4 pair tiles each), and
+// the split whose busiest CTA ends first is kept (the unsplit round included).
+static void split_last_round(std::vector<VoteItem> &items, int grid) {
+    const int64_t n = (int64_t)items.size();
+    if (grid <= 0 || n <= grid || n % grid == 0) return;
+    const int64_t full = n / grid * grid;
+    const std::vector<VoteItem> tail(items.begin() + full, items.end());
+    auto tiles = [](const VoteItem &it) { return (int64_t)(it.pair_end - it.pair_begin) / kPairTile; };
+    int64_t wr = 0;
+    for (const VoteItem &it : tail) wr += tiles(it);
+    auto split = [&](int k) {
+        std::vector<VoteItem> out;
+        const int64_t piece = std::max<int64_t>(4, (wr + (int64_t)k * grid - 1) / ((int64_t)k * grid));
+        for (const VoteItem &it : tail) {
+            const int64_t t = tiles(it);
+            const int64_t np = std::max<int64_t>(1, std::min<int64_t>((t + piece / 2) / piece, t / 4));
+            for (int64_t z = 0; z < np; ++z) {
+                VoteItem x = it;
+                x.pair_begin = it.pair_begin + (int32_t)(t * z / np * kPairTile);
+                x.pair_end = it.pair_begin + (int32_t)(t * (z + 1) / np * kPairTile);
+                out.push_back(x);
+            }
+        }
+        return out;
+    };
+    auto makespan = [&](const std::vector<VoteItem> &pieces) {  // the busiest CTA's tiles in the round
+        std::vector<int64_t> load((size_t)grid, 0);
+        for (size_t i = 0; i < pieces.size(); ++i) load[i % (size_t)grid] += tiles(pieces[i]);
+        return *std::max_element(load.begin(), load.end());
+    };
+    std::vector<VoteItem> best = tail;
+    int64_t best_ms = makespan(tail);
+    for (int k = 1; k <= 4; ++k) {
+        std::vector<VoteItem> cand = split(k);
+        const int64_t ms = makespan(cand);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = std::move(cand);
+        }
+    }
+    items.resize((size_t)full);
+    items.insert(items.end(), best.begin(), best.end());
+}
+
 // Host-side argument check of one problem; returns OK or EINVAL with a reason.
 int check_problem(const rot_vote_problem &p, int grid_n, int levels, std::string *why) {
     if (!p.a || !p.b) { *why = "null input pointer"; return ROT_VOTE_EINVAL; }
@@ -251,6 +300,7 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
                     items.push_back(it);
                 }
         }
+        if (tck) split_last_round(items, slots);
     }
     // top-K chunks per problem
     int64_t maxc = child_cap;

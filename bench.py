@@ -45,19 +45,20 @@ WORKLOAD_DESCS = {
 }
 FLOPS_PER_TEST = 20.0  # algorithmic: 10 multiply-adds of the (cell monomials . pair S entries) contraction
 K16_FLOPS_PER_TEST = 32.0  # the contraction with K padded to 16 (one kind::f16 MMA K step)
-# The tensor-core epilogue's CUDA-core bound: per 8 tests it issues 4 sign-byte permutes, 2
-# three-input adds and 4 three-input |D| minima, 1.25 ALU-pipe instructions per test, on an ALU
-# pipe of 64 lanes per SM per clock: 152 x 64 x f_max / 1.25 tests/s.
-EPI_ALU_INSTR_PER_TEST = 1.25
+# The tensor-core epilogue's CUDA-core bound: per 4 tests it issues 2 packed fma.rm.f32x2 sign
+# counters (FMA pipe) and 2 three-input |D| minima (ALU pipe), 0.5 ALU-pipe instructions per
+# test; the ALU pipe has 64 lanes per SM per clock (16 per scheduler, which also issues the
+# FMA-pipe half): 152 x 64 x f_max / 0.5 tests/s.
+EPI_ALU_INSTR_PER_TEST = 0.5
 EPI_ALU_LANES_PER_SM = 64
 # DRAM bytes (read + write) of one coarse-vote launch, from one ncu capture of the workload and
 # precision named in the key.  A figure stands only while the kernel's source file hashes to the
 # value it was captured with; otherwise the line reports null.
 NCU_TRAFFIC = {
-    ("lowp_n1e6_128L3", "fp16x2"): (5697486080 + 84834560, "k_vote_tc.cu",
-                                    "26b4a3dd5dcca3ec71d9abac376afe8602a45452b72afe27f5f720591feb7d21"),
-    ("fp32_n1e5_64L3", "fp16x2"): (26754304, "k_vote_tc.cu",
-                                   "26b4a3dd5dcca3ec71d9abac376afe8602a45452b72afe27f5f720591feb7d21"),
+    ("lowp_n1e6_128L3", "fp16x2"): (5780935936 + 84012288, "k_vote_tc.cu",
+                                    "08fe5898f026c4880e59f0137540424aaba9283cd37dfbf12020a33c495c767f"),
+    ("fp32_n1e5_64L3", "fp16x2"): (26757632, "k_vote_tc.cu",
+                                   "08fe5898f026c4880e59f0137540424aaba9283cd37dfbf12020a33c495c767f"),
     ("fp32_n1e5_64L3", "fp32"): (17170688, "k_vote_simt.cu",
                                  "7da99284336fef54f912b58e44b5284fab9b1d003d32dbeadaa929631cf286ca"),
 }
@@ -845,7 +846,8 @@ def roofline_of(stage_avg, tests0, prec, workload, peaks, peak_src, sms):
                  epilogue={"bound": "alu", "tests_per_s": tests0 / t, "peak_tests_per_s": epi,
                            "frac": tests0 / t / epi,
                            "peak_source": (f"{sms} SMs x {EPI_ALU_LANES_PER_SM} ALU lanes x {f_mhz} MHz / "
-                                           f"{EPI_ALU_INSTR_PER_TEST} ALU instructions per test")})
+                                           f"{EPI_ALU_INSTR_PER_TEST} ALU instructions per test (|D| minima; "
+                                           "the sign counts run on the FMA pipe)")})
     return r
 
 

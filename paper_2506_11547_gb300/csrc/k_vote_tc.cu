@@ -457,6 +457,8 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
         // ------------------------------ producer ------------------------------
         if (lane == 0) {
             int64_t j = 0;
+            int pbs = 0;
+            uint32_t pph = 0;
             bool ok = true;
             for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
                 ItemView v;
@@ -464,9 +466,13 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 const uint8_t *src = (const uint8_t *)pool.tcb +
                                      ((v.P.pool_off + v.W.pair_begin) / kPairTile) * (int64_t)kTileBytes;
                 for (int t = 0; t < v.ntiles; ++t, ++j) {
-                    const int bs = (int)(j % kNB);
-                    const uint32_t u = (uint32_t)(j / kNB);
-                    if (!mbar_wait(&b_empty[bs], (u & 1u) ^ 1u, wctl)) {
+                    const int bs = pbs;  // B stage of tile j and its phase parity, carried incrementally
+                    const uint32_t ph = pph;
+                    if (++pbs == kNB) {
+                        pbs = 0;
+                        pph ^= 1u;
+                    }
+                    if (!mbar_wait(&b_empty[bs], ph ^ 1u, wctl)) {
                         fail();
                         ok = false;
                         break;

@@ -597,8 +597,10 @@ int Context::enqueue_pipeline(Wave &w) {
             e = launch_vote_small(pl.d_probs, pl.d_tiles, (int)pl.tiles_h.size(), pl.d_lref, S, lev, pl.pool,
                                   pl.d_stats, pl.amb(lev), w.stream);
         if (e == cudaSuccess)
-            e = launch_resolve64(pl.amb(lev), pl.d_probs, P, pl.d_lref, S, lev, pl.pool, pl.d_stats, 4 * sm_count,
-                                 w.stream);
+            // the coarse level's queue holds millions of tests (1e6 pairs, 128^3): more blocks hide
+            // the dependent loads of its FP64 evaluations; the refinement levels' queues are short
+            e = launch_resolve64(pl.amb(lev), pl.d_probs, P, pl.d_lref, S, lev, pl.pool, pl.d_stats,
+                                 (lev == 0 ? 16 : 4) * sm_count, w.stream);
         done();
         mark(2, lev, lev == 0 ? 2 : 1);
         if (e == cudaSuccess) {

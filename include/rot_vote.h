@@ -81,7 +81,8 @@ typedef enum {
  *              rotation against the pair's outer product b a^T (App. A's
  *              bilinear form q^T M q = b^T R(q) a).
  *   FP16    -- tcgen05 tensor-core form, monomials and S entries in FP16
- *              (K = 10 + 2 threshold columns, padded to 16), FP32
+ *              (K = 10 + 2 threshold columns, padded to 16; the padding
+ *              carries the low halves of the four diagonal S entries), FP32
  *              accumulation in tensor memory.
  *   BF16    -- as FP16 with BF16 operands.
  *   FP16X2, BF16X2 -- hi/lo split operands (K = 32): far fewer re-checks. */

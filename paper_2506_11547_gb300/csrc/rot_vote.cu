@@ -213,20 +213,46 @@ int Context::tc_k_of(int prec) const {
 // Builds the plan for the valid problems `sel` (indices into p[]).
 int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<int> &sel) {
     Plan &pl = w.plan;
-    pl = Plan();
     const int P = (int)sel.size();
+    std::vector<int> gridn(P), levs(P);
+    bool all_dev = true;
+    for (int k = 0; k < P; ++k) {
+        const rot_vote_problem &q = p[sel[k]];
+        gridn[k] = q.grid_n > 0 ? q.grid_n : cfg.grid_n;
+        levs[k] = q.levels > 0 ? q.levels : (q.levels < 0 ? 0 : cfg.levels);
+        all_dev = all_dev && mem_kind(q.a) && mem_kind(q.b);
+    }
+    // same shapes as the wave's current plan, on the same workspace: keep its layout, items and
+    // tables, and refresh the inputs and tolerances of the problem table
+    if (pl.ws_base != nullptr && pl.ws_base == w.base && pl.nprob == P && pl.shape_dev == all_dev &&
+        pl.shape_amb_hook == test_amb_cap && (int)pl.shape_n.size() == P) {
+        bool same = true;
+        for (int k = 0; k < P && same; ++k)
+            same = pl.shape_n[k] == p[sel[k]].n && pl.shape_gl[k] == (((int64_t)gridn[k] << 32) | levs[k]);
+        if (same) {
+            for (int k = 0; k < P; ++k) {
+                const rot_vote_problem &q = p[sel[k]];
+                ProbRef &r = pl.probs_h[k];
+                const double d = (double)q.delta;
+                r.sin_d = std::sin(d);
+                r.cos_d = std::cos(d);
+                r.delta = q.delta;
+                if (all_dev) {
+                    r.a = q.a;
+                    r.b = q.b;
+                }
+            }
+            pl.reused = true;
+            return ROT_VOTE_OK;
+        }
+    }
+    pl = Plan();
     pl.nprob = P;
     pl.prec = cfg.precision;
     pl.top_k = cfg.top_k;
     pl.stride = 0;
     int max_levels = 0;
-    std::vector<int> gridn(P), levs(P);
-    for (int k = 0; k < P; ++k) {
-        const rot_vote_problem &q = p[sel[k]];
-        gridn[k] = q.grid_n > 0 ? q.grid_n : cfg.grid_n;
-        levs[k] = q.levels > 0 ? q.levels : (q.levels < 0 ? 0 : cfg.levels);
-        max_levels = std::max(max_levels, levs[k]);
-    }
+    for (int k = 0; k < P; ++k) max_levels = std::max(max_levels, levs[k]);
     pl.max_level = max_levels;
     pl.stride = max_levels + 1;
     const int S = pl.stride;
@@ -243,7 +269,6 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
     // pair pool layout and input residency
     pl.probs_h.resize(P);
     int64_t pool = 0, in_floats = 0;
-    bool all_dev = true;
     for (int k = 0; k < P; ++k) {
         const rot_vote_problem &q = p[sel[k]];
         ProbRef &r = pl.probs_h[k];
@@ -256,8 +281,6 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
         r.delta = q.delta;
         r.levels = levs[k];
         r.grid_n = gridn[k];
-        const bool dev = mem_kind(q.a) && mem_kind(q.b);
-        all_dev = all_dev && dev;
         in_floats += 3 * q.n;
     }
     pl.pool_pairs = pool;
@@ -498,6 +521,16 @@ int Context::plan_batch(Wave &w, const rot_vote_problem *p, const std::vector<in
         sig += buf;
     }
     pl.signature = sig;
+    pl.shape_n.resize(P);
+    pl.shape_gl.resize(P);
+    for (int k = 0; k < P; ++k) {
+        pl.shape_n[k] = pl.probs_h[k].n;
+        pl.shape_gl[k] = ((int64_t)gridn[k] << 32) | levs[k];
+    }
+    pl.shape_dev = all_dev;
+    pl.shape_amb_hook = test_amb_cap;
+    pl.ws_base = w.base;
+    pl.reused = false;
     return ROT_VOTE_OK;
 }
 
@@ -523,13 +556,15 @@ int Context::upload(Wave &w, const rot_vote_problem *p, const std::vector<int> &
         return e;
     };
     cudaError_t e = put(pl.d_probs, pl.probs_h.data(), sizeof(ProbRef) * P);
-    if (e == cudaSuccess) e = put(pl.d_lref, pl.lref_h.data(), sizeof(LevelRef) * (size_t)P * S);
-    for (int lev = 0; lev < S && e == cudaSuccess; ++lev)
-        e = put(pl.d_items[lev], pl.items_h[lev].data(), sizeof(VoteItem) * pl.items_h[lev].size());
-    if (e == cudaSuccess) e = put(pl.d_tiles, pl.tiles_h.data(), sizeof(int2) * pl.tiles_h.size());
-    if (e == cudaSuccess) e = put(pl.d_sloff, pl.slice_off_h.data(), sizeof(int64_t) * pl.slice_off_h.size());
-    if (e == cudaSuccess) e = put(pl.d_flist, pl.fit_list_h.data(), sizeof(int32_t) * pl.fit_list_h.size());
-    if (e == cudaSuccess) e = put(pl.d_bsoff, pl.fit_bsoff_h.data(), sizeof(int64_t) * pl.fit_bsoff_h.size());
+    if (!pl.reused) {  // a reused plan's tables are already in the workspace
+        if (e == cudaSuccess) e = put(pl.d_lref, pl.lref_h.data(), sizeof(LevelRef) * (size_t)P * S);
+        for (int lev = 0; lev < S && e == cudaSuccess; ++lev)
+            e = put(pl.d_items[lev], pl.items_h[lev].data(), sizeof(VoteItem) * pl.items_h[lev].size());
+        if (e == cudaSuccess) e = put(pl.d_tiles, pl.tiles_h.data(), sizeof(int2) * pl.tiles_h.size());
+        if (e == cudaSuccess) e = put(pl.d_sloff, pl.slice_off_h.data(), sizeof(int64_t) * pl.slice_off_h.size());
+        if (e == cudaSuccess) e = put(pl.d_flist, pl.fit_list_h.data(), sizeof(int32_t) * pl.fit_list_h.size());
+        if (e == cudaSuccess) e = put(pl.d_bsoff, pl.fit_bsoff_h.data(), sizeof(int64_t) * pl.fit_bsoff_h.size());
+    }
     if (e != cudaSuccess) return cuda_fail(e, "uploading descriptors");
     if (!pl.inputs_on_device) {
         // host inputs: direct copies from pinned caller memory when few problems, else pack
@@ -864,6 +899,7 @@ int Wave::ensure(size_t bytes, Context &ctx) {
     ctx.bytes_held -= cap;
     base = nullptr;
     cap = 0;
+    plan.ws_base = nullptr;  // the plan's tables lived in the old workspace
     if (graph_exec) {
         cudaGraphExecDestroy(graph_exec);
         graph_exec = nullptr;
@@ -947,6 +983,7 @@ void Wave::free_workspace(Context &ctx) {
     ctx.bytes_held -= cap;
     base = nullptr;
     cap = 0;
+    plan.ws_base = nullptr;
 }
 
 void Wave::release(Context &ctx) {
@@ -959,6 +996,7 @@ void Wave::release(Context &ctx) {
     }
     base = nullptr;
     cap = 0;
+    plan.ws_base = nullptr;
     if (pinned) cudaFreeHost(pinned);
     if (stage) cudaFreeHost(stage);
     if (results_h) cudaFreeHost(results_h);

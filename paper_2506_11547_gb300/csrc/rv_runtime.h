@@ -71,6 +71,15 @@ struct Plan {
     Amb64 *d_amb = nullptr; // tests deferred to the FP64 resolution pass (reused level after level)
     int *d_ambcnt = nullptr;  // per level: queue length, then queue-full flag (zeroed per solve)
     int amb_cap = 0;
+    // the shapes this layout was planned for: a batch with the same ones (sizes, grids, levels,
+    // input residency, FP64-queue capacity hook) on the same workspace reuses the plan and
+    // refreshes only the per-problem inputs
+    std::vector<int64_t> shape_n;
+    std::vector<int64_t> shape_gl;  // grid_n << 32 | levels, per problem
+    bool shape_dev = true;
+    int shape_amb_hook = -1;
+    void *ws_base = nullptr;
+    bool reused = false;  // this batch reused the plan: only the problem table is uploaded
     AmbQueue amb(int lev) const {
         AmbQueue q;
         q.q = d_amb;

@@ -196,6 +196,34 @@ def test_graph_replay_with_new_inputs():
     assert g1.best_cell != g2.best_cell or not np.array_equal(g1.q, g2.q)
 
 
+def test_batches_reusing_the_plan_equal_fresh_solves():
+    """A context keeps a batch's plan (layout, work items, tables) for the next
+    batch of the same shapes and refreshes only the inputs and tolerances.  A
+    sequence that repeats, changes and restores the shapes and switches the
+    inputs between device and host memory must give, batch by batch, the results
+    of a fresh context."""
+    def batch(seed, sizes, deltas):
+        return [synth.make_problem(n, rho=0.9, sigma=0.01, delta=d, seed=seed + k)
+                for k, (n, d) in enumerate(zip(sizes, deltas))]
+    s1, s2 = [300, 5000, 1200], [300, 700]
+    seq = [(batch(40, s1, [0.03, 0.03, 0.03]), True), (batch(50, s1, [0.04, 0.02, 0.035]), True),
+           (batch(60, s2, [0.03, 0.03]), True), (batch(70, s1, [0.03, 0.05, 0.03]), False),
+           (batch(80, s1, [0.025, 0.03, 0.03]), True)]
+    for prec in ("fp16x2", "fp32"):
+        with rv.Context(grid_n=16, levels=2, precision=prec) as ctx:
+            got = []
+            for probs, on_dev in seq:
+                args = [((dev(p.a), dev(p.b)) if on_dev else (p.a, p.b)) + (p.delta,) for p in probs]
+                got.append(ctx.solve(args))
+        for (probs, on_dev), res in zip(seq, got):
+            with rv.Context(grid_n=16, levels=2, precision=prec) as fresh:
+                ref = fresh.solve([(dev(p.a), dev(p.b), p.delta) for p in probs])
+            for r, f in zip(res, ref):
+                assert np.array_equal(r.q, f.q)
+                assert (r.best_count, r.best_cell, r.inliers, r.tests, r.rechecked, r.ambiguous, r.status) == \
+                       (f.best_count, f.best_cell, f.inliers, f.tests, f.rechecked, f.ambiguous, f.status)
+
+
 def test_invalid_inputs_are_rejected():
     p = synth.make_problem(300, rho=0.5, sigma=0.01, delta=0.03, seed=13)
     bad_nan = p.a.copy()

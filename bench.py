@@ -56,9 +56,9 @@ EPI_ALU_LANES_PER_SM = 64
 # value it was captured with; otherwise the line reports null.
 NCU_TRAFFIC = {
     ("lowp_n1e6_128L3", "fp16x2"): (5780432896 + 84005632, "k_vote_tc.cu",
-                                    "8d3ceb68e1c7e94362f85ef9bed655eb73182e7c4f030b1994d452edcf811f48"),
+                                    "ed71a6dcbfc176c6e07be02bd6c46998c7ab746d9170e3c4c18494b6bfe669fe"),
     ("fp32_n1e5_64L3", "fp16x2"): (26757376, "k_vote_tc.cu",
-                                   "8d3ceb68e1c7e94362f85ef9bed655eb73182e7c4f030b1994d452edcf811f48"),
+                                   "ed71a6dcbfc176c6e07be02bd6c46998c7ab746d9170e3c4c18494b6bfe669fe"),
     ("fp32_n1e5_64L3", "fp32"): (17170688, "k_vote_simt.cu",
                                  "7da99284336fef54f912b58e44b5284fab9b1d003d32dbeadaa929631cf286ca"),
 }

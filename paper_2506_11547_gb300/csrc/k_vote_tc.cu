@@ -6,7 +6,7 @@
 //   B row (pair i):  K = 16: [s_i (10), 1, 1, lo(s_0)..lo(s_3)]
 //                    K = 32: [s_hi (10), s_lo (10), s_hi (10), 1, 1]
 // so D = m.s - tau ~ q_c^T S_i q_c - tau_c, in FP32 in tensor memory.  The
-// cell votes for the pair iff D <= 0; the epilogue counts sign bits and flags
+// cell votes for the pair iff D <= 0; the epilogue counts D < 0 and flags
 // |D| <= band_c, a rigorous per-cell bound on |D - (v - tau)_exact| (operand
 // rounding to 16 bits, the FP32 pair step, FP32 accumulation).  Flagged tests
 // are re-evaluated with the FP32 re-check |b - R_c a|^2/4 - c_i, whose error
@@ -61,7 +61,7 @@ constexpr int kATileBytesMax = 128 * 32 * 2;   // 128 rows x K = 32 x 2 B
 constexpr int kBTileBytesMax = kPairTile * 32 * 2; // 256 rows x K = 32 x 2 B
 constexpr int kALbo = 128 * 16, kBLbo = kPairTile * 16;
 // Deferred re-check state, per epilogue warp / warpgroup (after the barriers):
-//   queue   kQCap entries {pair offset in the item, lane | sign << 5} per warp
+//   queue   kQCap entries {pair offset in the item, lane | (D < 0) << 5} per warp
 //   defer   kDCap entries {pair offset in the item, cell row} per warp: tests
 //           whose re-check lies within kBand64 of tau, staged for the FP64 pass
 //   rows    R (9), tau, table position, pad per cell row, per warpgroup
@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
                 __syncwarp();
             };
             // drains the re-check queue: one entry per lane, loads issued in parallel; the
-            // tests within kBand64 of tau are staged for the FP64 pass (their sign-bit vote
+            // tests within kBand64 of tau are staged for the FP64 pass (their fast-path count
             // removed here, their vote added there)
             auto flush = [&]() {
                 for (int k0 = 0; k0 < qn; k0 += 32) {
@@ -690,7 +690,7 @@ __global__ void __launch_bounds__(128 + 128 * G, 1)
             // queues the tests within the band of one chunk (pair offset poff in
             // the item) for the FP32 re-check; hit: this lane's chunk holds one
             auto chunk_queue = [&](const uint32_t(&r)[CH], int poff, bool hit) {
-                uint32_t fm = 0, sm = 0;  // flag and sign masks, constant register indices only
+                uint32_t fm = 0, sm = 0;  // flag and D < 0 masks, constant register indices only
                 if (hit) {
 #pragma unroll
                     for (int e = 0; e < CH; ++e) {

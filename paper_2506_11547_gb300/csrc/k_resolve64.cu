@@ -14,7 +14,9 @@
 //      count) are recounted from all of their pairs, one block per cell, with
 //      the same decision (FP32 re-check outside kBand64, FP64 inside); their
 //      queued tests, if any, are skipped in step 1.
-// The two steps touch disjoint cells, so they run in one launch in any order.
+// Step 2 clears each recounted cell's flag, so it runs as a second launch after
+// step 1 has finished: in one launch a block done with step 2 could clear a flag
+// that a slower block's step 1 still has to see.
 #include "rv_geom.cuh"
 #include "rv_internal.h"
 
@@ -46,7 +48,7 @@ __global__ void __launch_bounds__(kResolveThreads) resolve64_kernel(AmbQueue Q, 
                                                                     int nprob, const LevelRef *__restrict__ lref,
                                                                     int level_stride, int level, PairPool pool,
                                                                     ProbStats *stats) {
-    // ---- 1. the queued tests ----
+    // ---- 1. the queued tests (cells flagged in step 2's sense are left to it) ----
     const int n = min(*(volatile int *)Q.count, Q.cap);
     int cur = -1;  // the problem this thread's statistics belong to
     unsigned am = 0, rs = 0;
@@ -70,7 +72,12 @@ __global__ void __launch_bounds__(kResolveThreads) resolve64_kernel(AmbQueue Q, 
         ++rs;
     }
     flush_stats(cur, am, rs, stats);
+}
 
+__global__ void __launch_bounds__(kResolveThreads) recount64_kernel(AmbQueue Q, const ProbRef *__restrict__ probs,
+                                                                    int nprob, const LevelRef *__restrict__ lref,
+                                                                    int level_stride, int level, PairPool pool,
+                                                                    ProbStats *stats) {
     // ---- 2. cells flagged when the queue was full: recount from all pairs ----
     if (!*(volatile int *)Q.ovf) return;
     __shared__ unsigned red[3][kResolveThreads / 32];
@@ -128,8 +135,12 @@ __global__ void __launch_bounds__(kResolveThreads) resolve64_kernel(AmbQueue Q, 
 cudaError_t launch_resolve64(AmbQueue amb, const ProbRef *probs, int nprob, const LevelRef *lref, int level_stride,
                              int level, PairPool pool, ProbStats *stats, int grid_blocks, cudaStream_t s) {
     if (!amb.count || !amb.ovf) return cudaErrorInvalidValue;
-    resolve64_kernel<<<grid_blocks < 1 ? 1 : grid_blocks, kResolveThreads, 0, s>>>(amb, probs, nprob, lref,
-                                                                                    level_stride, level, pool, stats);
+    const int grid = grid_blocks < 1 ? 1 : grid_blocks;
+    resolve64_kernel<<<grid, kResolveThreads, 0, s>>>(amb, probs, nprob, lref, level_stride, level, pool, stats);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // step 2 after step 1 on the same stream (returns at once when the queue never filled)
+    recount64_kernel<<<grid, kResolveThreads, 0, s>>>(amb, probs, nprob, lref, level_stride, level, pool, stats);
     return cudaGetLastError();
 }
 

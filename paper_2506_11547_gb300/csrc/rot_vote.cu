@@ -625,7 +625,7 @@ int Context::enqueue_pipeline(Wave &w) {
     // levels (<= 8 top_k cells per problem): the pair-major vote and a one-block
     // top-K.  Each ranking step also writes the next level's children.
     for (int lev = 0; lev < S && e == cudaSuccess; ++lev) {
-        mark(1, lev, 2);  // the vote and its FP64 resolution pass
+        mark(1, lev, 3);  // the vote and its FP64 resolution pass (two launches)
         if (lev == 0)
             e = launch_vote(w, lev, pl.variant);
         else

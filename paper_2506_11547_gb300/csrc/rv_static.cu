@@ -2,10 +2,10 @@
 // cell list with every scratch buffer in one file-scope static device array,
 // so the call allocates no device memory.
 //
-// The call runs four launches on the caller's stream: a set-up kernel (header,
+// The call runs five launches on the caller's stream: a set-up kernel (header,
 // work lists, cell table, counts zeroed), the pair step (launch_pair_prep), the
 // CUDA-core FP32 vote (launch_vote_simt) and its FP64 resolution pass
-// (launch_resolve64), the kernels a solve runs, here with their pair pool, cell
+// (launch_resolve64: two kernels), the kernels a solve runs, here with their pair pool, cell
 // table, work lists and FP64 queue in the static array.  It then reads back two
 // flags (invalid pairs, invalid cells) and returns.
 #include <mutex>
